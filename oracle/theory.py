@@ -1,0 +1,181 @@
+"""Host-side theory of arXiv 2003.07968, in plain numpy/scipy FP64.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+* Carnahan-Starling EOS, Eq. (CSEOS), and psi, Eq. (DED).
+* Maxwell equal-area coexistence, Eq. (MLVDR) with equal bulk pressures.
+* Mechanical-stability coexistence of the pseudopotential method,
+  Eq. (PGLDR) with Eqs. (BPLP), (BPVP), epsilon = -2 A1 / (A2 + A3).
+* Lamb's oscillation period, Eq. (DOP).
+* Young-Laplace analysis of a static droplet, Eq. (YLR), with the interface
+  at rho_m = (rho_l + rho_g)/2 (Sec. IV.B).
+* Steady-state criterion, Eq. (SSC).
+"""
+from __future__ import annotations
+
+import math
+import warnings
+
+import numpy as np
+from scipy import integrate, optimize
+
+CS2 = 1.0 / 3.0
+CS_A = 3.852462257
+CS_B = 0.1304438842
+CS_C = 2.785855166
+CS_K = 0.01
+
+
+def eos_pressure(rho, T, a=CS_A, b=CS_B, c=CS_C, k=CS_K):
+    """Eq. (CSEOS): P = k [c rho T (1 + b rho + (b rho)^2 - (b rho)^3)/(1 - b rho)^3 - a rho^2]."""
+    br = b * rho
+    return k * (c * rho * T * (1 + br + br**2 - br**3) / (1 - br) ** 3 - a * rho**2)
+
+
+def dpdrho(rho, T):
+    """dP/drho by the complex-step derivative (exact to rounding for analytic P)."""
+    h = 1e-30
+    return np.imag(eos_pressure(np.asarray(rho, dtype=complex) + 1j * h, T)) / h
+
+
+def psi(rho, T, G=-1.0):
+    """Eq. (DED): psi = sqrt((P_EOS - c_s^2 rho)/G)."""
+    return np.sqrt((eos_pressure(rho, T) - CS2 * rho) / G)
+
+
+def critical_point(a=CS_A, b=CS_B, c=CS_C, k=CS_K):
+    """(rho_c, T_c, P_c): where dP/drho = d2P/drho2 = 0 (plain root solve)."""
+
+    def p(r, t):
+        return eos_pressure(r, t, a, b, c, k)
+
+    def d1(r, t):
+        hc = 1e-30
+        return np.imag(p(complex(r, hc), t)) / hc
+
+    def eqs(v):
+        r, t = v
+        h = 1e-5
+        return [d1(r, t) * 1e2, (d1(r + h, t) - d1(r - h, t)) / (2 * h) * 1e2]
+
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore", RuntimeWarning)
+        r, t = optimize.fsolve(eqs, [0.9, 1.1], xtol=1e-14)
+    return r, t, p(r, t)
+
+
+def _spinodals(T):
+    """Densities where dP/drho = 0 (the van-der-Waals loop ends), T < 1."""
+    rs = np.linspace(1e-3, 1 / CS_B - 1e-3, 20001)
+    d = dpdrho(rs, T)
+    idx = np.where(np.sign(d[:-1]) != np.sign(d[1:]))[0]
+    roots = [optimize.brentq(lambda r: dpdrho(r, T), rs[i], rs[i + 1], xtol=1e-15) for i in idx]
+    if len(roots) < 2:
+        raise ValueError(f"no two-phase region at T={T}")
+    return roots[0], roots[1]
+
+
+def maxwell(T):
+    """Maxwell coexistence (rho_g, rho_l) at reduced temperature T.
+
+    Unknown p0 with P(rho_g) = P(rho_l) = p0 and the equal-area condition of
+    Eq. (MLVDR), int_{rho_g}^{rho_l} (p0 - P) drho / rho^2 = 0.
+    """
+    s1, s2 = _spinodals(T)
+    pmin = eos_pressure(s2, T)
+    pmax = eos_pressure(s1, T)
+
+    def roots(p0):
+        rg = optimize.brentq(lambda r: eos_pressure(r, T) - p0, 1e-12, s1, xtol=1e-15)
+        rl = optimize.brentq(lambda r: eos_pressure(r, T) - p0, s2, 1 / CS_B - 1e-9, xtol=1e-15)
+        return rg, rl
+
+    def area(p0):
+        rg, rl = roots(p0)
+        val, _ = integrate.quad(lambda r: (p0 - eos_pressure(r, T)) / r**2, rg, rl,
+                                epsabs=1e-15, epsrel=1e-13, limit=400)
+        return val
+
+    lo = max(pmin, 0.0) + 1e-9 * pmax
+    p0 = optimize.brentq(area, lo, pmax * (1 - 1e-9), xtol=1e-17, rtol=1e-14)
+    return roots(p0)
+
+
+def pgldr(T, eps, G=-1.0):
+    """Coexistence (rho_g, rho_l) of the pseudopotential method, Eq. (PGLDR):
+    int_{rho_g}^{rho_l} (p0 - c_s^2 rho - G psi^2) psidot / psi^(1+eps) drho = 0,
+    with p0 = c_s^2 rho + G psi(rho)^2 at both ends (Eqs. BPLP, BPVP).  Since
+    c_s^2 rho + G psi^2 = P_EOS by Eq. (DED), the bulk condition is
+    P(rho_g) = P(rho_l) = p0.  psidot comes from 2 psi psidot = (P' - c_s^2)/G."""
+    s1, s2 = _spinodals(T)
+    pmin = eos_pressure(s2, T)
+    pmax = eos_pressure(s1, T)
+
+    def roots(p0):
+        rg = optimize.brentq(lambda r: eos_pressure(r, T) - p0, 1e-12, s1, xtol=1e-15)
+        rl = optimize.brentq(lambda r: eos_pressure(r, T) - p0, s2, 1 / CS_B - 1e-9, xtol=1e-15)
+        return rg, rl
+
+    def integrand(r, p0):
+        ps = psi(r, T, G)
+        # psidot from 2 psi psidot = (P' - c_s^2)/G
+        psidot = (dpdrho(r, T) - CS2) / (2 * G * ps)
+        return (p0 - CS2 * r - G * ps**2) * psidot / ps ** (1 + eps)
+
+    def area(p0):
+        rg, rl = roots(p0)
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore", integrate.IntegrationWarning)
+            val, _ = integrate.quad(integrand, rg, rl, args=(p0,), epsabs=1e-15,
+                                    epsrel=1e-13, limit=400)
+        return val
+
+    lo = max(pmin, 0.0) + 1e-9 * pmax
+    p0 = optimize.brentq(area, lo, pmax * (1 - 1e-9), xtol=1e-17, rtol=1e-14)
+    return roots(p0)
+
+
+def lamb_period(gamma, rho_l, r_max, r_min, n=2):
+    """Eq. (DOP): T_a = 2 pi [n (n^2 - 1) gamma / (rho_l R_m^3)]^(-1/2), R_m = sqrt(R_max R_min)."""
+    rm = math.sqrt(r_max * r_min)
+    return 2 * math.pi * (n * (n * n - 1) * gamma / (rho_l * rm**3)) ** -0.5
+
+
+def steady_state_metric(rho_now, rho_before):
+    """Left side of Eq. (SSC): sum|rho(t) - rho(t-100)| / sum|rho(t)|."""
+    return float(np.abs(rho_now - rho_before).sum() / np.abs(rho_now).sum())
+
+
+def droplet_radius(rho, rho_l, rho_g, center=None):
+    """Radius where rho crosses rho_m = (rho_l + rho_g)/2 (Sec. IV.B), as the
+    mean of the linearly interpolated crossings on the four axis rays from
+    the centre node."""
+    ny, nx = rho.shape
+    cx, cy = (nx // 2, ny // 2) if center is None else center
+    rm = 0.5 * (rho_l + rho_g)
+    rays = [rho[cy, cx:], rho[cy, cx::-1], rho[cy:, cx], rho[cy::-1, cx]]
+    rs = []
+    for ray in rays:
+        above = ray > rm
+        k = int(np.argmin(above)) if not above.all() else None
+        if k is None or k == 0:
+            continue
+        r0, r1 = ray[k - 1], ray[k]
+        rs.append((k - 1) + (r0 - rm) / (r0 - r1))
+    return float(np.mean(rs))
+
+
+def laplace_pressure(rho, T, center=None):
+    """Pressure jump P_EOS(rho at the centre) - P_EOS(rho at the far corner).
+    The bulk pressure c_s^2 rho + G psi^2 equals P_EOS by Eq. (DED)."""
+    ny, nx = rho.shape
+    cx, cy = (nx // 2, ny // 2) if center is None else center
+    return float(eos_pressure(rho[cy, cx], T) - eos_pressure(rho[0, 0], T))
+
+
+def surface_tension_fit(radii, dps):
+    """Least-squares slope and intercept of dP against 1/R (Eq. YLR, 2-D)."""
+    inv = 1.0 / np.asarray(radii, dtype=float)
+    A = np.vstack([inv, np.ones_like(inv)]).T
+    (slope, icpt), *_ = np.linalg.lstsq(A, np.asarray(dps, dtype=float), rcond=None)
+    return float(slope), float(icpt)
