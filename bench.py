@@ -1,0 +1,376 @@
+"""Benchmark of the D2Q9 pseudopotential step on GB300.
+
+Default workload: one 8192 x 8192 FP32 droplet lattice (R = 2048, T_r = 0.8,
+BGK tau = 1, eps = 1.73, sigma = 1), the roofline configuration.  A "step"
+is one time step of the whole hot path (psi pass + fused force / collision /
+pull-stream pass) over that lattice.  The working set (two population
+buffers, 4.8 GB) is far larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload roofline|batched]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle (the only reference this method has) on a bounded crop of the same
+workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BASELINE_METRIC = ("MLUPS and % of HBM peak per step; batched/served p50/p99 vs plain FP32 at "
+                   "1e-5")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="roofline", choices=["roofline", "batched"])
+    ap.add_argument("--eos", default="f64", choices=["f64", "df", "f32"])
+    ap.add_argument("--storage", default="f32dev", choices=["f32", "f32dev", "f16dev"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--size", type=int, default=8192,
+                    help="lattice side of the droplet workload (8192 is the benchmark; "
+                         "smaller sides are for profiler captures)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            v = float(json.load(fh)["hbm_gbs"])
+        return v, "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback (6.8 TB/s)"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2003_07968_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload_key):
+    """DRAM bytes per launch from a committed ncu summary, only while the
+    kernel sources are unchanged since the capture (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as fh:
+            tab = json.load(fh)
+    except Exception:
+        return None
+    ent = tab.get(workload_key, {}).get(kernel)
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{self.index}.csv")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workloads
+def roofline_workload(n=8192):
+    import synth
+
+    R, T = n / 4.0, 0.8
+    return dict(key=f"droplet_{n}", nx=n, ny=n, R=R, T=T, tau=1.0,
+                field=lambda: synth.droplet(n, n, R, T),
+                name=f"droplet {n}x{n} FP32, R={int(R)}, T_r={T}, BGK tau=1.0, eps=1.73, sigma=1")
+
+
+def cpu_baseline(seconds=12.0):
+    """The FP64 oracle, as it stands, on a bounded crop of the roofline
+    workload: a 1024 x 1024 periodic window across the droplet edge."""
+    import oracle
+    import synth
+
+    n, R, T = 8192, 2048.0, 0.8
+    full_x0 = n // 2 + int(R) - 512
+    y, x = np.mgrid[0:1024, 0:1024].astype(float)
+    y += n // 2 - 512
+    x += full_x0
+    rg, rl = synth.coexistence(T)
+    r = np.sqrt((x - n // 2) ** 2 + (y - n // 2) ** 2)
+    rho = 0.5 * (rl + rg) - 0.5 * (rl - rg) * np.tanh(2.0 * (r - R) / 5.0)
+    p = oracle.params(T=T, tau=1.0)
+    f = oracle.init_equilibrium(rho)
+    t0 = time.perf_counter()
+    oracle.step(p, f, 1)
+    one = time.perf_counter() - t0
+    k = max(1, min(200, int(seconds / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.step(p, f, k)
+    dt = time.perf_counter() - t0
+    return {"value": round(1024 * 1024 * k / dt / 1e6, 3), "unit": "MLUPS",
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"1024x1024 crop of the 8192^2 droplet across its interface, {k} steps, "
+                      f"FP64 C oracle with OpenMP ({dt:.1f} s)"}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    wl = roofline_workload()
+    n = 512  # crop per step: bounded so the whole run ends within minutes
+    import synth
+
+    T, R = wl["T"], wl["R"]
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    y += wl["ny"] // 2 - n // 2
+    x += wl["nx"] // 2 + int(R) - n // 2
+    rg, rl = synth.coexistence(T)
+    r = np.sqrt((x - wl["nx"] // 2) ** 2 + (y - wl["ny"] // 2) ** 2)
+    rho = 0.5 * (rl + rg) - 0.5 * (rl - rg) * np.tanh(2.0 * (r - R) / 5.0)
+    p = oracle.params(T=T, tau=wl["tau"])
+    f = oracle.init_equilibrium(rho)
+    oracle.step(p, f, args.warmup)
+    t0 = time.perf_counter()
+    oracle.step(p, f, args.steps)
+    dt = time.perf_counter() - t0
+    v = n * n * args.steps / dt / 1e6
+    sample = (f"{n}x{n} periodic crop of the 8192^2 droplet across its interface per step, "
+              f"FP64 C oracle with OpenMP")
+    out = {"impl": "reference", "metric": BASELINE_METRIC, "value": round(v, 3), "unit": "MLUPS",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(dt / args.steps * 1e3, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl["name"] + " (oracle crop)"},
+           "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": oracle.num_threads(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0},
+           "gpu_launches": 0}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2003_07968_gb300 import build, capi as P
+
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    P.load()
+    eos = {"f64": P.LBM_EOS_F64, "df": P.LBM_EOS_DF, "f32": P.LBM_EOS_F32}[args.eos]
+    storage = {"f32": P.LBM_STORE_F32, "f32dev": P.LBM_STORE_F32_DEV,
+               "f16dev": P.LBM_STORE_F16_DEV}[args.storage]
+    wl = roofline_workload(args.size)
+    rho = wl["field"]()
+    rg, rl = 0.0, 0.0
+    d = P.lbm_desc_default(wl["nx"], wl["ny"], T=wl["T"], tau=wl["tau"], eos_precision=eos,
+                           storage=storage)
+    if storage == P.LBM_STORE_F16_DEV:
+        import synth
+
+        rg, rl = synth.coexistence(wl["T"])
+        d.rho0 = 0.5 * (rg + rl)
+    h = P.lbm_create(d)
+    st = h.stream
+    P.lbm_init(h, 0, rho)
+    if args.autotune:
+        P.lbm_autotune(h, 3)
+    info = P.lbm_info(h)
+    sites = info["sites"]
+    P.lbm_step(h, args.warmup)
+    P.lbm_sync(h)
+
+    # ---- device-resident timed region (kernels profiled with events on h.stream)
+    P.lbm_profile(h, True)
+    P.lbm_profile_read(h)  # reset pending records
+    l0 = P.lbm_launch_count(h)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(st)
+        P.lbm_step(h, args.steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches = P.lbm_launch_count(h) - l0
+    ms = e0.elapsed_time(e1)
+    stats = {s["name"]: s for s in P.lbm_profile_read(h)}
+    P.lbm_profile(h, False)
+    P.lbm_sync(h)
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = sites * args.steps * world / (ms_max * 1e-3) / 1e6
+
+    # ---- end-to-end through the C ABI with host buffers (pinned)
+    host_rho = torch.from_numpy(rho).pin_memory().numpy()
+    host_out = torch.empty(rho.shape, dtype=torch.float64).pin_memory().numpy()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    P.lbm_init(h, 0, host_rho)
+    P.lbm_step(h, args.steps)
+    m = P.lbm_moments(h, 0, rho=True, u=False, mass=True, out={"rho": host_out})
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": round(sites * args.steps * world / e2e_s / 1e6, 3), "unit": "MLUPS",
+           "h2d_bytes_per_step": round(host_rho.nbytes / args.steps, 1),
+           "d2h_bytes_per_step": round((host_out.nbytes + 8) / args.steps, 1),
+           "mass_rel_drift": abs(m["mass"] - float(rho.sum())) / float(rho.sum())}
+    P.lbm_destroy(h)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peak, peak_src = measured_hbm_peak()
+    k2 = stats.get("collide_stream")
+    k1 = stats.get("psi_pass")
+    dom = max((k1, k2), key=lambda s: s["total_ms"])
+    avg_ms = dom["total_ms"] / max(dom["launches"], 1)
+    achieved = dom["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
+    kernels = {s["name"]: {"launches": s["launches"], "avg_ms": round(s["total_ms"] / max(s["launches"], 1), 5),
+                           "share": round(s["total_ms"] / max(k1["total_ms"] + k2["total_ms"], 1e-9), 4),
+                           "algorithmic_GBps": round(s["bytes_per_launch"] / (s["total_ms"] / max(s["launches"], 1) * 1e-3) / 1e9, 1)}
+               for s in (k1, k2)}
+    es = 2 if args.storage == "f16dev" else 4
+    step_bytes = 18 * es  # read 9 and write 9 populations: the method's minimum per site
+    out = {
+        "metric": BASELINE_METRIC, "value": round(value, 3), "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["name"], "storage": args.storage, "eos": args.eos,
+                   "schedule": "two_pass", "tile": [info["tile_x"], info["tile_y"]],
+                   "grid_ctas": info["grid_ctas"], "sites": sites,
+                   "l2": f"working set {info['device_bytes'] / 1e9:.2f} GB vs 129 MB L2: "
+                         "inputs larger than L2, no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": ncu_traffic(dom["name"], wl["key"]), "peak_source": peak_src,
+                     "bytes_per_launch": dom["bytes_per_launch"]},
+        "step_roofline": {"algorithmic_bytes_per_site": step_bytes,
+                          "effective_GBps": round(value * 1e6 * step_bytes / 1e9 / world, 1),
+                          "frac": round(value * 1e6 * step_bytes / 1e9 / world / peak, 4)},
+        "kernels": kernels,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * pplbm.h -- C ABI of the GB300 (sm_103a) pseudopotential lattice Boltzmann
+ * library: the per-time-step update of a D2Q9 lattice with the
+ * nearest-neighbour "force approach" of Czelusniak et al., arXiv 2003.07968.
+ *
+ * One time step (Eq. TLBE) on a periodic nx x ny lattice:
+ *   rho   = sum_i f_i                                   Eq. (FD)
+ *   psi   = sqrt((P_EOS(rho) - c_s^2 rho) / G)          Eqs. (DED), (CSEOS)
+ *   M1,M2 = psi moments over the 3x3 neighbourhood      Eqs. (FOMED), (SOMED)
+ *   F     = F^SC - 3/4 eps c_s^2 G F1 + (sigma-1) c_s^2 G F2
+ *                                                       Eqs. (SCF), (DFTCCC),
+ *                                                       (DFTCST), (IFT)
+ *   u     = (sum_i f_i c_i + F/2) / rho                 Eq. (FMD)
+ *   f_i(x + c_i, t + 1) = f_i - (f_i - f_i^eq)/tau + (1 - 1/(2 tau)) S_i
+ *                                                       Eqs. (BGKCO), (SEDF),
+ *                                                       (GFS), (GFSBGK)
+ * D2Q9 velocities and weights: Eq. (VelocitySet) and the text after Eq. (SEDF).
+ *
+ * Conventions for every entry point:
+ *   - All functions return an int status: LBM_OK (0), LBM_PENDING (1), or a
+ *     negative LBM_ERR_* code.  No C++ exception crosses this boundary.
+ *   - Host arrays are owned by the caller and only borrowed for the call.
+ *     Fields are row-major [ny][nx] FP64 (x fastest).
+ *   - Device memory and streams are owned by the handle.  Device memory comes
+ *     from the allocator in lbm_runtime_opts (e.g. a PyTorch caching
+ *     allocator), else from cudaMalloc.
+ *   - Work is queued on the handle's stream (the caller's, if given).
+ *     lbm_step returns once the work is queued.  lbm_moments, lbm_sync and
+ *     lbm_destroy wait for it.  A numeric fault found on the device
+ *     (psi undefined: rho <= 0, b rho >= 1 or a negative radicand in Eq. DED)
+ *     is reported as LBM_ERR_NUMERIC by the next lbm_sync / lbm_moments /
+ *     lbm_step, with the lattice index available from lbm_status_detail.
+ *   - A handle is used by one host thread at a time.
+ */
+#ifndef PPLBM_H
+#define PPLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define LBM_OK 0
+#define LBM_PENDING 1
+#define LBM_ERR_ARG (-1)            /* invalid argument                         */
+#define LBM_ERR_OOM (-2)            /* device or host allocation failed         */
+#define LBM_ERR_CUDA (-3)           /* CUDA runtime error (see lbm_last_error)  */
+#define LBM_ERR_NUMERIC (-4)        /* psi undefined somewhere (see above)      */
+#define LBM_ERR_TIMEOUT (-5)        /* a bounded device wait ran out            */
+#define LBM_ERR_STATE (-6)          /* call not valid in the handle's state     */
+#define LBM_ERR_UNKNOWN_TICKET (-7) /* lbm_poll of a ticket never issued        */
+#define LBM_ERR_CAPACITY (-8)       /* request larger than the server can hold  */
+
+/* ---- population storage (spec precision form) ---------------------- */
+#define LBM_STORE_F32 0     /* f_i in FP32                                       */
+#define LBM_STORE_F32_DEV 1 /* f_i - w_i rho0 in FP32                            */
+#define LBM_STORE_F16_DEV 2 /* f_i - w_i rho0 in FP16 (IEEE binary16)            */
+
+/* ---- arithmetic of psi / Eq. (CSEOS) ------------------------------------- */
+#define LBM_EOS_F64 0 /* native FP64                                             */
+#define LBM_EOS_DF 1  /* float-float pairs (about 48 significant bits)           */
+#define LBM_EOS_F32 2 /* FP32                                                    */
+
+/* ---- collision operator -------------------------------------------------- */
+#define LBM_COLL_BGK 0 /* Eq. (BGKCO) with Guo forcing Eq. (GFSBGK)            */
+#define LBM_COLL_MRT 1 /* Eq. (MRTCO), Gram-Schmidt M of Appendix A, Eq. (GFSMRT) */
+
+/* ---- step schedule ------------------------------------------------------- */
+#define LBM_SCHED_TWO_PASS 0 /* psi pass, then fused force+collide+pull pass    */
+#define LBM_SCHED_FUSED 1    /* one pass; psi rebuilt from a 2-site halo        */
+
+/* One lattice.  Defaults (lbm_desc_default): tau = 1, G = -1, eps = 1.73,
+ * sigma = 1, T = 0.8, a/b/c/k = 3.852462257 / 0.1304438842 / 2.785855166 /
+ * 0.01 (Sec. IV.A), rho0 = 1, LBM_STORE_F32_DEV, LBM_EOS_F64, direct trace,
+ * BGK, MRT rates diag(1,1,1,1,1,1,1,1/tau,1/tau) (Eq. RM). */
+typedef struct {
+    int32_t nx, ny;           /* lattice size, each >= 2                        */
+    double tau;               /* relaxation time, > 0.5                         */
+    double G;                 /* interaction parameter (sign keeps psi real)    */
+    double eps, sigma;        /* Eq. (IFT)                                       */
+    double T;                 /* reduced temperature in Eq. (CSEOS)             */
+    double eos_a, eos_b, eos_c, eos_k;
+    double rho0;              /* reference density of deviation storage         */
+    int32_t storage;          /* LBM_STORE_*                                     */
+    int32_t eos_precision;    /* LBM_EOS_*                                       */
+    int32_t m2_trace_variant; /* 0: M2_bb direct trace (Eq. SOMED);
+                                 1: 2 c_s^2 (M0 - psi) (text after Eq. DFTCST)  */
+    int32_t collision;        /* LBM_COLL_*                                      */
+    double mrt_rates[9];      /* diagonal of Lambda (Eq. RelaxationMatrix)      */
+} lbm_lattice_desc;
+
+/* Optional runtime settings; pass NULL for defaults. */
+typedef struct {
+    /* Device allocator: alloc returns a device pointer aligned to >= 256 bytes,
+       or NULL on failure; free releases it.  Both NULL: cudaMalloc/cudaFree. */
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free)(void* ptr, size_t bytes, void* ctx);
+    void* alloc_ctx;
+    void* stream;      /* cudaStream_t to queue work on; NULL: a private stream */
+    int32_t tile_x;    /* tile width in sites (0: tuned/default)               */
+    int32_t tile_y;    /* tile height in sites (0: tuned/default)              */
+    int32_t grid_ctas; /* CTAs of the persistent launches (0: SMs x occupancy) */
+    int32_t schedule;  /* LBM_SCHED_*                                          */
+    int32_t graph_steps; /* steps per captured CUDA graph (0: default, <0: off) */
+} lbm_runtime_opts;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Fill *d with the defaults listed above for an nx x ny lattice. */
+void lbm_desc_default(lbm_lattice_desc* d, int32_t nx, int32_t ny);
+
+/* Create a handle over n_lattices independent lattices (n_lattices = 1: one
+ * lattice; > 1: a batch stepped together in persistent launches over one tile
+ * list).  All lattices of a handle share storage, eos_precision, collision
+ * and m2_trace_variant; tau, G, eps, sigma, T, EOS constants and rho0 may
+ * differ per lattice.  Allocates all device memory now.
+ * Errors: LBM_ERR_ARG (bad sizes/params, mixed storage), LBM_ERR_OOM,
+ * LBM_ERR_CUDA.  *out is NULL on error. */
+int lbm_create(const lbm_lattice_desc* descs, int32_t n_lattices,
+               const lbm_runtime_opts* opts, lbm_handle** out);
+
+/* Initialise one lattice at equilibrium, f_i = f_i^eq(rho, u) (the
+ * initialisation described after Eq. ISD).  rho, ux, uy: host [ny][nx] FP64,
+ * ux/uy may be NULL (zero velocity).  Copies the fields in, then returns
+ * with the work queued.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
+int lbm_init(lbm_handle* h, int32_t lattice, const double* rho, const double* ux,
+             const double* uy);
+
+/* Advance every lattice of the handle by nsteps >= 0 time steps.  Queues the
+ * work and returns.  Reports an earlier numeric fault if one is already
+ * known.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_NUMERIC. */
+int lbm_step(lbm_handle* h, int64_t nsteps);
+
+/* Macroscopic fields of one lattice at the current time: rho (Eq. FD), the
+ * force-shifted velocity (Eq. FMD) and the total mass sum_x rho, summed in
+ * FP64.  Any output may be NULL.  Waits for queued work.
+ * Errors: LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_NUMERIC. */
+int lbm_moments(lbm_handle* h, int32_t lattice, double* rho, double* ux, double* uy,
+                double* mass);
+
+/* Total mass of one lattice (FP64 sum of the stored populations) into *mass.
+ * Waits.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
+int lbm_mass(lbm_handle* h, int32_t lattice, double* mass);
+
+/* Wait for all queued work; returns LBM_ERR_NUMERIC if a numeric fault was
+ * flagged, LBM_ERR_CUDA on a CUDA error, else LBM_OK. */
+int lbm_sync(lbm_handle* h);
+
+/* Index of the first lattice with a numeric fault, or -1. */
+int lbm_status_detail(lbm_handle* h, int32_t* lattice);
+
+/* Release everything (waits for queued work first).  NULL is ignored. */
+void lbm_destroy(lbm_handle* h);
+
+/* Static text for a status code. */
+const char* lbm_strerror(int code);
+
+/* Text of the handle's last CUDA or argument error ("" if none).  The string
+ * belongs to the handle and lives until the next call on it. */
+const char* lbm_last_error(lbm_handle* h);
+
+/* ---- measurement and tuning --------------------------------------------- */
+
+/* Record CUDA events around every kernel launch from now on (on = 1) or stop
+ * (on = 0).  Launches are not captured into graphs while recording. */
+int lbm_profile(lbm_handle* h, int32_t on);
+
+typedef struct {
+    char name[32];      /* kernel name                                         */
+    int64_t launches;   /* launches recorded                                   */
+    double total_ms;    /* summed event time                                   */
+    double bytes_per_launch; /* algorithmic bytes one launch moves            */
+} lbm_kernel_stat;
+
+/* Waits, then reads the per-kernel records since lbm_profile(h, 1) into
+ * out[0..max), returning the number of kernels in *n. */
+int lbm_profile_read(lbm_handle* h, lbm_kernel_stat* out, int32_t max, int32_t* n);
+
+/* Number of kernels this handle has launched so far (graph replays count
+ * each contained kernel). */
+int64_t lbm_launch_count(lbm_handle* h);
+
+/* Handle facts: sites, device bytes held, tile shape, tile count, grid. */
+typedef struct {
+    int64_t sites;
+    int64_t device_bytes;
+    int32_t tile_x, tile_y, n_tiles, grid_ctas;
+    int32_t schedule;
+    int32_t n_lattices;
+} lbm_info_t;
+int lbm_info(lbm_handle* h, lbm_info_t* out);
+
+/* Autotune tile shape and grid size on this handle's lattices by timing
+ * candidate configurations with CUDA events (repeat trial steps that leave
+ * the state unchanged).  Keeps the fastest; results are cached per device,
+ * storage and size class for the life of the process.  Errors: LBM_ERR_CUDA. */
+int lbm_autotune(lbm_handle* h, int32_t repeats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PPLBM_H */

@@ -1,0 +1,325 @@
+"""Thin ctypes binding of include/pplbm.h (argument marshalling only).
+
+Every function here forwards to the CUDA library ``_lib/libpplbm.so``; there
+is no CPU path.  PyTorch is used for two pieces of plumbing only: device
+memory (the library allocates through torch's caching allocator) and the
+CUDA stream the library queues its kernels on.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpplbm.so")
+
+LBM_OK = 0
+LBM_PENDING = 1
+LBM_ERR_ARG = -1
+LBM_ERR_OOM = -2
+LBM_ERR_CUDA = -3
+LBM_ERR_NUMERIC = -4
+LBM_ERR_TIMEOUT = -5
+LBM_ERR_STATE = -6
+LBM_ERR_UNKNOWN_TICKET = -7
+LBM_ERR_CAPACITY = -8
+
+LBM_STORE_F32 = 0
+LBM_STORE_F32_DEV = 1
+LBM_STORE_F16_DEV = 2
+LBM_EOS_F64 = 0
+LBM_EOS_DF = 1
+LBM_EOS_F32 = 2
+LBM_COLL_BGK = 0
+LBM_COLL_MRT = 1
+LBM_SCHED_TWO_PASS = 0
+LBM_SCHED_FUSED = 1
+
+
+class LatticeDesc(ctypes.Structure):
+    """lbm_lattice_desc."""
+
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("tau", ctypes.c_double), ("G", ctypes.c_double),
+                ("eps", ctypes.c_double), ("sigma", ctypes.c_double), ("T", ctypes.c_double),
+                ("eos_a", ctypes.c_double), ("eos_b", ctypes.c_double),
+                ("eos_c", ctypes.c_double), ("eos_k", ctypes.c_double),
+                ("rho0", ctypes.c_double),
+                ("storage", ctypes.c_int32), ("eos_precision", ctypes.c_int32),
+                ("m2_trace_variant", ctypes.c_int32), ("collision", ctypes.c_int32),
+                ("mrt_rates", ctypes.c_double * 9)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class RuntimeOpts(ctypes.Structure):
+    """lbm_runtime_opts."""
+
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+                ("stream", ctypes.c_void_p), ("tile_x", ctypes.c_int32),
+                ("tile_y", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
+                ("schedule", ctypes.c_int32), ("graph_steps", ctypes.c_int32)]
+
+
+class KernelStat(ctypes.Structure):
+    """lbm_kernel_stat."""
+
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("bytes_per_launch", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    """lbm_info_t."""
+
+    _fields_ = [("sites", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
+                ("n_tiles", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
+                ("schedule", ctypes.c_int32), ("n_lattices", ctypes.c_int32)]
+
+
+# Every symbol include/pplbm.h declares, with (restype, argtypes).
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+SIGNATURES = {
+    "lbm_desc_default": (None, [ctypes.POINTER(LatticeDesc), ctypes.c_int32, ctypes.c_int32]),
+    "lbm_create": (ctypes.c_int, [ctypes.POINTER(LatticeDesc), ctypes.c_int32,
+                                  ctypes.POINTER(RuntimeOpts), ctypes.POINTER(_vp)]),
+    "lbm_init": (ctypes.c_int, [_vp, ctypes.c_int32, _dp, _dp, _dp]),
+    "lbm_step": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "lbm_moments": (ctypes.c_int, [_vp, ctypes.c_int32, _dp, _dp, _dp, _dp]),
+    "lbm_mass": (ctypes.c_int, [_vp, ctypes.c_int32, _dp]),
+    "lbm_sync": (ctypes.c_int, [_vp]),
+    "lbm_status_detail": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32)]),
+    "lbm_destroy": (None, [_vp]),
+    "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "lbm_last_error": (ctypes.c_char_p, [_vp]),
+    "lbm_profile": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "lbm_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(KernelStat), ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_int32)]),
+    "lbm_launch_count": (ctypes.c_int64, [_vp]),
+    "lbm_info": (ctypes.c_int, [_vp, ctypes.POINTER(Info)]),
+    "lbm_autotune": (ctypes.c_int, [_vp, ctypes.c_int32]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library; raises if it was not built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise ImportError(f"CUDA library {path} is missing: run "
+                                  "paper_2003_07968_gb300.build.build() first")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        msg = f"{where}: {lbm_strerror(code)} ({code})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+def lbm_strerror(code: int) -> str:
+    return load().lbm_strerror(int(code)).decode()
+
+
+def _check(rc: int, where: str, h=None) -> int:
+    if rc < 0:
+        detail = load().lbm_last_error(h.ptr).decode() if h is not None else ""
+        raise LbmError(rc, where, detail)
+    return rc
+
+
+# --------------------------------------------------------------- torch plumbing
+class _TorchAllocator:
+    """Device memory for the library from torch's caching allocator."""
+
+    def __init__(self, device):
+        import torch
+
+        self.torch = torch
+        self.device = device
+        self.live = {}
+        self.alloc = ALLOC_FN(self._alloc)
+        self.free = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, _ctx):
+        try:
+            t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
+        except Exception:  # out of memory: the library reports LBM_ERR_OOM
+            return None
+        p = t.data_ptr()
+        self.live[p] = t
+        return p
+
+    def _free(self, ptr, _nbytes, _ctx):
+        self.live.pop(int(ptr), None)
+
+
+class Handle:
+    """An lbm_handle* plus the Python objects that must outlive it."""
+
+    def __init__(self, ptr, stream, allocator, descs):
+        self.ptr = ptr
+        self.stream = stream  # torch.cuda.Stream the kernels run on
+        self.allocator = allocator
+        self.descs = descs
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                lbm_destroy(self)
+            except Exception:
+                pass
+
+
+def lbm_desc_default(nx: int, ny: int, **kw) -> LatticeDesc:
+    d = LatticeDesc()
+    load().lbm_desc_default(ctypes.byref(d), int(nx), int(ny))
+    for k, v in kw.items():
+        if k == "mrt_rates":
+            for i in range(9):
+                d.mrt_rates[i] = float(v[i])
+        else:
+            if not hasattr(d, k):
+                raise AttributeError(k)
+            setattr(d, k, v)
+    return d
+
+
+def lbm_create(descs, tile=None, grid_ctas=0, schedule=LBM_SCHED_TWO_PASS, graph_steps=0,
+               stream=None, device=None) -> Handle:
+    """Create a handle over one descriptor or a list of them."""
+    import torch
+
+    if isinstance(descs, LatticeDesc):
+        descs = [descs]
+    n = len(descs)
+    arr = (LatticeDesc * n)(*descs)
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    if stream is None:
+        stream = torch.cuda.Stream(device=dev)
+    alloc = _TorchAllocator(dev)
+    o = RuntimeOpts()
+    o.alloc, o.free, o.alloc_ctx = alloc.alloc, alloc.free, None
+    o.stream = stream.cuda_stream
+    o.tile_x, o.tile_y = (tile or (0, 0))
+    o.grid_ctas, o.schedule, o.graph_steps = grid_ctas, schedule, graph_steps
+    out = ctypes.c_void_p()
+    with torch.cuda.device(dev):
+        rc = load().lbm_create(arr, n, ctypes.byref(o), ctypes.byref(out))
+    _check(rc, "lbm_create")
+    return Handle(out, stream, alloc, list(descs))
+
+
+def _f64(a, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+def lbm_init(h: Handle, lattice: int, rho, ux=None, uy=None) -> None:
+    d = h.descs[lattice]
+    shp = (d.ny, d.nx)
+    r, x, y = _f64(rho, shp), _f64(ux, shp), _f64(uy, shp)
+    _check(load().lbm_init(h.ptr, lattice, _ptr(r), _ptr(x), _ptr(y)), "lbm_init", h)
+    # pageable host arrays were copied before lbm_init returned
+
+
+def lbm_step(h: Handle, nsteps: int) -> None:
+    _check(load().lbm_step(h.ptr, int(nsteps)), "lbm_step", h)
+
+
+def lbm_moments(h: Handle, lattice: int, rho=True, u=True, mass=True, out=None) -> dict:
+    """rho, ux, uy ([ny, nx] FP64) and mass of one lattice.  ``out`` may hold
+    preallocated (e.g. pinned) host arrays under the same keys."""
+    d = h.descs[lattice]
+    shp = (d.ny, d.nx)
+    out = dict(out or {})
+    if rho and "rho" not in out:
+        out["rho"] = np.empty(shp)
+    if u:
+        out.setdefault("ux", np.empty(shp))
+        out.setdefault("uy", np.empty(shp))
+    m = ctypes.c_double(0.0)
+    rc = load().lbm_moments(h.ptr, lattice, _ptr(out.get("rho") if rho else None),
+                            _ptr(out.get("ux") if u else None), _ptr(out.get("uy") if u else None),
+                            ctypes.byref(m) if mass else None)
+    _check(rc, "lbm_moments", h)
+    if mass:
+        out["mass"] = m.value
+    return out
+
+
+def lbm_mass(h: Handle, lattice: int) -> float:
+    m = ctypes.c_double(0.0)
+    _check(load().lbm_mass(h.ptr, lattice, ctypes.byref(m)), "lbm_mass", h)
+    return m.value
+
+
+def lbm_sync(h: Handle) -> None:
+    _check(load().lbm_sync(h.ptr), "lbm_sync", h)
+
+
+def lbm_status_detail(h: Handle) -> int:
+    i = ctypes.c_int32(-1)
+    _check(load().lbm_status_detail(h.ptr, ctypes.byref(i)), "lbm_status_detail", h)
+    return i.value
+
+
+def lbm_destroy(h: Handle) -> None:
+    if h.ptr:
+        load().lbm_destroy(h.ptr)
+        h.ptr = None
+
+
+def lbm_profile(h: Handle, on: bool) -> None:
+    _check(load().lbm_profile(h.ptr, 1 if on else 0), "lbm_profile", h)
+
+
+def lbm_profile_read(h: Handle) -> list[dict]:
+    arr = (KernelStat * 8)()
+    n = ctypes.c_int32(0)
+    _check(load().lbm_profile_read(h.ptr, arr, 8, ctypes.byref(n)), "lbm_profile_read", h)
+    return [dict(name=arr[i].name.decode(), launches=arr[i].launches,
+                 total_ms=arr[i].total_ms, bytes_per_launch=arr[i].bytes_per_launch)
+            for i in range(n.value)]
+
+
+def lbm_launch_count(h: Handle) -> int:
+    return int(load().lbm_launch_count(h.ptr))
+
+
+def lbm_info(h: Handle) -> dict:
+    i = Info()
+    _check(load().lbm_info(h.ptr, ctypes.byref(i)), "lbm_info", h)
+    return {k: getattr(i, k) for k, _ in Info._fields_}
+
+
+def lbm_autotune(h: Handle, repeats: int = 3) -> dict:
+    _check(load().lbm_autotune(h.ptr, int(repeats)), "lbm_autotune", h)
+    return lbm_info(h)

@@ -1,0 +1,252 @@
+// lbm_device.cuh -- device-side data layout and per-site arithmetic of the
+// D2Q9 pseudopotential step (arXiv 2003.07968) for sm_103a.
+//
+// Layout in HBM (per lattice, per population buffer):
+//   nine SoA planes, one per velocity c_i (Eq. VelocitySet order), each a
+//   pitched 2-D array with a ghost frame: rows [-GY, ny+GY), columns
+//   [-gx, pitch-gx).  Ghost sites within GW of the interior hold periodic
+//   images, written by the same kernel that writes the interior site, so
+//   readers never wrap indices.  Two population buffers (A/B) alternate
+//   between steps; a float psi plane with the same ghost frame sits beside.
+//   The buffers hold POST-collision, PRE-streaming populations f*; a step
+//   pulls f_i(x) = f*_i(x - c_i) (streaming of Eq. TLBE in pull form).
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pplbm {
+
+constexpr int GW = 2;  // depth of the periodic images kept around the interior
+constexpr int GY = 2;  // ghost rows above and below
+
+// D2Q9 velocity set, Eq. (VelocitySet); weights from the text after Eq. (SEDF).
+__device__ __constant__ static const int kCx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__device__ __constant__ static const int kCy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+template <int I> struct Vel;
+template <> struct Vel<0> { static constexpr int x = 0, y = 0; static constexpr float w = 4.f / 9.f; };
+template <> struct Vel<1> { static constexpr int x = 1, y = 0; static constexpr float w = 1.f / 9.f; };
+template <> struct Vel<2> { static constexpr int x = 0, y = 1; static constexpr float w = 1.f / 9.f; };
+template <> struct Vel<3> { static constexpr int x = -1, y = 0; static constexpr float w = 1.f / 9.f; };
+template <> struct Vel<4> { static constexpr int x = 0, y = -1; static constexpr float w = 1.f / 9.f; };
+template <> struct Vel<5> { static constexpr int x = 1, y = 1; static constexpr float w = 1.f / 36.f; };
+template <> struct Vel<6> { static constexpr int x = -1, y = 1; static constexpr float w = 1.f / 36.f; };
+template <> struct Vel<7> { static constexpr int x = -1, y = -1; static constexpr float w = 1.f / 36.f; };
+template <> struct Vel<8> { static constexpr int x = 1, y = -1; static constexpr float w = 1.f / 36.f; };
+
+// A float-float number hi + lo with |lo| <= ulp(hi)/2.
+struct df2 {
+    float hi, lo;
+};
+
+// Per-lattice constants, precomputed on the host.
+struct LatDev {
+    int64_t off_f[2];  // element offset of plane 0 of buffers A, B in the population arena
+    int64_t off_psi;   // element offset of the psi plane in the psi arena
+    int64_t plane;     // population plane stride (elements)
+    int32_t nx, ny;
+    int32_t pitch;      // population row pitch (elements)
+    int32_t gx;         // column of x = 0 inside a population row
+    int32_t pitch_psi;  // psi row pitch (floats)
+    int32_t gx_psi;     // column of x = 0 inside a psi row
+    float omega;        // 1 / tau                                   Eq. (BGKCO)
+    float guo;          // 1 - 1/(2 tau)                             Eq. (GFSBGK)
+    // F = k_sc psi M1 + k1 (M1.M2) + k2 (M1 tr M2 - M1.M2), i.e. Eq. (IFT) with
+    // F^SC of Eq. (SCF), F1 of Eq. (DFTCCC) and F2 of Eq. (DFTCST) expanded:
+    float k_sc;         // -2 G / c_s^2                  = -6 G
+    float k1;           // (-3/4 eps c_s^2 G)(-2 / c_s^6) = 13.5 eps G
+    float k2;           // (sigma - 1) c_s^2 G / c_s^6    = 9 (sigma - 1) G
+    float rho0;         // deviation reference (0 for plain FP32 storage)
+    int32_t m2_variant; // 0: direct trace; 1: 2 c_s^2 (M0 - psi)
+    int32_t lattice;    // index for the status word
+    // psi(rho)^2 = (P_EOS - c_s^2 rho)/G = rho (e1 q(rho) - e2 rho - e3),
+    // q = (1 + eta + eta^2 - eta^3)/(1 - eta)^3, eta = b rho      Eqs. (DED), (CSEOS)
+    double eb, e1, e2, e3;
+    df2 fb, f1, f2, f3;  // the same constants as float-float pairs
+    float sb, s1, s2, s3; // ... and as floats
+    // MRT relaxation rates (Eq. RelaxationMatrix), used by the MRT kernels
+    float mrt_s[9];
+};
+
+struct StepArgs {
+    const LatDev* lats;
+    const int4* tiles;  // (lattice, x0, y0, unused)
+    int ntiles;
+    void* pop;          // population arena
+    float* psi;         // psi arena
+    uint32_t* status;   // per-lattice fault bits
+    int parity;         // which population buffer holds the current state
+};
+
+// ---- storage traits ---------------------------------------------------------
+struct StoreF32 {
+    using T = float;
+    static constexpr int kGx = 4;  // 16 bytes of ghost columns keep rows aligned
+    static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float cv(float v) { return v; }
+};
+struct StoreF16 {
+    using T = __half;
+    static constexpr int kGx = 8;
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ __half cv(float v) { return __float2half_rn(v); }
+};
+
+// Write v at interior site (x, y) and at every periodic image of it that lies
+// within GW of the interior.  Requires nx, ny >= GW.
+template <class T>
+__device__ __forceinline__ void store_img(T* plane, int pitch, int gx, int x, int y, int nx,
+                                          int ny, T v) {
+    plane[(int64_t)(y + GY) * pitch + (x + gx)] = v;
+    const bool ex = (x < GW) | (x >= nx - GW);
+    const bool ey = (y < GW) | (y >= ny - GW);
+    if (ex | ey) {
+        int xs[3], ys[3], nxs = 1, nys = 1;
+        xs[0] = x;
+        ys[0] = y;
+        if (x < GW) xs[nxs++] = x + nx;
+        if (x >= nx - GW) xs[nxs++] = x - nx;
+        if (y < GW) ys[nys++] = y + ny;
+        if (y >= ny - GW) ys[nys++] = y - ny;
+        for (int b = 0; b < nys; ++b)
+            for (int a = 0; a < nxs; ++a)
+                if (a | b) plane[(int64_t)(ys[b] + GY) * pitch + (xs[a] + gx)] = v;
+    }
+}
+
+// ---- float-float arithmetic (error-free transformations) ---------------------
+// TwoSum: Knuth, TAOCP vol. 2; FastTwoSum: Dekker 1971; TwoProd via FMA.
+// Intrinsics (__fadd_rn etc.) are never contracted or reordered by nvcc.
+__device__ __forceinline__ df2 two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ df2 fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df2 df_add(df2 a, df2 b) {
+    df2 s = two_sum(a.hi, b.hi);
+    df2 t = two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df2 df_neg(df2 a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df2 df_mul(df2 a, df2 b) {
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df2 df_mul_f(df2 a, float b) {
+    float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return fast_two_sum(p, e);
+}
+// Long division with two correction quotients (Bailey's double-double scheme).
+__device__ __forceinline__ df2 df_div(df2 a, df2 b) {
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    df2 r = df_add(a, df_neg(df_mul_f(b, q1)));
+    float q2 = __fdiv_rn(r.hi, b.hi);
+    r = df_add(r, df_neg(df_mul_f(b, q2)));
+    float q3 = __fdiv_rn(r.hi, b.hi);
+    df2 q = fast_two_sum(q1, q2);
+    return df_add(q, df2{q3, 0.f});
+}
+
+// ---- psi(rho), Eqs. (DED) and (CSEOS) --------------------------------------
+// Returns psi and sets ok = false where psi is undefined (rho <= 0 or not
+// finite, b rho >= 1, negative radicand).
+enum { EOS_F64 = 0, EOS_DF = 1, EOS_F32 = 2 };
+
+template <int P>
+__device__ __forceinline__ float eval_psi(const LatDev& L, float rho, bool& ok);
+
+template <>
+__device__ __forceinline__ float eval_psi<EOS_F64>(const LatDev& L, float rho, bool& ok) {
+    const double r = (double)rho;
+    const double eta = L.eb * r;
+    const double num = 1.0 + eta * (1.0 + eta * (1.0 - eta));
+    const double s = 1.0 - eta;
+    const double q = num / (s * s * s);
+    const double arg = r * (L.e1 * q - L.e2 * r - L.e3);
+    ok = (rho > 0.f) && (eta < 1.0) && (arg >= 0.0) && isfinite(arg);
+    return sqrtf((float)arg);
+}
+
+template <>
+__device__ __forceinline__ float eval_psi<EOS_DF>(const LatDev& L, float rho, bool& ok) {
+    const df2 r = {rho, 0.f};
+    const df2 one = {1.f, 0.f};
+    const df2 eta = df_mul_f(L.fb, rho);
+    const df2 num = df_add(one, df_mul(eta, df_add(one, df_mul(eta, df_add(one, df_neg(eta))))));
+    const df2 s = df_add(one, df_neg(eta));
+    const df2 den = df_mul(df_mul(s, s), s);
+    const df2 q = df_div(num, den);
+    const df2 inner = df_add(df_add(df_mul(L.f1, q), df_neg(df_mul_f(L.f2, rho))), df_neg(L.f3));
+    const df2 arg = df_mul(r, inner);
+    ok = (rho > 0.f) && (eta.hi < 1.f) && (arg.hi >= 0.f) && isfinite(arg.hi);
+    return sqrtf(arg.hi);
+}
+
+template <>
+__device__ __forceinline__ float eval_psi<EOS_F32>(const LatDev& L, float rho, bool& ok) {
+    const float eta = L.sb * rho;
+    const float num = 1.f + eta * (1.f + eta * (1.f - eta));
+    const float s = 1.f - eta;
+    const float q = num / (s * s * s);
+    const float arg = rho * (L.s1 * q - L.s2 * rho - L.s3);
+    ok = (rho > 0.f) && (eta < 1.f) && (arg >= 0.f) && isfinite(arg);
+    return sqrtf(arg);
+}
+
+// ---- force of Eq. (IFT) from the nine psi values around a site ------------
+// p[0] = psi(x); p[i] = psi(x + c_i).
+// M1 and M2 (Eqs. FOMED, SOMED) with the D2Q9 weights multiplied out.
+struct Force {
+    float x, y;
+};
+__device__ __forceinline__ Force site_force(const LatDev& L, float p0, float pE, float pN,
+                                            float pW, float pS, float pNE, float pNW,
+                                            float pSW, float pSE) {
+    const float m1x = (4.f * (pE - pW) + (pNE - pNW) + (pSE - pSW)) * (1.f / 36.f);
+    const float m1y = (4.f * (pN - pS) + (pNE + pNW) - (pSW + pSE)) * (1.f / 36.f);
+    const float sd = (pNE + pNW) + (pSW + pSE);
+    const float sx = pE + pW, sy = pN + pS;
+    const float m2xx = (-8.f * p0 + 4.f * sx - 2.f * sy + sd) * (1.f / 54.f);
+    const float m2yy = (-8.f * p0 + 4.f * sy - 2.f * sx + sd) * (1.f / 54.f);
+    const float m2xy = ((pNE - pNW) + (pSW - pSE)) * (1.f / 36.f);
+    const float tr = L.m2_variant ? (-20.f * p0 + 4.f * (sx + sy) + sd) * (1.f / 54.f)
+                                  : (m2xx + m2yy);
+    const float ax = m1x * m2xx + m1y * m2xy;  // M1_b M2_ab
+    const float ay = m1x * m2xy + m1y * m2yy;
+    Force F;
+    F.x = L.k_sc * p0 * m1x + L.k1 * ax + L.k2 * (m1x * tr - ax);
+    F.y = L.k_sc * p0 * m1y + L.k1 * ay + L.k2 * (m1y * tr - ay);
+    return F;
+}
+
+// ---- BGK collision with Guo forcing for direction I ------------------------
+// g: stored (deviation) population; returns the post-collision value.
+// f^eq - w rho0 = w (drho + rho (3 cu + 9/2 cu^2 - 3/2 u^2))          Eq. (SEDF)
+// S = (1 - 1/2tau) w (3 cF + 9 cF cu - 3 F.u)                          Eqs. (GFS), (GFSBGK)
+template <int I>
+__device__ __forceinline__ float bgk_guo(float g, float drho, float rho, float ux, float uy,
+                                         float usq, float Fx, float Fy, float Fu, float omega,
+                                         float guo) {
+    constexpr float w = Vel<I>::w;
+    const float cu = (float)Vel<I>::x * ux + (float)Vel<I>::y * uy;
+    const float cF = (float)Vel<I>::x * Fx + (float)Vel<I>::y * Fy;
+    const float feq = w * (drho + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * usq));
+    const float src = guo * w * (3.f * cF + 9.f * cF * cu - 3.f * Fu);
+    return g + omega * (feq - g) + src;
+}
+
+}  // namespace pplbm

@@ -1,0 +1,318 @@
+// lbm_kernels.cu -- CUDA kernels of the D2Q9 pseudopotential step
+// (arXiv 2003.07968) for sm_103a, and their host launchers.
+//
+//   k_psi      pass 1: pull f, rho (Eq. FD), psi (Eqs. DED, CSEOS) -> psi plane
+//   k_collide  pass 2: psi tile + halo in shared memory, force (Eq. IFT),
+//              velocity (Eq. FMD), BGK + Guo (Eqs. BGKCO, SEDF, GFS), store f*
+//   k_init     f* such that the next pull yields f^eq(rho, u)
+//   k_moments  rho, force-shifted u of the current state (FP64 out)
+//   k_mass_*   FP64 sum of the stored populations (two-level reduction)
+//
+// Both passes walk a global tile list with a persistent grid, so one launch
+// covers one lattice or a batch of uneven lattices alike.
+#include "lbm_kernels.h"
+
+namespace pplbm {
+
+// ---------------------------------------------------------------- pass 1: psi
+template <class S, int EOSP>
+__global__ void __launch_bounds__(512) k_psi(StepArgs a) {
+    using T = typename S::T;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const int4 tl = __ldg(&a.tiles[t]);
+        const LatDev& L = a.lats[tl.x];
+        const int x = tl.y + threadIdx.x;
+        const int y = tl.z + threadIdx.y;
+        const int nx = L.nx, ny = L.ny;
+        if (x >= nx || y >= ny) continue;
+        const int pitch = L.pitch;
+        const int64_t plane = L.plane;
+        const T* f = reinterpret_cast<const T*>(a.pop) + L.off_f[a.parity] +
+                     (int64_t)(y + GY) * pitch + (x + L.gx);
+        // pull f_i(x) = f*_i(x - c_i)
+        float d = S::ld(f);
+        d += S::ld(f + 1 * plane - 1);
+        d += S::ld(f + 2 * plane - pitch);
+        d += S::ld(f + 3 * plane + 1);
+        d += S::ld(f + 4 * plane + pitch);
+        d += S::ld(f + 5 * plane - pitch - 1);
+        d += S::ld(f + 6 * plane - pitch + 1);
+        d += S::ld(f + 7 * plane + pitch + 1);
+        d += S::ld(f + 8 * plane + pitch - 1);
+        const float rho = d + L.rho0;
+        bool ok;
+        float psi = eval_psi<EOSP>(L, rho, ok);
+        if (!ok) {
+            atomicOr(&a.status[L.lattice], 1u);
+            psi = __int_as_float(0x7fc00000);
+        }
+        store_img(a.psi + L.off_psi, L.pitch_psi, L.gx_psi, x, y, nx, ny, psi);
+    }
+}
+
+// --------------------------------------------- pass 2: force + collide + store
+template <class S>
+__global__ void __launch_bounds__(512) k_collide(StepArgs a) {
+    using T = typename S::T;
+    extern __shared__ float sps[];
+    const int TX = blockDim.x, TY = blockDim.y;
+    const int W = TX + 2;
+    const int nthr = TX * TY;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const int4 tl = __ldg(&a.tiles[t]);
+        const LatDev& L = a.lats[tl.x];
+        const int nx = L.nx, ny = L.ny;
+        const int xend = min(tl.y + TX, nx);  // one past the last active column
+        const int yend = min(tl.z + TY, ny);
+        __syncthreads();  // the previous tile is done with sps
+        {
+            const float* ps = a.psi + L.off_psi;
+            const int pp = L.pitch_psi, gxp = L.gx_psi;
+            const int n = W * (TY + 2);
+            for (int k = tid; k < n; k += nthr) {
+                const int ly = k / W, lx = k - ly * W;
+                const int gx = tl.y - 1 + lx, gy = tl.z - 1 + ly;
+                if (gx <= xend && gy <= yend) sps[k] = ps[(int64_t)(gy + GY) * pp + (gx + gxp)];
+            }
+        }
+        __syncthreads();
+        const int x = tl.y + threadIdx.x;
+        const int y = tl.z + threadIdx.y;
+        if (x >= nx || y >= ny) continue;
+        const int pitch = L.pitch;
+        const int64_t plane = L.plane;
+        const int64_t site = (int64_t)(y + GY) * pitch + (x + L.gx);
+        const T* f = reinterpret_cast<const T*>(a.pop) + L.off_f[a.parity] + site;
+        const float g0 = S::ld(f);
+        const float g1 = S::ld(f + 1 * plane - 1);
+        const float g2 = S::ld(f + 2 * plane - pitch);
+        const float g3 = S::ld(f + 3 * plane + 1);
+        const float g4 = S::ld(f + 4 * plane + pitch);
+        const float g5 = S::ld(f + 5 * plane - pitch - 1);
+        const float g6 = S::ld(f + 6 * plane - pitch + 1);
+        const float g7 = S::ld(f + 7 * plane + pitch + 1);
+        const float g8 = S::ld(f + 8 * plane + pitch - 1);
+        const float drho = ((g0 + g1) + (g2 + g3)) + ((g4 + g5) + (g6 + g7)) + g8;
+        const float rho = drho + L.rho0;
+        const float jx = (g1 - g3) + (g5 - g6) + (g8 - g7);
+        const float jy = (g2 - g4) + (g5 + g6) - (g7 + g8);
+        const float* c = sps + (threadIdx.y + 1) * W + (threadIdx.x + 1);
+        const Force F = site_force(L, c[0], c[1], c[W], c[-1], c[-W], c[W + 1], c[W - 1],
+                                   c[-W - 1], c[-W + 1]);
+        const float inv = 1.f / rho;
+        const float ux = (jx + 0.5f * F.x) * inv;  // Eq. (FMD)
+        const float uy = (jy + 0.5f * F.y) * inv;
+        const float usq = ux * ux + uy * uy;
+        const float Fu = F.x * ux + F.y * uy;
+        const float om = L.omega, gu = L.guo;
+        T* o = reinterpret_cast<T*>(a.pop) + L.off_f[a.parity ^ 1];
+        const int gx = L.gx;
+#define PPLBM_OUT(I, G)                                                                   \
+    store_img(o + I * plane, pitch, gx, x, y, nx, ny,                                     \
+              S::cv(bgk_guo<I>(G, drho, rho, ux, uy, usq, F.x, F.y, Fu, om, gu)))
+        PPLBM_OUT(0, g0);
+        PPLBM_OUT(1, g1);
+        PPLBM_OUT(2, g2);
+        PPLBM_OUT(3, g3);
+        PPLBM_OUT(4, g4);
+        PPLBM_OUT(5, g5);
+        PPLBM_OUT(6, g6);
+        PPLBM_OUT(7, g7);
+        PPLBM_OUT(8, g8);
+#undef PPLBM_OUT
+    }
+}
+
+// ------------------------------------------------------------------ init
+// Stores at site x the value f_i^eq(x + c_i) - w_i rho0, so that the next
+// pull f_i(x) = f*_i(x - c_i) yields f_i^eq(x).  Equilibrium in FP64.
+template <class S>
+__global__ void k_init(LatDev L, void* pop, int parity, const double* rho, const double* ux,
+                       const double* uy) {
+    using T = typename S::T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int nx = L.nx, ny = L.ny;
+    if (x >= nx || y >= ny) return;
+    T* o = reinterpret_cast<T*>(pop) + L.off_f[parity];
+    const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                         1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        int sx = x + kCx[i], sy = y + kCy[i];
+        sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+        sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+        const int64_t s = (int64_t)sy * nx + sx;
+        const double r = rho[s];
+        const double vx = ux ? ux[s] : 0.0, vy = uy ? uy[s] : 0.0;
+        const double cu = kCx[i] * vx + kCy[i] * vy;
+        const double feq = w[i] * (r + r * (3.0 * cu + 4.5 * cu * cu - 1.5 * (vx * vx + vy * vy)));
+        const double g = feq - w[i] * (double)L.rho0;
+        store_img(o + i * L.plane, L.pitch, L.gx, x, y, nx, ny, S::cv((float)g));
+    }
+}
+
+// ------------------------------------------------------------------ moments
+// rho (FP64 sum of the pulled populations) and u = (j + F/2)/rho, with F from
+// the psi plane of the current state (computed by k_psi just before).
+template <class S>
+__global__ void k_moments(LatDev L, const void* pop, int parity, const float* psi_arena,
+                          double* rho_out, double* ux_out, double* uy_out) {
+    using T = typename S::T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int nx = L.nx, ny = L.ny;
+    if (x >= nx || y >= ny) return;
+    const int pitch = L.pitch;
+    const int64_t plane = L.plane;
+    const T* f = reinterpret_cast<const T*>(pop) + L.off_f[parity] + (int64_t)(y + GY) * pitch +
+                 (x + L.gx);
+    double g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = (double)S::ld(f + i * plane - kCy[i] * pitch - kCx[i]);
+    double d = 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        d += g[i];
+        jx += kCx[i] * g[i];
+        jy += kCy[i] * g[i];
+    }
+    const double rho = d + (double)L.rho0;
+    const float* c = psi_arena + L.off_psi + (int64_t)(y + GY) * L.pitch_psi + (x + L.gx_psi);
+    const int W = L.pitch_psi;
+    const Force F = site_force(L, c[0], c[1], c[W], c[-1], c[-W], c[W + 1], c[W - 1], c[-W - 1],
+                               c[-W + 1]);
+    const int64_t s = (int64_t)y * nx + x;
+    if (rho_out) rho_out[s] = rho;
+    if (ux_out) ux_out[s] = (jx + 0.5 * (double)F.x) / rho;
+    if (uy_out) uy_out[s] = (jy + 0.5 * (double)F.y) / rho;
+}
+
+// ------------------------------------------------------------------ mass
+// Each block sums whole rows of all nine planes in FP64 and writes one
+// partial; k_mass_final adds the partials in block order (deterministic).
+template <class S>
+__global__ void __launch_bounds__(256) k_mass_partial(LatDev L, const void* pop, int parity,
+                                                      double* partials) {
+    using T = typename S::T;
+    const T* f = reinterpret_cast<const T*>(pop) + L.off_f[parity];
+    const int nx = L.nx, ny = L.ny;
+    double acc = 0.0;
+    for (int y = blockIdx.x; y < ny; y += gridDim.x) {
+        const T* row = f + (int64_t)(y + GY) * L.pitch + L.gx;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            double s = 0.0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) s += (double)S::ld(row + i * L.plane + x);
+            acc += s + (double)L.rho0;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ double red[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = acc;
+    __syncthreads();
+    if (wid == 0) {
+        acc = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) partials[blockIdx.x] = acc;
+    }
+}
+
+__global__ void k_mass_final(const double* partials, int n, double* out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double m = 0.0;
+        for (int i = 0; i < n; ++i) m += partials[i];
+        *out = m;
+    }
+}
+
+// ================================================================ launchers
+namespace {
+template <class S>
+cudaError_t psi_dispatch(int eos, const StepArgs& a, dim3 g, dim3 b, cudaStream_t st) {
+    switch (eos) {
+        case EOS_F64: k_psi<S, EOS_F64><<<g, b, 0, st>>>(a); break;
+        case EOS_DF: k_psi<S, EOS_DF><<<g, b, 0, st>>>(a); break;
+        case EOS_F32: k_psi<S, EOS_F32><<<g, b, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_psi(int storage_f16, int eos, const StepArgs& a, dim3 g, dim3 b,
+                       cudaStream_t st) {
+    return storage_f16 ? psi_dispatch<StoreF16>(eos, a, g, b, st)
+                       : psi_dispatch<StoreF32>(eos, a, g, b, st);
+}
+
+cudaError_t launch_collide(int storage_f16, const StepArgs& a, dim3 g, dim3 b, size_t smem,
+                           cudaStream_t st) {
+    if (storage_f16)
+        k_collide<StoreF16><<<g, b, smem, st>>>(a);
+    else
+        k_collide<StoreF32><<<g, b, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(int storage_f16, const LatDev& L, void* pop, int parity,
+                        const double* rho, const double* ux, const double* uy,
+                        cudaStream_t st) {
+    dim3 b(32, 8), g((L.nx + 31) / 32, (L.ny + 7) / 8);
+    if (storage_f16)
+        k_init<StoreF16><<<g, b, 0, st>>>(L, pop, parity, rho, ux, uy);
+    else
+        k_init<StoreF32><<<g, b, 0, st>>>(L, pop, parity, rho, ux, uy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(int storage_f16, const LatDev& L, const void* pop, int parity,
+                           const float* psi, double* rho, double* ux, double* uy,
+                           cudaStream_t st) {
+    dim3 b(32, 8), g((L.nx + 31) / 32, (L.ny + 7) / 8);
+    if (storage_f16)
+        k_moments<StoreF16><<<g, b, 0, st>>>(L, pop, parity, psi, rho, ux, uy);
+    else
+        k_moments<StoreF32><<<g, b, 0, st>>>(L, pop, parity, psi, rho, ux, uy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mass(int storage_f16, const LatDev& L, const void* pop, int parity,
+                        double* partials, int n_partials, double* out, cudaStream_t st) {
+    const int nb = n_partials < L.ny ? n_partials : L.ny;
+    if (storage_f16)
+        k_mass_partial<StoreF16><<<nb, 256, 0, st>>>(L, pop, parity, partials);
+    else
+        k_mass_partial<StoreF32><<<nb, 256, 0, st>>>(L, pop, parity, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_mass_final<<<1, 32, 0, st>>>(partials, nb, out);
+    return cudaGetLastError();
+}
+
+int occupancy_psi(int storage_f16, int eos, int threads) {
+    int n = 0;
+    const void* fn = nullptr;
+    if (storage_f16) {
+        fn = eos == EOS_F64 ? (const void*)k_psi<StoreF16, EOS_F64>
+           : eos == EOS_DF  ? (const void*)k_psi<StoreF16, EOS_DF>
+                            : (const void*)k_psi<StoreF16, EOS_F32>;
+    } else {
+        fn = eos == EOS_F64 ? (const void*)k_psi<StoreF32, EOS_F64>
+           : eos == EOS_DF  ? (const void*)k_psi<StoreF32, EOS_DF>
+                            : (const void*)k_psi<StoreF32, EOS_F32>;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+int occupancy_collide(int storage_f16, int threads, size_t smem) {
+    int n = 0;
+    const void* fn = storage_f16 ? (const void*)k_collide<StoreF16> : (const void*)k_collide<StoreF32>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+}  // namespace pplbm

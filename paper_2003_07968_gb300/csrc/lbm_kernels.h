@@ -1,0 +1,22 @@
+// lbm_kernels.h -- host launchers of the kernels in lbm_kernels.cu.
+#pragma once
+#include "lbm_device.cuh"
+
+namespace pplbm {
+
+cudaError_t launch_psi(int storage_f16, int eos, const StepArgs& a, dim3 g, dim3 b,
+                       cudaStream_t st);
+cudaError_t launch_collide(int storage_f16, const StepArgs& a, dim3 g, dim3 b, size_t smem,
+                           cudaStream_t st);
+cudaError_t launch_init(int storage_f16, const LatDev& L, void* pop, int parity,
+                        const double* rho, const double* ux, const double* uy,
+                        cudaStream_t st);
+cudaError_t launch_moments(int storage_f16, const LatDev& L, const void* pop, int parity,
+                           const float* psi, double* rho, double* ux, double* uy,
+                           cudaStream_t st);
+cudaError_t launch_mass(int storage_f16, const LatDev& L, const void* pop, int parity,
+                        double* partials, int n_partials, double* out, cudaStream_t st);
+int occupancy_psi(int storage_f16, int eos, int threads);
+int occupancy_collide(int storage_f16, int threads, size_t smem);
+
+}  // namespace pplbm

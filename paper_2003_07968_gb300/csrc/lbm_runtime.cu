@@ -1,0 +1,761 @@
+// lbm_runtime.cu -- the C ABI of include/pplbm.h: handles, device memory
+// layout, step scheduling (direct launches or captured CUDA graphs),
+// measurement hooks and the tile-shape autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/pplbm.h"
+#include "lbm_kernels.h"
+
+using namespace pplbm;
+
+namespace {
+
+constexpr int kMassPartials = 1024;
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+struct ProfRec {
+    std::string name;
+    int64_t launches = 0;
+    double total_ms = 0.0;
+    double bytes = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+};
+
+struct TuneKey {
+    int device, storage, eos, schedule;
+    int64_t sites_class, nlat_class;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(device, storage, eos, schedule, sites_class, nlat_class) <
+               std::tie(o.device, o.storage, o.eos, o.schedule, o.sites_class, o.nlat_class);
+    }
+};
+struct TuneVal {
+    int tx, ty, grid;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+}  // namespace
+
+struct lbm_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    lbm_runtime_opts opts{};
+    std::vector<lbm_lattice_desc> desc;
+    std::vector<LatDev> lat;
+    int storage = LBM_STORE_F32_DEV;
+    int f16 = 0;
+    int eos = LBM_EOS_F64;
+    int collision = LBM_COLL_BGK;
+    int schedule = LBM_SCHED_TWO_PASS;
+    // device memory
+    void* pop = nullptr;
+    size_t pop_bytes = 0;
+    float* psi = nullptr;
+    size_t psi_bytes = 0;
+    LatDev* lat_dev = nullptr;
+    uint32_t* status = nullptr;
+    int4* tiles = nullptr;
+    size_t tiles_cap = 0;
+    double* partials = nullptr;  // mass partials + one result slot
+    double* staging = nullptr;   // FP64 field staging (rho, ux, uy)
+    size_t staging_elems = 0;
+    int64_t device_bytes = 0;
+    // host side
+    uint32_t* status_host = nullptr;  // pinned
+    cudaEvent_t status_ev = nullptr;
+    bool status_pending = false;
+    int numeric_lattice = -1;
+    int tx = 32, ty = 8, grid = 0, ntiles = 0;
+    int sm_count = 0;
+    int parity = 0;
+    int64_t sites = 0;
+    int64_t launches = 0;
+    // graphs
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by starting parity
+    int graph_steps = 32;
+    std::vector<int> tile_begin, tile_count;        // per-lattice tile ranges
+    // profiling
+    bool prof = false;
+    ProfRec rec[2];
+    std::vector<cudaEvent_t> ev_pool;
+    std::string err;
+};
+
+// ------------------------------------------------------------------ helpers
+namespace {
+
+int cuda_fail(lbm_handle* h, cudaError_t e, const char* what) {
+    if (h) {
+        h->err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    }
+    return LBM_ERR_CUDA;
+}
+
+#define CK(h, call)                                        \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+void* dev_alloc(lbm_handle* h, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (h->opts.alloc) {
+        p = h->opts.alloc(bytes, h->opts.alloc_ctx);
+        if (p && (reinterpret_cast<uintptr_t>(p) & 255u)) {
+            h->opts.free(p, bytes, h->opts.alloc_ctx);
+            h->err = "allocator returned memory not aligned to 256 bytes";
+            return nullptr;
+        }
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) h->device_bytes += (int64_t)bytes;
+    return p;
+}
+
+void dev_free(lbm_handle* h, void* p, size_t bytes) {
+    if (!p) return;
+    if (bytes == 0) bytes = 256;
+    if (h->opts.alloc)
+        h->opts.free(p, bytes, h->opts.alloc_ctx);
+    else
+        cudaFree(p);
+    h->device_bytes -= (int64_t)bytes;
+}
+
+void split_df(double v, df2& out) {
+    out.hi = (float)v;
+    out.lo = (float)(v - (double)out.hi);
+}
+
+int validate(const lbm_lattice_desc& d, std::string& why) {
+    if (d.nx < 2 || d.ny < 2) return why = "nx and ny must be >= 2", LBM_ERR_ARG;
+    if ((int64_t)d.nx * d.ny > (int64_t)1 << 31) return why = "lattice too large", LBM_ERR_ARG;
+    if (!(d.tau > 0.5) || !std::isfinite(d.tau)) return why = "tau must be > 0.5", LBM_ERR_ARG;
+    if (!(d.G != 0.0) || !std::isfinite(d.G)) return why = "G must be nonzero", LBM_ERR_ARG;
+    if (!std::isfinite(d.eps) || !std::isfinite(d.sigma) || !std::isfinite(d.T) ||
+        !std::isfinite(d.rho0))
+        return why = "non-finite parameter", LBM_ERR_ARG;
+    if (!(d.eos_b > 0.0) || !std::isfinite(d.eos_a) || !std::isfinite(d.eos_c) ||
+        !std::isfinite(d.eos_k))
+        return why = "bad EOS constants", LBM_ERR_ARG;
+    if (d.storage < LBM_STORE_F32 || d.storage > LBM_STORE_F16_DEV)
+        return why = "unknown storage", LBM_ERR_ARG;
+    if (d.eos_precision < LBM_EOS_F64 || d.eos_precision > LBM_EOS_F32)
+        return why = "unknown eos_precision", LBM_ERR_ARG;
+    if (d.m2_trace_variant != 0 && d.m2_trace_variant != 1)
+        return why = "m2_trace_variant must be 0 or 1", LBM_ERR_ARG;
+    if (d.collision != LBM_COLL_BGK) return why = "only BGK collision is built", LBM_ERR_ARG;
+    return LBM_OK;
+}
+
+LatDev make_lat(const lbm_lattice_desc& d, int index, int64_t& pop_cursor,
+                int64_t& psi_cursor) {
+    LatDev L{};
+    const int s = d.storage == LBM_STORE_F16_DEV ? 2 : 4;
+    const int gx = 16 / s;
+    L.nx = d.nx;
+    L.ny = d.ny;
+    L.gx = gx;
+    L.pitch = (int)round_up(d.nx + 2 * gx, 32 / s);
+    const int64_t rows = d.ny + 2 * GY;
+    L.plane = round_up((int64_t)L.pitch * rows, 256 / s);
+    L.off_f[0] = pop_cursor;
+    pop_cursor += 9 * L.plane;
+    L.off_f[1] = pop_cursor;
+    pop_cursor += 9 * L.plane;
+    L.gx_psi = 4;
+    L.pitch_psi = (int)round_up(d.nx + 8, 8);
+    L.off_psi = psi_cursor;
+    psi_cursor += round_up((int64_t)L.pitch_psi * rows, 64);
+    L.omega = (float)(1.0 / d.tau);
+    L.guo = (float)(1.0 - 1.0 / (2.0 * d.tau));
+    L.k_sc = (float)(-6.0 * d.G);
+    L.k1 = (float)(13.5 * d.eps * d.G);
+    L.k2 = (float)(9.0 * (d.sigma - 1.0) * d.G);
+    L.rho0 = d.storage == LBM_STORE_F32 ? 0.f : (float)d.rho0;
+    L.m2_variant = d.m2_trace_variant;
+    L.lattice = index;
+    // psi^2 = rho (e1 q - e2 rho - e3): e1 = k c T / G, e2 = k a / G, e3 = 1/(3G)
+    L.eb = d.eos_b;
+    L.e1 = d.eos_k * d.eos_c * d.T / d.G;
+    L.e2 = d.eos_k * d.eos_a / d.G;
+    L.e3 = 1.0 / (3.0 * d.G);
+    split_df(L.eb, L.fb);
+    split_df(L.e1, L.f1);
+    split_df(L.e2, L.f2);
+    split_df(L.e3, L.f3);
+    L.sb = (float)L.eb;
+    L.s1 = (float)L.e1;
+    L.s2 = (float)L.e2;
+    L.s3 = (float)L.e3;
+    for (int i = 0; i < 9; ++i) L.mrt_s[i] = (float)d.mrt_rates[i];
+    return L;
+}
+
+void drop_graph(lbm_handle* h);
+
+int build_tiles(lbm_handle* h, int tx, int ty) {
+    drop_graph(h);  // captured launches embed the tile list and grid
+    std::vector<int4> t;
+    h->tile_begin.assign(h->lat.size(), 0);
+    h->tile_count.assign(h->lat.size(), 0);
+    for (size_t l = 0; l < h->lat.size(); ++l) {
+        const LatDev& L = h->lat[l];
+        h->tile_begin[l] = (int)t.size();
+        for (int y0 = 0; y0 < L.ny; y0 += ty)
+            for (int x0 = 0; x0 < L.nx; x0 += tx) t.push_back(make_int4((int)l, x0, y0, 0));
+        h->tile_count[l] = (int)t.size() - h->tile_begin[l];
+    }
+    const size_t bytes = t.size() * sizeof(int4);
+    if (bytes > h->tiles_cap) {
+        dev_free(h, h->tiles, h->tiles_cap);
+        h->tiles = (int4*)dev_alloc(h, bytes);
+        if (!h->tiles) {
+            h->tiles_cap = 0;
+            return LBM_ERR_OOM;
+        }
+        h->tiles_cap = bytes;
+    }
+    CK(h, cudaMemcpyAsync(h->tiles, t.data(), bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->tx = tx;
+    h->ty = ty;
+    h->ntiles = (int)t.size();
+    return LBM_OK;
+}
+
+size_t collide_smem(int tx, int ty) { return (size_t)(tx + 2) * (ty + 2) * sizeof(float); }
+
+int default_grid(lbm_handle* h) {
+    const int thr = h->tx * h->ty;
+    const int occ = std::min(occupancy_psi(h->f16, h->eos, thr),
+                             occupancy_collide(h->f16, thr, collide_smem(h->tx, h->ty)));
+    return std::max(1, std::min(h->ntiles, h->sm_count * occ));
+}
+
+void drop_graph(lbm_handle* h) {
+    for (auto& g : h->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+StepArgs step_args(lbm_handle* h, int parity) {
+    StepArgs a;
+    a.lats = h->lat_dev;
+    a.tiles = h->tiles;
+    a.ntiles = h->ntiles;
+    a.pop = h->pop;
+    a.psi = h->psi;
+    a.status = h->status;
+    a.parity = parity;
+    return a;
+}
+
+cudaEvent_t take_event(lbm_handle* h) {
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch the two passes of one step on parity p (state in buffer p, result
+// in buffer p^1).  Records events around each launch when profiling.
+int launch_step(lbm_handle* h, int p) {
+    const StepArgs a = step_args(h, p);
+    const dim3 g(h->grid), b(h->tx, h->ty);
+    const size_t smem = collide_smem(h->tx, h->ty);
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    if (h->prof) {
+        e0 = take_event(h);
+        e1 = take_event(h);
+        e2 = take_event(h);
+        CK(h, cudaEventRecord(e0, h->stream));
+    }
+    CK(h, launch_psi(h->f16, h->eos, a, g, b, h->stream));
+    if (h->prof) CK(h, cudaEventRecord(e1, h->stream));
+    CK(h, launch_collide(h->f16, a, g, b, smem, h->stream));
+    if (h->prof) {
+        CK(h, cudaEventRecord(e2, h->stream));
+        h->rec[0].pending.emplace_back(e0, e1);
+        h->rec[1].pending.emplace_back(e1, e2);
+        // e1 is shared: keep it out of the pool until both pairs are read
+    }
+    h->launches += 2;
+    return LBM_OK;
+}
+
+int capture_graph(lbm_handle* h) {
+    cudaGraphExec_t& slot = h->graph[h->parity];
+    if (slot) {
+        cudaGraphExecDestroy(slot);
+        slot = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int p = h->parity;
+    const int64_t before = h->launches;
+    int rc = LBM_OK;
+    for (int s = 0; s < h->graph_steps && rc == LBM_OK; ++s) {
+        rc = launch_step(h, p);
+        p ^= 1;
+    }
+    h->launches = before;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (rc != LBM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&slot, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        slot = nullptr;
+        return cuda_fail(h, e, "cudaGraphInstantiate");
+    }
+    return LBM_OK;
+}
+
+int check_status_async(lbm_handle* h) {
+    if (h->status_pending && cudaEventQuery(h->status_ev) == cudaSuccess) {
+        h->status_pending = false;
+        for (size_t l = 0; l < h->lat.size(); ++l)
+            if (h->status_host[l]) {
+                if (h->numeric_lattice < 0) h->numeric_lattice = (int)l;
+            }
+    }
+    return h->numeric_lattice >= 0 ? LBM_ERR_NUMERIC : LBM_OK;
+}
+
+int sync_status(lbm_handle* h) {
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(h->status_host, h->status, h->lat.size() * sizeof(uint32_t),
+                     cudaMemcpyDeviceToHost));
+    h->status_pending = false;
+    for (size_t l = 0; l < h->lat.size(); ++l)
+        if (h->status_host[l] && h->numeric_lattice < 0) h->numeric_lattice = (int)l;
+    return h->numeric_lattice >= 0 ? LBM_ERR_NUMERIC : LBM_OK;
+}
+
+int ensure_staging(lbm_handle* h, size_t elems) {
+    if (elems <= h->staging_elems) return LBM_OK;
+    dev_free(h, h->staging, h->staging_elems * 3 * sizeof(double));
+    h->staging = (double*)dev_alloc(h, elems * 3 * sizeof(double));
+    if (!h->staging) {
+        h->staging_elems = 0;
+        return LBM_ERR_OOM;
+    }
+    h->staging_elems = elems;
+    return LBM_OK;
+}
+
+void release(lbm_handle* h) {
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graph(h);
+    // kernel-0 pairs own (e0, e1); kernel-1 pairs share e1 and own e2
+    for (auto& pr : h->rec[0].pending) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (auto& pr : h->rec[1].pending) cudaEventDestroy(pr.second);
+    h->rec[0].pending.clear();
+    h->rec[1].pending.clear();
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    h->ev_pool.clear();
+    if (h->status_ev) cudaEventDestroy(h->status_ev);
+    if (h->status_host) cudaFreeHost(h->status_host);
+    dev_free(h, h->staging, h->staging_elems * 3 * sizeof(double));
+    dev_free(h, h->partials, (kMassPartials + 1) * sizeof(double));
+    dev_free(h, h->tiles, h->tiles_cap);
+    dev_free(h, h->status, h->lat.size() * sizeof(uint32_t));
+    dev_free(h, h->lat_dev, h->lat.size() * sizeof(LatDev));
+    dev_free(h, h->psi, h->psi_bytes);
+    dev_free(h, h->pop, h->pop_bytes);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+void lbm_desc_default(lbm_lattice_desc* d, int32_t nx, int32_t ny) {
+    if (!d) return;
+    std::memset(d, 0, sizeof(*d));
+    d->nx = nx;
+    d->ny = ny;
+    d->tau = 1.0;
+    d->G = -1.0;
+    d->eps = 1.73;
+    d->sigma = 1.0;
+    d->T = 0.8;
+    d->eos_a = 3.852462257;
+    d->eos_b = 0.1304438842;
+    d->eos_c = 2.785855166;
+    d->eos_k = 0.01;
+    d->rho0 = 1.0;
+    d->storage = LBM_STORE_F32_DEV;
+    d->eos_precision = LBM_EOS_F64;
+    d->m2_trace_variant = 0;
+    d->collision = LBM_COLL_BGK;
+    for (int i = 0; i < 9; ++i) d->mrt_rates[i] = i < 7 ? 1.0 : 1.0 / d->tau;
+}
+
+const char* lbm_strerror(int code) {
+    switch (code) {
+        case LBM_OK: return "ok";
+        case LBM_PENDING: return "pending";
+        case LBM_ERR_ARG: return "invalid argument";
+        case LBM_ERR_OOM: return "out of memory";
+        case LBM_ERR_CUDA: return "CUDA error";
+        case LBM_ERR_NUMERIC: return "psi undefined (rho <= 0, b rho >= 1 or negative radicand)";
+        case LBM_ERR_TIMEOUT: return "bounded device wait timed out";
+        case LBM_ERR_STATE: return "call not valid in this state";
+        case LBM_ERR_UNKNOWN_TICKET: return "unknown ticket";
+        case LBM_ERR_CAPACITY: return "request exceeds server capacity";
+        default: return "unknown status";
+    }
+}
+
+const char* lbm_last_error(lbm_handle* h) { return h ? h->err.c_str() : ""; }
+
+int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts* opts,
+               lbm_handle** out) {
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (!descs || n < 1) return LBM_ERR_ARG;
+    std::string why;
+    for (int i = 0; i < n; ++i) {
+        int rc = validate(descs[i], why);
+        if (rc) return rc;
+        if (descs[i].storage != descs[0].storage || descs[i].eos_precision != descs[0].eos_precision ||
+            descs[i].collision != descs[0].collision ||
+            descs[i].m2_trace_variant != descs[0].m2_trace_variant)
+            return LBM_ERR_ARG;
+    }
+    if (opts && (opts->alloc == nullptr) != (opts->free == nullptr)) return LBM_ERR_ARG;
+    if (opts && (opts->tile_x < 0 || opts->tile_y < 0 || opts->grid_ctas < 0)) return LBM_ERR_ARG;
+    if (opts) {
+        const int tx = opts->tile_x ? opts->tile_x : 32, ty = opts->tile_y ? opts->tile_y : 8;
+        if ((tx % 32) || tx * ty > 512) return LBM_ERR_ARG;
+    }
+    if (opts && opts->schedule != LBM_SCHED_TWO_PASS) return LBM_ERR_ARG;
+
+    lbm_handle* h = new (std::nothrow) lbm_handle();
+    if (!h) return LBM_ERR_OOM;
+    if (opts) h->opts = *opts;
+    h->desc.assign(descs, descs + n);
+    h->storage = descs[0].storage;
+    h->f16 = h->storage == LBM_STORE_F16_DEV;
+    h->eos = descs[0].eos_precision;
+    h->collision = descs[0].collision;
+    h->graph_steps = (opts && opts->graph_steps != 0) ? opts->graph_steps : 32;
+    if (h->graph_steps > 0 && (h->graph_steps & 1)) h->graph_steps += 1;
+
+    auto fail = [&](int rc) {
+        release(h);
+        delete h;
+        return rc;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess) return fail(LBM_ERR_CUDA);
+    if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) !=
+        cudaSuccess)
+        return fail(LBM_ERR_CUDA);
+    if (opts && opts->stream) {
+        h->stream = (cudaStream_t)opts->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(LBM_ERR_CUDA);
+        h->own_stream = true;
+    }
+    int64_t pc = 0, qc = 0;
+    for (int i = 0; i < n; ++i) {
+        h->lat.push_back(make_lat(descs[i], i, pc, qc));
+        h->sites += (int64_t)descs[i].nx * descs[i].ny;
+    }
+    const size_t es = h->f16 ? 2 : 4;
+    h->pop_bytes = (size_t)pc * es;
+    h->psi_bytes = (size_t)qc * sizeof(float);
+    h->pop = dev_alloc(h, h->pop_bytes);
+    h->psi = (float*)dev_alloc(h, h->psi_bytes);
+    h->lat_dev = (LatDev*)dev_alloc(h, n * sizeof(LatDev));
+    h->status = (uint32_t*)dev_alloc(h, n * sizeof(uint32_t));
+    h->partials = (double*)dev_alloc(h, (kMassPartials + 1) * sizeof(double));
+    if (!h->pop || !h->psi || !h->lat_dev || !h->status || !h->partials) return fail(LBM_ERR_OOM);
+    if (cudaMallocHost(&h->status_host, n * sizeof(uint32_t)) != cudaSuccess)
+        return fail(LBM_ERR_OOM);
+    if (cudaEventCreateWithFlags(&h->status_ev, cudaEventDisableTiming) != cudaSuccess)
+        return fail(LBM_ERR_CUDA);
+    if (cudaMemsetAsync(h->pop, 0, h->pop_bytes, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->psi, 0, h->psi_bytes, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->status, 0, n * sizeof(uint32_t), h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->lat_dev, h->lat.data(), n * sizeof(LatDev), cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess)
+        return fail(LBM_ERR_CUDA);
+    int tx = (opts && opts->tile_x) ? opts->tile_x : 32;
+    int ty = (opts && opts->tile_y) ? opts->tile_y : 8;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        TuneKey k{h->device, h->storage, h->eos, h->schedule, (int64_t)std::log2((double)h->sites),
+                  (int64_t)std::log2((double)n)};
+        auto it = g_tune_cache.find(k);
+        if (it != g_tune_cache.end() && !(opts && opts->tile_x)) {
+            tx = it->second.tx;
+            ty = it->second.ty;
+        }
+    }
+    int rc = build_tiles(h, tx, ty);
+    if (rc) return fail(rc);
+    h->grid = (opts && opts->grid_ctas) ? std::min(opts->grid_ctas, h->ntiles) : default_grid(h);
+    h->rec[0].name = "psi_pass";
+    h->rec[1].name = "collide_stream";
+    h->rec[0].bytes = (double)h->sites * (9.0 * es + 4.0);
+    h->rec[1].bytes = (double)h->sites * (18.0 * es + 4.0);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(LBM_ERR_CUDA);
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_init(lbm_handle* h, int32_t lattice, const double* rho, const double* ux,
+             const double* uy) {
+    if (!h || !rho || lattice < 0 || lattice >= (int)h->lat.size()) return LBM_ERR_ARG;
+    const LatDev& L = h->lat[lattice];
+    const size_t n = (size_t)L.nx * L.ny;
+    int rc = ensure_staging(h, n);
+    if (rc) return rc;
+    double* dr = h->staging;
+    double* dx = h->staging + h->staging_elems;
+    double* dy = h->staging + 2 * h->staging_elems;
+    CK(h, cudaMemcpyAsync(dr, rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (ux) CK(h, cudaMemcpyAsync(dx, ux, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (uy) CK(h, cudaMemcpyAsync(dy, uy, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, launch_init(h->f16, L, h->pop, h->parity, dr, ux ? dx : nullptr, uy ? dy : nullptr,
+                      h->stream));
+    h->launches += 1;
+    CK(h, cudaMemsetAsync(h->status + lattice, 0, sizeof(uint32_t), h->stream));
+    if (h->numeric_lattice == lattice) h->numeric_lattice = -1;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle* h, int64_t nsteps) {
+    if (!h || nsteps < 0) return LBM_ERR_ARG;
+    int rc = check_status_async(h);
+    if (rc) return rc;
+    int64_t left = nsteps;
+    if (!h->prof && h->graph_steps > 0 && left >= h->graph_steps) {
+        if (!h->graph[h->parity]) {
+            rc = capture_graph(h);
+            if (rc) return rc;
+        }
+        while (left >= h->graph_steps) {
+            CK(h, cudaGraphLaunch(h->graph[h->parity], h->stream));
+            h->launches += 2 * (int64_t)h->graph_steps;
+            left -= h->graph_steps;  // graph_steps is even: parity unchanged
+        }
+    }
+    for (; left > 0; --left) {
+        rc = launch_step(h, h->parity);
+        if (rc) return rc;
+        h->parity ^= 1;
+    }
+    if (!h->status_pending) {
+        CK(h, cudaMemcpyAsync(h->status_host, h->status, h->lat.size() * sizeof(uint32_t),
+                              cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaEventRecord(h->status_ev, h->stream));
+        h->status_pending = true;
+    }
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_handle* h) {
+    if (!h) return LBM_ERR_ARG;
+    return sync_status(h);
+}
+
+int lbm_status_detail(lbm_handle* h, int32_t* lattice) {
+    if (!h || !lattice) return LBM_ERR_ARG;
+    *lattice = h->numeric_lattice;
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_handle* h, int32_t lattice, double* rho, double* ux, double* uy,
+                double* mass) {
+    if (!h || lattice < 0 || lattice >= (int)h->lat.size()) return LBM_ERR_ARG;
+    const LatDev& L = h->lat[lattice];
+    const size_t n = (size_t)L.nx * L.ny;
+    if (rho || ux || uy) {
+        int rc = ensure_staging(h, n);
+        if (rc) return rc;
+        // psi of the current state for this lattice's tiles (all tiles: cheap
+        // relative to a D2H copy, and keeps one code path)
+        StepArgs a = step_args(h, h->parity);
+        a.tiles = h->tiles + h->tile_begin[lattice];
+        a.ntiles = h->tile_count[lattice];
+        CK(h, launch_psi(h->f16, h->eos, a, dim3(std::min(h->grid, a.ntiles)), dim3(h->tx, h->ty),
+                         h->stream));
+        double* dr = h->staging;
+        double* dx = h->staging + h->staging_elems;
+        double* dy = h->staging + 2 * h->staging_elems;
+        CK(h, launch_moments(h->f16, L, h->pop, h->parity, h->psi, dr, dx, dy, h->stream));
+        h->launches += 2;
+        if (rho) CK(h, cudaMemcpyAsync(rho, dr, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (ux) CK(h, cudaMemcpyAsync(ux, dx, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (uy) CK(h, cudaMemcpyAsync(uy, dy, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    }
+    if (mass) {
+        CK(h, launch_mass(h->f16, L, h->pop, h->parity, h->partials, kMassPartials,
+                          h->partials + kMassPartials, h->stream));
+        h->launches += 2;
+        CK(h, cudaMemcpyAsync(mass, h->partials + kMassPartials, sizeof(double),
+                              cudaMemcpyDeviceToHost, h->stream));
+    }
+    return sync_status(h);
+}
+
+int lbm_mass(lbm_handle* h, int32_t lattice, double* mass) {
+    if (!mass) return LBM_ERR_ARG;
+    return lbm_moments(h, lattice, nullptr, nullptr, nullptr, mass);
+}
+
+void lbm_destroy(lbm_handle* h) {
+    if (!h) return;
+    release(h);
+    delete h;
+}
+
+int lbm_profile(lbm_handle* h, int32_t on) {
+    if (!h) return LBM_ERR_ARG;
+    h->prof = on != 0;
+    return LBM_OK;
+}
+
+int lbm_profile_read(lbm_handle* h, lbm_kernel_stat* out, int32_t max, int32_t* n) {
+    if (!h || !n) return LBM_ERR_ARG;
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 2; ++k) {
+        ProfRec& r = h->rec[k];
+        for (auto& pr : r.pending) {
+            float ms = 0.f;
+            CK(h, cudaEventElapsedTime(&ms, pr.first, pr.second));
+            r.total_ms += ms;
+            r.launches += 1;
+        }
+    }
+    // return events to the pool: kernel 0 pairs own (e0, e1), kernel 1 pairs own e2
+    for (auto& pr : h->rec[0].pending) {
+        h->ev_pool.push_back(pr.first);
+        h->ev_pool.push_back(pr.second);
+    }
+    for (auto& pr : h->rec[1].pending) h->ev_pool.push_back(pr.second);
+    h->rec[0].pending.clear();
+    h->rec[1].pending.clear();
+    const int cnt = 2;
+    for (int k = 0; k < cnt && k < max && out; ++k) {
+        std::memset(&out[k], 0, sizeof(lbm_kernel_stat));
+        std::snprintf(out[k].name, sizeof(out[k].name), "%s", h->rec[k].name.c_str());
+        out[k].launches = h->rec[k].launches;
+        out[k].total_ms = h->rec[k].total_ms;
+        out[k].bytes_per_launch = h->rec[k].bytes;
+    }
+    *n = cnt;
+    return LBM_OK;
+}
+
+int64_t lbm_launch_count(lbm_handle* h) { return h ? h->launches : 0; }
+
+int lbm_info(lbm_handle* h, lbm_info_t* out) {
+    if (!h || !out) return LBM_ERR_ARG;
+    out->sites = h->sites;
+    out->device_bytes = h->device_bytes;
+    out->tile_x = h->tx;
+    out->tile_y = h->ty;
+    out->n_tiles = h->ntiles;
+    out->grid_ctas = h->grid;
+    out->schedule = h->schedule;
+    out->n_lattices = (int32_t)h->lat.size();
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_handle* h, int32_t repeats) {
+    if (!h || repeats < 1) return LBM_ERR_ARG;
+    CK(h, cudaStreamSynchronize(h->stream));
+    static const int cand[][2] = {{32, 4},  {32, 8},  {32, 16}, {64, 2},  {64, 4},
+                                  {64, 8},  {128, 1}, {128, 2}, {128, 4}, {256, 1},
+                                  {256, 2}, {512, 1}};
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(h, cudaEventCreate(&a));
+    CK(h, cudaEventCreate(&b));
+    const bool was_prof = h->prof;
+    h->prof = false;
+    const int64_t launches0 = h->launches;
+    float best = 1e30f;
+    int btx = h->tx, bty = h->ty, bgrid = h->grid;
+    int rc = LBM_OK;
+    for (const auto& c : cand) {
+        rc = build_tiles(h, c[0], c[1]);
+        if (rc) break;
+        for (int mode = 0; mode < 2; ++mode) {
+            h->grid = mode == 0 ? default_grid(h) : h->ntiles;
+            // trial steps read buffer `parity` and write the other one, so
+            // repeating them leaves the state unchanged
+            rc = launch_step(h, h->parity);
+            if (rc) break;
+            cudaEventRecord(a, h->stream);
+            for (int r = 0; r < repeats && rc == LBM_OK; ++r) rc = launch_step(h, h->parity);
+            cudaEventRecord(b, h->stream);
+            if (rc) break;
+            if (cudaEventSynchronize(b) != cudaSuccess) {
+                rc = cuda_fail(h, cudaGetLastError(), "autotune");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (ms < best) {
+                best = ms;
+                btx = c[0];
+                bty = c[1];
+                bgrid = h->grid;
+            }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    h->launches = launches0;
+    h->prof = was_prof;
+    if (rc) return rc;
+    rc = build_tiles(h, btx, bty);
+    if (rc) return rc;
+    h->grid = bgrid;
+    drop_graph(h);
+    // trial steps may have flagged nothing new; statuses are per state, keep them
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneKey k{h->device, h->storage, h->eos, h->schedule, (int64_t)std::log2((double)h->sites),
+              (int64_t)std::log2((double)h->lat.size())};
+    g_tune_cache[k] = TuneVal{btx, bty, bgrid};
+    return LBM_OK;
+}
+
+}  // extern "C"
