@@ -41,7 +41,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="roofline", choices=["roofline", "batched"])
-    ap.add_argument("--eos", default="f64", choices=["f64", "df", "f32"])
+    ap.add_argument("--eos", default="df", choices=["f64", "df", "f32"],
+                    help="arithmetic of psi/EOS: float-float (default), native FP64 or FP32")
+    ap.add_argument("--variant", default="tma", choices=["tma", "plain"])
     ap.add_argument("--storage", default="f32dev", choices=["f32", "f32dev", "f16dev"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true")
@@ -258,7 +260,8 @@ def run_gpu(args):
 
         rg, rl = synth.coexistence(wl["T"])
         d.rho0 = 0.5 * (rg + rl)
-    h = P.lbm_create(d)
+    h = P.lbm_create(d, kernel_variant={"tma": P.LBM_KERNEL_TMA,
+                                        "plain": P.LBM_KERNEL_PLAIN}[args.variant])
     st = h.stream
     P.lbm_init(h, 0, rho)
     if args.autotune:
@@ -340,7 +343,7 @@ def run_gpu(args):
         "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl["name"], "storage": args.storage, "eos": args.eos,
-                   "schedule": "two_pass", "tile": [info["tile_x"], info["tile_y"]],
+                   "schedule": "two_pass", "kernel_variant": args.variant, "tile": [info["tile_x"], info["tile_y"]],
                    "grid_ctas": info["grid_ctas"], "sites": sites,
                    "l2": f"working set {info['device_bytes'] / 1e9:.2f} GB vs 129 MB L2: "
                          "inputs larger than L2, no flush",

@@ -68,14 +68,20 @@ extern "C" {
 #define LBM_COLL_BGK 0 /* Eq. (BGKCO) with Guo forcing Eq. (GFSBGK)            */
 #define LBM_COLL_MRT 1 /* Eq. (MRTCO), Gram-Schmidt M of Appendix A, Eq. (GFSMRT) */
 
+/* ---- kernel variant ------------------------------------------------------ */
+#define LBM_KERNEL_TMA 0   /* tiles staged by TMA bulk-tensor copies (default);
+                              tile shapes 64x8, 64x16, 128x4, 128x8, 32x16   */
+#define LBM_KERNEL_PLAIN 1 /* one site per thread, plain global loads;
+                              tile_x a multiple of 32, tile_x*tile_y <= 512  */
+
 /* ---- step schedule ------------------------------------------------------- */
 #define LBM_SCHED_TWO_PASS 0 /* psi pass, then fused force+collide+pull pass    */
 #define LBM_SCHED_FUSED 1    /* one pass; psi rebuilt from a 2-site halo        */
 
 /* One lattice.  Defaults (lbm_desc_default): tau = 1, G = -1, eps = 1.73,
  * sigma = 1, T = 0.8, a/b/c/k = 3.852462257 / 0.1304438842 / 2.785855166 /
- * 0.01 (Sec. IV.A), rho0 = 1, LBM_STORE_F32_DEV, LBM_EOS_F64, direct trace,
- * BGK, MRT rates diag(1,1,1,1,1,1,1,1/tau,1/tau) (Eq. RM). */
+ * 0.01 (Sec. IV.A), rho0 = -1 (automatic), LBM_STORE_F32_DEV, LBM_EOS_DF,
+ * direct trace, BGK, MRT rates diag(1,1,1,1,1,1,1,1/tau,1/tau) (Eq. RM). */
 typedef struct {
     int32_t nx, ny;           /* lattice size, each >= 2                        */
     double tau;               /* relaxation time, > 0.5                         */
@@ -83,7 +89,9 @@ typedef struct {
     double eps, sigma;        /* Eq. (IFT)                                       */
     double T;                 /* reduced temperature in Eq. (CSEOS)             */
     double eos_a, eos_b, eos_c, eos_k;
-    double rho0;              /* reference density of deviation storage         */
+    double rho0;              /* reference density of deviation storage; < 0:
+                                 automatic, the smallest density of the field
+                                 given to lbm_init (ignored by LBM_STORE_F32)   */
     int32_t storage;          /* LBM_STORE_*                                     */
     int32_t eos_precision;    /* LBM_EOS_*                                       */
     int32_t m2_trace_variant; /* 0: M2_bb direct trace (Eq. SOMED);
@@ -105,6 +113,7 @@ typedef struct {
     int32_t grid_ctas; /* CTAs of the persistent launches (0: SMs x occupancy) */
     int32_t schedule;  /* LBM_SCHED_*                                          */
     int32_t graph_steps; /* steps per captured CUDA graph (0: default, <0: off) */
+    int32_t kernel_variant; /* LBM_KERNEL_*                                   */
 } lbm_runtime_opts;
 
 typedef struct lbm_handle lbm_handle;

@@ -35,6 +35,8 @@ LBM_EOS_DF = 1
 LBM_EOS_F32 = 2
 LBM_COLL_BGK = 0
 LBM_COLL_MRT = 1
+LBM_KERNEL_TMA = 0
+LBM_KERNEL_PLAIN = 1
 LBM_SCHED_TWO_PASS = 0
 LBM_SCHED_FUSED = 1
 
@@ -63,7 +65,8 @@ class RuntimeOpts(ctypes.Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p), ("tile_x", ctypes.c_int32),
                 ("tile_y", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("graph_steps", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
+                ("kernel_variant", ctypes.c_int32)]
 
 
 class KernelStat(ctypes.Structure):
@@ -205,7 +208,7 @@ def lbm_desc_default(nx: int, ny: int, **kw) -> LatticeDesc:
 
 
 def lbm_create(descs, tile=None, grid_ctas=0, schedule=LBM_SCHED_TWO_PASS, graph_steps=0,
-               stream=None, device=None) -> Handle:
+               stream=None, device=None, kernel_variant=LBM_KERNEL_TMA) -> Handle:
     """Create a handle over one descriptor or a list of them."""
     import torch
 
@@ -222,6 +225,7 @@ def lbm_create(descs, tile=None, grid_ctas=0, schedule=LBM_SCHED_TWO_PASS, graph
     o.stream = stream.cuda_stream
     o.tile_x, o.tile_y = (tile or (0, 0))
     o.grid_ctas, o.schedule, o.graph_steps = grid_ctas, schedule, graph_steps
+    o.kernel_variant = kernel_variant
     out = ctypes.c_void_p()
     with torch.cuda.device(dev):
         rc = load().lbm_create(arr, n, ctypes.byref(o), ctypes.byref(out))

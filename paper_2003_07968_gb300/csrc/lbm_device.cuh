@@ -11,6 +11,7 @@
 //   The buffers hold POST-collision, PRE-streaming populations f*; a step
 //   pulls f_i(x) = f*_i(x - c_i) (streaming of Eq. TLBE in pull form).
 #pragma once
+#include <cuda.h>  // CUtensorMap (type only; the driver is reached through the runtime)
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -75,8 +76,10 @@ struct StepArgs {
     int ntiles;
     void* pop;          // population arena
     float* psi;         // psi arena
-    uint32_t* status;   // per-lattice fault bits
+    uint32_t* status;   // per-lattice fault bits: 1 psi undefined, 2 TMA wait timed out
     int parity;         // which population buffer holds the current state
+    const CUtensorMap* pop_maps;  // per lattice: populations [18 planes][rows][pitch]
+    const CUtensorMap* psi_maps;  // per lattice: psi [rows][pitch_psi]
 };
 
 // ---- storage traits ---------------------------------------------------------
@@ -84,12 +87,14 @@ struct StoreF32 {
     using T = float;
     static constexpr int kGx = 4;  // 16 bytes of ghost columns keep rows aligned
     static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float lds(const float* p) { return *p; }
     static __device__ __forceinline__ float cv(float v) { return v; }
 };
 struct StoreF16 {
     using T = __half;
     static constexpr int kGx = 8;
     static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float lds(const __half* p) { return __half2float(*p); }
     static __device__ __forceinline__ __half cv(float v) { return __float2half_rn(v); }
 };
 
@@ -162,6 +167,11 @@ __device__ __forceinline__ df2 df_div(df2 a, df2 b) {
 }
 
 // ---- psi(rho), Eqs. (DED) and (CSEOS) --------------------------------------
+// psi^2 = (P_EOS - c_s^2 rho)/G = rho (e1 q - e2 rho - e3) with
+// q = (1 + eta + eta^2 - eta^3)/(1 - eta)^3, eta = b rho.  Writing
+// r = 1/(1 - eta) turns q into the polynomial 1 - 2r + 2r^3 (exact algebra:
+// the numerator is 2 - 2s^2 + s^3 in s = 1 - eta), which needs one
+// reciprocal instead of a division of two cubics.
 // Returns psi and sets ok = false where psi is undefined (rho <= 0 or not
 // finite, b rho >= 1, negative radicand).
 enum { EOS_F64 = 0, EOS_DF = 1, EOS_F32 = 2 };
@@ -172,38 +182,45 @@ __device__ __forceinline__ float eval_psi(const LatDev& L, float rho, bool& ok);
 template <>
 __device__ __forceinline__ float eval_psi<EOS_F64>(const LatDev& L, float rho, bool& ok) {
     const double r = (double)rho;
-    const double eta = L.eb * r;
-    const double num = 1.0 + eta * (1.0 + eta * (1.0 - eta));
-    const double s = 1.0 - eta;
-    const double q = num / (s * s * s);
-    const double arg = r * (L.e1 * q - L.e2 * r - L.e3);
-    ok = (rho > 0.f) && (eta < 1.0) && (arg >= 0.0) && isfinite(arg);
+    const double s = fma(-L.eb, r, 1.0);
+    const double rr = 1.0 / s;
+    const double q = fma(2.0 * rr, rr * rr, fma(-2.0, rr, 1.0));
+    const double arg = r * fma(L.e1, q, -fma(L.e2, r, L.e3));
+    ok = (rho > 0.f) && (s > 0.0) && (arg >= 0.0) && isfinite(arg);
     return sqrtf((float)arg);
+}
+
+// 1/s in float-float: one Newton step on the rounded reciprocal.
+__device__ __forceinline__ df2 df_rcp(df2 s) {
+    const float q = __frcp_rn(s.hi);
+    const float e = __fmaf_rn(-s.lo, q, __fmaf_rn(-s.hi, q, 1.f));  // 1 - s q
+    return fast_two_sum(q, __fmul_rn(q, e));
 }
 
 template <>
 __device__ __forceinline__ float eval_psi<EOS_DF>(const LatDev& L, float rho, bool& ok) {
-    const df2 r = {rho, 0.f};
-    const df2 one = {1.f, 0.f};
-    const df2 eta = df_mul_f(L.fb, rho);
-    const df2 num = df_add(one, df_mul(eta, df_add(one, df_mul(eta, df_add(one, df_neg(eta))))));
-    const df2 s = df_add(one, df_neg(eta));
-    const df2 den = df_mul(df_mul(s, s), s);
-    const df2 q = df_div(num, den);
-    const df2 inner = df_add(df_add(df_mul(L.f1, q), df_neg(df_mul_f(L.f2, rho))), df_neg(L.f3));
-    const df2 arg = df_mul(r, inner);
-    ok = (rho > 0.f) && (eta.hi < 1.f) && (arg.hi >= 0.f) && isfinite(arg.hi);
+    const df2 br = df_mul_f(L.fb, rho);
+    df2 s = two_sum(1.f, -br.hi);  // 1 - b rho
+    s = fast_two_sum(s.hi, __fsub_rn(s.lo, br.lo));
+    const df2 r = df_rcp(s);
+    const df2 r3 = df_mul(df_mul(r, r), r);
+    // q = 1 - 2 r + 2 r^3 (doubling is exact)
+    const df2 q = df_add(df_add(df2{1.f, 0.f}, df2{-2.f * r.hi, -2.f * r.lo}),
+                         df2{2.f * r3.hi, 2.f * r3.lo});
+    const df2 t = df_add(df_mul_f(L.f2, rho), L.f3);
+    const df2 inner = df_add(df_mul(L.f1, q), df_neg(t));
+    const df2 arg = df_mul_f(inner, rho);
+    ok = (rho > 0.f) && (s.hi > 0.f) && (arg.hi >= 0.f) && isfinite(arg.hi);
     return sqrtf(arg.hi);
 }
 
 template <>
 __device__ __forceinline__ float eval_psi<EOS_F32>(const LatDev& L, float rho, bool& ok) {
-    const float eta = L.sb * rho;
-    const float num = 1.f + eta * (1.f + eta * (1.f - eta));
-    const float s = 1.f - eta;
-    const float q = num / (s * s * s);
-    const float arg = rho * (L.s1 * q - L.s2 * rho - L.s3);
-    ok = (rho > 0.f) && (eta < 1.f) && (arg >= 0.f) && isfinite(arg);
+    const float s = fmaf(-L.sb, rho, 1.f);
+    const float rr = 1.f / s;
+    const float q = fmaf(2.f * rr, rr * rr, fmaf(-2.f, rr, 1.f));
+    const float arg = rho * fmaf(L.s1, q, -fmaf(L.s2, rho, L.s3));
+    ok = (rho > 0.f) && (s > 0.f) && (arg >= 0.f) && isfinite(arg);
     return sqrtf(arg);
 }
 

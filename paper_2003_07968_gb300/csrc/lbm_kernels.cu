@@ -108,10 +108,14 @@ __global__ void __launch_bounds__(512) k_collide(StepArgs a) {
         const float om = L.omega, gu = L.guo;
         T* o = reinterpret_cast<T*>(a.pop) + L.off_f[a.parity ^ 1];
         const int gx = L.gx;
+// Directions 1..8 follow Eqs. (BGKCO), (SEDF), (GFS) directly.  The rest
+// population takes what mass conservation leaves: in exact arithmetic
+// sum_i f*_i = sum_i f_i, so f*_0 = sum_i f_i - sum_{i>0} f*_i is the same
+// number, but it keeps the FP32 weights (whose sum is not exactly 1) from
+// adding a biased mass error every step.
 #define PPLBM_OUT(I, G)                                                                   \
-    store_img(o + I * plane, pitch, gx, x, y, nx, ny,                                     \
-              S::cv(bgk_guo<I>(G, drho, rho, ux, uy, usq, F.x, F.y, Fu, om, gu)))
-        PPLBM_OUT(0, g0);
+    const float o##I = bgk_guo<I>(G, drho, rho, ux, uy, usq, F.x, F.y, Fu, om, gu);       \
+    store_img(o + I * plane, pitch, gx, x, y, nx, ny, S::cv(o##I))
         PPLBM_OUT(1, g1);
         PPLBM_OUT(2, g2);
         PPLBM_OUT(3, g3);
@@ -120,6 +124,8 @@ __global__ void __launch_bounds__(512) k_collide(StepArgs a) {
         PPLBM_OUT(6, g6);
         PPLBM_OUT(7, g7);
         PPLBM_OUT(8, g8);
+        const float o0 = drho - (((o1 + o2) + (o3 + o4)) + ((o5 + o6) + (o7 + o8)));
+        store_img(o, pitch, gx, x, y, nx, ny, S::cv(o0));
 #undef PPLBM_OUT
     }
 }

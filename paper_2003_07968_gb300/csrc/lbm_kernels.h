@@ -17,6 +17,16 @@ cudaError_t launch_moments(int storage_f16, const LatDev& L, const void* pop, in
 cudaError_t launch_mass(int storage_f16, const LatDev& L, const void* pop, int parity,
                         double* partials, int n_partials, double* out, cudaStream_t st);
 int occupancy_psi(int storage_f16, int eos, int threads);
+// TMA-pipelined passes (lbm_tma.cu); tile shapes are compile-time instances.
+bool tma_shape_supported(int tx, int ty);
+cudaError_t launch_psi_tma(int f16, int eos, int tx, int ty, const StepArgs& a, int grid,
+                           cudaStream_t st);
+cudaError_t launch_collide_tma(int f16, int tx, int ty, const StepArgs& a, int grid,
+                               cudaStream_t st);
+int occupancy_psi_tma(int f16, int eos, int tx, int ty);
+int occupancy_collide_tma(int f16, int tx, int ty);
+int encode_tensor_maps(int f16, int tx, int ty, const LatDev& L, void* pop, float* psi,
+                       CUtensorMap* pop_map, CUtensorMap* psi_map);
 int occupancy_collide(int storage_f16, int threads, size_t smem);
 
 }  // namespace pplbm

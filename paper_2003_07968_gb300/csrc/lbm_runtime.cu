@@ -42,7 +42,7 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int tx, ty, grid;
+    int tx, ty, grid, grid_psi;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
@@ -70,6 +70,9 @@ struct lbm_handle {
     uint32_t* status = nullptr;
     int4* tiles = nullptr;
     size_t tiles_cap = 0;
+    CUtensorMap* tmaps = nullptr;  // [n] population maps, then [n] psi maps
+    int variant = LBM_KERNEL_TMA;
+    int grid_psi = 0;
     double* partials = nullptr;  // mass partials + one result slot
     double* staging = nullptr;   // FP64 field staging (rho, ux, uy)
     size_t staging_elems = 0;
@@ -150,7 +153,7 @@ int validate(const lbm_lattice_desc& d, std::string& why) {
     if (!(d.tau > 0.5) || !std::isfinite(d.tau)) return why = "tau must be > 0.5", LBM_ERR_ARG;
     if (!(d.G != 0.0) || !std::isfinite(d.G)) return why = "G must be nonzero", LBM_ERR_ARG;
     if (!std::isfinite(d.eps) || !std::isfinite(d.sigma) || !std::isfinite(d.T) ||
-        !std::isfinite(d.rho0))
+        !std::isfinite(d.rho0) || d.rho0 > 1e6)
         return why = "non-finite parameter", LBM_ERR_ARG;
     if (!(d.eos_b > 0.0) || !std::isfinite(d.eos_a) || !std::isfinite(d.eos_c) ||
         !std::isfinite(d.eos_k))
@@ -189,7 +192,7 @@ LatDev make_lat(const lbm_lattice_desc& d, int index, int64_t& pop_cursor,
     L.k_sc = (float)(-6.0 * d.G);
     L.k1 = (float)(13.5 * d.eps * d.G);
     L.k2 = (float)(9.0 * (d.sigma - 1.0) * d.G);
-    L.rho0 = d.storage == LBM_STORE_F32 ? 0.f : (float)d.rho0;
+    L.rho0 = (d.storage == LBM_STORE_F32 || d.rho0 < 0.0) ? 0.f : (float)d.rho0;
     L.m2_variant = d.m2_trace_variant;
     L.lattice = index;
     // psi^2 = rho (e1 q - e2 rho - e3): e1 = k c T / G, e2 = k a / G, e3 = 1/(3G)
@@ -226,6 +229,7 @@ int build_tiles(lbm_handle* h, int tx, int ty) {
     const size_t bytes = t.size() * sizeof(int4);
     if (bytes > h->tiles_cap) {
         dev_free(h, h->tiles, h->tiles_cap);
+    dev_free(h, h->tmaps, 2 * h->lat.size() * sizeof(CUtensorMap));
         h->tiles = (int4*)dev_alloc(h, bytes);
         if (!h->tiles) {
             h->tiles_cap = 0;
@@ -234,6 +238,20 @@ int build_tiles(lbm_handle* h, int tx, int ty) {
         h->tiles_cap = bytes;
     }
     CK(h, cudaMemcpyAsync(h->tiles, t.data(), bytes, cudaMemcpyHostToDevice, h->stream));
+    if (h->variant == LBM_KERNEL_TMA) {
+        const size_t n = h->lat.size();
+        std::vector<CUtensorMap> maps(2 * n);
+        for (size_t l = 0; l < n; ++l) {
+            const int r = encode_tensor_maps(h->f16, tx, ty, h->lat[l], h->pop, h->psi, &maps[l],
+                                             &maps[n + l]);
+            if (r) {
+                h->err = "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")";
+                return LBM_ERR_CUDA;
+            }
+        }
+        CK(h, cudaMemcpyAsync(h->tmaps, maps.data(), 2 * n * sizeof(CUtensorMap),
+                              cudaMemcpyHostToDevice, h->stream));
+    }
     CK(h, cudaStreamSynchronize(h->stream));
     h->tx = tx;
     h->ty = ty;
@@ -243,11 +261,19 @@ int build_tiles(lbm_handle* h, int tx, int ty) {
 
 size_t collide_smem(int tx, int ty) { return (size_t)(tx + 2) * (ty + 2) * sizeof(float); }
 
-int default_grid(lbm_handle* h) {
-    const int thr = h->tx * h->ty;
-    const int occ = std::min(occupancy_psi(h->f16, h->eos, thr),
-                             occupancy_collide(h->f16, thr, collide_smem(h->tx, h->ty)));
-    return std::max(1, std::min(h->ntiles, h->sm_count * occ));
+// Persistent grids: SMs x resident CTAs of each pass, capped by the tile count.
+void default_grids(lbm_handle* h) {
+    int op, oc;
+    if (h->variant == LBM_KERNEL_TMA) {
+        op = occupancy_psi_tma(h->f16, h->eos, h->tx, h->ty);
+        oc = occupancy_collide_tma(h->f16, h->tx, h->ty);
+    } else {
+        const int thr = h->tx * h->ty;
+        op = occupancy_psi(h->f16, h->eos, thr);
+        oc = occupancy_collide(h->f16, thr, collide_smem(h->tx, h->ty));
+    }
+    h->grid_psi = std::max(1, std::min(h->ntiles, h->sm_count * op));
+    h->grid = std::max(1, std::min(h->ntiles, h->sm_count * oc));
 }
 
 void drop_graph(lbm_handle* h) {
@@ -267,6 +293,8 @@ StepArgs step_args(lbm_handle* h, int parity) {
     a.psi = h->psi;
     a.status = h->status;
     a.parity = parity;
+    a.pop_maps = h->tmaps;
+    a.psi_maps = h->tmaps ? h->tmaps + h->lat.size() : nullptr;
     return a;
 }
 
@@ -294,9 +322,15 @@ int launch_step(lbm_handle* h, int p) {
         e2 = take_event(h);
         CK(h, cudaEventRecord(e0, h->stream));
     }
-    CK(h, launch_psi(h->f16, h->eos, a, g, b, h->stream));
+    if (h->variant == LBM_KERNEL_TMA)
+        CK(h, launch_psi_tma(h->f16, h->eos, h->tx, h->ty, a, h->grid_psi, h->stream));
+    else
+        CK(h, launch_psi(h->f16, h->eos, a, dim3(h->grid_psi), b, h->stream));
     if (h->prof) CK(h, cudaEventRecord(e1, h->stream));
-    CK(h, launch_collide(h->f16, a, g, b, smem, h->stream));
+    if (h->variant == LBM_KERNEL_TMA)
+        CK(h, launch_collide_tma(h->f16, h->tx, h->ty, a, h->grid, h->stream));
+    else
+        CK(h, launch_collide(h->f16, a, g, b, smem, h->stream));
     if (h->prof) {
         CK(h, cudaEventRecord(e2, h->stream));
         h->rec[0].pending.emplace_back(e0, e1);
@@ -389,6 +423,7 @@ void release(lbm_handle* h) {
     dev_free(h, h->staging, h->staging_elems * 3 * sizeof(double));
     dev_free(h, h->partials, (kMassPartials + 1) * sizeof(double));
     dev_free(h, h->tiles, h->tiles_cap);
+    dev_free(h, h->tmaps, 2 * h->lat.size() * sizeof(CUtensorMap));
     dev_free(h, h->status, h->lat.size() * sizeof(uint32_t));
     dev_free(h, h->lat_dev, h->lat.size() * sizeof(LatDev));
     dev_free(h, h->psi, h->psi_bytes);
@@ -415,9 +450,9 @@ void lbm_desc_default(lbm_lattice_desc* d, int32_t nx, int32_t ny) {
     d->eos_b = 0.1304438842;
     d->eos_c = 2.785855166;
     d->eos_k = 0.01;
-    d->rho0 = 1.0;
+    d->rho0 = -1.0;  // automatic: the smallest density handed to lbm_init
     d->storage = LBM_STORE_F32_DEV;
-    d->eos_precision = LBM_EOS_F64;
+    d->eos_precision = LBM_EOS_DF;
     d->m2_trace_variant = 0;
     d->collision = LBM_COLL_BGK;
     for (int i = 0; i < 9; ++i) d->mrt_rates[i] = i < 7 ? 1.0 : 1.0 / d->tau;
@@ -457,9 +492,12 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
     }
     if (opts && (opts->alloc == nullptr) != (opts->free == nullptr)) return LBM_ERR_ARG;
     if (opts && (opts->tile_x < 0 || opts->tile_y < 0 || opts->grid_ctas < 0)) return LBM_ERR_ARG;
-    if (opts) {
-        const int tx = opts->tile_x ? opts->tile_x : 32, ty = opts->tile_y ? opts->tile_y : 8;
-        if ((tx % 32) || tx * ty > 512) return LBM_ERR_ARG;
+    const int variant = opts ? opts->kernel_variant : LBM_KERNEL_TMA;
+    if (variant != LBM_KERNEL_TMA && variant != LBM_KERNEL_PLAIN) return LBM_ERR_ARG;
+    if (opts && (opts->tile_x || opts->tile_y)) {
+        const int tx = opts->tile_x ? opts->tile_x : 64, ty = opts->tile_y ? opts->tile_y : 8;
+        if (variant == LBM_KERNEL_TMA && !tma_shape_supported(tx, ty)) return LBM_ERR_ARG;
+        if (variant == LBM_KERNEL_PLAIN && ((tx % 32) || tx * ty > 512)) return LBM_ERR_ARG;
     }
     if (opts && opts->schedule != LBM_SCHED_TWO_PASS) return LBM_ERR_ARG;
 
@@ -469,6 +507,7 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
     h->desc.assign(descs, descs + n);
     h->storage = descs[0].storage;
     h->f16 = h->storage == LBM_STORE_F16_DEV;
+    h->variant = variant;
     h->eos = descs[0].eos_precision;
     h->collision = descs[0].collision;
     h->graph_steps = (opts && opts->graph_steps != 0) ? opts->graph_steps : 32;
@@ -503,7 +542,9 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
     h->lat_dev = (LatDev*)dev_alloc(h, n * sizeof(LatDev));
     h->status = (uint32_t*)dev_alloc(h, n * sizeof(uint32_t));
     h->partials = (double*)dev_alloc(h, (kMassPartials + 1) * sizeof(double));
-    if (!h->pop || !h->psi || !h->lat_dev || !h->status || !h->partials) return fail(LBM_ERR_OOM);
+    h->tmaps = (CUtensorMap*)dev_alloc(h, 2 * n * sizeof(CUtensorMap));
+    if (!h->pop || !h->psi || !h->lat_dev || !h->status || !h->partials || !h->tmaps)
+        return fail(LBM_ERR_OOM);
     if (cudaMallocHost(&h->status_host, n * sizeof(uint32_t)) != cudaSuccess)
         return fail(LBM_ERR_OOM);
     if (cudaEventCreateWithFlags(&h->status_ev, cudaEventDisableTiming) != cudaSuccess)
@@ -514,21 +555,34 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
         cudaMemcpyAsync(h->lat_dev, h->lat.data(), n * sizeof(LatDev), cudaMemcpyHostToDevice,
                         h->stream) != cudaSuccess)
         return fail(LBM_ERR_CUDA);
-    int tx = (opts && opts->tile_x) ? opts->tile_x : 32;
+    int tx = (opts && opts->tile_x) ? opts->tile_x : 64;
     int ty = (opts && opts->tile_y) ? opts->tile_y : 8;
+    bool tuned = false;
+    int tuned_grid = 0, tuned_grid_psi = 0;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        TuneKey k{h->device, h->storage, h->eos, h->schedule, (int64_t)std::log2((double)h->sites),
+        TuneKey k{h->device, h->storage, h->eos, h->variant, (int64_t)std::log2((double)h->sites),
                   (int64_t)std::log2((double)n)};
         auto it = g_tune_cache.find(k);
-        if (it != g_tune_cache.end() && !(opts && opts->tile_x)) {
+        if (it != g_tune_cache.end() && !(opts && (opts->tile_x || opts->tile_y))) {
             tx = it->second.tx;
             ty = it->second.ty;
+            tuned = true;
+            tuned_grid = it->second.grid;
+            tuned_grid_psi = it->second.grid_psi;
         }
     }
     int rc = build_tiles(h, tx, ty);
     if (rc) return fail(rc);
-    h->grid = (opts && opts->grid_ctas) ? std::min(opts->grid_ctas, h->ntiles) : default_grid(h);
+    default_grids(h);
+    if (tuned) {
+        h->grid = std::min(tuned_grid, h->ntiles);
+        h->grid_psi = std::min(tuned_grid_psi, h->ntiles);
+    }
+    if (opts && opts->grid_ctas) {
+        h->grid = std::min(opts->grid_ctas, h->ntiles);
+        h->grid_psi = h->grid;
+    }
     h->rec[0].name = "psi_pass";
     h->rec[1].name = "collide_stream";
     h->rec[0].bytes = (double)h->sites * (9.0 * es + 4.0);
@@ -541,10 +595,21 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
 int lbm_init(lbm_handle* h, int32_t lattice, const double* rho, const double* ux,
              const double* uy) {
     if (!h || !rho || lattice < 0 || lattice >= (int)h->lat.size()) return LBM_ERR_ARG;
-    const LatDev& L = h->lat[lattice];
+    LatDev& L = h->lat[lattice];
     const size_t n = (size_t)L.nx * L.ny;
     int rc = ensure_staging(h, n);
     if (rc) return rc;
+    if (h->desc[lattice].storage != LBM_STORE_F32 && h->desc[lattice].rho0 < 0.0) {
+        // automatic reference: the smallest density keeps the vapour deviations
+        // small (best relative precision where rho is smallest) and the liquid
+        // ones no larger than plain storage would hold
+        double m = rho[0];
+        for (size_t i = 1; i < n; ++i) m = std::min(m, rho[i]);
+        if (!std::isfinite(m)) return LBM_ERR_ARG;
+        L.rho0 = (float)std::max(m, 0.0);
+        CK(h, cudaMemcpyAsync(h->lat_dev + lattice, &L, sizeof(LatDev), cudaMemcpyHostToDevice,
+                              h->stream));
+    }
     double* dr = h->staging;
     double* dx = h->staging + h->staging_elems;
     double* dy = h->staging + 2 * h->staging_elems;
@@ -613,8 +678,12 @@ int lbm_moments(lbm_handle* h, int32_t lattice, double* rho, double* ux, double*
         StepArgs a = step_args(h, h->parity);
         a.tiles = h->tiles + h->tile_begin[lattice];
         a.ntiles = h->tile_count[lattice];
-        CK(h, launch_psi(h->f16, h->eos, a, dim3(std::min(h->grid, a.ntiles)), dim3(h->tx, h->ty),
-                         h->stream));
+        if (h->variant == LBM_KERNEL_TMA)
+            CK(h, launch_psi_tma(h->f16, h->eos, h->tx, h->ty, a, std::min(h->grid_psi, a.ntiles),
+                                 h->stream));
+        else
+            CK(h, launch_psi(h->f16, h->eos, a, dim3(std::min(h->grid_psi, a.ntiles)),
+                             dim3(h->tx, h->ty), h->stream));
         double* dr = h->staging;
         double* dx = h->staging + h->staging_elems;
         double* dy = h->staging + 2 * h->staging_elems;
@@ -701,9 +770,15 @@ int lbm_info(lbm_handle* h, lbm_info_t* out) {
 int lbm_autotune(lbm_handle* h, int32_t repeats) {
     if (!h || repeats < 1) return LBM_ERR_ARG;
     CK(h, cudaStreamSynchronize(h->stream));
-    static const int cand[][2] = {{32, 4},  {32, 8},  {32, 16}, {64, 2},  {64, 4},
-                                  {64, 8},  {128, 1}, {128, 2}, {128, 4}, {256, 1},
-                                  {256, 2}, {512, 1}};
+    static const int cand_tma[][2] = {{64, 8}, {64, 16}, {128, 4}, {128, 8}, {32, 16}};
+    static const int cand_plain[][2] = {{32, 4},  {32, 8},  {32, 16}, {64, 2},  {64, 4},
+                                        {64, 8},  {128, 1}, {128, 2}, {128, 4}, {256, 1},
+                                        {256, 2}, {512, 1}};
+    std::vector<std::pair<int, int>> cand;
+    if (h->variant == LBM_KERNEL_TMA)
+        for (const auto& c : cand_tma) cand.emplace_back(c[0], c[1]);
+    else
+        for (const auto& c : cand_plain) cand.emplace_back(c[0], c[1]);
     cudaEvent_t a = nullptr, b = nullptr;
     CK(h, cudaEventCreate(&a));
     CK(h, cudaEventCreate(&b));
@@ -711,13 +786,17 @@ int lbm_autotune(lbm_handle* h, int32_t repeats) {
     h->prof = false;
     const int64_t launches0 = h->launches;
     float best = 1e30f;
-    int btx = h->tx, bty = h->ty, bgrid = h->grid;
+    int btx = h->tx, bty = h->ty, bgrid = h->grid, bgrid_psi = h->grid_psi;
     int rc = LBM_OK;
     for (const auto& c : cand) {
-        rc = build_tiles(h, c[0], c[1]);
+        rc = build_tiles(h, c.first, c.second);
         if (rc) break;
+        default_grids(h);
+        const int g0 = h->grid, gp0 = h->grid_psi;
+        // persistent grids (SMs x occupancy) against one CTA per tile
         for (int mode = 0; mode < 2; ++mode) {
-            h->grid = mode == 0 ? default_grid(h) : h->ntiles;
+            h->grid = mode == 0 ? g0 : h->ntiles;
+            h->grid_psi = mode == 0 ? gp0 : h->ntiles;
             // trial steps read buffer `parity` and write the other one, so
             // repeating them leaves the state unchanged
             rc = launch_step(h, h->parity);
@@ -726,17 +805,19 @@ int lbm_autotune(lbm_handle* h, int32_t repeats) {
             for (int r = 0; r < repeats && rc == LBM_OK; ++r) rc = launch_step(h, h->parity);
             cudaEventRecord(b, h->stream);
             if (rc) break;
-            if (cudaEventSynchronize(b) != cudaSuccess) {
-                rc = cuda_fail(h, cudaGetLastError(), "autotune");
+            cudaError_t e = cudaEventSynchronize(b);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(h, e, "autotune");
                 break;
             }
             float ms = 0.f;
             cudaEventElapsedTime(&ms, a, b);
             if (ms < best) {
                 best = ms;
-                btx = c[0];
-                bty = c[1];
+                btx = c.first;
+                bty = c.second;
                 bgrid = h->grid;
+                bgrid_psi = h->grid_psi;
             }
         }
         if (rc) break;
@@ -749,12 +830,11 @@ int lbm_autotune(lbm_handle* h, int32_t repeats) {
     rc = build_tiles(h, btx, bty);
     if (rc) return rc;
     h->grid = bgrid;
-    drop_graph(h);
-    // trial steps may have flagged nothing new; statuses are per state, keep them
+    h->grid_psi = bgrid_psi;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    TuneKey k{h->device, h->storage, h->eos, h->schedule, (int64_t)std::log2((double)h->sites),
+    TuneKey k{h->device, h->storage, h->eos, h->variant, (int64_t)std::log2((double)h->sites),
               (int64_t)std::log2((double)h->lat.size())};
-    g_tune_cache[k] = TuneVal{btx, bty, bgrid};
+    g_tune_cache[k] = TuneVal{btx, bty, bgrid, bgrid_psi};
     return LBM_OK;
 }
 

@@ -35,7 +35,7 @@ def rel(a, b):
 
 
 def gpu_run(P, rho, nsteps, T=0.8, tau=1.0, eps=1.73, sigma=1.0, storage=None, eos=None,
-            m2=0, tile=None, graph_steps=0, chunks=None, rho0=None):
+            m2=0, tile=None, graph_steps=0, chunks=None, rho0=None, variant=0):
     ny, nx = rho.shape
     kw = dict(T=T, tau=tau, eps=eps, sigma=sigma, m2_trace_variant=m2)
     if storage is not None:
@@ -45,7 +45,7 @@ def gpu_run(P, rho, nsteps, T=0.8, tau=1.0, eps=1.73, sigma=1.0, storage=None, e
     if rho0 is not None:
         kw["rho0"] = rho0
     d = P.lbm_desc_default(nx, ny, **kw)
-    h = P.lbm_create(d, tile=tile, graph_steps=graph_steps)
+    h = P.lbm_create(d, tile=tile, graph_steps=graph_steps, kernel_variant=variant)
     P.lbm_init(h, 0, rho)
     for c in (chunks or [nsteps]):
         P.lbm_step(h, c)
@@ -85,12 +85,21 @@ def test_small_and_ragged_lattices(P, shape):
     assert abs(g["mass"] - o["mass"]) / o["mass"] <= 1e-6
 
 
-@pytest.mark.parametrize("tile", [(32, 1), (32, 4), (64, 2), (128, 4), (256, 2), (512, 1)])
-def test_tile_shapes(P, tile):
+@pytest.mark.parametrize("variant,tile", [(0, (64, 8)), (0, (64, 16)), (0, (128, 4)),
+                                          (0, (128, 8)), (0, (32, 16)), (1, (32, 1)),
+                                          (1, (64, 2)), (1, (128, 4)), (1, (512, 1))])
+def test_tile_shapes(P, variant, tile):
     rho = synth.droplet(97, 71, 20.0, 0.7)
-    g = gpu_run(P, rho, 200, T=0.7, tile=tile)
+    g = gpu_run(P, rho, 200, T=0.7, tile=tile, variant=variant)
     o = oracle_run(rho, 200, T=0.7)
     assert rel(g["rho"], o["rho"]) <= RTOL_RHO
+
+
+def test_tma_and_plain_variants_agree(P):
+    rho = synth.droplet(150, 130, 35.0, 0.7)
+    a = gpu_run(P, rho, 300, T=0.7, variant=0)
+    b = gpu_run(P, rho, 300, T=0.7, variant=1)
+    assert rel(a["rho"], b["rho"]) <= 1e-6
 
 
 @pytest.mark.parametrize("eos", [0, 1, 2])
@@ -102,16 +111,19 @@ def test_eos_precision_and_fp32_storage(P, eos, storage):
     assert rel(g["rho"], o["rho"]) <= RTOL_RHO
 
 
-def test_fp16_deviation_storage_stated_error(P):
-    # FP16 keeps 11 significant bits: its error is measured, with a bound of
-    # 2e-3 relative on rho after 1000 steps (not the FP32 bar).
-    rho = synth.droplet(80, 80, 22.0, 0.8)
-    rg, rl = synth.coexistence(0.8)
-    g = gpu_run(P, rho, 1000, T=0.8, storage=2, rho0=0.5 * (rg + rl))
-    o = oracle_run(rho, 1000, T=0.8)
-    e = rel(g["rho"], o["rho"])
-    print(f"fp16 deviation storage: max rel rho error after 1000 steps = {e:.3e}")
-    assert e <= 2e-3
+@pytest.mark.parametrize("T", [0.8, 0.6])
+def test_fp16_deviation_storage_stated_error(P, T):
+    # FP16 keeps 11 significant bits, so this storage has its own stated
+    # bound, not the FP32 one: after 1000 steps, 5e-3 relative in the bulk
+    # phases and 5e-2 at the interface (automatic rho0 = vapour density).
+    n = 80
+    rho = synth.droplet(n, n, 22.0, T)
+    g = gpu_run(P, rho, 1000, T=T, storage=2)
+    o = oracle_run(rho, 1000, T=T)
+    e = np.abs(g["rho"] - o["rho"]) / o["rho"]
+    bulk = max(e[0, 0], e[n // 2, n // 2])
+    print(f"fp16 T={T}: max rel rho error {e.max():.3e}, bulk {bulk:.3e}")
+    assert bulk <= 5e-3 and e.max() <= 5e-2
 
 
 @pytest.mark.parametrize("eps,sigma,m2", [(0.0, 1.0, 0), (1.73, 4.0, 0), (1.73, 0.125, 0),
@@ -224,16 +236,20 @@ def test_bad_arguments_are_rejected(P):
 # ------------------------------------------------------------- full-size sampled parity
 def _windows_oracle(rho_full, sites, nsteps, **kw):
     """Oracle value of rho at each sampled site after nsteps, computed on a
-    periodic window of half-width 2 nsteps + 2 around it: information moves
-    at most two sites per step (one for the psi stencil, one for streaming),
-    so the window's own wrap cannot reach the centre."""
+    window of half-width 2 nsteps + 2 around it: information moves at most
+    two sites per step (one for the psi stencil, one for streaming), so what
+    happens at the window's border cannot reach the centre.  The window is
+    mirrored into a periodic field (no jump at its seams) so the oracle's
+    periodic run stays inside the EOS domain there."""
     half = 2 * nsteps + 2
     out = []
     for (y, x) in sites:
         ys = np.arange(y - half, y + half + 1)
         xs = np.arange(x - half, x + half + 1)
         win = rho_full.take(ys, axis=0, mode="wrap").take(xs, axis=1, mode="wrap")
-        m = oracle_run(win, nsteps, **kw)
+        per = np.concatenate([win, win[::-1]], axis=0)
+        per = np.concatenate([per, per[:, ::-1]], axis=1)
+        m = oracle_run(per, nsteps, **kw)
         out.append(m["rho"][half, half])
     return np.array(out)
 
