@@ -252,14 +252,8 @@ def run_gpu(args):
                "f16dev": P.LBM_STORE_F16_DEV}[args.storage]
     wl = roofline_workload(args.size)
     rho = wl["field"]()
-    rg, rl = 0.0, 0.0
     d = P.lbm_desc_default(wl["nx"], wl["ny"], T=wl["T"], tau=wl["tau"], eos_precision=eos,
                            storage=storage)
-    if storage == P.LBM_STORE_F16_DEV:
-        import synth
-
-        rg, rl = synth.coexistence(wl["T"])
-        d.rho0 = 0.5 * (rg + rl)
     h = P.lbm_create(d, kernel_variant={"tma": P.LBM_KERNEL_TMA,
                                         "plain": P.LBM_KERNEL_PLAIN}[args.variant])
     st = h.stream
