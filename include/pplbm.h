@@ -69,7 +69,7 @@ extern "C" {
 #define LBM_COLL_MRT 1 /* Eq. (MRTCO), Gram-Schmidt M of Appendix A, Eq. (GFSMRT) */
 
 /* ---- kernel variant ------------------------------------------------------ */
-#define LBM_KERNEL_TMA 0   /* tiles staged by TMA bulk-tensor copies (default);
+#define LBM_KERNEL_TMA 0   /* tiles staged by TMA bulk copies (default);
                               tile shapes 64x8, 64x16, 128x4, 128x8, 32x16   */
 #define LBM_KERNEL_PLAIN 1 /* one site per thread, plain global loads;
                               tile_x a multiple of 32, tile_x*tile_y <= 512  */
@@ -207,6 +207,15 @@ int lbm_info(lbm_handle* h, lbm_info_t* out);
  * the state unchanged).  Keeps the fastest; results are cached per device,
  * storage and size class for the life of the process.  Errors: LBM_ERR_CUDA. */
 int lbm_autotune(lbm_handle* h, int32_t repeats);
+
+/* Host-only consistency proof of the shared-memory staging used by the
+ * LBM_KERNEL_TMA passes: for a set of lattice shapes, every tile shape, both
+ * storages and both population buffers, each bulk copy is 16-byte aligned
+ * on both sides, has a size that is a multiple of 16 bytes, stays inside
+ * its lattice's allocation and its shared-memory box, and the copies cover
+ * every value an active site reads.  Writes a one-line report.  Needs no GPU.
+ * Returns LBM_OK, or LBM_ERR_STATE with the first violation in the report. */
+int lbm_selfcheck(char* report, int32_t report_len);
 
 #ifdef __cplusplus
 }

@@ -107,6 +107,7 @@ SIGNATURES = {
     "lbm_launch_count": (ctypes.c_int64, [_vp]),
     "lbm_info": (ctypes.c_int, [_vp, ctypes.POINTER(Info)]),
     "lbm_autotune": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "lbm_selfcheck": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int32]),
 }
 
 _lib = None
@@ -322,6 +323,12 @@ def lbm_info(h: Handle) -> dict:
     i = Info()
     _check(load().lbm_info(h.ptr, ctypes.byref(i)), "lbm_info", h)
     return {k: getattr(i, k) for k, _ in Info._fields_}
+
+
+def lbm_selfcheck() -> tuple[int, str]:
+    buf = ctypes.create_string_buffer(512)
+    rc = load().lbm_selfcheck(buf, 512)
+    return rc, buf.value.decode()
 
 
 def lbm_autotune(h: Handle, repeats: int = 3) -> dict:

@@ -1,0 +1,80 @@
+// lbm_copy_plan.h -- which bulk copies stage one tile of the TMA-pipelined
+// passes into shared memory.  Shared by the kernels (device) and by the
+// host self-check (lbm_selfcheck), which proves on the CPU, for many
+// lattice shapes, that every copy is 16-byte aligned on both sides, has a
+// size that is a multiple of 16, stays inside its lattice's allocation and
+// its shared-memory box, and that together the copies cover every value an
+// active site reads.
+//
+// Stage layout (bytes): nine population boxes of BOXB bytes, then (for the
+// collision pass) the psi box.  Population box i holds rows
+// y0 - c_iy + r (r < TY) and lattice columns [x0 - H, x0 + TX + H): the
+// value a site pulls, f*_i(x - c_i, y - c_iy), sits in box row y - y0 at
+// column x - x0 + H - c_ix.  The psi box holds rows y0 - 1 + rr (rr < TY + 2)
+// and columns [x0 - 4, x0 + TX + 4).
+#pragma once
+#include "lbm_device.cuh"
+
+namespace pplbm {
+
+__host__ __device__ constexpr int align128(int v) { return (v + 127) / 128 * 128; }
+__host__ __device__ constexpr int plane_cy(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int plane_cx(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+
+template <int ES, int TX, int TY, bool WITH_PSI>
+struct TileGeo {
+    static constexpr int H = 16 / ES;                  // halo columns kept per side (16 bytes)
+    static constexpr int BW = TX + 2 * H;              // population box width (elements)
+    static constexpr int BOXB = align128(TY * BW * ES);
+    static constexpr int BOXE = BOXB / ES;             // box stride in elements
+    static constexpr int PW = TX + 8;                  // psi box width (floats)
+    static constexpr int PSIB = WITH_PSI ? align128((TY + 2) * PW * 4) : 0;
+    static constexpr int STAGEB = 9 * BOXB + PSIB;
+    static constexpr int NCOPY = 9 * TY + (WITH_PSI ? TY + 2 : 0);
+};
+
+struct CopyOp {
+    int64_t src;  // byte offset into the population arena (psi = false) or psi arena
+    int32_t dst;  // byte offset inside the stage
+    int32_t bytes;
+    bool psi;
+};
+
+// Copy q of the tile with origin (x0, y0) of lattice L, reading population
+// buffer `parity`.  Returns false when the copy is not needed (its rows lie
+// beyond what active sites read).
+template <int ES, int TX, int TY, bool WITH_PSI>
+__host__ __device__ inline bool plan_copy(const LatDev& L, int parity, int x0, int y0, int q,
+                                          CopyOp& op) {
+    using G = TileGeo<ES, TX, TY, WITH_PSI>;
+    if (q < 9 * TY) {
+        const int i = q / TY, r = q - (q / TY) * TY;
+        const int y = y0 - plane_cy(i) + r;  // lattice row held by box row r
+        if (y < -1 || y > L.ny) return false;
+        const int avail = L.pitch - (x0 - G::H + L.gx);  // columns left in the row
+        const int cols = avail < G::BW ? avail : G::BW;
+        op.src = (L.off_f[parity] + (int64_t)i * L.plane + (int64_t)(y + GY) * L.pitch +
+                  (x0 - G::H + L.gx)) *
+                 ES;
+        op.dst = i * G::BOXB + r * G::BW * ES;
+        op.bytes = cols * ES;
+        op.psi = false;
+        return true;
+    }
+    const int rr = q - 9 * TY;
+    const int y = y0 - 1 + rr;
+    if (y > L.ny) return false;
+    const int avail = L.pitch_psi - (x0 - 4 + L.gx_psi);
+    const int cols = avail < G::PW ? avail : G::PW;
+    op.src = (L.off_psi + (int64_t)(y + GY) * L.pitch_psi + (x0 - 4 + L.gx_psi)) * 4;
+    op.dst = 9 * G::BOXB + rr * G::PW * 4;
+    op.bytes = cols * 4;
+    op.psi = true;
+    return true;
+}
+
+}  // namespace pplbm

@@ -11,7 +11,6 @@
 //   The buffers hold POST-collision, PRE-streaming populations f*; a step
 //   pulls f_i(x) = f*_i(x - c_i) (streaming of Eq. TLBE in pull form).
 #pragma once
-#include <cuda.h>  // CUtensorMap (type only; the driver is reached through the runtime)
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -76,10 +75,9 @@ struct StepArgs {
     int ntiles;
     void* pop;          // population arena
     float* psi;         // psi arena
-    uint32_t* status;   // per-lattice fault bits: 1 psi undefined, 2 TMA wait timed out
+    uint32_t* status;   // per-lattice fault bits: 1 psi undefined, 2 copy wait timed out,
+                        // 4 a staging copy broke the alignment rules (skipped)
     int parity;         // which population buffer holds the current state
-    const CUtensorMap* pop_maps;  // per lattice: populations [18 planes][rows][pitch]
-    const CUtensorMap* psi_maps;  // per lattice: psi [rows][pitch_psi]
 };
 
 // ---- storage traits ---------------------------------------------------------

@@ -25,8 +25,6 @@ cudaError_t launch_collide_tma(int f16, int tx, int ty, const StepArgs& a, int g
                                cudaStream_t st);
 int occupancy_psi_tma(int f16, int eos, int tx, int ty);
 int occupancy_collide_tma(int f16, int tx, int ty);
-int encode_tensor_maps(int f16, int tx, int ty, const LatDev& L, void* pop, float* psi,
-                       CUtensorMap* pop_map, CUtensorMap* psi_map);
 int occupancy_collide(int storage_f16, int threads, size_t smem);
 
 }  // namespace pplbm

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/pplbm.h"
+#include "lbm_copy_plan.h"
 #include "lbm_kernels.h"
 
 using namespace pplbm;
@@ -70,7 +71,6 @@ struct lbm_handle {
     uint32_t* status = nullptr;
     int4* tiles = nullptr;
     size_t tiles_cap = 0;
-    CUtensorMap* tmaps = nullptr;  // [n] population maps, then [n] psi maps
     int variant = LBM_KERNEL_TMA;
     int grid_psi = 0;
     double* partials = nullptr;  // mass partials + one result slot
@@ -81,7 +81,8 @@ struct lbm_handle {
     uint32_t* status_host = nullptr;  // pinned
     cudaEvent_t status_ev = nullptr;
     bool status_pending = false;
-    int numeric_lattice = -1;
+    int numeric_lattice = -1;  // first lattice with a device fault bit
+    uint32_t fault_bits = 0;   // OR of the device fault bits seen
     int tx = 32, ty = 8, grid = 0, ntiles = 0;
     int sm_count = 0;
     int parity = 0;
@@ -229,7 +230,6 @@ int build_tiles(lbm_handle* h, int tx, int ty) {
     const size_t bytes = t.size() * sizeof(int4);
     if (bytes > h->tiles_cap) {
         dev_free(h, h->tiles, h->tiles_cap);
-    dev_free(h, h->tmaps, 2 * h->lat.size() * sizeof(CUtensorMap));
         h->tiles = (int4*)dev_alloc(h, bytes);
         if (!h->tiles) {
             h->tiles_cap = 0;
@@ -238,20 +238,6 @@ int build_tiles(lbm_handle* h, int tx, int ty) {
         h->tiles_cap = bytes;
     }
     CK(h, cudaMemcpyAsync(h->tiles, t.data(), bytes, cudaMemcpyHostToDevice, h->stream));
-    if (h->variant == LBM_KERNEL_TMA) {
-        const size_t n = h->lat.size();
-        std::vector<CUtensorMap> maps(2 * n);
-        for (size_t l = 0; l < n; ++l) {
-            const int r = encode_tensor_maps(h->f16, tx, ty, h->lat[l], h->pop, h->psi, &maps[l],
-                                             &maps[n + l]);
-            if (r) {
-                h->err = "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")";
-                return LBM_ERR_CUDA;
-            }
-        }
-        CK(h, cudaMemcpyAsync(h->tmaps, maps.data(), 2 * n * sizeof(CUtensorMap),
-                              cudaMemcpyHostToDevice, h->stream));
-    }
     CK(h, cudaStreamSynchronize(h->stream));
     h->tx = tx;
     h->ty = ty;
@@ -293,8 +279,6 @@ StepArgs step_args(lbm_handle* h, int parity) {
     a.psi = h->psi;
     a.status = h->status;
     a.parity = parity;
-    a.pop_maps = h->tmaps;
-    a.psi_maps = h->tmaps ? h->tmaps + h->lat.size() : nullptr;
     return a;
 }
 
@@ -372,15 +356,29 @@ int capture_graph(lbm_handle* h) {
     return LBM_OK;
 }
 
+int fault_code(lbm_handle* h) {
+    if (h->fault_bits & 2u) return LBM_ERR_TIMEOUT;
+    if (h->fault_bits & 4u) {
+        h->err = "a staging copy broke the bulk-copy alignment rules and was skipped";
+        return LBM_ERR_STATE;
+    }
+    return h->numeric_lattice >= 0 ? LBM_ERR_NUMERIC : LBM_OK;
+}
+
+void absorb_status(lbm_handle* h) {
+    for (size_t l = 0; l < h->lat.size(); ++l)
+        if (h->status_host[l]) {
+            h->fault_bits |= h->status_host[l];
+            if (h->numeric_lattice < 0) h->numeric_lattice = (int)l;
+        }
+}
+
 int check_status_async(lbm_handle* h) {
     if (h->status_pending && cudaEventQuery(h->status_ev) == cudaSuccess) {
         h->status_pending = false;
-        for (size_t l = 0; l < h->lat.size(); ++l)
-            if (h->status_host[l]) {
-                if (h->numeric_lattice < 0) h->numeric_lattice = (int)l;
-            }
+        absorb_status(h);
     }
-    return h->numeric_lattice >= 0 ? LBM_ERR_NUMERIC : LBM_OK;
+    return fault_code(h);
 }
 
 int sync_status(lbm_handle* h) {
@@ -388,9 +386,8 @@ int sync_status(lbm_handle* h) {
     CK(h, cudaMemcpy(h->status_host, h->status, h->lat.size() * sizeof(uint32_t),
                      cudaMemcpyDeviceToHost));
     h->status_pending = false;
-    for (size_t l = 0; l < h->lat.size(); ++l)
-        if (h->status_host[l] && h->numeric_lattice < 0) h->numeric_lattice = (int)l;
-    return h->numeric_lattice >= 0 ? LBM_ERR_NUMERIC : LBM_OK;
+    absorb_status(h);
+    return fault_code(h);
 }
 
 int ensure_staging(lbm_handle* h, size_t elems) {
@@ -423,12 +420,86 @@ void release(lbm_handle* h) {
     dev_free(h, h->staging, h->staging_elems * 3 * sizeof(double));
     dev_free(h, h->partials, (kMassPartials + 1) * sizeof(double));
     dev_free(h, h->tiles, h->tiles_cap);
-    dev_free(h, h->tmaps, 2 * h->lat.size() * sizeof(CUtensorMap));
     dev_free(h, h->status, h->lat.size() * sizeof(uint32_t));
     dev_free(h, h->lat_dev, h->lat.size() * sizeof(LatDev));
     dev_free(h, h->psi, h->psi_bytes);
     dev_free(h, h->pop, h->pop_bytes);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+// Host proof of one tile's copy plan (see lbm_copy_plan.h).
+template <int ES, int TX, int TY, bool P>
+std::string check_plan_t(const LatDev& L, int par, int x0, int y0, int64_t lo, int64_t hi,
+                         int64_t plo, int64_t phi) {
+    using G = TileGeo<ES, TX, TY, P>;
+    char buf[256];
+    // bytes of the stage written by some copy
+    std::vector<char> cov(G::STAGEB, 0);
+    int64_t total = 0;
+    for (int q = 0; q < G::NCOPY; ++q) {
+        CopyOp op;
+        if (!plan_copy<ES, TX, TY, P>(L, par, x0, y0, q, op)) continue;
+        const int64_t a = op.psi ? plo : lo, b = op.psi ? phi : hi;
+        if (op.src % 16 || op.dst % 16 || op.bytes % 16 || op.bytes <= 0 || op.src < a ||
+            op.src + op.bytes > b || op.dst < 0 || op.dst + op.bytes > G::STAGEB) {
+            std::snprintf(buf, sizeof buf,
+                          "bad copy: es=%d tile=%dx%d psi=%d lattice %dx%d x0=%d y0=%d q=%d src=%lld "
+                          "dst=%d bytes=%d range=[%lld,%lld)",
+                          ES, TX, TY, (int)P, L.nx, L.ny, x0, y0, q, (long long)op.src, op.dst,
+                          op.bytes, (long long)a, (long long)b);
+            return buf;
+        }
+        // a population copy must stay inside its own box
+        if (!op.psi) {
+            const int box = op.dst / G::BOXB;
+            if (op.dst + op.bytes > box * G::BOXB + TY * G::BW * ES) return "copy crosses its box";
+        }
+        for (int k = 0; k < op.bytes; ++k) cov[op.dst + k] = 1;
+        total += op.bytes;
+    }
+    if (total >= (1 << 20)) return "transaction count too large";
+    // every value an active site reads is covered
+    for (int ty = 0; ty < TY; ++ty)
+        for (int tx = 0; tx < TX; ++tx) {
+            const int x = x0 + tx, y = y0 + ty;
+            if (x >= L.nx || y >= L.ny) continue;
+            for (int i = 0; i < 9; ++i) {
+                const int off = i * G::BOXB + (ty * G::BW + tx + G::H - plane_cx(i)) * ES;
+                for (int k = 0; k < ES; ++k)
+                    if (!cov[off + k]) {
+                        std::snprintf(buf, sizeof buf, "uncovered read: plane %d site (%d,%d)", i, x, y);
+                        return buf;
+                    }
+            }
+            if (P)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int off = 9 * G::BOXB + ((ty + 1 + dy) * G::PW + tx + 4 + dx) * 4;
+                        for (int k = 0; k < 4; ++k)
+                            if (!cov[off + k]) return "uncovered psi read";
+                    }
+        }
+    return "";
+}
+
+template <int ES, bool P>
+std::string check_shape(int tx, int ty, const LatDev& L, int par, int x0, int y0, int64_t lo,
+                        int64_t hi, int64_t plo, int64_t phi) {
+    if (tx == 64 && ty == 8) return check_plan_t<ES, 64, 8, P>(L, par, x0, y0, lo, hi, plo, phi);
+    if (tx == 64 && ty == 16) return check_plan_t<ES, 64, 16, P>(L, par, x0, y0, lo, hi, plo, phi);
+    if (tx == 128 && ty == 4) return check_plan_t<ES, 128, 4, P>(L, par, x0, y0, lo, hi, plo, phi);
+    if (tx == 128 && ty == 8) return check_plan_t<ES, 128, 8, P>(L, par, x0, y0, lo, hi, plo, phi);
+    if (tx == 32 && ty == 16) return check_plan_t<ES, 32, 16, P>(L, par, x0, y0, lo, hi, plo, phi);
+    return "unknown tile shape";
+}
+
+std::string check_tile_plan(int f16, int tx, int ty, bool with_psi, const LatDev& L, int par,
+                            int x0, int y0, int64_t lo, int64_t hi, int64_t plo, int64_t phi) {
+    if (f16)
+        return with_psi ? check_shape<2, true>(tx, ty, L, par, x0, y0, lo, hi, plo, phi)
+                        : check_shape<2, false>(tx, ty, L, par, x0, y0, lo, hi, plo, phi);
+    return with_psi ? check_shape<4, true>(tx, ty, L, par, x0, y0, lo, hi, plo, phi)
+                    : check_shape<4, false>(tx, ty, L, par, x0, y0, lo, hi, plo, phi);
 }
 
 }  // namespace
@@ -542,8 +613,7 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
     h->lat_dev = (LatDev*)dev_alloc(h, n * sizeof(LatDev));
     h->status = (uint32_t*)dev_alloc(h, n * sizeof(uint32_t));
     h->partials = (double*)dev_alloc(h, (kMassPartials + 1) * sizeof(double));
-    h->tmaps = (CUtensorMap*)dev_alloc(h, 2 * n * sizeof(CUtensorMap));
-    if (!h->pop || !h->psi || !h->lat_dev || !h->status || !h->partials || !h->tmaps)
+    if (!h->pop || !h->psi || !h->lat_dev || !h->status || !h->partials)
         return fail(LBM_ERR_OOM);
     if (cudaMallocHost(&h->status_host, n * sizeof(uint32_t)) != cudaSuccess)
         return fail(LBM_ERR_OOM);
@@ -620,7 +690,10 @@ int lbm_init(lbm_handle* h, int32_t lattice, const double* rho, const double* ux
                       h->stream));
     h->launches += 1;
     CK(h, cudaMemsetAsync(h->status + lattice, 0, sizeof(uint32_t), h->stream));
-    if (h->numeric_lattice == lattice) h->numeric_lattice = -1;
+    if (h->numeric_lattice == lattice) {
+        h->numeric_lattice = -1;
+        h->fault_bits = 0;
+    }
     return LBM_OK;
 }
 
@@ -836,6 +909,52 @@ int lbm_autotune(lbm_handle* h, int32_t repeats) {
               (int64_t)std::log2((double)h->lat.size())};
     g_tune_cache[k] = TuneVal{btx, bty, bgrid, bgrid_psi};
     return LBM_OK;
+}
+
+int lbm_selfcheck(char* report, int32_t report_len) {
+    std::string msg;
+    const int shapes[][2] = {{2, 2},   {3, 5},   {4, 4},    {7, 5},   {31, 33}, {32, 32},
+                             {64, 3},  {65, 9},  {100, 37}, {127, 129}, {128, 8}, {200, 120},
+                             {257, 63}, {512, 17}, {1000, 3}};
+    const int tiles[][2] = {{64, 8}, {64, 16}, {128, 4}, {128, 8}, {32, 16}};
+    int64_t checked = 0;
+    for (int f16 = 0; f16 < 2 && msg.empty(); ++f16) {
+        for (const auto& tt : tiles) {
+            for (int wp = 0; wp < 2 && msg.empty(); ++wp) {
+                // lay out all shapes in one arena, as a batch handle would
+                int64_t pc = 0, qc = 0;
+                std::vector<LatDev> lats;
+                int idx = 0;
+                for (const auto& sh : shapes) {
+                    lbm_lattice_desc d;
+                    lbm_desc_default(&d, sh[0], sh[1]);
+                    d.storage = f16 ? LBM_STORE_F16_DEV : LBM_STORE_F32_DEV;
+                    lats.push_back(make_lat(d, idx++, pc, qc));
+                }
+                const int es = f16 ? 2 : 4;
+                for (const LatDev& L : lats) {
+                    const int64_t lo = L.off_f[0] * es, hi = (L.off_f[1] + 9 * L.plane) * es;
+                    const int64_t plo = L.off_psi * 4,
+                                  phi = (L.off_psi + (int64_t)L.pitch_psi * (L.ny + 2 * GY)) * 4;
+                    for (int y0 = 0; y0 < L.ny; y0 += tt[1])
+                        for (int x0 = 0; x0 < L.nx; x0 += tt[0])
+                            for (int par = 0; par < 2; ++par) {
+                                std::string e = check_tile_plan(f16, tt[0], tt[1], wp != 0, L, par,
+                                                                x0, y0, lo, hi, plo, phi);
+                                ++checked;
+                                if (!e.empty()) {
+                                    msg = e;
+                                    goto done;
+                                }
+                            }
+                }
+            }
+        }
+    }
+done:
+    if (msg.empty()) msg = "ok: " + std::to_string(checked) + " tile plans checked";
+    if (report && report_len > 0) std::snprintf(report, (size_t)report_len, "%s", msg.c_str());
+    return msg.rfind("ok:", 0) == 0 ? LBM_OK : LBM_ERR_STATE;
 }
 
 }  // extern "C"

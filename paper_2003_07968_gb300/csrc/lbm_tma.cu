@@ -1,23 +1,20 @@
 // lbm_tma.cu -- TMA-pipelined versions of the two passes of the step.
 //
-// Each CTA walks its share of the global tile list.  For every tile one
-// elected thread issues nine tiled bulk-tensor copies (cp.async.bulk.tensor,
-// one box per population plane, already shifted by -c_i so that the box row
-// holding site y carries f*_i(x - c_i)), plus the psi tile with its one-site
-// halo for the collision pass.  Copies complete on an mbarrier per stage;
-// three stages keep two tiles in flight while the third is computed, so the
-// bytes in flight cost no registers.  Outputs leave through plain coalesced
-// stores (the periodic images of edge sites go to the ghost frame at the
-// same time).  Box x-coordinates are the tile origin x0, a multiple of 32,
-// and boxes are (TX + 2H) wide with H = 16 bytes of halo, so every copy
-// starts on a 16-byte boundary; rows and columns past the allocation read
-// as zero and only feed inactive lanes.
+// Each CTA walks its share of the global tile list.  For every tile the
+// first warp issues bulk asynchronous copies (cp.async.bulk, executed by the
+// TMA unit) of whole row segments into shared memory: for each population
+// plane the TY rows the tile pulls from (already shifted by -c_iy, with 16
+// bytes of halo columns on each side), plus the psi rows of the tile and its
+// one-site halo for the collision pass (lbm_copy_plan.h).  The copies
+// complete on an mbarrier per stage; three stages keep two tiles in flight
+// while the third is computed, so the bytes in flight cost no registers.
+// Outputs leave through plain coalesced stores (the periodic images of edge
+// sites go to the ghost frame at the same time).
 //
 // Every mbarrier wait is bounded by a clock budget: on expiry the CTA sets
 // bit 1 of the lattice status word, waits (again bounded) for the copies it
 // still has in flight, and returns.
-#include <cudaTypedefs.h>
-
+#include "lbm_copy_plan.h"
 #include "lbm_kernels.h"
 
 namespace pplbm {
@@ -26,8 +23,6 @@ namespace {
 constexpr int kStages = 3;
 constexpr int kThreads = 256;
 constexpr long long kWaitBudgetCycles = 4000000000LL;  // about 2 s at 2 GHz
-
-__host__ __device__ constexpr int align128(int v) { return (v + 127) / 128 * 128; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -65,60 +60,60 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     }
     return false;
 }
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int c0, int c1, int c2) {
+// Bulk copy global -> shared completing on *bar (both addresses 16-byte
+// aligned, size a multiple of 16: guaranteed by the copy plan).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int c0, int c1) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
 
 template <class S, int TX, int TY, bool WITH_PSI>
-struct Geo {
-    using T = typename S::T;
-    static constexpr int H = S::kGx;                      // halo columns per side in a box
-    static constexpr int BW = TX + 2 * H;                 // population box width
-    static constexpr int BOXB = align128(TY * BW * (int)sizeof(T));
-    static constexpr int BOXE = BOXB / (int)sizeof(T);   // box stride in elements
-    static constexpr int PW = TX + 8;                     // psi box width (4 floats each side)
-    static constexpr int PSIB = WITH_PSI ? align128((TY + 2) * PW * 4) : 0;
-    static constexpr int STAGEB = 9 * BOXB + PSIB;
-    static constexpr int SMEM = kStages * STAGEB + 64;   // + mbarriers
-    static constexpr uint32_t TXB = 9u * TY * BW * sizeof(T) + (WITH_PSI ? (TY + 2) * PW * 4 : 0);
-    static constexpr int RP = kThreads / TX;              // rows per pass of the block
+struct Geo : TileGeo<(int)sizeof(typename S::T), TX, TY, WITH_PSI> {
+    using B = TileGeo<(int)sizeof(typename S::T), TX, TY, WITH_PSI>;
+    static constexpr int SMEM = kStages * B::STAGEB + 64;  // + mbarriers
+    static constexpr int RP = kThreads / TX;               // rows per pass of the block
     static_assert(TY % RP == 0, "tile height must be a multiple of the block's rows");
-    static_assert(BW <= 256 && TY + 2 <= 256, "TMA box too large");
 };
 
-// Issue the copies of tile `t` into `stage` (called by one thread).
+// Issue the copies of tile `t` into `stage`; called by all 32 lanes of warp 0.
 template <class S, int TX, int TY, bool WITH_PSI>
 __device__ __forceinline__ void issue_tile(const StepArgs& a, int t, unsigned char* stage,
                                            uint64_t* bar) {
     using G = Geo<S, TX, TY, WITH_PSI>;
+    constexpr int ES = (int)sizeof(typename S::T);
+    constexpr int PER = (G::NCOPY + 31) / 32;
+    const int lane = threadIdx.x & 31;
     const int4 tl = __ldg(&a.tiles[t]);
-    const CUtensorMap* pm = a.pop_maps + tl.x;
-    mbar_expect_tx(bar, G::TXB);
-    const int x0 = tl.y, y0 = tl.z + GY, p9 = 9 * a.parity;
-    // box column 0 is lattice x0 - H (ghost offset gx == H), box row 0 is y0 - c_iy
-    tma_load_3d(stage + 0 * G::BOXB, pm, bar, x0, y0, p9 + 0);
-    tma_load_3d(stage + 1 * G::BOXB, pm, bar, x0, y0, p9 + 1);
-    tma_load_3d(stage + 2 * G::BOXB, pm, bar, x0, y0 - 1, p9 + 2);
-    tma_load_3d(stage + 3 * G::BOXB, pm, bar, x0, y0, p9 + 3);
-    tma_load_3d(stage + 4 * G::BOXB, pm, bar, x0, y0 + 1, p9 + 4);
-    tma_load_3d(stage + 5 * G::BOXB, pm, bar, x0, y0 - 1, p9 + 5);
-    tma_load_3d(stage + 6 * G::BOXB, pm, bar, x0, y0 - 1, p9 + 6);
-    tma_load_3d(stage + 7 * G::BOXB, pm, bar, x0, y0 + 1, p9 + 7);
-    tma_load_3d(stage + 8 * G::BOXB, pm, bar, x0, y0 + 1, p9 + 8);
-    if (WITH_PSI) tma_load_2d(stage + 9 * G::BOXB, a.psi_maps + tl.x, bar, x0, y0 - 1);
+    const LatDev& L = a.lats[tl.x];
+    CopyOp op[PER];
+    bool on[PER];
+    uint32_t bytes = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int q = lane + 32 * k;
+        on[k] = q < G::NCOPY && plan_copy<ES, TX, TY, WITH_PSI>(L, a.parity, tl.y, tl.z, q, op[k]);
+        // the plan is proven on the host (lbm_selfcheck); a copy that still broke
+        // the bulk-copy rules would be skipped and flagged, never issued
+        if (on[k] && ((op[k].src | op[k].dst | op[k].bytes) & 15)) {
+            atomicOr(&a.status[tl.x], 4u);
+            on[k] = false;
+        }
+        if (on[k]) bytes += (uint32_t)op[k].bytes;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+    if (lane == 0) mbar_expect_tx(bar, bytes);
+    __syncwarp();
+    const char* pop = reinterpret_cast<const char*>(a.pop);
+    const char* psi = reinterpret_cast<const char*>(a.psi);
+#pragma unroll
+    for (int k = 0; k < PER; ++k)
+        if (on[k])
+            bulk_g2s(stage + op[k].dst, (op[k].psi ? psi : pop) + op[k].src, (uint32_t)op[k].bytes,
+                     bar);
 }
 
 // Shared pipeline driver: calls body(tile, stage) for each tile of this CTA.
@@ -131,6 +126,9 @@ __device__ __forceinline__ void run_pipeline(const StepArgs& a, Body&& body) {
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
         mbar_fence_init();
+    }
+    __syncwarp();
+    if (tid < 32) {
         for (int s = 0; s < kStages; ++s) {
             const int t = blockIdx.x + s * gridDim.x;
             if (t < a.ntiles) issue_tile<S, TX, TY, WITH_PSI>(a, t, smem + s * G::STAGEB, &bars[s]);
@@ -157,11 +155,13 @@ __device__ __forceinline__ void run_pipeline(const StepArgs& a, Body&& body) {
         }
         body(t, smem + s * G::STAGEB);
         __syncthreads();  // every thread is done reading this stage
-        if (tid == 0) {
-            // order the generic-proxy reads of this stage before the async-proxy refill
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (tid < 32) {
             const int tn = t + kStages * gridDim.x;
-            if (tn < a.ntiles) issue_tile<S, TX, TY, WITH_PSI>(a, tn, smem + s * G::STAGEB, &bars[s]);
+            if (tn < a.ntiles) {
+                // order the generic-proxy reads of this stage before the async-proxy refill
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue_tile<S, TX, TY, WITH_PSI>(a, tn, smem + s * G::STAGEB, &bars[s]);
+            }
         }
     }
 }
@@ -359,43 +359,6 @@ int occupancy_collide_tma(int f16, int tx, int ty) {
     cudaError_t e = f16 ? collide_any<StoreF16>(tx, ty, a, 0, nullptr, true, &occ)
                         : collide_any<StoreF32>(tx, ty, a, 0, nullptr, true, &occ);
     return (e == cudaSuccess && occ > 0) ? occ : 1;
-}
-
-// Tensor maps of one lattice: populations as a 3-D tensor [18 planes][rows][pitch]
-// (buffers A and B are adjacent with one plane stride), psi as [rows][pitch_psi].
-int encode_tensor_maps(int f16, int tx, int ty, const LatDev& L, void* pop, float* psi,
-                       CUtensorMap* pop_map, CUtensorMap* psi_map) {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
-        cudaDriverEntryPointQueryResult q;
-        void* fn = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
-                                             cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn)
-            return -1;
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
-    const int es = f16 ? 2 : 4;
-    const int H = 16 / es;
-    const int rows = L.ny + 2 * GY;
-    char* base = reinterpret_cast<char*>(pop) + L.off_f[0] * es;
-    cuuint64_t gdim[3] = {(cuuint64_t)L.pitch, (cuuint64_t)rows, 18};
-    cuuint64_t gstr[2] = {(cuuint64_t)L.pitch * es, (cuuint64_t)L.plane * es};
-    cuuint32_t box[3] = {(cuuint32_t)(tx + 2 * H), (cuuint32_t)ty, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = encode(pop_map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                        3, base, gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return -2;
-    cuuint64_t pdim[2] = {(cuuint64_t)L.pitch_psi, (cuuint64_t)rows};
-    cuuint64_t pstr[1] = {(cuuint64_t)L.pitch_psi * 4};
-    cuuint32_t pbox[2] = {(cuuint32_t)(tx + 8), (cuuint32_t)(ty + 2)};
-    cuuint32_t pes[2] = {1, 1};
-    r = encode(psi_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, psi + L.off_psi, pdim, pstr, pbox,
-               pes, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? 0 : -3;
 }
 
 }  // namespace pplbm

@@ -85,3 +85,14 @@ def test_product_package_does_not_import_the_oracle():
                 txt = open(os.path.join(dp, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "pplbm_oracle" not in txt, f
+
+
+def test_staging_copy_plans_are_proven_on_the_host():
+    # every bulk copy the TMA passes issue is 16-byte aligned on both sides,
+    # a multiple of 16 bytes long, inside its allocation and box, and the
+    # copies cover every value an active site reads (no GPU involved)
+    from paper_2003_07968_gb300 import capi
+
+    rc, report = capi.lbm_selfcheck()
+    assert rc == 0, report
+    assert report.startswith("ok:")
