@@ -264,4 +264,84 @@ __device__ __forceinline__ float bgk_guo(float g, float drho, float rho, float u
     return g + omega * (feq - g) + src;
 }
 
+// Per-lattice constants of one site update, held in registers for a tile.
+struct SiteConsts {
+    float omega, guo, rho0, k_sc, k1, k2;
+    int m2v;
+};
+__device__ __forceinline__ SiteConsts site_consts(const LatDev& L) {
+    return SiteConsts{L.omega, L.guo, L.rho0, L.k_sc, L.k1, L.k2, L.m2_variant};
+}
+
+// One site of the collision pass: pulled (deviation) populations g[0..8]
+// and psi at x + c_i (p[0] = psi(x), then E, N, W, S, NE, NW, SW, SE) in,
+// post-collision deviations o[0..8] out.
+//   rho, j     Eqs. (FD), (FMD)
+//   F          Eq. (IFT) via site_force
+//   f*_i       Eqs. (BGKCO), (SEDF), (GFS), (GFSBGK), with opposite
+//              directions sharing their terms: for c and -c,
+//              f^eq = w (base + rho cu (3 +- 9/2 cu)) with base = drho - 3/2 rho u^2,
+//              S    = gu w (9 cF cu +- 3 cF - 3 F.u);
+// the rest population f*_0 takes what mass conservation leaves (in exact
+// arithmetic the same number; it keeps the FP32 weights, whose sum is not
+// exactly 1, from adding a biased mass error every step).
+__device__ __forceinline__ void collide_site(const SiteConsts& C, const float g[9],
+                                             const float p[9], float o[9]) {
+    const float drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    const float rho = drho + C.rho0;
+    const float jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+    const float jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+    LatDev dummy;  // site_force reads only the force coefficients and the trace flag
+    dummy.k_sc = C.k_sc;
+    dummy.k1 = C.k1;
+    dummy.k2 = C.k2;
+    dummy.m2_variant = C.m2v;
+    const Force F = site_force(dummy, p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], p[8]);
+    const float inv = __frcp_rn(rho);
+    const float ux = fmaf(0.5f, F.x, jx) * inv;  // Eq. (FMD)
+    const float uy = fmaf(0.5f, F.y, jy) * inv;
+    const float usq = ux * ux + uy * uy;
+    const float f3u = 3.f * (F.x * ux + F.y * uy);
+    const float base = drho - 1.5f * rho * usq;
+    const float om = C.omega;
+    const float ga = C.guo * (1.f / 9.f), gd = C.guo * (1.f / 36.f);
+    float s1 = 0.f;
+    // one pair of opposite directions (I, J = opposite of I), weight w, guo weight gw
+#define PPLBM_PAIR(I, J, W, GW, CU, CF)                                             \
+    {                                                                               \
+        const float cu = (CU), cF = (CF);                                           \
+        const float t = rho * cu;                                                   \
+        const float a = 4.5f * t * cu, b = 3.f * t;                                 \
+        const float s2 = 9.f * cF * cu - f3u, s3 = 3.f * cF;                        \
+        const float fi = (W) * (base + a + b), fj = (W) * (base + a - b);          \
+        const float oi = fmaf(om, fi - g[I], g[I]) + (GW) * (s2 + s3);              \
+        const float oj = fmaf(om, fj - g[J], g[J]) + (GW) * (s2 - s3);              \
+        o[I] = oi;                                                                  \
+        o[J] = oj;                                                                  \
+        s1 += oi + oj;                                                              \
+    }
+    PPLBM_PAIR(1, 3, 1.f / 9.f, ga, ux, F.x)
+    PPLBM_PAIR(2, 4, 1.f / 9.f, ga, uy, F.y)
+    PPLBM_PAIR(5, 7, 1.f / 36.f, gd, ux + uy, F.x + F.y)
+    PPLBM_PAIR(6, 8, 1.f / 36.f, gd, uy - ux, F.y - F.x)
+#undef PPLBM_PAIR
+    o[0] = drho - s1;
+}
+
+// Store the nine outputs of site (x, y): interior sites with plain stores,
+// sites within GW of an edge also into their periodic images.
+template <class S>
+__device__ __forceinline__ void store_site(typename S::T* o, int64_t plane, int pitch, int gx,
+                                           int x, int y, int nx, int ny, const float v[9]) {
+    const bool interior = (x >= GW) & (x < nx - GW) & (y >= GW) & (y < ny - GW);
+    if (interior) {
+        typename S::T* q = o + (int64_t)(y + GY) * pitch + (x + gx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) q[i * plane] = S::cv(v[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) store_img(o + i * plane, pitch, gx, x, y, nx, ny, S::cv(v[i]));
+    }
+}
+
 }  // namespace pplbm

@@ -82,51 +82,31 @@ __global__ void __launch_bounds__(512) k_collide(StepArgs a) {
         if (x >= nx || y >= ny) continue;
         const int pitch = L.pitch;
         const int64_t plane = L.plane;
-        const int64_t site = (int64_t)(y + GY) * pitch + (x + L.gx);
-        const T* f = reinterpret_cast<const T*>(a.pop) + L.off_f[a.parity] + site;
-        const float g0 = S::ld(f);
-        const float g1 = S::ld(f + 1 * plane - 1);
-        const float g2 = S::ld(f + 2 * plane - pitch);
-        const float g3 = S::ld(f + 3 * plane + 1);
-        const float g4 = S::ld(f + 4 * plane + pitch);
-        const float g5 = S::ld(f + 5 * plane - pitch - 1);
-        const float g6 = S::ld(f + 6 * plane - pitch + 1);
-        const float g7 = S::ld(f + 7 * plane + pitch + 1);
-        const float g8 = S::ld(f + 8 * plane + pitch - 1);
-        const float drho = ((g0 + g1) + (g2 + g3)) + ((g4 + g5) + (g6 + g7)) + g8;
-        const float rho = drho + L.rho0;
-        const float jx = (g1 - g3) + (g5 - g6) + (g8 - g7);
-        const float jy = (g2 - g4) + (g5 + g6) - (g7 + g8);
+        const T* f = reinterpret_cast<const T*>(a.pop) + L.off_f[a.parity] +
+                     (int64_t)(y + GY) * pitch + (x + L.gx);
+        float g[9], p[9], v[9];
+        g[0] = S::ld(f);
+        g[1] = S::ld(f + 1 * plane - 1);
+        g[2] = S::ld(f + 2 * plane - pitch);
+        g[3] = S::ld(f + 3 * plane + 1);
+        g[4] = S::ld(f + 4 * plane + pitch);
+        g[5] = S::ld(f + 5 * plane - pitch - 1);
+        g[6] = S::ld(f + 6 * plane - pitch + 1);
+        g[7] = S::ld(f + 7 * plane + pitch + 1);
+        g[8] = S::ld(f + 8 * plane + pitch - 1);
         const float* c = sps + (threadIdx.y + 1) * W + (threadIdx.x + 1);
-        const Force F = site_force(L, c[0], c[1], c[W], c[-1], c[-W], c[W + 1], c[W - 1],
-                                   c[-W - 1], c[-W + 1]);
-        const float inv = 1.f / rho;
-        const float ux = (jx + 0.5f * F.x) * inv;  // Eq. (FMD)
-        const float uy = (jy + 0.5f * F.y) * inv;
-        const float usq = ux * ux + uy * uy;
-        const float Fu = F.x * ux + F.y * uy;
-        const float om = L.omega, gu = L.guo;
-        T* o = reinterpret_cast<T*>(a.pop) + L.off_f[a.parity ^ 1];
-        const int gx = L.gx;
-// Directions 1..8 follow Eqs. (BGKCO), (SEDF), (GFS) directly.  The rest
-// population takes what mass conservation leaves: in exact arithmetic
-// sum_i f*_i = sum_i f_i, so f*_0 = sum_i f_i - sum_{i>0} f*_i is the same
-// number, but it keeps the FP32 weights (whose sum is not exactly 1) from
-// adding a biased mass error every step.
-#define PPLBM_OUT(I, G)                                                                   \
-    const float o##I = bgk_guo<I>(G, drho, rho, ux, uy, usq, F.x, F.y, Fu, om, gu);       \
-    store_img(o + I * plane, pitch, gx, x, y, nx, ny, S::cv(o##I))
-        PPLBM_OUT(1, g1);
-        PPLBM_OUT(2, g2);
-        PPLBM_OUT(3, g3);
-        PPLBM_OUT(4, g4);
-        PPLBM_OUT(5, g5);
-        PPLBM_OUT(6, g6);
-        PPLBM_OUT(7, g7);
-        PPLBM_OUT(8, g8);
-        const float o0 = drho - (((o1 + o2) + (o3 + o4)) + ((o5 + o6) + (o7 + o8)));
-        store_img(o, pitch, gx, x, y, nx, ny, S::cv(o0));
-#undef PPLBM_OUT
+        p[0] = c[0];
+        p[1] = c[1];
+        p[2] = c[W];
+        p[3] = c[-1];
+        p[4] = c[-W];
+        p[5] = c[W + 1];
+        p[6] = c[W - 1];
+        p[7] = c[-W - 1];
+        p[8] = c[-W + 1];
+        collide_site(site_consts(L), g, p, v);
+        store_site<S>(reinterpret_cast<T*>(a.pop) + L.off_f[a.parity ^ 1], plane, pitch, L.gx, x,
+                      y, nx, ny, v);
     }
 }
 

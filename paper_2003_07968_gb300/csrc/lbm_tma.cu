@@ -5,9 +5,13 @@
 // TMA unit) of whole row segments into shared memory: for each population
 // plane the TY rows the tile pulls from (already shifted by -c_iy, with 16
 // bytes of halo columns on each side), plus the psi rows of the tile and its
-// one-site halo for the collision pass (lbm_copy_plan.h).  The copies
-// complete on an mbarrier per stage; three stages keep two tiles in flight
-// while the third is computed, so the bytes in flight cost no registers.
+// one-site halo for the collision pass (lbm_copy_plan.h).  The warps are
+// specialised: one producer warp only issues copies, eight consumer warps
+// only compute.  Each stage has a "full" mbarrier (completed by the copies'
+// byte count) and an "empty" mbarrier (one arrival per consumer warp once it
+// has read the stage), so no CTA-wide barrier sits in the loop and the
+// producer runs up to kStages tiles ahead; the bytes in flight cost no
+// registers.
 // Outputs leave through plain coalesced stores (the periodic images of edge
 // sites go to the ghost frame at the same time).
 //
@@ -20,8 +24,9 @@
 namespace pplbm {
 namespace {
 
-constexpr int kStages = 3;
-constexpr int kThreads = 256;
+constexpr int kStages = 4;
+constexpr int kThreads = 256;              // consumer threads (eight warps)
+constexpr int kBlock = kThreads + 32;      // plus one producer warp
 constexpr long long kWaitBudgetCycles = 4000000000LL;  // about 2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -38,6 +43,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(bytes)
                  : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
@@ -73,7 +81,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 template <class S, int TX, int TY, bool WITH_PSI>
 struct Geo : TileGeo<(int)sizeof(typename S::T), TX, TY, WITH_PSI> {
     using B = TileGeo<(int)sizeof(typename S::T), TX, TY, WITH_PSI>;
-    static constexpr int SMEM = kStages * B::STAGEB + 64;  // + mbarriers
+    static constexpr int SMEM = kStages * B::STAGEB + 2 * kStages * 8 + 16;  // + mbarriers, flag
     static constexpr int RP = kThreads / TX;               // rows per pass of the block
     static_assert(TY % RP == 0, "tile height must be a multiple of the block's rows");
 };
@@ -116,53 +124,68 @@ __device__ __forceinline__ void issue_tile(const StepArgs& a, int t, unsigned ch
                      bar);
 }
 
-// Shared pipeline driver: calls body(tile, stage) for each tile of this CTA.
+// Warp-specialised pipeline: the producer warp (the last one) fills stages,
+// the consumer warps call body(tile, stage) for each tile of this CTA.
+// Waits are bounded; a consumer that gives up raises the CTA's abort flag,
+// the producer then stops issuing and, before it exits, waits (bounded) for
+// every copy it has issued, so no copy lands after the CTA is gone.
 template <class S, int TX, int TY, bool WITH_PSI, class Body>
 __device__ __forceinline__ void run_pipeline(const StepArgs& a, Body&& body) {
     using G = Geo<S, TX, TY, WITH_PSI>;
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * G::STAGEB);
-    const int tid = threadIdx.y * TX + threadIdx.x;
-    if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * G::STAGEB);
+    uint64_t* empty = full + kStages;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kStages);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kConsumerWarps = kThreads / 32;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumerWarps);
+        }
+        *abort_flag = 0;
         mbar_fence_init();
     }
-    __syncwarp();
-    if (tid < 32) {
-        for (int s = 0; s < kStages; ++s) {
-            const int t = blockIdx.x + s * gridDim.x;
-            if (t < a.ntiles) issue_tile<S, TX, TY, WITH_PSI>(a, t, smem + s * G::STAGEB, &bars[s]);
-        }
-    }
     __syncthreads();
+    if (warp == kConsumerWarps) {
+        // ---------------- producer
+        int k = 0;
+        for (;; ++k) {
+            const int t = blockIdx.x + k * gridDim.x;
+            if (t >= a.ntiles || *abort_flag) break;
+            const int s = k % kStages;
+            if (k >= kStages) {
+                const bool ok = mbar_wait_bounded(&empty[s], (uint32_t)(k / kStages - 1) & 1u);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    if (lane == 0) atomicOr(&a.status[__ldg(&a.tiles[t]).x], 2u);
+                    break;
+                }
+                // order the consumers' generic-proxy reads before the async refill
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            }
+            issue_tile<S, TX, TY, WITH_PSI>(a, t, smem + s * G::STAGEB, &full[s]);
+        }
+        // drain: the last issue into each stage must have landed before exit
+        for (int j = (k > kStages ? k - kStages : 0); j < k; ++j)
+            mbar_wait_bounded(&full[j % kStages], (uint32_t)(j / kStages) & 1u);
+        return;
+    }
+    // ---------------- consumers
     for (int k = 0;; ++k) {
         const int t = blockIdx.x + k * gridDim.x;
         if (t >= a.ntiles) break;
         const int s = k % kStages;
-        const uint32_t par = (uint32_t)(k / kStages) & 1u;
-        const bool ok = mbar_wait_bounded(&bars[s], par);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                // drain the copies still in flight (this tile's and later ones), then flag
-                for (int j = 0; j < kStages; ++j) {
-                    const int tj = blockIdx.x + (k + j) * gridDim.x;
-                    if (tj < a.ntiles)
-                        mbar_wait_bounded(&bars[(k + j) % kStages], (uint32_t)((k + j) / kStages) & 1u);
-                }
+        const bool ok = mbar_wait_bounded(&full[s], (uint32_t)(k / kStages) & 1u);
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) {
+                *abort_flag = 1;
                 atomicOr(&a.status[__ldg(&a.tiles[t]).x], 2u);
             }
             return;
         }
         body(t, smem + s * G::STAGEB);
-        __syncthreads();  // every thread is done reading this stage
-        if (tid < 32) {
-            const int tn = t + kStages * gridDim.x;
-            if (tn < a.ntiles) {
-                // order the generic-proxy reads of this stage before the async-proxy refill
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue_tile<S, TX, TY, WITH_PSI>(a, tn, smem + s * G::STAGEB, &bars[s]);
-            }
-        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
     }
 }
 
@@ -170,33 +193,30 @@ __device__ __forceinline__ void run_pipeline(const StepArgs& a, Body&& body) {
 
 // ---------------------------------------------------------------- pass 1: psi
 template <class S, int EOSP, int TX, int TY>
-__global__ void __launch_bounds__(kThreads, 2) k_psi_tma(StepArgs a) {
+__global__ void __launch_bounds__(kBlock, 2) k_psi_tma(StepArgs a) {
     using G = Geo<S, TX, TY, false>;
     using T = typename S::T;
+    const int tx = threadIdx.x % TX, ty0 = threadIdx.x / TX;
     run_pipeline<S, TX, TY, false>(a, [&](int t, unsigned char* stage) {
         const int4 tl = __ldg(&a.tiles[t]);
         const LatDev& L = a.lats[tl.x];
         const int nx = L.nx, ny = L.ny;
+        const float rho0 = L.rho0;
         const T* P = reinterpret_cast<const T*>(stage);
-        const int x = tl.y + threadIdx.x;
+        const int x = tl.y + tx;
         if (x >= nx) return;
 #pragma unroll
-        for (int ty = threadIdx.y; ty < TY; ty += G::RP) {
+        for (int ty = ty0; ty < TY; ty += G::RP) {
             const int y = tl.z + ty;
             if (y >= ny) break;
-            const T* b = P + ty * G::BW + threadIdx.x + G::H;
-            float d = S::lds(b);
-            d += S::lds(b + 1 * G::BOXE - 1);
-            d += S::lds(b + 2 * G::BOXE);
-            d += S::lds(b + 3 * G::BOXE + 1);
-            d += S::lds(b + 4 * G::BOXE);
-            d += S::lds(b + 5 * G::BOXE - 1);
-            d += S::lds(b + 6 * G::BOXE + 1);
-            d += S::lds(b + 7 * G::BOXE + 1);
-            d += S::lds(b + 8 * G::BOXE - 1);
-            const float rho = d + L.rho0;
+            const T* b = P + ty * G::BW + tx + G::H;
+            const float d = ((S::lds(b) + S::lds(b + 1 * G::BOXE - 1)) +
+                             (S::lds(b + 2 * G::BOXE) + S::lds(b + 3 * G::BOXE + 1))) +
+                            ((S::lds(b + 4 * G::BOXE) + S::lds(b + 5 * G::BOXE - 1)) +
+                             (S::lds(b + 6 * G::BOXE + 1) + S::lds(b + 7 * G::BOXE + 1))) +
+                            S::lds(b + 8 * G::BOXE - 1);
             bool ok;
-            float psi = eval_psi<EOSP>(L, rho, ok);
+            float psi = eval_psi<EOSP>(L, d + rho0, ok);
             if (!ok) {
                 atomicOr(&a.status[L.lattice], 1u);
                 psi = __int_as_float(0x7fc00000);
@@ -208,64 +228,50 @@ __global__ void __launch_bounds__(kThreads, 2) k_psi_tma(StepArgs a) {
 
 // --------------------------------------------- pass 2: force + collide + store
 template <class S, int TX, int TY>
-__global__ void __launch_bounds__(kThreads, 2) k_collide_tma(StepArgs a) {
+__global__ void __launch_bounds__(kBlock, 2) k_collide_tma(StepArgs a) {
     using G = Geo<S, TX, TY, true>;
     using T = typename S::T;
+    const int tx = threadIdx.x % TX, ty0 = threadIdx.x / TX;
     run_pipeline<S, TX, TY, true>(a, [&](int t, unsigned char* stage) {
         const int4 tl = __ldg(&a.tiles[t]);
         const LatDev& L = a.lats[tl.x];
         const int nx = L.nx, ny = L.ny;
-        const T* P = reinterpret_cast<const T*>(stage);
-        const float* PS = reinterpret_cast<const float*>(stage + 9 * G::BOXB);
-        const int x = tl.y + threadIdx.x;
+        const int x = tl.y + tx;
         if (x >= nx) return;
+        const SiteConsts C = site_consts(L);
         const int pitch = L.pitch, gx = L.gx;
         const int64_t plane = L.plane;
         T* o = reinterpret_cast<T*>(a.pop) + L.off_f[a.parity ^ 1];
-        const float om = L.omega, gu = L.guo, rho0 = L.rho0;
+        const T* P = reinterpret_cast<const T*>(stage);
+        const float* PS = reinterpret_cast<const float*>(stage + 9 * G::BOXB);
 #pragma unroll 1
-        for (int ty = threadIdx.y; ty < TY; ty += G::RP) {
+        for (int ty = ty0; ty < TY; ty += G::RP) {
             const int y = tl.z + ty;
             if (y >= ny) break;
-            const T* b = P + ty * G::BW + threadIdx.x + G::H;
-            const float g0 = S::lds(b);
-            const float g1 = S::lds(b + 1 * G::BOXE - 1);
-            const float g2 = S::lds(b + 2 * G::BOXE);
-            const float g3 = S::lds(b + 3 * G::BOXE + 1);
-            const float g4 = S::lds(b + 4 * G::BOXE);
-            const float g5 = S::lds(b + 5 * G::BOXE - 1);
-            const float g6 = S::lds(b + 6 * G::BOXE + 1);
-            const float g7 = S::lds(b + 7 * G::BOXE + 1);
-            const float g8 = S::lds(b + 8 * G::BOXE - 1);
-            const float drho = ((g0 + g1) + (g2 + g3)) + ((g4 + g5) + (g6 + g7)) + g8;
-            const float rho = drho + rho0;
-            const float jx = (g1 - g3) + (g5 - g6) + (g8 - g7);
-            const float jy = (g2 - g4) + (g5 + g6) - (g7 + g8);
-            const float* c = PS + (ty + 1) * G::PW + threadIdx.x + 4;
+            const T* b = P + ty * G::BW + tx + G::H;
+            float g[9], p[9], v[9];
+            g[0] = S::lds(b);
+            g[1] = S::lds(b + 1 * G::BOXE - 1);
+            g[2] = S::lds(b + 2 * G::BOXE);
+            g[3] = S::lds(b + 3 * G::BOXE + 1);
+            g[4] = S::lds(b + 4 * G::BOXE);
+            g[5] = S::lds(b + 5 * G::BOXE - 1);
+            g[6] = S::lds(b + 6 * G::BOXE + 1);
+            g[7] = S::lds(b + 7 * G::BOXE + 1);
+            g[8] = S::lds(b + 8 * G::BOXE - 1);
             constexpr int W = G::PW;
-            const Force F = site_force(L, c[0], c[1], c[W], c[-1], c[-W], c[W + 1], c[W - 1],
-                                       c[-W - 1], c[-W + 1]);
-            const float inv = 1.f / rho;
-            const float ux = (jx + 0.5f * F.x) * inv;  // Eq. (FMD)
-            const float uy = (jy + 0.5f * F.y) * inv;
-            const float usq = ux * ux + uy * uy;
-            const float Fu = F.x * ux + F.y * uy;
-            // Directions 1..8 by Eqs. (BGKCO), (SEDF), (GFS); the rest population
-            // from mass conservation (see k_collide).
-#define PPLBM_OUT(I, GV)                                                                  \
-    const float o##I = bgk_guo<I>(GV, drho, rho, ux, uy, usq, F.x, F.y, Fu, om, gu);      \
-    store_img(o + I * plane, pitch, gx, x, y, nx, ny, S::cv(o##I))
-            PPLBM_OUT(1, g1);
-            PPLBM_OUT(2, g2);
-            PPLBM_OUT(3, g3);
-            PPLBM_OUT(4, g4);
-            PPLBM_OUT(5, g5);
-            PPLBM_OUT(6, g6);
-            PPLBM_OUT(7, g7);
-            PPLBM_OUT(8, g8);
-#undef PPLBM_OUT
-            const float o0 = drho - (((o1 + o2) + (o3 + o4)) + ((o5 + o6) + (o7 + o8)));
-            store_img(o, pitch, gx, x, y, nx, ny, S::cv(o0));
+            const float* c = PS + (ty + 1) * W + tx + 4;
+            p[0] = c[0];
+            p[1] = c[1];
+            p[2] = c[W];
+            p[3] = c[-1];
+            p[4] = c[-W];
+            p[5] = c[W + 1];
+            p[6] = c[W - 1];
+            p[7] = c[-W - 1];
+            p[8] = c[-W + 1];
+            collide_site(C, g, p, v);
+            store_site<S>(o, plane, pitch, gx, x, y, nx, ny, v);
         }
     });
 }
@@ -282,8 +288,8 @@ cudaError_t psi_shape(int eos, const StepArgs& a, int grid, cudaStream_t st, boo
                                     : (const void*)k_psi_tma<S, EOS_F32, TX, TY>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
     if (e != cudaSuccess) return e;
-    if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fn, kThreads, G::SMEM);
-    const dim3 b(TX, kThreads / TX);
+    if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fn, kBlock, G::SMEM);
+    const dim3 b(kBlock);
     switch (eos) {
         case EOS_F64: k_psi_tma<S, EOS_F64, TX, TY><<<grid, b, G::SMEM, st>>>(a); break;
         case EOS_DF: k_psi_tma<S, EOS_DF, TX, TY><<<grid, b, G::SMEM, st>>>(a); break;
@@ -298,8 +304,8 @@ cudaError_t collide_shape(const StepArgs& a, int grid, cudaStream_t st, bool que
     const void* fn = (const void*)k_collide_tma<S, TX, TY>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
     if (e != cudaSuccess) return e;
-    if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fn, kThreads, G::SMEM);
-    k_collide_tma<S, TX, TY><<<grid, dim3(TX, kThreads / TX), G::SMEM, st>>>(a);
+    if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fn, kBlock, G::SMEM);
+    k_collide_tma<S, TX, TY><<<grid, dim3(kBlock), G::SMEM, st>>>(a);
     return cudaGetLastError();
 }
 
