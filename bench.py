@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--workload", default="roofline", choices=["roofline", "batched"])
     ap.add_argument("--eos", default="df", choices=["f64", "df", "f32"],
                     help="arithmetic of psi/EOS: float-float (default), native FP64 or FP32")
-    ap.add_argument("--variant", default="tma", choices=["tma", "plain"])
+    ap.add_argument("--variant", default="auto", choices=["auto", "tma", "plain"])
     ap.add_argument("--storage", default="f32dev", choices=["f32", "f32dev", "f16dev"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true")
@@ -254,7 +254,7 @@ def run_gpu(args):
     rho = wl["field"]()
     d = P.lbm_desc_default(wl["nx"], wl["ny"], T=wl["T"], tau=wl["tau"], eos_precision=eos,
                            storage=storage)
-    h = P.lbm_create(d, kernel_variant={"tma": P.LBM_KERNEL_TMA,
+    h = P.lbm_create(d, kernel_variant={"auto": P.LBM_KERNEL_AUTO, "tma": P.LBM_KERNEL_TMA,
                                         "plain": P.LBM_KERNEL_PLAIN}[args.variant])
     st = h.stream
     P.lbm_init(h, 0, rho)
@@ -337,8 +337,14 @@ def run_gpu(args):
         "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl["name"], "storage": args.storage, "eos": args.eos,
-                   "schedule": "two_pass", "kernel_variant": args.variant, "tile": [info["tile_x"], info["tile_y"]],
-                   "grid_ctas": info["grid_ctas"], "sites": sites,
+                   "schedule": "two_pass", "kernel_variant": args.variant,
+                   "psi_pass": {"variant": ["auto", "plain", "tma"][info["psi_variant"]],
+                                "tile": [info["psi_tile_x"], info["psi_tile_y"]],
+                                "grid_ctas": info["psi_grid_ctas"]},
+                   "collide_pass": {"variant": ["auto", "plain", "tma"][info["collide_variant"]],
+                                    "tile": [info["tile_x"], info["tile_y"]],
+                                    "grid_ctas": info["grid_ctas"]},
+                   "sites": sites,
                    "l2": f"working set {info['device_bytes'] / 1e9:.2f} GB vs 129 MB L2: "
                          "inputs larger than L2, no flush",
                    "parallelism": f"replicas x{world}"},

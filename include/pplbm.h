@@ -69,10 +69,13 @@ extern "C" {
 #define LBM_COLL_MRT 1 /* Eq. (MRTCO), Gram-Schmidt M of Appendix A, Eq. (GFSMRT) */
 
 /* ---- kernel variant ------------------------------------------------------ */
-#define LBM_KERNEL_TMA 0   /* tiles staged by TMA bulk copies (default);
-                              tile shapes 64x8, 64x16, 128x4, 128x8, 32x16   */
+#define LBM_KERNEL_AUTO 0  /* per pass, the variant and tile measured fastest
+                              on GB300 (or found by lbm_autotune)            */
 #define LBM_KERNEL_PLAIN 1 /* one site per thread, plain global loads;
                               tile_x a multiple of 32, tile_x*tile_y <= 512  */
+#define LBM_KERNEL_TMA 2   /* tiles staged by TMA bulk copies through a
+                              warp-specialised mbarrier pipeline; tile shapes
+                              64x8, 64x16, 128x4, 128x8, 32x16               */
 
 /* ---- step schedule ------------------------------------------------------- */
 #define LBM_SCHED_TWO_PASS 0 /* psi pass, then fused force+collide+pull pass    */
@@ -192,20 +195,25 @@ int lbm_profile_read(lbm_handle* h, lbm_kernel_stat* out, int32_t max, int32_t* 
  * each contained kernel). */
 int64_t lbm_launch_count(lbm_handle* h);
 
-/* Handle facts: sites, device bytes held, tile shape, tile count, grid. */
+/* Handle facts: sites, device bytes held, and per pass (psi pass, collision
+ * pass) the kernel variant, tile shape, tile count and grid. */
 typedef struct {
     int64_t sites;
     int64_t device_bytes;
-    int32_t tile_x, tile_y, n_tiles, grid_ctas;
+    int32_t tile_x, tile_y, n_tiles, grid_ctas;                 /* collision pass */
+    int32_t psi_tile_x, psi_tile_y, psi_n_tiles, psi_grid_ctas; /* psi pass       */
+    int32_t psi_variant, collide_variant;                       /* LBM_KERNEL_*   */
     int32_t schedule;
     int32_t n_lattices;
 } lbm_info_t;
 int lbm_info(lbm_handle* h, lbm_info_t* out);
 
-/* Autotune tile shape and grid size on this handle's lattices by timing
- * candidate configurations with CUDA events (repeat trial steps that leave
- * the state unchanged).  Keeps the fastest; results are cached per device,
- * storage and size class for the life of the process.  Errors: LBM_ERR_CUDA. */
+/* Autotune each pass on this handle's lattices: kernel variant (unless the
+ * handle was created with a fixed one), tile shape and grid (persistent or
+ * one CTA per tile), timed with CUDA events over repeated trial launches
+ * that leave the state unchanged.  Keeps the fastest per pass; results are
+ * cached per device, storage, EOS arithmetic and size class for the life of
+ * the process and used by later lbm_create calls.  Errors: LBM_ERR_CUDA. */
 int lbm_autotune(lbm_handle* h, int32_t repeats);
 
 /* Host-only consistency proof of the shared-memory staging used by the

@@ -35,8 +35,9 @@ LBM_EOS_DF = 1
 LBM_EOS_F32 = 2
 LBM_COLL_BGK = 0
 LBM_COLL_MRT = 1
-LBM_KERNEL_TMA = 0
+LBM_KERNEL_AUTO = 0
 LBM_KERNEL_PLAIN = 1
+LBM_KERNEL_TMA = 2
 LBM_SCHED_TWO_PASS = 0
 LBM_SCHED_FUSED = 1
 
@@ -82,6 +83,9 @@ class Info(ctypes.Structure):
     _fields_ = [("sites", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
                 ("n_tiles", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
+                ("psi_tile_x", ctypes.c_int32), ("psi_tile_y", ctypes.c_int32),
+                ("psi_n_tiles", ctypes.c_int32), ("psi_grid_ctas", ctypes.c_int32),
+                ("psi_variant", ctypes.c_int32), ("collide_variant", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("n_lattices", ctypes.c_int32)]
 
 
@@ -209,7 +213,7 @@ def lbm_desc_default(nx: int, ny: int, **kw) -> LatticeDesc:
 
 
 def lbm_create(descs, tile=None, grid_ctas=0, schedule=LBM_SCHED_TWO_PASS, graph_steps=0,
-               stream=None, device=None, kernel_variant=LBM_KERNEL_TMA) -> Handle:
+               stream=None, device=None, kernel_variant=LBM_KERNEL_AUTO) -> Handle:
     """Create a handle over one descriptor or a list of them."""
     import torch
 

@@ -33,7 +33,9 @@ struct TileGeo {
     static constexpr int BOXE = BOXB / ES;             // box stride in elements
     static constexpr int PW = TX + 8;                  // psi box width (floats)
     static constexpr int PSIB = WITH_PSI ? align128((TY + 2) * PW * 4) : 0;
-    static constexpr int STAGEB = 9 * BOXB + PSIB;
+    static constexpr int HDRB = align128((int)sizeof(LatDev) + 16);  // tile + its lattice
+    static constexpr int HDR = 9 * BOXB + PSIB;                       // header offset
+    static constexpr int STAGEB = HDR + HDRB;
     static constexpr int NCOPY = 9 * TY + (WITH_PSI ? TY + 2 : 0);
 };
 

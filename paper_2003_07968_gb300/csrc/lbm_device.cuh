@@ -97,24 +97,29 @@ struct StoreF16 {
 };
 
 // Write v at interior site (x, y) and at every periodic image of it that lies
-// within GW of the interior.  Requires nx, ny >= GW.
+// within GW of the interior (two images per axis when the lattice is
+// narrower than 2 GW).  Requires nx, ny >= GW.
 template <class T>
 __device__ __forceinline__ void store_img(T* plane, int pitch, int gx, int x, int y, int nx,
                                           int ny, T v) {
-    plane[(int64_t)(y + GY) * pitch + (x + gx)] = v;
-    const bool ex = (x < GW) | (x >= nx - GW);
-    const bool ey = (y < GW) | (y >= ny - GW);
-    if (ex | ey) {
-        int xs[3], ys[3], nxs = 1, nys = 1;
-        xs[0] = x;
-        ys[0] = y;
-        if (x < GW) xs[nxs++] = x + nx;
-        if (x >= nx - GW) xs[nxs++] = x - nx;
-        if (y < GW) ys[nys++] = y + ny;
-        if (y >= ny - GW) ys[nys++] = y - ny;
-        for (int b = 0; b < nys; ++b)
-            for (int a = 0; a < nxs; ++a)
-                if (a | b) plane[(int64_t)(ys[b] + GY) * pitch + (xs[a] + gx)] = v;
+    T* const row = plane + (int64_t)(y + GY) * pitch + gx;
+    row[x] = v;
+    const bool xl = x < GW, xh = x >= nx - GW, yl = y < GW, yh = y >= ny - GW;
+    if (xl | xh | yl | yh) {
+        if (xl) row[x + nx] = v;
+        if (xh) row[x - nx] = v;
+        if (yl) {
+            T* const r = row + (int64_t)ny * pitch;
+            r[x] = v;
+            if (xl) r[x + nx] = v;
+            if (xh) r[x - nx] = v;
+        }
+        if (yh) {
+            T* const r = row - (int64_t)ny * pitch;
+            r[x] = v;
+            if (xl) r[x + nx] = v;
+            if (xh) r[x - nx] = v;
+        }
     }
 }
 

@@ -42,8 +42,21 @@ struct TuneKey {
                std::tie(o.device, o.storage, o.eos, o.schedule, o.sites_class, o.nlat_class);
     }
 };
+struct PassCfg {
+    int variant, tx, ty, grid;
+};
 struct TuneVal {
-    int tx, ty, grid, grid_psi;
+    PassCfg pass[2];
+};
+
+// One pass of the step (0: psi, 1: force + collision + stream): its kernel
+// variant, tile shape, tile list and persistent grid.
+struct Pass {
+    int variant = LBM_KERNEL_TMA;
+    int tx = 64, ty = 8, grid = 1, ntiles = 0;
+    int4* tiles = nullptr;
+    size_t cap = 0;
+    std::vector<int> begin, count;  // per-lattice tile ranges
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
@@ -69,10 +82,7 @@ struct lbm_handle {
     size_t psi_bytes = 0;
     LatDev* lat_dev = nullptr;
     uint32_t* status = nullptr;
-    int4* tiles = nullptr;
-    size_t tiles_cap = 0;
-    int variant = LBM_KERNEL_TMA;
-    int grid_psi = 0;
+    Pass pass[2];
     double* partials = nullptr;  // mass partials + one result slot
     double* staging = nullptr;   // FP64 field staging (rho, ux, uy)
     size_t staging_elems = 0;
@@ -83,7 +93,6 @@ struct lbm_handle {
     bool status_pending = false;
     int numeric_lattice = -1;  // first lattice with a device fault bit
     uint32_t fault_bits = 0;   // OR of the device fault bits seen
-    int tx = 32, ty = 8, grid = 0, ntiles = 0;
     int sm_count = 0;
     int parity = 0;
     int64_t sites = 0;
@@ -91,7 +100,7 @@ struct lbm_handle {
     // graphs
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by starting parity
     int graph_steps = 32;
-    std::vector<int> tile_begin, tile_count;        // per-lattice tile ranges
+    int tune_variant = LBM_KERNEL_AUTO;  // the kernel_variant the handle was created with
     // profiling
     bool prof = false;
     ProfRec rec[2];
@@ -215,51 +224,55 @@ LatDev make_lat(const lbm_lattice_desc& d, int index, int64_t& pop_cursor,
 
 void drop_graph(lbm_handle* h);
 
-int build_tiles(lbm_handle* h, int tx, int ty) {
-    drop_graph(h);  // captured launches embed the tile list and grid
+int build_tiles(lbm_handle* h, int k, int tx, int ty) {
+    drop_graph(h);  // captured launches embed the tile lists and grids
+    Pass& P = h->pass[k];
     std::vector<int4> t;
-    h->tile_begin.assign(h->lat.size(), 0);
-    h->tile_count.assign(h->lat.size(), 0);
+    P.begin.assign(h->lat.size(), 0);
+    P.count.assign(h->lat.size(), 0);
     for (size_t l = 0; l < h->lat.size(); ++l) {
         const LatDev& L = h->lat[l];
-        h->tile_begin[l] = (int)t.size();
+        P.begin[l] = (int)t.size();
         for (int y0 = 0; y0 < L.ny; y0 += ty)
             for (int x0 = 0; x0 < L.nx; x0 += tx) t.push_back(make_int4((int)l, x0, y0, 0));
-        h->tile_count[l] = (int)t.size() - h->tile_begin[l];
+        P.count[l] = (int)t.size() - P.begin[l];
     }
     const size_t bytes = t.size() * sizeof(int4);
-    if (bytes > h->tiles_cap) {
-        dev_free(h, h->tiles, h->tiles_cap);
-        h->tiles = (int4*)dev_alloc(h, bytes);
-        if (!h->tiles) {
-            h->tiles_cap = 0;
+    if (bytes > P.cap) {
+        dev_free(h, P.tiles, P.cap);
+        P.tiles = (int4*)dev_alloc(h, bytes);
+        if (!P.tiles) {
+            P.cap = 0;
             return LBM_ERR_OOM;
         }
-        h->tiles_cap = bytes;
+        P.cap = bytes;
     }
-    CK(h, cudaMemcpyAsync(h->tiles, t.data(), bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(P.tiles, t.data(), bytes, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
-    h->tx = tx;
-    h->ty = ty;
-    h->ntiles = (int)t.size();
+    P.tx = tx;
+    P.ty = ty;
+    P.ntiles = (int)t.size();
     return LBM_OK;
+}
+
+bool shape_ok(int variant, int tx, int ty) {
+    if (variant == LBM_KERNEL_TMA) return tma_shape_supported(tx, ty);
+    return tx > 0 && ty > 0 && (tx % 32) == 0 && tx * ty <= 512;
 }
 
 size_t collide_smem(int tx, int ty) { return (size_t)(tx + 2) * (ty + 2) * sizeof(float); }
 
-// Persistent grids: SMs x resident CTAs of each pass, capped by the tile count.
-void default_grids(lbm_handle* h) {
-    int op, oc;
-    if (h->variant == LBM_KERNEL_TMA) {
-        op = occupancy_psi_tma(h->f16, h->eos, h->tx, h->ty);
-        oc = occupancy_collide_tma(h->f16, h->tx, h->ty);
-    } else {
-        const int thr = h->tx * h->ty;
-        op = occupancy_psi(h->f16, h->eos, thr);
-        oc = occupancy_collide(h->f16, thr, collide_smem(h->tx, h->ty));
-    }
-    h->grid_psi = std::max(1, std::min(h->ntiles, h->sm_count * op));
-    h->grid = std::max(1, std::min(h->ntiles, h->sm_count * oc));
+// Persistent grid of pass k: SMs x resident CTAs, capped by the tile count.
+void default_grid(lbm_handle* h, int k) {
+    Pass& P = h->pass[k];
+    int occ;
+    if (P.variant == LBM_KERNEL_TMA)
+        occ = k == 0 ? occupancy_psi_tma(h->f16, h->eos, P.tx, P.ty)
+                     : occupancy_collide_tma(h->f16, P.tx, P.ty);
+    else
+        occ = k == 0 ? occupancy_psi(h->f16, h->eos, P.tx * P.ty)
+                     : occupancy_collide(h->f16, P.tx * P.ty, collide_smem(P.tx, P.ty));
+    P.grid = std::max(1, std::min(P.ntiles, h->sm_count * occ));
 }
 
 void drop_graph(lbm_handle* h) {
@@ -270,16 +283,28 @@ void drop_graph(lbm_handle* h) {
         }
 }
 
-StepArgs step_args(lbm_handle* h, int parity) {
+StepArgs step_args(lbm_handle* h, int parity, int k) {
     StepArgs a;
     a.lats = h->lat_dev;
-    a.tiles = h->tiles;
-    a.ntiles = h->ntiles;
+    a.tiles = h->pass[k].tiles;
+    a.ntiles = h->pass[k].ntiles;
     a.pop = h->pop;
     a.psi = h->psi;
     a.status = h->status;
     a.parity = parity;
     return a;
+}
+
+cudaError_t launch_pass(lbm_handle* h, int k, const StepArgs& a, int grid) {
+    const Pass& P = h->pass[k];
+    if (k == 0)
+        return P.variant == LBM_KERNEL_TMA
+                   ? launch_psi_tma(h->f16, h->eos, P.tx, P.ty, a, grid, h->stream)
+                   : launch_psi(h->f16, h->eos, a, dim3(grid), dim3(P.tx, P.ty), h->stream);
+    return P.variant == LBM_KERNEL_TMA
+               ? launch_collide_tma(h->f16, P.tx, P.ty, a, grid, h->stream)
+               : launch_collide(h->f16, a, dim3(grid), dim3(P.tx, P.ty), collide_smem(P.tx, P.ty),
+                                h->stream);
 }
 
 cudaEvent_t take_event(lbm_handle* h) {
@@ -296,9 +321,6 @@ cudaEvent_t take_event(lbm_handle* h) {
 // Launch the two passes of one step on parity p (state in buffer p, result
 // in buffer p^1).  Records events around each launch when profiling.
 int launch_step(lbm_handle* h, int p) {
-    const StepArgs a = step_args(h, p);
-    const dim3 g(h->grid), b(h->tx, h->ty);
-    const size_t smem = collide_smem(h->tx, h->ty);
     cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
     if (h->prof) {
         e0 = take_event(h);
@@ -306,15 +328,9 @@ int launch_step(lbm_handle* h, int p) {
         e2 = take_event(h);
         CK(h, cudaEventRecord(e0, h->stream));
     }
-    if (h->variant == LBM_KERNEL_TMA)
-        CK(h, launch_psi_tma(h->f16, h->eos, h->tx, h->ty, a, h->grid_psi, h->stream));
-    else
-        CK(h, launch_psi(h->f16, h->eos, a, dim3(h->grid_psi), b, h->stream));
+    CK(h, launch_pass(h, 0, step_args(h, p, 0), h->pass[0].grid));
     if (h->prof) CK(h, cudaEventRecord(e1, h->stream));
-    if (h->variant == LBM_KERNEL_TMA)
-        CK(h, launch_collide_tma(h->f16, h->tx, h->ty, a, h->grid, h->stream));
-    else
-        CK(h, launch_collide(h->f16, a, g, b, smem, h->stream));
+    CK(h, launch_pass(h, 1, step_args(h, p, 1), h->pass[1].grid));
     if (h->prof) {
         CK(h, cudaEventRecord(e2, h->stream));
         h->rec[0].pending.emplace_back(e0, e1);
@@ -419,7 +435,7 @@ void release(lbm_handle* h) {
     if (h->status_host) cudaFreeHost(h->status_host);
     dev_free(h, h->staging, h->staging_elems * 3 * sizeof(double));
     dev_free(h, h->partials, (kMassPartials + 1) * sizeof(double));
-    dev_free(h, h->tiles, h->tiles_cap);
+    for (auto& P : h->pass) dev_free(h, P.tiles, P.cap);
     dev_free(h, h->status, h->lat.size() * sizeof(uint32_t));
     dev_free(h, h->lat_dev, h->lat.size() * sizeof(LatDev));
     dev_free(h, h->psi, h->psi_bytes);
@@ -563,12 +579,20 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
     }
     if (opts && (opts->alloc == nullptr) != (opts->free == nullptr)) return LBM_ERR_ARG;
     if (opts && (opts->tile_x < 0 || opts->tile_y < 0 || opts->grid_ctas < 0)) return LBM_ERR_ARG;
-    const int variant = opts ? opts->kernel_variant : LBM_KERNEL_TMA;
-    if (variant != LBM_KERNEL_TMA && variant != LBM_KERNEL_PLAIN) return LBM_ERR_ARG;
+    const int variant = opts ? opts->kernel_variant : LBM_KERNEL_AUTO;
+    if (variant != LBM_KERNEL_AUTO && variant != LBM_KERNEL_TMA && variant != LBM_KERNEL_PLAIN)
+        return LBM_ERR_ARG;
+    // per-pass defaults (measured on GB300): psi pass with plain loads, the
+    // collision pass through the TMA pipeline with 128 x 4 tiles
+    PassCfg cfg[2] = {{LBM_KERNEL_PLAIN, 64, 8, 0}, {LBM_KERNEL_TMA, 128, 4, 0}};
+    if (variant != LBM_KERNEL_AUTO)
+        for (auto& c : cfg) c = PassCfg{variant, 64, 8, 0};
     if (opts && (opts->tile_x || opts->tile_y)) {
-        const int tx = opts->tile_x ? opts->tile_x : 64, ty = opts->tile_y ? opts->tile_y : 8;
-        if (variant == LBM_KERNEL_TMA && !tma_shape_supported(tx, ty)) return LBM_ERR_ARG;
-        if (variant == LBM_KERNEL_PLAIN && ((tx % 32) || tx * ty > 512)) return LBM_ERR_ARG;
+        for (auto& c : cfg) {
+            c.tx = opts->tile_x ? opts->tile_x : 64;
+            c.ty = opts->tile_y ? opts->tile_y : 8;
+            if (!shape_ok(c.variant, c.tx, c.ty)) return LBM_ERR_ARG;
+        }
     }
     if (opts && opts->schedule != LBM_SCHED_TWO_PASS) return LBM_ERR_ARG;
 
@@ -578,7 +602,6 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
     h->desc.assign(descs, descs + n);
     h->storage = descs[0].storage;
     h->f16 = h->storage == LBM_STORE_F16_DEV;
-    h->variant = variant;
     h->eos = descs[0].eos_precision;
     h->collision = descs[0].collision;
     h->graph_steps = (opts && opts->graph_steps != 0) ? opts->graph_steps : 32;
@@ -625,34 +648,23 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
         cudaMemcpyAsync(h->lat_dev, h->lat.data(), n * sizeof(LatDev), cudaMemcpyHostToDevice,
                         h->stream) != cudaSuccess)
         return fail(LBM_ERR_CUDA);
-    int tx = (opts && opts->tile_x) ? opts->tile_x : 64;
-    int ty = (opts && opts->tile_y) ? opts->tile_y : 8;
-    bool tuned = false;
-    int tuned_grid = 0, tuned_grid_psi = 0;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        TuneKey k{h->device, h->storage, h->eos, h->variant, (int64_t)std::log2((double)h->sites),
+        TuneKey k{h->device, h->storage, h->eos, variant, (int64_t)std::log2((double)h->sites),
                   (int64_t)std::log2((double)n)};
         auto it = g_tune_cache.find(k);
-        if (it != g_tune_cache.end() && !(opts && (opts->tile_x || opts->tile_y))) {
-            tx = it->second.tx;
-            ty = it->second.ty;
-            tuned = true;
-            tuned_grid = it->second.grid;
-            tuned_grid_psi = it->second.grid_psi;
-        }
+        if (it != g_tune_cache.end() && !(opts && (opts->tile_x || opts->tile_y)))
+            for (int q = 0; q < 2; ++q) cfg[q] = it->second.pass[q];
     }
-    int rc = build_tiles(h, tx, ty);
-    if (rc) return fail(rc);
-    default_grids(h);
-    if (tuned) {
-        h->grid = std::min(tuned_grid, h->ntiles);
-        h->grid_psi = std::min(tuned_grid_psi, h->ntiles);
+    for (int q = 0; q < 2; ++q) {
+        h->pass[q].variant = cfg[q].variant;
+        int rc = build_tiles(h, q, cfg[q].tx, cfg[q].ty);
+        if (rc) return fail(rc);
+        default_grid(h, q);
+        if (cfg[q].grid > 0) h->pass[q].grid = std::min(cfg[q].grid, h->pass[q].ntiles);
+        if (opts && opts->grid_ctas) h->pass[q].grid = std::min(opts->grid_ctas, h->pass[q].ntiles);
     }
-    if (opts && opts->grid_ctas) {
-        h->grid = std::min(opts->grid_ctas, h->ntiles);
-        h->grid_psi = h->grid;
-    }
+    h->tune_variant = variant;
     h->rec[0].name = "psi_pass";
     h->rec[1].name = "collide_stream";
     h->rec[0].bytes = (double)h->sites * (9.0 * es + 4.0);
@@ -748,15 +760,10 @@ int lbm_moments(lbm_handle* h, int32_t lattice, double* rho, double* ux, double*
         if (rc) return rc;
         // psi of the current state for this lattice's tiles (all tiles: cheap
         // relative to a D2H copy, and keeps one code path)
-        StepArgs a = step_args(h, h->parity);
-        a.tiles = h->tiles + h->tile_begin[lattice];
-        a.ntiles = h->tile_count[lattice];
-        if (h->variant == LBM_KERNEL_TMA)
-            CK(h, launch_psi_tma(h->f16, h->eos, h->tx, h->ty, a, std::min(h->grid_psi, a.ntiles),
-                                 h->stream));
-        else
-            CK(h, launch_psi(h->f16, h->eos, a, dim3(std::min(h->grid_psi, a.ntiles)),
-                             dim3(h->tx, h->ty), h->stream));
+        StepArgs a = step_args(h, h->parity, 0);
+        a.tiles = h->pass[0].tiles + h->pass[0].begin[lattice];
+        a.ntiles = h->pass[0].count[lattice];
+        CK(h, launch_pass(h, 0, a, std::min(h->pass[0].grid, a.ntiles)));
         double* dr = h->staging;
         double* dx = h->staging + h->staging_elems;
         double* dy = h->staging + 2 * h->staging_elems;
@@ -831,10 +838,16 @@ int lbm_info(lbm_handle* h, lbm_info_t* out) {
     if (!h || !out) return LBM_ERR_ARG;
     out->sites = h->sites;
     out->device_bytes = h->device_bytes;
-    out->tile_x = h->tx;
-    out->tile_y = h->ty;
-    out->n_tiles = h->ntiles;
-    out->grid_ctas = h->grid;
+    out->tile_x = h->pass[1].tx;
+    out->tile_y = h->pass[1].ty;
+    out->n_tiles = h->pass[1].ntiles;
+    out->grid_ctas = h->pass[1].grid;
+    out->psi_tile_x = h->pass[0].tx;
+    out->psi_tile_y = h->pass[0].ty;
+    out->psi_n_tiles = h->pass[0].ntiles;
+    out->psi_grid_ctas = h->pass[0].grid;
+    out->psi_variant = h->pass[0].variant;
+    out->collide_variant = h->pass[1].variant;
     out->schedule = h->schedule;
     out->n_lattices = (int32_t)h->lat.size();
     return LBM_OK;
@@ -843,71 +856,76 @@ int lbm_info(lbm_handle* h, lbm_info_t* out) {
 int lbm_autotune(lbm_handle* h, int32_t repeats) {
     if (!h || repeats < 1) return LBM_ERR_ARG;
     CK(h, cudaStreamSynchronize(h->stream));
-    static const int cand_tma[][2] = {{64, 8}, {64, 16}, {128, 4}, {128, 8}, {32, 16}};
-    static const int cand_plain[][2] = {{32, 4},  {32, 8},  {32, 16}, {64, 2},  {64, 4},
-                                        {64, 8},  {128, 1}, {128, 2}, {128, 4}, {256, 1},
-                                        {256, 2}, {512, 1}};
-    std::vector<std::pair<int, int>> cand;
-    if (h->variant == LBM_KERNEL_TMA)
-        for (const auto& c : cand_tma) cand.emplace_back(c[0], c[1]);
-    else
-        for (const auto& c : cand_plain) cand.emplace_back(c[0], c[1]);
-    cudaEvent_t a = nullptr, b = nullptr;
-    CK(h, cudaEventCreate(&a));
-    CK(h, cudaEventCreate(&b));
+    static const int shapes_tma[][2] = {{64, 8}, {64, 16}, {128, 4}, {128, 8}, {32, 16}};
+    static const int shapes_plain[][2] = {{32, 4}, {32, 8}, {32, 16}, {64, 2}, {64, 4}, {64, 8},
+                                          {128, 1}, {128, 2}, {128, 4}, {256, 1}, {256, 2}};
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    CK(h, cudaEventCreate(&ea));
+    CK(h, cudaEventCreate(&eb));
     const bool was_prof = h->prof;
     h->prof = false;
     const int64_t launches0 = h->launches;
-    float best = 1e30f;
-    int btx = h->tx, bty = h->ty, bgrid = h->grid, bgrid_psi = h->grid_psi;
     int rc = LBM_OK;
-    for (const auto& c : cand) {
-        rc = build_tiles(h, c.first, c.second);
-        if (rc) break;
-        default_grids(h);
-        const int g0 = h->grid, gp0 = h->grid_psi;
-        // persistent grids (SMs x occupancy) against one CTA per tile
-        for (int mode = 0; mode < 2; ++mode) {
-            h->grid = mode == 0 ? g0 : h->ntiles;
-            h->grid_psi = mode == 0 ? gp0 : h->ntiles;
-            // trial steps read buffer `parity` and write the other one, so
-            // repeating them leaves the state unchanged
-            rc = launch_step(h, h->parity);
+    TuneVal best_cfg{};
+    // Each pass is tuned on its own.  Trial launches read population buffer
+    // `parity` and write psi or the other buffer only, so repeating them
+    // leaves the state unchanged; the collision trials run on the psi of
+    // the current state, computed first.
+    for (int k = 0; k < 2 && rc == LBM_OK; ++k) {
+        std::vector<std::pair<int, std::pair<int, int>>> cand;
+        const bool allow_tma = h->tune_variant != LBM_KERNEL_PLAIN;
+        const bool allow_plain = h->tune_variant != LBM_KERNEL_TMA;
+        if (allow_tma)
+            for (const auto& c : shapes_tma) cand.push_back({LBM_KERNEL_TMA, {c[0], c[1]}});
+        if (allow_plain)
+            for (const auto& c : shapes_plain) cand.push_back({LBM_KERNEL_PLAIN, {c[0], c[1]}});
+        float best = 1e30f;
+        PassCfg bc{h->pass[k].variant, h->pass[k].tx, h->pass[k].ty, h->pass[k].grid};
+        for (const auto& c : cand) {
+            h->pass[k].variant = c.first;
+            rc = build_tiles(h, k, c.second.first, c.second.second);
             if (rc) break;
-            cudaEventRecord(a, h->stream);
-            for (int r = 0; r < repeats && rc == LBM_OK; ++r) rc = launch_step(h, h->parity);
-            cudaEventRecord(b, h->stream);
-            if (rc) break;
-            cudaError_t e = cudaEventSynchronize(b);
-            if (e != cudaSuccess) {
-                rc = cuda_fail(h, e, "autotune");
-                break;
-            }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, a, b);
-            if (ms < best) {
-                best = ms;
-                btx = c.first;
-                bty = c.second;
-                bgrid = h->grid;
-                bgrid_psi = h->grid_psi;
+            default_grid(h, k);
+            const int g0 = h->pass[k].grid;
+            for (int mode = 0; mode < 2 && rc == LBM_OK; ++mode) {
+                const int grid = mode == 0 ? g0 : h->pass[k].ntiles;  // persistent vs one CTA per tile
+                const StepArgs a = step_args(h, h->parity, k);
+                if (k == 1) {
+                    cudaError_t e = launch_pass(h, 0, step_args(h, h->parity, 0), h->pass[0].grid);
+                    if (e != cudaSuccess) { rc = cuda_fail(h, e, "autotune psi"); break; }
+                }
+                cudaError_t e = launch_pass(h, k, a, grid);  // warm-up
+                if (e != cudaSuccess) { rc = cuda_fail(h, e, "autotune"); break; }
+                cudaEventRecord(ea, h->stream);
+                for (int r = 0; r < repeats && e == cudaSuccess; ++r) e = launch_pass(h, k, a, grid);
+                cudaEventRecord(eb, h->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(eb);
+                if (e != cudaSuccess) { rc = cuda_fail(h, e, "autotune"); break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ea, eb);
+                if (ms < best) {
+                    best = ms;
+                    bc = PassCfg{c.first, c.second.first, c.second.second, grid};
+                }
             }
         }
         if (rc) break;
+        h->pass[k].variant = bc.variant;
+        rc = build_tiles(h, k, bc.tx, bc.ty);
+        h->pass[k].grid = bc.grid;
+        best_cfg.pass[k] = bc;
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb);
     h->launches = launches0;
     h->prof = was_prof;
     if (rc) return rc;
-    rc = build_tiles(h, btx, bty);
+    rc = sync_status(h);
     if (rc) return rc;
-    h->grid = bgrid;
-    h->grid_psi = bgrid_psi;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    TuneKey k{h->device, h->storage, h->eos, h->variant, (int64_t)std::log2((double)h->sites),
-              (int64_t)std::log2((double)h->lat.size())};
-    g_tune_cache[k] = TuneVal{btx, bty, bgrid, bgrid_psi};
+    TuneKey key{h->device, h->storage, h->eos, h->tune_variant,
+                (int64_t)std::log2((double)h->sites), (int64_t)std::log2((double)h->lat.size())};
+    g_tune_cache[key] = best_cfg;
     return LBM_OK;
 }
 

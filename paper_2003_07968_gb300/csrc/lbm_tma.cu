@@ -78,6 +78,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+struct StageHeader {
+    int4 tile;
+    LatDev lat;
+};
+
 template <class S, int TX, int TY, bool WITH_PSI>
 struct Geo : TileGeo<(int)sizeof(typename S::T), TX, TY, WITH_PSI> {
     using B = TileGeo<(int)sizeof(typename S::T), TX, TY, WITH_PSI>;
@@ -96,6 +101,13 @@ __device__ __forceinline__ void issue_tile(const StepArgs& a, int t, unsigned ch
     const int lane = threadIdx.x & 31;
     const int4 tl = __ldg(&a.tiles[t]);
     const LatDev& L = a.lats[tl.x];
+    // stage header: the tile and its lattice's constants, so consumers read
+    // them from shared memory; written before the arrive (release) below
+    if (lane == 0) {
+        StageHeader* h = reinterpret_cast<StageHeader*>(stage + G::HDR);
+        h->tile = tl;
+        h->lat = L;
+    }
     CopyOp op[PER];
     bool on[PER];
     uint32_t bytes = 0;
@@ -113,7 +125,7 @@ __device__ __forceinline__ void issue_tile(const StepArgs& a, int t, unsigned ch
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
-    if (lane == 0) mbar_expect_tx(bar, bytes);
+    if (lane == 0) mbar_expect_tx(bar, bytes);  // arrive: releases the header writes
     __syncwarp();
     const char* pop = reinterpret_cast<const char*>(a.pop);
     const char* psi = reinterpret_cast<const char*>(a.psi);
@@ -197,9 +209,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_psi_tma(StepArgs a) {
     using G = Geo<S, TX, TY, false>;
     using T = typename S::T;
     const int tx = threadIdx.x % TX, ty0 = threadIdx.x / TX;
-    run_pipeline<S, TX, TY, false>(a, [&](int t, unsigned char* stage) {
-        const int4 tl = __ldg(&a.tiles[t]);
-        const LatDev& L = a.lats[tl.x];
+    run_pipeline<S, TX, TY, false>(a, [&](int, unsigned char* stage) {
+        const StageHeader& hd = *reinterpret_cast<const StageHeader*>(stage + G::HDR);
+        const int4 tl = hd.tile;
+        const LatDev& L = hd.lat;
         const int nx = L.nx, ny = L.ny;
         const float rho0 = L.rho0;
         const T* P = reinterpret_cast<const T*>(stage);
@@ -232,9 +245,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_collide_tma(StepArgs a) {
     using G = Geo<S, TX, TY, true>;
     using T = typename S::T;
     const int tx = threadIdx.x % TX, ty0 = threadIdx.x / TX;
-    run_pipeline<S, TX, TY, true>(a, [&](int t, unsigned char* stage) {
-        const int4 tl = __ldg(&a.tiles[t]);
-        const LatDev& L = a.lats[tl.x];
+    run_pipeline<S, TX, TY, true>(a, [&](int, unsigned char* stage) {
+        const StageHeader& hd = *reinterpret_cast<const StageHeader*>(stage + G::HDR);
+        const int4 tl = hd.tile;
+        const LatDev& L = hd.lat;
         const int nx = L.nx, ny = L.ny;
         const int x = tl.y + tx;
         if (x >= nx) return;

@@ -85,8 +85,9 @@ def test_small_and_ragged_lattices(P, shape):
     assert abs(g["mass"] - o["mass"]) / o["mass"] <= 1e-6
 
 
-@pytest.mark.parametrize("variant,tile", [(0, (64, 8)), (0, (64, 16)), (0, (128, 4)),
-                                          (0, (128, 8)), (0, (32, 16)), (1, (32, 1)),
+# kernel variants: 1 plain loads, 2 TMA pipeline
+@pytest.mark.parametrize("variant,tile", [(2, (64, 8)), (2, (64, 16)), (2, (128, 4)),
+                                          (2, (128, 8)), (2, (32, 16)), (1, (32, 1)),
                                           (1, (64, 2)), (1, (128, 4)), (1, (512, 1))])
 def test_tile_shapes(P, variant, tile):
     rho = synth.droplet(97, 71, 20.0, 0.7)
@@ -96,10 +97,12 @@ def test_tile_shapes(P, variant, tile):
 
 
 def test_tma_and_plain_variants_agree(P):
+    # same arithmetic, different summation order of rho in the psi pass:
+    # they agree to the FP32 parity bar, not bitwise
     rho = synth.droplet(150, 130, 35.0, 0.7)
-    a = gpu_run(P, rho, 300, T=0.7, variant=0)
+    a = gpu_run(P, rho, 300, T=0.7, variant=2)
     b = gpu_run(P, rho, 300, T=0.7, variant=1)
-    assert rel(a["rho"], b["rho"]) <= 1e-6
+    assert rel(a["rho"], b["rho"]) <= RTOL_RHO
 
 
 @pytest.mark.parametrize("eos", [0, 1, 2])
