@@ -71,8 +71,10 @@ extern "C" {
 /* ---- kernel variant ------------------------------------------------------ */
 #define LBM_KERNEL_AUTO 0  /* per pass, the variant and tile measured fastest
                               on GB300 (or found by lbm_autotune)            */
-#define LBM_KERNEL_PLAIN 1 /* one site per thread, plain global loads;
-                              tile_x a multiple of 32, tile_x*tile_y <= 512  */
+#define LBM_KERNEL_PLAIN 1 /* plain global loads, 1, 2 or 4 sites per thread;
+                              tile_x a multiple of 32, tile_x*tile_y <= 512
+                              (tiles given through lbm_runtime_opts use one
+                              site per thread)                               */
 #define LBM_KERNEL_TMA 2   /* tiles staged by TMA bulk copies through a
                               warp-specialised mbarrier pipeline; tile shapes
                               64x8, 64x16, 128x4, 128x8, 32x16               */

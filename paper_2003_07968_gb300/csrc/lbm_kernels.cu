@@ -14,50 +14,58 @@
 
 namespace pplbm {
 
+// Both plain passes give each thread SPT sites of one column (rows
+// threadIdx.y + k blockDim.y): all SPT x 9 loads are issued before any of
+// them is used, which keeps more bytes in flight per thread.
+
 // ---------------------------------------------------------------- pass 1: psi
-template <class S, int EOSP>
+template <class S, int EOSP, int SPT>
 __global__ void __launch_bounds__(512) k_psi(StepArgs a) {
     using T = typename S::T;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const int4 tl = __ldg(&a.tiles[t]);
         const LatDev& L = a.lats[tl.x];
-        const int x = tl.y + threadIdx.x;
-        const int y = tl.z + threadIdx.y;
         const int nx = L.nx, ny = L.ny;
-        if (x >= nx || y >= ny) continue;
+        const int x = tl.y + threadIdx.x;
+        if (x >= nx) continue;
         const int pitch = L.pitch;
         const int64_t plane = L.plane;
-        const T* f = reinterpret_cast<const T*>(a.pop) + L.off_f[a.parity] +
-                     (int64_t)(y + GY) * pitch + (x + L.gx);
-        // pull f_i(x) = f*_i(x - c_i)
-        float d = S::ld(f);
-        d += S::ld(f + 1 * plane - 1);
-        d += S::ld(f + 2 * plane - pitch);
-        d += S::ld(f + 3 * plane + 1);
-        d += S::ld(f + 4 * plane + pitch);
-        d += S::ld(f + 5 * plane - pitch - 1);
-        d += S::ld(f + 6 * plane - pitch + 1);
-        d += S::ld(f + 7 * plane + pitch + 1);
-        d += S::ld(f + 8 * plane + pitch - 1);
-        const float rho = d + L.rho0;
-        bool ok;
-        float psi = eval_psi<EOSP>(L, rho, ok);
-        if (!ok) {
-            atomicOr(&a.status[L.lattice], 1u);
-            psi = __int_as_float(0x7fc00000);
+        const T* base = reinterpret_cast<const T*>(a.pop) + L.off_f[a.parity] + (x + L.gx);
+        float d[SPT];
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) {
+            const int y = min(tl.z + (int)threadIdx.y + k * (int)blockDim.y, ny - 1);
+            const T* f = base + (int64_t)(y + GY) * pitch;
+            // pull f_i(x) = f*_i(x - c_i)
+            d[k] = ((S::ld(f) + S::ld(f + 1 * plane - 1)) +
+                    (S::ld(f + 2 * plane - pitch) + S::ld(f + 3 * plane + 1))) +
+                   ((S::ld(f + 4 * plane + pitch) + S::ld(f + 5 * plane - pitch - 1)) +
+                    (S::ld(f + 6 * plane - pitch + 1) + S::ld(f + 7 * plane + pitch + 1))) +
+                   S::ld(f + 8 * plane + pitch - 1);
         }
-        store_img(a.psi + L.off_psi, L.pitch_psi, L.gx_psi, x, y, nx, ny, psi);
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) {
+            const int y = tl.z + (int)threadIdx.y + k * (int)blockDim.y;
+            if (y >= ny) break;
+            bool ok;
+            float psi = eval_psi<EOSP>(L, d[k] + L.rho0, ok);
+            if (!ok) {
+                atomicOr(&a.status[L.lattice], 1u);
+                psi = __int_as_float(0x7fc00000);
+            }
+            store_img(a.psi + L.off_psi, L.pitch_psi, L.gx_psi, x, y, nx, ny, psi);
+        }
     }
 }
 
 // --------------------------------------------- pass 2: force + collide + store
-template <class S>
+template <class S, int SPT>
 __global__ void __launch_bounds__(512) k_collide(StepArgs a) {
     using T = typename S::T;
     extern __shared__ float sps[];
-    const int TX = blockDim.x, TY = blockDim.y;
+    const int TX = blockDim.x, BY = blockDim.y, TY = BY * SPT;
     const int W = TX + 2;
-    const int nthr = TX * TY;
+    const int nthr = TX * BY;
     const int tid = threadIdx.y * TX + threadIdx.x;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const int4 tl = __ldg(&a.tiles[t]);
@@ -76,37 +84,50 @@ __global__ void __launch_bounds__(512) k_collide(StepArgs a) {
                 if (gx <= xend && gy <= yend) sps[k] = ps[(int64_t)(gy + GY) * pp + (gx + gxp)];
             }
         }
-        __syncthreads();
         const int x = tl.y + threadIdx.x;
-        const int y = tl.z + threadIdx.y;
-        if (x >= nx || y >= ny) continue;
         const int pitch = L.pitch;
         const int64_t plane = L.plane;
-        const T* f = reinterpret_cast<const T*>(a.pop) + L.off_f[a.parity] +
-                     (int64_t)(y + GY) * pitch + (x + L.gx);
-        float g[9], p[9], v[9];
-        g[0] = S::ld(f);
-        g[1] = S::ld(f + 1 * plane - 1);
-        g[2] = S::ld(f + 2 * plane - pitch);
-        g[3] = S::ld(f + 3 * plane + 1);
-        g[4] = S::ld(f + 4 * plane + pitch);
-        g[5] = S::ld(f + 5 * plane - pitch - 1);
-        g[6] = S::ld(f + 6 * plane - pitch + 1);
-        g[7] = S::ld(f + 7 * plane + pitch + 1);
-        g[8] = S::ld(f + 8 * plane + pitch - 1);
-        const float* c = sps + (threadIdx.y + 1) * W + (threadIdx.x + 1);
-        p[0] = c[0];
-        p[1] = c[1];
-        p[2] = c[W];
-        p[3] = c[-1];
-        p[4] = c[-W];
-        p[5] = c[W + 1];
-        p[6] = c[W - 1];
-        p[7] = c[-W - 1];
-        p[8] = c[-W + 1];
-        collide_site(site_consts(L), g, p, v);
-        store_site<S>(reinterpret_cast<T*>(a.pop) + L.off_f[a.parity ^ 1], plane, pitch, L.gx, x,
-                      y, nx, ny, v);
+        const T* base = reinterpret_cast<const T*>(a.pop) + L.off_f[a.parity] + (x + L.gx);
+        float g[SPT][9];
+        if (x < nx) {
+#pragma unroll
+            for (int k = 0; k < SPT; ++k) {
+                const int y = min(tl.z + (int)threadIdx.y + k * BY, ny - 1);
+                const T* f = base + (int64_t)(y + GY) * pitch;
+                g[k][0] = S::ld(f);
+                g[k][1] = S::ld(f + 1 * plane - 1);
+                g[k][2] = S::ld(f + 2 * plane - pitch);
+                g[k][3] = S::ld(f + 3 * plane + 1);
+                g[k][4] = S::ld(f + 4 * plane + pitch);
+                g[k][5] = S::ld(f + 5 * plane - pitch - 1);
+                g[k][6] = S::ld(f + 6 * plane - pitch + 1);
+                g[k][7] = S::ld(f + 7 * plane + pitch + 1);
+                g[k][8] = S::ld(f + 8 * plane + pitch - 1);
+            }
+        }
+        __syncthreads();  // psi tile complete
+        if (x >= nx) continue;
+        const SiteConsts C = site_consts(L);
+        T* o = reinterpret_cast<T*>(a.pop) + L.off_f[a.parity ^ 1];
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) {
+            const int ly = (int)threadIdx.y + k * BY;
+            const int y = tl.z + ly;
+            if (y >= ny) break;
+            const float* c = sps + (ly + 1) * W + (threadIdx.x + 1);
+            float p[9], v[9];
+            p[0] = c[0];
+            p[1] = c[1];
+            p[2] = c[W];
+            p[3] = c[-1];
+            p[4] = c[-W];
+            p[5] = c[W + 1];
+            p[6] = c[W - 1];
+            p[7] = c[-W - 1];
+            p[8] = c[-W + 1];
+            collide_site(C, g[k], p, v);
+            store_site<S>(o, plane, pitch, L.gx, x, y, nx, ny, v);
+        }
     }
 }
 
@@ -216,31 +237,69 @@ __global__ void k_mass_final(const double* partials, int n, double* out) {
 
 // ================================================================ launchers
 namespace {
-template <class S>
+template <class S, int SPT>
 cudaError_t psi_dispatch(int eos, const StepArgs& a, dim3 g, dim3 b, cudaStream_t st) {
     switch (eos) {
-        case EOS_F64: k_psi<S, EOS_F64><<<g, b, 0, st>>>(a); break;
-        case EOS_DF: k_psi<S, EOS_DF><<<g, b, 0, st>>>(a); break;
-        case EOS_F32: k_psi<S, EOS_F32><<<g, b, 0, st>>>(a); break;
+        case EOS_F64: k_psi<S, EOS_F64, SPT><<<g, b, 0, st>>>(a); break;
+        case EOS_DF: k_psi<S, EOS_DF, SPT><<<g, b, 0, st>>>(a); break;
+        case EOS_F32: k_psi<S, EOS_F32, SPT><<<g, b, 0, st>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
+template <class S>
+cudaError_t psi_spt(int spt, int eos, const StepArgs& a, dim3 g, dim3 b, cudaStream_t st) {
+    switch (spt) {
+        case 1: return psi_dispatch<S, 1>(eos, a, g, b, st);
+        case 2: return psi_dispatch<S, 2>(eos, a, g, b, st);
+        case 4: return psi_dispatch<S, 4>(eos, a, g, b, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+template <class S>
+cudaError_t collide_spt(int spt, const StepArgs& a, dim3 g, dim3 b, size_t smem,
+                        cudaStream_t st) {
+    switch (spt) {
+        case 1: k_collide<S, 1><<<g, b, smem, st>>>(a); break;
+        case 2: k_collide<S, 2><<<g, b, smem, st>>>(a); break;
+        case 4: k_collide<S, 4><<<g, b, smem, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+template <class S>
+const void* psi_fn(int spt, int eos) {
+#define PPLBM_F(N)                                                                  \
+    if (spt == N)                                                                   \
+        return eos == EOS_F64 ? (const void*)k_psi<S, EOS_F64, N>                   \
+             : eos == EOS_DF  ? (const void*)k_psi<S, EOS_DF, N>                    \
+                              : (const void*)k_psi<S, EOS_F32, N>;
+    PPLBM_F(1)
+    PPLBM_F(2)
+    PPLBM_F(4)
+#undef PPLBM_F
+    return nullptr;
+}
+template <class S>
+const void* collide_fn(int spt) {
+    return spt == 1 ? (const void*)k_collide<S, 1>
+         : spt == 2 ? (const void*)k_collide<S, 2>
+         : spt == 4 ? (const void*)k_collide<S, 4> : nullptr;
+}
 }  // namespace
 
-cudaError_t launch_psi(int storage_f16, int eos, const StepArgs& a, dim3 g, dim3 b,
+bool plain_spt_supported(int spt) { return spt == 1 || spt == 2 || spt == 4; }
+
+cudaError_t launch_psi(int storage_f16, int eos, int spt, const StepArgs& a, dim3 g, dim3 b,
                        cudaStream_t st) {
-    return storage_f16 ? psi_dispatch<StoreF16>(eos, a, g, b, st)
-                       : psi_dispatch<StoreF32>(eos, a, g, b, st);
+    return storage_f16 ? psi_spt<StoreF16>(spt, eos, a, g, b, st)
+                       : psi_spt<StoreF32>(spt, eos, a, g, b, st);
 }
 
-cudaError_t launch_collide(int storage_f16, const StepArgs& a, dim3 g, dim3 b, size_t smem,
-                           cudaStream_t st) {
-    if (storage_f16)
-        k_collide<StoreF16><<<g, b, smem, st>>>(a);
-    else
-        k_collide<StoreF32><<<g, b, smem, st>>>(a);
-    return cudaGetLastError();
+cudaError_t launch_collide(int storage_f16, int spt, const StepArgs& a, dim3 g, dim3 b,
+                           size_t smem, cudaStream_t st) {
+    return storage_f16 ? collide_spt<StoreF16>(spt, a, g, b, smem, st)
+                       : collide_spt<StoreF32>(spt, a, g, b, smem, st);
 }
 
 cudaError_t launch_init(int storage_f16, const LatDev& L, void* pop, int parity,
@@ -278,26 +337,19 @@ cudaError_t launch_mass(int storage_f16, const LatDev& L, const void* pop, int p
     return cudaGetLastError();
 }
 
-int occupancy_psi(int storage_f16, int eos, int threads) {
+int occupancy_psi(int storage_f16, int eos, int spt, int threads) {
     int n = 0;
-    const void* fn = nullptr;
-    if (storage_f16) {
-        fn = eos == EOS_F64 ? (const void*)k_psi<StoreF16, EOS_F64>
-           : eos == EOS_DF  ? (const void*)k_psi<StoreF16, EOS_DF>
-                            : (const void*)k_psi<StoreF16, EOS_F32>;
-    } else {
-        fn = eos == EOS_F64 ? (const void*)k_psi<StoreF32, EOS_F64>
-           : eos == EOS_DF  ? (const void*)k_psi<StoreF32, EOS_DF>
-                            : (const void*)k_psi<StoreF32, EOS_F32>;
-    }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0) != cudaSuccess) return 1;
+    const void* fn = storage_f16 ? psi_fn<StoreF16>(spt, eos) : psi_fn<StoreF32>(spt, eos);
+    if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0) != cudaSuccess)
+        return 1;
     return n > 0 ? n : 1;
 }
 
-int occupancy_collide(int storage_f16, int threads, size_t smem) {
+int occupancy_collide(int storage_f16, int spt, int threads, size_t smem) {
     int n = 0;
-    const void* fn = storage_f16 ? (const void*)k_collide<StoreF16> : (const void*)k_collide<StoreF32>;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess) return 1;
+    const void* fn = storage_f16 ? collide_fn<StoreF16>(spt) : collide_fn<StoreF32>(spt);
+    if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess)
+        return 1;
     return n > 0 ? n : 1;
 }
 

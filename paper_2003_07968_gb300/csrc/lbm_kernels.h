@@ -4,10 +4,12 @@
 
 namespace pplbm {
 
-cudaError_t launch_psi(int storage_f16, int eos, const StepArgs& a, dim3 g, dim3 b,
+// Plain-load passes: block (tile_x, tile_y / spt), spt sites per thread.
+bool plain_spt_supported(int spt);
+cudaError_t launch_psi(int storage_f16, int eos, int spt, const StepArgs& a, dim3 g, dim3 b,
                        cudaStream_t st);
-cudaError_t launch_collide(int storage_f16, const StepArgs& a, dim3 g, dim3 b, size_t smem,
-                           cudaStream_t st);
+cudaError_t launch_collide(int storage_f16, int spt, const StepArgs& a, dim3 g, dim3 b,
+                           size_t smem, cudaStream_t st);
 cudaError_t launch_init(int storage_f16, const LatDev& L, void* pop, int parity,
                         const double* rho, const double* ux, const double* uy,
                         cudaStream_t st);
@@ -16,7 +18,7 @@ cudaError_t launch_moments(int storage_f16, const LatDev& L, const void* pop, in
                            cudaStream_t st);
 cudaError_t launch_mass(int storage_f16, const LatDev& L, const void* pop, int parity,
                         double* partials, int n_partials, double* out, cudaStream_t st);
-int occupancy_psi(int storage_f16, int eos, int threads);
+int occupancy_psi(int storage_f16, int eos, int spt, int threads);
 // TMA-pipelined passes (lbm_tma.cu); tile shapes are compile-time instances.
 bool tma_shape_supported(int tx, int ty);
 cudaError_t launch_psi_tma(int f16, int eos, int tx, int ty, const StepArgs& a, int grid,
@@ -25,6 +27,6 @@ cudaError_t launch_collide_tma(int f16, int tx, int ty, const StepArgs& a, int g
                                cudaStream_t st);
 int occupancy_psi_tma(int f16, int eos, int tx, int ty);
 int occupancy_collide_tma(int f16, int tx, int ty);
-int occupancy_collide(int storage_f16, int threads, size_t smem);
+int occupancy_collide(int storage_f16, int spt, int threads, size_t smem);
 
 }  // namespace pplbm

@@ -43,7 +43,7 @@ struct TuneKey {
     }
 };
 struct PassCfg {
-    int variant, tx, ty, grid;
+    int variant, tx, ty, grid, spt;
 };
 struct TuneVal {
     PassCfg pass[2];
@@ -54,6 +54,7 @@ struct TuneVal {
 struct Pass {
     int variant = LBM_KERNEL_TMA;
     int tx = 64, ty = 8, grid = 1, ntiles = 0;
+    int spt = 1;  // sites per thread of the plain kernels (the block is tx x ty/spt)
     int4* tiles = nullptr;
     size_t cap = 0;
     std::vector<int> begin, count;  // per-lattice tile ranges
@@ -255,9 +256,10 @@ int build_tiles(lbm_handle* h, int k, int tx, int ty) {
     return LBM_OK;
 }
 
-bool shape_ok(int variant, int tx, int ty) {
+bool shape_ok(int variant, int tx, int ty, int spt) {
     if (variant == LBM_KERNEL_TMA) return tma_shape_supported(tx, ty);
-    return tx > 0 && ty > 0 && (tx % 32) == 0 && tx * ty <= 512;
+    return tx > 0 && ty > 0 && (tx % 32) == 0 && plain_spt_supported(spt) && ty % spt == 0 &&
+           tx * (ty / spt) <= 512;
 }
 
 size_t collide_smem(int tx, int ty) { return (size_t)(tx + 2) * (ty + 2) * sizeof(float); }
@@ -270,8 +272,9 @@ void default_grid(lbm_handle* h, int k) {
         occ = k == 0 ? occupancy_psi_tma(h->f16, h->eos, P.tx, P.ty)
                      : occupancy_collide_tma(h->f16, P.tx, P.ty);
     else
-        occ = k == 0 ? occupancy_psi(h->f16, h->eos, P.tx * P.ty)
-                     : occupancy_collide(h->f16, P.tx * P.ty, collide_smem(P.tx, P.ty));
+        occ = k == 0 ? occupancy_psi(h->f16, h->eos, P.spt, P.tx * (P.ty / P.spt))
+                     : occupancy_collide(h->f16, P.spt, P.tx * (P.ty / P.spt),
+                                         collide_smem(P.tx, P.ty));
     P.grid = std::max(1, std::min(P.ntiles, h->sm_count * occ));
 }
 
@@ -297,13 +300,14 @@ StepArgs step_args(lbm_handle* h, int parity, int k) {
 
 cudaError_t launch_pass(lbm_handle* h, int k, const StepArgs& a, int grid) {
     const Pass& P = h->pass[k];
+    const dim3 block(P.tx, P.ty / P.spt);
     if (k == 0)
         return P.variant == LBM_KERNEL_TMA
                    ? launch_psi_tma(h->f16, h->eos, P.tx, P.ty, a, grid, h->stream)
-                   : launch_psi(h->f16, h->eos, a, dim3(grid), dim3(P.tx, P.ty), h->stream);
+                   : launch_psi(h->f16, h->eos, P.spt, a, dim3(grid), block, h->stream);
     return P.variant == LBM_KERNEL_TMA
                ? launch_collide_tma(h->f16, P.tx, P.ty, a, grid, h->stream)
-               : launch_collide(h->f16, a, dim3(grid), dim3(P.tx, P.ty), collide_smem(P.tx, P.ty),
+               : launch_collide(h->f16, P.spt, a, dim3(grid), block, collide_smem(P.tx, P.ty),
                                 h->stream);
 }
 
@@ -584,14 +588,15 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
         return LBM_ERR_ARG;
     // per-pass defaults (measured on GB300): psi pass with plain loads, the
     // collision pass through the TMA pipeline with 128 x 4 tiles
-    PassCfg cfg[2] = {{LBM_KERNEL_PLAIN, 64, 8, 0}, {LBM_KERNEL_TMA, 128, 4, 0}};
-    if (variant != LBM_KERNEL_AUTO)
-        for (auto& c : cfg) c = PassCfg{variant, 64, 8, 0};
+    PassCfg cfg[2] = {{LBM_KERNEL_PLAIN, 64, 4, 0, 2}, {LBM_KERNEL_PLAIN, 32, 8, 0, 2}};
+    if (variant == LBM_KERNEL_TMA)
+        for (auto& c : cfg) c = PassCfg{variant, 64, 8, 0, 1};
     if (opts && (opts->tile_x || opts->tile_y)) {
         for (auto& c : cfg) {
             c.tx = opts->tile_x ? opts->tile_x : 64;
             c.ty = opts->tile_y ? opts->tile_y : 8;
-            if (!shape_ok(c.variant, c.tx, c.ty)) return LBM_ERR_ARG;
+            c.spt = 1;
+            if (!shape_ok(c.variant, c.tx, c.ty, c.spt)) return LBM_ERR_ARG;
         }
     }
     if (opts && opts->schedule != LBM_SCHED_TWO_PASS) return LBM_ERR_ARG;
@@ -658,6 +663,7 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
     }
     for (int q = 0; q < 2; ++q) {
         h->pass[q].variant = cfg[q].variant;
+        h->pass[q].spt = cfg[q].variant == LBM_KERNEL_TMA ? 1 : cfg[q].spt;
         int rc = build_tiles(h, q, cfg[q].tx, cfg[q].ty);
         if (rc) return fail(rc);
         default_grid(h, q);
@@ -857,8 +863,11 @@ int lbm_autotune(lbm_handle* h, int32_t repeats) {
     if (!h || repeats < 1) return LBM_ERR_ARG;
     CK(h, cudaStreamSynchronize(h->stream));
     static const int shapes_tma[][2] = {{64, 8}, {64, 16}, {128, 4}, {128, 8}, {32, 16}};
-    static const int shapes_plain[][2] = {{32, 4}, {32, 8}, {32, 16}, {64, 2}, {64, 4}, {64, 8},
-                                          {128, 1}, {128, 2}, {128, 4}, {256, 1}, {256, 2}};
+    // plain: tile width, tile height, sites per thread
+    static const int shapes_plain[][3] = {{32, 4, 1}, {32, 8, 1}, {64, 2, 1}, {64, 4, 1},
+                                          {128, 2, 1}, {32, 8, 2}, {32, 16, 2}, {64, 4, 2},
+                                          {64, 8, 2}, {128, 4, 2}, {32, 16, 4}, {64, 8, 4},
+                                          {32, 32, 4}};
     cudaEvent_t ea = nullptr, eb = nullptr;
     CK(h, cudaEventCreate(&ea));
     CK(h, cudaEventCreate(&eb));
@@ -872,18 +881,21 @@ int lbm_autotune(lbm_handle* h, int32_t repeats) {
     // leaves the state unchanged; the collision trials run on the psi of
     // the current state, computed first.
     for (int k = 0; k < 2 && rc == LBM_OK; ++k) {
-        std::vector<std::pair<int, std::pair<int, int>>> cand;
+        std::vector<PassCfg> cand;
         const bool allow_tma = h->tune_variant != LBM_KERNEL_PLAIN;
         const bool allow_plain = h->tune_variant != LBM_KERNEL_TMA;
         if (allow_tma)
-            for (const auto& c : shapes_tma) cand.push_back({LBM_KERNEL_TMA, {c[0], c[1]}});
+            for (const auto& c : shapes_tma) cand.push_back({LBM_KERNEL_TMA, c[0], c[1], 0, 1});
         if (allow_plain)
-            for (const auto& c : shapes_plain) cand.push_back({LBM_KERNEL_PLAIN, {c[0], c[1]}});
+            for (const auto& c : shapes_plain)
+                cand.push_back({LBM_KERNEL_PLAIN, c[0], c[1], 0, c[2]});
         float best = 1e30f;
-        PassCfg bc{h->pass[k].variant, h->pass[k].tx, h->pass[k].ty, h->pass[k].grid};
+        PassCfg bc{h->pass[k].variant, h->pass[k].tx, h->pass[k].ty, h->pass[k].grid,
+                   h->pass[k].spt};
         for (const auto& c : cand) {
-            h->pass[k].variant = c.first;
-            rc = build_tiles(h, k, c.second.first, c.second.second);
+            h->pass[k].variant = c.variant;
+            h->pass[k].spt = c.spt;
+            rc = build_tiles(h, k, c.tx, c.ty);
             if (rc) break;
             default_grid(h, k);
             const int g0 = h->pass[k].grid;
@@ -905,12 +917,13 @@ int lbm_autotune(lbm_handle* h, int32_t repeats) {
                 cudaEventElapsedTime(&ms, ea, eb);
                 if (ms < best) {
                     best = ms;
-                    bc = PassCfg{c.first, c.second.first, c.second.second, grid};
+                    bc = PassCfg{c.variant, c.tx, c.ty, grid, c.spt};
                 }
             }
         }
         if (rc) break;
         h->pass[k].variant = bc.variant;
+        h->pass[k].spt = bc.spt;
         rc = build_tiles(h, k, bc.tx, bc.ty);
         h->pass[k].grid = bc.grid;
         best_cfg.pass[k] = bc;
