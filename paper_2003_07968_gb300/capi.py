@@ -26,6 +26,7 @@ LBM_ERR_TIMEOUT = -5
 LBM_ERR_STATE = -6
 LBM_ERR_UNKNOWN_TICKET = -7
 LBM_ERR_CAPACITY = -8
+LBM_NOALLOC_MAX_COUNT = 1073741824
 
 LBM_STORE_F32 = 0
 LBM_STORE_F32_DEV = 1
@@ -112,6 +113,8 @@ SIGNATURES = {
     "lbm_info": (ctypes.c_int, [_vp, ctypes.POINTER(Info)]),
     "lbm_autotune": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "lbm_selfcheck": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int32]),
+    "lbm_mass_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 _lib = None
@@ -327,6 +330,15 @@ def lbm_info(h: Handle) -> dict:
     i = Info()
     _check(load().lbm_info(h.ptr, ctypes.byref(i)), "lbm_info", h)
     return {k: getattr(i, k) for k, _ in Info._fields_}
+
+
+def lbm_mass_noalloc(values_ptr: int, count: int, offset: float, mass_out_ptr: int,
+                     stream_ptr: int) -> int:
+    """FP64 sum of `count` FP32 device values plus `offset` into the device
+    double at `mass_out_ptr`, queued on `stream_ptr`; allocates nothing.
+    Returns the status code (raises on errors)."""
+    return _check(load().lbm_mass_noalloc(values_ptr, int(count), float(offset), mass_out_ptr,
+                                          stream_ptr), "lbm_mass_noalloc")
 
 
 def lbm_selfcheck() -> tuple[int, str]:
