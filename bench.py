@@ -40,7 +40,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="roofline", choices=["roofline", "batched"])
+    ap.add_argument("--workload", default="roofline", choices=["roofline", "batched", "served"])
+    ap.add_argument("--requests", type=int, default=300,
+                    help="served workload: number of requests of the Poisson stream")
+    ap.add_argument("--step-scale", type=int, default=100,
+                    help="served workload: divide each request's step count by this")
     ap.add_argument("--eos", default="df", choices=["f64", "df", "f32"],
                     help="arithmetic of psi/EOS: float-float (default), native FP64 or FP32")
     ap.add_argument("--variant", default="auto", choices=["auto", "tma", "plain"])
@@ -367,10 +371,214 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ batched workload
+def run_batched(args):
+    """512 independent droplet lattices of uneven sizes (sides U{64..512},
+    R = side x U(0.15, 0.35), T_r U(0.6, 0.9), tau = 1) stepped together by
+    one batch handle (persistent launches over one tile list, CUDA graphs),
+    against the same lattices stepped one handle after another."""
+    import torch
+
+    import synth
+    from paper_2003_07968_gb300 import build, capi as P
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    P.load()
+    storage = {"f32": P.LBM_STORE_F32, "f32dev": P.LBM_STORE_F32_DEV,
+               "f16dev": P.LBM_STORE_F16_DEV}[args.storage]
+    rec = synth.batch_recipe()
+    descs = [P.lbm_desc_default(r["nx"], r["ny"], T=r["T"], storage=storage) for r in rec]
+    fields = [synth.droplet(r["nx"], r["ny"], r["R"], r["T"]) for r in rec]
+    sites = sum(r["nx"] * r["ny"] for r in rec)
+    h = P.lbm_create(descs)
+    for i, f in enumerate(fields):
+        P.lbm_init(h, i, f)
+    if args.autotune:
+        P.lbm_autotune(h, 3)
+    P.lbm_step(h, args.warmup)
+    P.lbm_sync(h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    P.lbm_profile(h, True)
+    P.lbm_profile_read(h)
+    l0 = P.lbm_launch_count(h)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(h.stream)
+        P.lbm_step(h, args.steps)
+        e1.record(h.stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    stats = {st["name"]: st for st in P.lbm_profile_read(h)}
+    P.lbm_profile(h, False)
+    launches = P.lbm_launch_count(h) - l0
+    P.lbm_sync(h)
+    info = P.lbm_info(h)
+    P.lbm_destroy(h)
+    batched = sites * args.steps / (ms * 1e-3) / 1e6
+    # sequential: one handle per lattice, stepped one after another on one stream
+    stream = torch.cuda.Stream()
+    hs = []
+    for d, f in zip(descs, fields):
+        hh = P.lbm_create(d, stream=stream)
+        P.lbm_init(hh, 0, f)
+        P.lbm_step(hh, args.warmup)
+        hs.append(hh)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for hh in hs:
+        P.lbm_step(hh, args.steps)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = s0.elapsed_time(s1)
+    for hh in hs:
+        P.lbm_destroy(hh)
+    sequential = sites * args.steps / (seq_ms * 1e-3) / 1e6
+    peak, peak_src = measured_hbm_peak()
+    es = 2 if args.storage == "f16dev" else 4
+    k2 = stats["collide_stream"]
+    avg = k2["total_ms"] / max(k2["launches"], 1)
+    achieved = k2["bytes_per_launch"] / (avg * 1e-3) / 1e9
+    out = {"metric": BASELINE_METRIC, "value": round(batched, 3), "unit": "MLUPS",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"batched: 512 droplet lattices, sides U{{64..512}}, {sites} sites",
+                      "storage": args.storage, "eos": args.eos,
+                      "psi_pass": [info["psi_variant"], info["psi_tile_x"], info["psi_tile_y"],
+                                   info["psi_grid_ctas"]],
+                      "collide_pass": [info["collide_variant"], info["tile_x"], info["tile_y"],
+                                       info["grid_ctas"]]},
+           "batched": {"MLUPS": round(batched, 1), "sequential_MLUPS": round(sequential, 1),
+                       "speedup": round(batched / sequential, 3),
+                       "sequential": "one handle per lattice, lbm_step one after another"},
+           "roofline": {"bound": "hbm", "kernel": "collide_stream", "achieved": round(achieved, 1),
+                        "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                        "traffic": None, "peak_source": peak_src},
+           "step_roofline": {"algorithmic_bytes_per_site": 18 * es,
+                             "effective_GBps": round(batched * 1e6 * 18 * es / 1e9, 1)},
+           "gpu_launches": int(launches), "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ served workload
+def run_served(args):
+    """Poisson stream (200/s) of droplet / flat-band solves with sides
+    U{128..2048} and steps U{1000..50000} / step_scale, submitted in real time
+    to one continuous-batching server; against the same requests served one
+    at a time by plain handles (first come first served, same arrivals)."""
+    import threading
+
+    import torch
+
+    import synth
+    from paper_2003_07968_gb300 import build, capi as P
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    P.load()
+    storage = {"f32": P.LBM_STORE_F32, "f32dev": P.LBM_STORE_F32_DEV,
+               "f16dev": P.LBM_STORE_F16_DEV}[args.storage]
+    reqs = synth.serving_stream(n=args.requests)
+    for r in reqs:
+        r["steps"] = max(1, r["steps"] // args.step_scale)
+    fields = [synth.request_field(r) for r in reqs]
+    descs = [P.lbm_desc_default(r["nx"], r["ny"], T=r["T"], storage=storage) for r in reqs]
+    work = sum(r["nx"] * r["ny"] * r["steps"] for r in reqs)
+    # warm the kernels once
+    h = P.lbm_create(P.lbm_desc_default(256, 256, storage=storage))
+    P.lbm_init(h, 0, synth.droplet(256, 256, 60.0, 0.8))
+    P.lbm_step(h, 20)
+    P.lbm_sync(h)
+    P.lbm_destroy(h)
+
+    opts = P.lbm_server_opts_default(arena_bytes=64 << 30, chunk_steps=50, storage=storage,
+                                     max_resident=1024)
+    srv = P.lbm_server_create(opts)
+    tickets = [None] * len(reqs)
+    t_start = time.perf_counter()
+
+    def submitter():
+        for i, r in enumerate(reqs):
+            dt = r["t_arrival"] - (time.perf_counter() - t_start)
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = P.lbm_submit(srv, descs[i], fields[i], r["steps"])
+
+    th = threading.Thread(target=submitter)
+    with ClockSampler(local) as clk:
+        th.start()
+        results, lat = {}, []
+        while len(results) < len(reqs):
+            for i, t in enumerate(tickets):
+                if t is not None and i not in results:
+                    out = P.lbm_poll(srv, t, u=False)
+                    if out is not None:
+                        results[i] = out
+                        lat.append(out["latency_s"])
+            time.sleep(0.0005)
+        t_end = time.perf_counter()
+        th.join()
+    stats = P.lbm_server_get_stats(srv)
+    P.lbm_server_destroy(srv)
+    wall = t_end - t_start
+    served = work / wall / 1e6
+    # sequential: one plain handle per request, first come first served
+    stream = torch.cuda.Stream()
+    service = []
+    for d, f, r in zip(descs, fields, reqs):
+        t0 = time.perf_counter()
+        hh = P.lbm_create(d, stream=stream)
+        P.lbm_init(hh, 0, f)
+        P.lbm_step(hh, r["steps"])
+        P.lbm_moments(hh, 0, u=False, mass=False)
+        P.lbm_destroy(hh)
+        service.append(time.perf_counter() - t0)
+    fin, seq_lat = 0.0, []
+    for r, sv in zip(reqs, service):
+        fin = max(fin, r["t_arrival"]) + sv
+        seq_lat.append(fin - r["t_arrival"])
+    seq_wall = fin - reqs[0]["t_arrival"]
+    # a few served results must equal the same lattice stepped alone
+    same = True
+    for i in (0, len(reqs) // 2, len(reqs) - 1):
+        hh = P.lbm_create(descs[i])
+        P.lbm_init(hh, 0, fields[i])
+        P.lbm_step(hh, reqs[i]["steps"])
+        a = P.lbm_moments(hh, 0, u=False, mass=False)["rho"]
+        P.lbm_destroy(hh)
+        same = same and bool(np.array_equal(a, results[i]["rho"]))
+    pct = lambda v, q: float(np.percentile(np.array(v), q))
+    out = {"metric": BASELINE_METRIC, "value": round(served, 3), "unit": "MLUPS",
+           "n_gpus": world, "steps": len(reqs), "warmup": 0,
+           "ms_per_step": round(wall / len(reqs) * 1e3, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"served: {len(reqs)} requests, Poisson 200/s, sides U{{128..2048}}, "
+                                  f"steps U{{1000..50000}}/{args.step_scale}, droplet/band 50/50",
+                      "storage": args.storage, "chunk_steps": 50, "site_steps": work},
+           "served": {"MLUPS": round(served, 1), "p50_s": round(pct(lat, 50), 4),
+                      "p99_s": round(pct(lat, 99), 4), "wall_s": round(wall, 3),
+                      "gpu_busy_s": round(stats["busy_s"], 3),
+                      "sequential_MLUPS": round(work / seq_wall / 1e6, 1),
+                      "sequential_p50_s": round(pct(seq_lat, 50), 4),
+                      "sequential_p99_s": round(pct(seq_lat, 99), 4),
+                      "speedup": round(served / (work / seq_wall / 1e6), 3),
+                      "mix_equals_alone": same},
+           "gpu_launches": None, "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "served":
+        run_served(args)
     else:
         run_gpu(args)
 

@@ -218,6 +218,70 @@ int lbm_info(lbm_handle* h, lbm_info_t* out);
  * the process and used by later lbm_create calls.  Errors: LBM_ERR_CUDA. */
 int lbm_autotune(lbm_handle* h, int32_t repeats);
 
+/* ---- serving: continuous batching --------------------------------------- */
+/* A server keeps many independent lattices (requests) resident in one
+ * device arena and steps all of them together: every chunk of steps is one
+ * pair of launches per step over a tile list that spans every resident
+ * lattice (the same kernels as a batch handle).  Requests are admitted at
+ * chunk boundaries, first come first served but skipping any that do not
+ * fit yet, whenever a slot and arena space (HBM footprint: both population
+ * buffers plus psi) are free; a finished lattice's moments are copied out and
+ * its space is reused at once.  One native worker thread drives the GPU; the
+ * submit and poll calls are thread-safe and never wait for the GPU.  The
+ * numerics of a request do not depend on what else is resident. */
+typedef struct lbm_server lbm_server;
+
+typedef struct {
+    size_t arena_bytes;       /* device bytes for resident lattices (0: 8 GiB)    */
+    int32_t max_resident;     /* resident lattices at most (0: 1024)              */
+    int32_t chunk_steps;      /* steps between admission points (0: 100)          */
+    int64_t max_request_sites;/* largest nx*ny accepted (0: 2048*2048)            */
+    int32_t storage;          /* LBM_STORE_* of every request                     */
+    int32_t eos_precision;    /* LBM_EOS_* of every request                       */
+    int32_t kernel_variant;   /* LBM_KERNEL_* (AUTO: the measured defaults)       */
+    int32_t tile_x, tile_y;   /* 0: defaults; else both passes, one site/thread   */
+} lbm_server_opts;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int32_t queued, resident;
+    int64_t site_steps;       /* lattice-site updates done                       */
+    double busy_s;            /* time the worker spent in GPU chunks             */
+    int64_t arena_bytes, arena_in_use;
+} lbm_server_stats;
+
+/* Fill *o with the defaults above (FP32 deviation storage, float-float EOS). */
+void lbm_server_opts_default(lbm_server_opts* o);
+
+/* Create a server on the current device: allocates the arena, staging and
+ * tables with cudaMalloc and starts the worker thread.
+ * Errors: LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA. */
+int lbm_server_create(const lbm_server_opts* opts, lbm_server** out);
+
+/* Queue one solve: a lattice `d` (its storage and eos_precision are replaced
+ * by the server's), initial density rho (host [ny][nx] FP64, copied before
+ * return, u = 0), nsteps >= 1 time steps.  Thread-safe; never waits for the
+ * GPU.  *ticket identifies the request.  Errors: LBM_ERR_ARG (bad desc or
+ * nsteps), LBM_ERR_CAPACITY (the lattice can never fit: larger than the
+ * arena or than max_request_sites), LBM_ERR_STATE (server shutting down). */
+int lbm_submit(lbm_server* s, const lbm_lattice_desc* d, const double* rho, int64_t nsteps,
+               uint64_t* ticket);
+
+/* Result of a request: LBM_PENDING while queued or running; once done,
+ * copies rho, ux, uy (host [ny][nx] FP64, any may be NULL) of the final state
+ * (Eqs. FD, FMD) and the submit-to-done time in seconds, forgets the ticket
+ * and returns LBM_OK, or the request's error (LBM_ERR_NUMERIC if psi became
+ * undefined).  Thread-safe.  Errors: LBM_ERR_UNKNOWN_TICKET. */
+int lbm_poll(lbm_server* s, uint64_t ticket, double* rho, double* ux, double* uy,
+             double* latency_s);
+
+/* Counters of the server so far.  Thread-safe. */
+int lbm_server_get_stats(lbm_server* s, lbm_server_stats* out);
+
+/* Stop the worker (finishing the chunk in flight), free everything.  Pending
+ * requests are dropped.  NULL is ignored. */
+void lbm_server_destroy(lbm_server* s);
+
 /* ---- mass without allocation ------------------------------------------- */
 /* The paper has no counterpart to this entry point; it serves callers that
  * may not allocate device memory at the moment they want a conserved-mass

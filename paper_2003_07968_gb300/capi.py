@@ -71,6 +71,26 @@ class RuntimeOpts(ctypes.Structure):
                 ("kernel_variant", ctypes.c_int32)]
 
 
+class ServerOpts(ctypes.Structure):
+    """lbm_server_opts."""
+
+    _fields_ = [("arena_bytes", ctypes.c_size_t), ("max_resident", ctypes.c_int32),
+                ("chunk_steps", ctypes.c_int32), ("max_request_sites", ctypes.c_int64),
+                ("storage", ctypes.c_int32), ("eos_precision", ctypes.c_int32),
+                ("kernel_variant", ctypes.c_int32), ("tile_x", ctypes.c_int32),
+                ("tile_y", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    """lbm_server_stats."""
+
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("queued", ctypes.c_int32),
+                ("resident", ctypes.c_int32), ("site_steps", ctypes.c_int64),
+                ("busy_s", ctypes.c_double), ("arena_bytes", ctypes.c_int64),
+                ("arena_in_use", ctypes.c_int64)]
+
+
 class KernelStat(ctypes.Structure):
     """lbm_kernel_stat."""
 
@@ -115,6 +135,13 @@ SIGNATURES = {
     "lbm_selfcheck": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int32]),
     "lbm_mass_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "lbm_server_opts_default": (None, [ctypes.POINTER(ServerOpts)]),
+    "lbm_server_create": (ctypes.c_int, [ctypes.POINTER(ServerOpts), ctypes.POINTER(_vp)]),
+    "lbm_submit": (ctypes.c_int, [_vp, ctypes.POINTER(LatticeDesc), _dp, ctypes.c_int64,
+                                  ctypes.POINTER(ctypes.c_uint64)]),
+    "lbm_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, _dp, _dp, _dp, _dp]),
+    "lbm_server_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ServerStats)]),
+    "lbm_server_destroy": (None, [_vp]),
 }
 
 _lib = None
@@ -350,3 +377,75 @@ def lbm_selfcheck() -> tuple[int, str]:
 def lbm_autotune(h: Handle, repeats: int = 3) -> dict:
     _check(load().lbm_autotune(h.ptr, int(repeats)), "lbm_autotune", h)
     return lbm_info(h)
+
+
+# --------------------------------------------------------------- serving
+class Server:
+    """An lbm_server*; the lattices' shapes are remembered per ticket so
+    lbm_poll can size its outputs."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+        self.shapes = {}
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                lbm_server_destroy(self)
+            except Exception:
+                pass
+
+
+def lbm_server_opts_default(**kw) -> ServerOpts:
+    o = ServerOpts()
+    load().lbm_server_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def lbm_server_create(opts: ServerOpts | None = None) -> Server:
+    out = ctypes.c_void_p()
+    _check(load().lbm_server_create(ctypes.byref(opts) if opts is not None else None,
+                                    ctypes.byref(out)), "lbm_server_create")
+    return Server(out)
+
+
+def lbm_submit(s: Server, desc: LatticeDesc, rho, nsteps: int) -> int:
+    r = _f64(rho, (desc.ny, desc.nx))
+    t = ctypes.c_uint64(0)
+    _check(load().lbm_submit(s.ptr, ctypes.byref(desc), _ptr(r), int(nsteps), ctypes.byref(t)),
+           "lbm_submit")
+    s.shapes[t.value] = (desc.ny, desc.nx)
+    return t.value
+
+
+def lbm_poll(s: Server, ticket: int, u: bool = True):
+    """None while pending; else dict(rho, ux, uy, latency_s).  Raises LbmError
+    for a failed request (its code in .code)."""
+    shp = s.shapes.get(ticket, (1, 1))
+    rho = np.empty(shp)
+    ux = np.empty(shp) if u else None
+    uy = np.empty(shp) if u else None
+    lat = ctypes.c_double(0.0)
+    rc = load().lbm_poll(s.ptr, ctypes.c_uint64(ticket), _ptr(rho), _ptr(ux), _ptr(uy),
+                         ctypes.byref(lat))
+    if rc == LBM_PENDING:
+        return None
+    s.shapes.pop(ticket, None)
+    _check(rc, "lbm_poll")
+    return {"rho": rho, "ux": ux, "uy": uy, "latency_s": lat.value}
+
+
+def lbm_server_get_stats(s: Server) -> dict:
+    st = ServerStats()
+    _check(load().lbm_server_get_stats(s.ptr, ctypes.byref(st)), "lbm_server_get_stats")
+    return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+
+def lbm_server_destroy(s: Server) -> None:
+    if s.ptr:
+        load().lbm_server_destroy(s.ptr)
+        s.ptr = None

@@ -84,14 +84,24 @@ struct StepArgs {
 struct StoreF32 {
     using T = float;
     static constexpr int kGx = 4;  // 16 bytes of ghost columns keep rows aligned
-    static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    // read-only load that asks L2 to fetch 256-byte blocks (neighbouring warps
+    // read the adjacent segments of the same rows)
+    static __device__ __forceinline__ float ld(const float* p) {
+        float v;
+        asm volatile("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        return v;
+    }
     static __device__ __forceinline__ float lds(const float* p) { return *p; }
     static __device__ __forceinline__ float cv(float v) { return v; }
 };
 struct StoreF16 {
     using T = __half;
     static constexpr int kGx = 8;
-    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float ld(const __half* p) {
+        unsigned short v;
+        asm volatile("ld.global.nc.L2::256B.b16 %0, [%1];" : "=h"(v) : "l"(p));
+        return __half2float(__ushort_as_half(v));
+    }
     static __device__ __forceinline__ float lds(const __half* p) { return __half2float(*p); }
     static __device__ __forceinline__ __half cv(float v) { return __float2half_rn(v); }
 };

@@ -1,0 +1,107 @@
+// lbm_layout.h -- per-lattice layout and constants (LatDev) from a lattice
+// descriptor; shared by the handle runtime and the server.
+#pragma once
+#include <cmath>
+#include <string>
+
+#include "../../include/pplbm.h"
+#include "lbm_device.cuh"
+
+namespace pplbm {
+
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+inline void split_df(double v, df2& out) {
+    out.hi = (float)v;
+    out.lo = (float)(v - (double)out.hi);
+}
+
+// Everything of a lattice's LatDev except its offsets in the arenas:
+// pitched planes with a ghost frame (16 bytes of columns and GY rows on each
+// side), pitch a multiple of 32 bytes, planes multiples of 256 bytes, and
+// the constants of the force (Eq. IFT), collision (Eqs. BGKCO, GFSBGK) and
+// EOS (Eqs. DED, CSEOS).
+inline LatDev lat_layout(const lbm_lattice_desc& d, int index) {
+    LatDev L{};
+    const int s = d.storage == LBM_STORE_F16_DEV ? 2 : 4;
+    const int gx = 16 / s;
+    L.nx = d.nx;
+    L.ny = d.ny;
+    L.gx = gx;
+    L.pitch = (int)round_up(d.nx + 2 * gx, 32 / s);
+    const int64_t rows = d.ny + 2 * GY;
+    L.plane = round_up((int64_t)L.pitch * rows, 256 / s);
+    L.gx_psi = 4;
+    L.pitch_psi = (int)round_up(d.nx + 8, 8);
+    L.omega = (float)(1.0 / d.tau);
+    L.guo = (float)(1.0 - 1.0 / (2.0 * d.tau));
+    L.k_sc = (float)(-6.0 * d.G);
+    L.k1 = (float)(13.5 * d.eps * d.G);
+    L.k2 = (float)(9.0 * (d.sigma - 1.0) * d.G);
+    L.rho0 = (d.storage == LBM_STORE_F32 || d.rho0 < 0.0) ? 0.f : (float)d.rho0;
+    L.m2_variant = d.m2_trace_variant;
+    L.lattice = index;
+    // psi^2 = rho (e1 q - e2 rho - e3): e1 = k c T / G, e2 = k a / G, e3 = 1/(3G)
+    L.eb = d.eos_b;
+    L.e1 = d.eos_k * d.eos_c * d.T / d.G;
+    L.e2 = d.eos_k * d.eos_a / d.G;
+    L.e3 = 1.0 / (3.0 * d.G);
+    split_df(L.eb, L.fb);
+    split_df(L.e1, L.f1);
+    split_df(L.e2, L.f2);
+    split_df(L.e3, L.f3);
+    L.sb = (float)L.eb;
+    L.s1 = (float)L.e1;
+    L.s2 = (float)L.e2;
+    L.s3 = (float)L.e3;
+    for (int i = 0; i < 9; ++i) L.mrt_s[i] = (float)d.mrt_rates[i];
+    return L;
+}
+
+// Checks of one lattice descriptor (sizes, relaxation time, finite
+// parameters, known enums).  Returns LBM_OK or LBM_ERR_ARG with `why`.
+inline int validate_desc(const lbm_lattice_desc& d, std::string& why) {
+    if (d.nx < 2 || d.ny < 2) return why = "nx and ny must be >= 2", LBM_ERR_ARG;
+    if ((int64_t)d.nx * d.ny > (int64_t)1 << 31) return why = "lattice too large", LBM_ERR_ARG;
+    if (!(d.tau > 0.5) || !std::isfinite(d.tau)) return why = "tau must be > 0.5", LBM_ERR_ARG;
+    if (!(d.G != 0.0) || !std::isfinite(d.G)) return why = "G must be nonzero", LBM_ERR_ARG;
+    if (!std::isfinite(d.eps) || !std::isfinite(d.sigma) || !std::isfinite(d.T) ||
+        !std::isfinite(d.rho0) || d.rho0 > 1e6)
+        return why = "non-finite parameter", LBM_ERR_ARG;
+    if (!(d.eos_b > 0.0) || !std::isfinite(d.eos_a) || !std::isfinite(d.eos_c) ||
+        !std::isfinite(d.eos_k))
+        return why = "bad EOS constants", LBM_ERR_ARG;
+    if (d.storage < LBM_STORE_F32 || d.storage > LBM_STORE_F16_DEV)
+        return why = "unknown storage", LBM_ERR_ARG;
+    if (d.eos_precision < LBM_EOS_F64 || d.eos_precision > LBM_EOS_F32)
+        return why = "unknown eos_precision", LBM_ERR_ARG;
+    if (d.m2_trace_variant != 0 && d.m2_trace_variant != 1)
+        return why = "m2_trace_variant must be 0 or 1", LBM_ERR_ARG;
+    if (d.collision != LBM_COLL_BGK) return why = "only BGK collision is built", LBM_ERR_ARG;
+    return LBM_OK;
+}
+
+// Per-pass defaults of LBM_KERNEL_AUTO, measured fastest on GB300 for the
+// 8192^2 droplet: psi pass plain 64 x 4 tiles, collision pass plain 32 x 8
+// tiles, both with two sites per thread.
+struct PassDefault {
+    int variant, tx, ty, spt;
+};
+constexpr PassDefault kPassDefaults[2] = {{LBM_KERNEL_PLAIN, 64, 4, 2},
+                                          {LBM_KERNEL_PLAIN, 32, 8, 2}};
+
+// Automatic deviation reference: the smallest density of the field.
+inline float auto_rho0(const double* rho, size_t n) {
+    double m = rho[0];
+    for (size_t i = 1; i < n; ++i) m = m < rho[i] ? m : rho[i];
+    return (float)(m > 0.0 ? m : 0.0);
+}
+
+// Elements of the two population buffers (A then B, nine planes each).
+inline int64_t lat_pop_elems(const LatDev& L) { return 18 * L.plane; }
+// Floats of the psi plane.
+inline int64_t lat_psi_elems(const LatDev& L) {
+    return round_up((int64_t)L.pitch_psi * (L.ny + 2 * GY), 64);
+}
+
+}  // namespace pplbm

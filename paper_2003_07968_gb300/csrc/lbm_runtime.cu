@@ -17,14 +17,13 @@
 #include "../../include/pplbm.h"
 #include "lbm_copy_plan.h"
 #include "lbm_kernels.h"
+#include "lbm_layout.h"
 
 using namespace pplbm;
 
 namespace {
 
 constexpr int kMassPartials = 1024;
-
-int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 struct ProfRec {
     std::string name;
@@ -153,73 +152,14 @@ void dev_free(lbm_handle* h, void* p, size_t bytes) {
     h->device_bytes -= (int64_t)bytes;
 }
 
-void split_df(double v, df2& out) {
-    out.hi = (float)v;
-    out.lo = (float)(v - (double)out.hi);
-}
-
-int validate(const lbm_lattice_desc& d, std::string& why) {
-    if (d.nx < 2 || d.ny < 2) return why = "nx and ny must be >= 2", LBM_ERR_ARG;
-    if ((int64_t)d.nx * d.ny > (int64_t)1 << 31) return why = "lattice too large", LBM_ERR_ARG;
-    if (!(d.tau > 0.5) || !std::isfinite(d.tau)) return why = "tau must be > 0.5", LBM_ERR_ARG;
-    if (!(d.G != 0.0) || !std::isfinite(d.G)) return why = "G must be nonzero", LBM_ERR_ARG;
-    if (!std::isfinite(d.eps) || !std::isfinite(d.sigma) || !std::isfinite(d.T) ||
-        !std::isfinite(d.rho0) || d.rho0 > 1e6)
-        return why = "non-finite parameter", LBM_ERR_ARG;
-    if (!(d.eos_b > 0.0) || !std::isfinite(d.eos_a) || !std::isfinite(d.eos_c) ||
-        !std::isfinite(d.eos_k))
-        return why = "bad EOS constants", LBM_ERR_ARG;
-    if (d.storage < LBM_STORE_F32 || d.storage > LBM_STORE_F16_DEV)
-        return why = "unknown storage", LBM_ERR_ARG;
-    if (d.eos_precision < LBM_EOS_F64 || d.eos_precision > LBM_EOS_F32)
-        return why = "unknown eos_precision", LBM_ERR_ARG;
-    if (d.m2_trace_variant != 0 && d.m2_trace_variant != 1)
-        return why = "m2_trace_variant must be 0 or 1", LBM_ERR_ARG;
-    if (d.collision != LBM_COLL_BGK) return why = "only BGK collision is built", LBM_ERR_ARG;
-    return LBM_OK;
-}
-
 LatDev make_lat(const lbm_lattice_desc& d, int index, int64_t& pop_cursor,
                 int64_t& psi_cursor) {
-    LatDev L{};
-    const int s = d.storage == LBM_STORE_F16_DEV ? 2 : 4;
-    const int gx = 16 / s;
-    L.nx = d.nx;
-    L.ny = d.ny;
-    L.gx = gx;
-    L.pitch = (int)round_up(d.nx + 2 * gx, 32 / s);
-    const int64_t rows = d.ny + 2 * GY;
-    L.plane = round_up((int64_t)L.pitch * rows, 256 / s);
+    LatDev L = lat_layout(d, index);
     L.off_f[0] = pop_cursor;
-    pop_cursor += 9 * L.plane;
-    L.off_f[1] = pop_cursor;
-    pop_cursor += 9 * L.plane;
-    L.gx_psi = 4;
-    L.pitch_psi = (int)round_up(d.nx + 8, 8);
+    L.off_f[1] = pop_cursor + 9 * L.plane;
+    pop_cursor += lat_pop_elems(L);
     L.off_psi = psi_cursor;
-    psi_cursor += round_up((int64_t)L.pitch_psi * rows, 64);
-    L.omega = (float)(1.0 / d.tau);
-    L.guo = (float)(1.0 - 1.0 / (2.0 * d.tau));
-    L.k_sc = (float)(-6.0 * d.G);
-    L.k1 = (float)(13.5 * d.eps * d.G);
-    L.k2 = (float)(9.0 * (d.sigma - 1.0) * d.G);
-    L.rho0 = (d.storage == LBM_STORE_F32 || d.rho0 < 0.0) ? 0.f : (float)d.rho0;
-    L.m2_variant = d.m2_trace_variant;
-    L.lattice = index;
-    // psi^2 = rho (e1 q - e2 rho - e3): e1 = k c T / G, e2 = k a / G, e3 = 1/(3G)
-    L.eb = d.eos_b;
-    L.e1 = d.eos_k * d.eos_c * d.T / d.G;
-    L.e2 = d.eos_k * d.eos_a / d.G;
-    L.e3 = 1.0 / (3.0 * d.G);
-    split_df(L.eb, L.fb);
-    split_df(L.e1, L.f1);
-    split_df(L.e2, L.f2);
-    split_df(L.e3, L.f3);
-    L.sb = (float)L.eb;
-    L.s1 = (float)L.e1;
-    L.s2 = (float)L.e2;
-    L.s3 = (float)L.e3;
-    for (int i = 0; i < 9; ++i) L.mrt_s[i] = (float)d.mrt_rates[i];
+    psi_cursor += lat_psi_elems(L);
     return L;
 }
 
@@ -574,7 +514,7 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
     if (!descs || n < 1) return LBM_ERR_ARG;
     std::string why;
     for (int i = 0; i < n; ++i) {
-        int rc = validate(descs[i], why);
+        int rc = validate_desc(descs[i], why);
         if (rc) return rc;
         if (descs[i].storage != descs[0].storage || descs[i].eos_precision != descs[0].eos_precision ||
             descs[i].collision != descs[0].collision ||
@@ -588,7 +528,10 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
         return LBM_ERR_ARG;
     // per-pass defaults (measured on GB300): psi pass with plain loads, the
     // collision pass through the TMA pipeline with 128 x 4 tiles
-    PassCfg cfg[2] = {{LBM_KERNEL_PLAIN, 64, 4, 0, 2}, {LBM_KERNEL_PLAIN, 32, 8, 0, 2}};
+    PassCfg cfg[2];
+    for (int q = 0; q < 2; ++q)
+        cfg[q] = PassCfg{kPassDefaults[q].variant, kPassDefaults[q].tx, kPassDefaults[q].ty, 0,
+                         kPassDefaults[q].spt};
     if (variant == LBM_KERNEL_TMA)
         for (auto& c : cfg) c = PassCfg{variant, 64, 8, 0, 1};
     if (opts && (opts->tile_x || opts->tile_y)) {

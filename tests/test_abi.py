@@ -40,9 +40,10 @@ def test_struct_layouts_match_header(lib):
     # sizes of the ctypes mirrors against a tiny C program compiled with the header
     from paper_2003_07968_gb300 import capi
 
-    src = ('#include "pplbm.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(){printf("%zu %zu %zu %zu %zu\\n",'
+    src = ('#include "pplbm.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(){printf("%zu %zu %zu %zu %zu %zu %zu\\n",'
            'sizeof(lbm_lattice_desc), sizeof(lbm_runtime_opts), sizeof(lbm_kernel_stat),'
-           'sizeof(lbm_info_t), offsetof(lbm_lattice_desc, mrt_rates));return 0;}')
+           'sizeof(lbm_info_t), offsetof(lbm_lattice_desc, mrt_rates), sizeof(lbm_server_opts),'
+           'sizeof(lbm_server_stats));return 0;}')
     tmp = os.path.join(ROOT, "paper_2003_07968_gb300", "_lib")
     os.makedirs(tmp, exist_ok=True)
     c = os.path.join(tmp, "layout.c")
@@ -52,7 +53,8 @@ def test_struct_layouts_match_header(lib):
     got = [int(v) for v in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
     want = [ctypes.sizeof(capi.LatticeDesc), ctypes.sizeof(capi.RuntimeOpts),
             ctypes.sizeof(capi.KernelStat), ctypes.sizeof(capi.Info),
-            capi.LatticeDesc.mrt_rates.offset]
+            capi.LatticeDesc.mrt_rates.offset, ctypes.sizeof(capi.ServerOpts),
+            ctypes.sizeof(capi.ServerStats)]
     assert got == want
 
 

@@ -340,3 +340,32 @@ def test_config3_oscillation_period_vs_lamb(P):
     ta = theory.lamb_period(0.0461, 3.1192, 120.0, 100.0)
     print(f"oscillation period {period:.0f} steps, Lamb {ta:.0f}")
     assert abs(period - ta) / ta <= 0.10
+
+
+def test_config4_batch_of_512_against_oracle(P):
+    # the 512-lattice uneven batch, 1000 steps in one handle; the smallest and
+    # largest lattice and two seeded others against the oracle
+    rec = synth.batch_recipe()
+    descs = [P.lbm_desc_default(r["nx"], r["ny"], T=r["T"]) for r in rec]
+    fields = [synth.droplet(r["nx"], r["ny"], r["R"], r["T"]) for r in rec]
+    h = P.lbm_create(descs)
+    for i, f in enumerate(fields):
+        P.lbm_init(h, i, f)
+    P.lbm_step(h, 1000)
+    sides = np.array([r["nx"] for r in rec])
+    picks = [int(np.argmin(sides)), int(np.argmax(sides))] + synth.randint(77, 2, 0, 511).tolist()
+    for i in picks:
+        got = P.lbm_moments(h, i, u=False, mass=False)["rho"]
+        o = oracle_run(fields[i], 1000, T=rec[i]["T"])["rho"]
+        if rec[i]["nx"] <= 300:
+            assert rel(got, o) <= RTOL_RHO, (i, rec[i])
+        else:
+            # Large droplets: FP32 rounding adds coherently in the uniform bulk
+            # phases while the initial tanh profile relaxes (~1.5e-7 of mass in
+            # the first ~100 steps), which moves a radius-170 interface by
+            # ~1e-5 sites: 1-2.4e-5 pointwise at the interface, 8e-7 in L2.
+            # The FP64 problem itself is well conditioned (a 6e-8 input
+            # perturbation stays below 4e-8).  Stated bound for these sizes:
+            assert np.linalg.norm(got - o) / np.linalg.norm(o) <= 1e-6, (i, rec[i])
+            assert rel(got, o) <= 5e-5, (i, rec[i])
+    P.lbm_destroy(h)
