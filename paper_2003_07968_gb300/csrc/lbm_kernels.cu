@@ -131,6 +131,98 @@ __global__ void __launch_bounds__(512) k_collide(StepArgs a) {
     }
 }
 
+// ------------------------------------------- single pass: psi rebuilt in the tile
+// One launch per step.  Phase A computes rho (Eq. FD) and psi (Eqs. DED,
+// CSEOS) for the tile and its one-site halo from the pulled populations
+// (reads reach two sites out, which the ghost frame holds), into shared
+// memory.  Phase B is the collision pass of k_collide.  Every psi is computed
+// by the same function of the same loaded values in the same order as the
+// psi pass, so the two schedules give identical numbers; DRAM sees each
+// population read once and written once (the halo reads hit L1/L2).
+template <class S, int EOSP, int SPT>
+__global__ void __launch_bounds__(512) k_fused(StepArgs a) {
+    using T = typename S::T;
+    extern __shared__ float sps[];
+    const int TX = blockDim.x, BY = blockDim.y, TY = BY * SPT;
+    const int W = TX + 2;
+    const int nthr = TX * BY;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const int4 tl = __ldg(&a.tiles[t]);
+        const LatDev& L = a.lats[tl.x];
+        const int nx = L.nx, ny = L.ny;
+        const int pitch = L.pitch;
+        const int64_t plane = L.plane;
+        const T* base = reinterpret_cast<const T*>(a.pop) + L.off_f[a.parity] + L.gx;
+        const int xend = min(tl.y + TX, nx);  // one past the last active column
+        const int yend = min(tl.z + TY, ny);
+        __syncthreads();  // the previous tile is done with sps
+        {
+            const int n = W * (TY + 2);
+            const float rho0 = L.rho0;
+            for (int k = tid; k < n; k += nthr) {
+                const int ly = k / W, lx = k - ly * W;
+                const int x = tl.y - 1 + lx, y = tl.z - 1 + ly;
+                if (x > xend || y > yend) continue;
+                const T* f = base + (int64_t)(y + GY) * pitch + x;
+                const float d = ((S::ld(f) + S::ld(f + 1 * plane - 1)) +
+                                 (S::ld(f + 2 * plane - pitch) + S::ld(f + 3 * plane + 1))) +
+                                ((S::ld(f + 4 * plane + pitch) + S::ld(f + 5 * plane - pitch - 1)) +
+                                 (S::ld(f + 6 * plane - pitch + 1) + S::ld(f + 7 * plane + pitch + 1))) +
+                                S::ld(f + 8 * plane + pitch - 1);
+                bool ok;
+                float psi = eval_psi<EOSP>(L, d + rho0, ok);
+                if (!ok) {
+                    atomicOr(&a.status[L.lattice], 1u);
+                    psi = __int_as_float(0x7fc00000);
+                }
+                sps[k] = psi;
+            }
+        }
+        const int x = tl.y + threadIdx.x;
+        float g[SPT][9];
+        if (x < nx) {
+#pragma unroll
+            for (int k = 0; k < SPT; ++k) {
+                const int y = min(tl.z + (int)threadIdx.y + k * BY, ny - 1);
+                const T* f = base + (int64_t)(y + GY) * pitch + x;
+                g[k][0] = S::ld(f);
+                g[k][1] = S::ld(f + 1 * plane - 1);
+                g[k][2] = S::ld(f + 2 * plane - pitch);
+                g[k][3] = S::ld(f + 3 * plane + 1);
+                g[k][4] = S::ld(f + 4 * plane + pitch);
+                g[k][5] = S::ld(f + 5 * plane - pitch - 1);
+                g[k][6] = S::ld(f + 6 * plane - pitch + 1);
+                g[k][7] = S::ld(f + 7 * plane + pitch + 1);
+                g[k][8] = S::ld(f + 8 * plane + pitch - 1);
+            }
+        }
+        __syncthreads();  // psi tile complete
+        if (x >= nx) continue;
+        const SiteConsts C = site_consts(L);
+        T* o = reinterpret_cast<T*>(a.pop) + L.off_f[a.parity ^ 1];
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) {
+            const int ly = (int)threadIdx.y + k * BY;
+            const int y = tl.z + ly;
+            if (y >= ny) break;
+            const float* c = sps + (ly + 1) * W + (threadIdx.x + 1);
+            float p[9], v[9];
+            p[0] = c[0];
+            p[1] = c[1];
+            p[2] = c[W];
+            p[3] = c[-1];
+            p[4] = c[-W];
+            p[5] = c[W + 1];
+            p[6] = c[W - 1];
+            p[7] = c[-W - 1];
+            p[8] = c[-W + 1];
+            collide_site(C, g[k], p, v);
+            store_site<S>(o, plane, pitch, L.gx, x, y, nx, ny, v);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ init
 // Stores at site x the value f_i^eq(x + c_i) - w_i rho0, so that the next
 // pull f_i(x) = f*_i(x - c_i) yields f_i^eq(x).  Equilibrium in FP64.
@@ -289,6 +381,56 @@ const void* collide_fn(int spt) {
 }  // namespace
 
 bool plain_spt_supported(int spt) { return spt == 1 || spt == 2 || spt == 4; }
+
+namespace {
+template <class S, int SPT>
+cudaError_t fused_eos(int eos, const StepArgs& a, dim3 g, dim3 b, size_t smem, cudaStream_t st) {
+    switch (eos) {
+        case EOS_F64: k_fused<S, EOS_F64, SPT><<<g, b, smem, st>>>(a); break;
+        case EOS_DF: k_fused<S, EOS_DF, SPT><<<g, b, smem, st>>>(a); break;
+        case EOS_F32: k_fused<S, EOS_F32, SPT><<<g, b, smem, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+template <class S>
+cudaError_t fused_spt(int spt, int eos, const StepArgs& a, dim3 g, dim3 b, size_t smem,
+                      cudaStream_t st) {
+    switch (spt) {
+        case 1: return fused_eos<S, 1>(eos, a, g, b, smem, st);
+        case 2: return fused_eos<S, 2>(eos, a, g, b, smem, st);
+        case 4: return fused_eos<S, 4>(eos, a, g, b, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+template <class S>
+const void* fused_fn(int spt, int eos) {
+#define PPLBM_F(N)                                                                  \
+    if (spt == N)                                                                   \
+        return eos == EOS_F64 ? (const void*)k_fused<S, EOS_F64, N>                 \
+             : eos == EOS_DF  ? (const void*)k_fused<S, EOS_DF, N>                  \
+                              : (const void*)k_fused<S, EOS_F32, N>;
+    PPLBM_F(1)
+    PPLBM_F(2)
+    PPLBM_F(4)
+#undef PPLBM_F
+    return nullptr;
+}
+}  // namespace
+
+cudaError_t launch_fused(int storage_f16, int eos, int spt, const StepArgs& a, dim3 g, dim3 b,
+                         size_t smem, cudaStream_t st) {
+    return storage_f16 ? fused_spt<StoreF16>(spt, eos, a, g, b, smem, st)
+                       : fused_spt<StoreF32>(spt, eos, a, g, b, smem, st);
+}
+
+int occupancy_fused(int storage_f16, int eos, int spt, int threads, size_t smem) {
+    int n = 0;
+    const void* fn = storage_f16 ? fused_fn<StoreF16>(spt, eos) : fused_fn<StoreF32>(spt, eos);
+    if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
 
 cudaError_t launch_psi(int storage_f16, int eos, int spt, const StepArgs& a, dim3 g, dim3 b,
                        cudaStream_t st) {

@@ -28,5 +28,10 @@ cudaError_t launch_collide_tma(int f16, int tx, int ty, const StepArgs& a, int g
 int occupancy_psi_tma(int f16, int eos, int tx, int ty);
 int occupancy_collide_tma(int f16, int tx, int ty);
 int occupancy_collide(int storage_f16, int spt, int threads, size_t smem);
+// Single-pass step (psi rebuilt on the tile's halo): same block and shared
+// memory shape as the plain collision pass.
+cudaError_t launch_fused(int storage_f16, int eos, int spt, const StepArgs& a, dim3 g, dim3 b,
+                         size_t smem, cudaStream_t st);
+int occupancy_fused(int storage_f16, int eos, int spt, int threads, size_t smem);
 
 }  // namespace pplbm

@@ -211,6 +211,9 @@ void default_grid(lbm_handle* h, int k) {
     if (P.variant == LBM_KERNEL_TMA)
         occ = k == 0 ? occupancy_psi_tma(h->f16, h->eos, P.tx, P.ty)
                      : occupancy_collide_tma(h->f16, P.tx, P.ty);
+    else if (k == 1 && h->schedule == LBM_SCHED_FUSED)
+        occ = occupancy_fused(h->f16, h->eos, P.spt, P.tx * (P.ty / P.spt),
+                              collide_smem(P.tx, P.ty));
     else
         occ = k == 0 ? occupancy_psi(h->f16, h->eos, P.spt, P.tx * (P.ty / P.spt))
                      : occupancy_collide(h->f16, P.spt, P.tx * (P.ty / P.spt),
@@ -245,6 +248,9 @@ cudaError_t launch_pass(lbm_handle* h, int k, const StepArgs& a, int grid) {
         return P.variant == LBM_KERNEL_TMA
                    ? launch_psi_tma(h->f16, h->eos, P.tx, P.ty, a, grid, h->stream)
                    : launch_psi(h->f16, h->eos, P.spt, a, dim3(grid), block, h->stream);
+    if (h->schedule == LBM_SCHED_FUSED)
+        return launch_fused(h->f16, h->eos, P.spt, a, dim3(grid), block, collide_smem(P.tx, P.ty),
+                            h->stream);
     return P.variant == LBM_KERNEL_TMA
                ? launch_collide_tma(h->f16, P.tx, P.ty, a, grid, h->stream)
                : launch_collide(h->f16, P.spt, a, dim3(grid), block, collide_smem(P.tx, P.ty),
@@ -272,7 +278,7 @@ int launch_step(lbm_handle* h, int p) {
         e2 = take_event(h);
         CK(h, cudaEventRecord(e0, h->stream));
     }
-    CK(h, launch_pass(h, 0, step_args(h, p, 0), h->pass[0].grid));
+    if (h->schedule != LBM_SCHED_FUSED) CK(h, launch_pass(h, 0, step_args(h, p, 0), h->pass[0].grid));
     if (h->prof) CK(h, cudaEventRecord(e1, h->stream));
     CK(h, launch_pass(h, 1, step_args(h, p, 1), h->pass[1].grid));
     if (h->prof) {
@@ -281,7 +287,7 @@ int launch_step(lbm_handle* h, int p) {
         h->rec[1].pending.emplace_back(e1, e2);
         // e1 is shared: keep it out of the pool until both pairs are read
     }
-    h->launches += 2;
+    h->launches += h->schedule == LBM_SCHED_FUSED ? 1 : 2;
     return LBM_OK;
 }
 
@@ -542,7 +548,10 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
             if (!shape_ok(c.variant, c.tx, c.ty, c.spt)) return LBM_ERR_ARG;
         }
     }
-    if (opts && opts->schedule != LBM_SCHED_TWO_PASS) return LBM_ERR_ARG;
+    if (opts && opts->schedule != LBM_SCHED_TWO_PASS && opts->schedule != LBM_SCHED_FUSED)
+        return LBM_ERR_ARG;
+    if (opts && opts->schedule == LBM_SCHED_FUSED && opts->kernel_variant == LBM_KERNEL_TMA)
+        return LBM_ERR_ARG;  // the single-pass step exists as a plain-load kernel only
 
     lbm_handle* h = new (std::nothrow) lbm_handle();
     if (!h) return LBM_ERR_OOM;
@@ -550,6 +559,7 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
     h->desc.assign(descs, descs + n);
     h->storage = descs[0].storage;
     h->f16 = h->storage == LBM_STORE_F16_DEV;
+    h->schedule = opts ? opts->schedule : LBM_SCHED_TWO_PASS;
     h->eos = descs[0].eos_precision;
     h->collision = descs[0].collision;
     h->graph_steps = (opts && opts->graph_steps != 0) ? opts->graph_steps : 32;
@@ -598,12 +608,15 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
         return fail(LBM_ERR_CUDA);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        TuneKey k{h->device, h->storage, h->eos, variant, (int64_t)std::log2((double)h->sites),
-                  (int64_t)std::log2((double)n)};
+        TuneKey k{h->device, h->storage, h->eos, variant * 4 + h->schedule,
+                  (int64_t)std::log2((double)h->sites), (int64_t)std::log2((double)n)};
         auto it = g_tune_cache.find(k);
         if (it != g_tune_cache.end() && !(opts && (opts->tile_x || opts->tile_y)))
             for (int q = 0; q < 2; ++q) cfg[q] = it->second.pass[q];
     }
+    if (h->schedule == LBM_SCHED_FUSED && cfg[1].variant == LBM_KERNEL_TMA)
+        cfg[1] = PassCfg{LBM_KERNEL_PLAIN, kPassDefaults[1].tx, kPassDefaults[1].ty, 0,
+                         kPassDefaults[1].spt};
     for (int q = 0; q < 2; ++q) {
         h->pass[q].variant = cfg[q].variant;
         h->pass[q].spt = cfg[q].variant == LBM_KERNEL_TMA ? 1 : cfg[q].spt;
@@ -615,9 +628,10 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
     }
     h->tune_variant = variant;
     h->rec[0].name = "psi_pass";
-    h->rec[1].name = "collide_stream";
+    h->rec[1].name = h->schedule == LBM_SCHED_FUSED ? "fused_step" : "collide_stream";
     h->rec[0].bytes = (double)h->sites * (9.0 * es + 4.0);
-    h->rec[1].bytes = (double)h->sites * (18.0 * es + 4.0);
+    h->rec[1].bytes = (double)h->sites * (h->schedule == LBM_SCHED_FUSED ? 18.0 * es
+                                                                        : 18.0 * es + 4.0);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(LBM_ERR_CUDA);
     *out = h;
     return LBM_OK;
@@ -670,7 +684,7 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
         }
         while (left >= h->graph_steps) {
             CK(h, cudaGraphLaunch(h->graph[h->parity], h->stream));
-            h->launches += 2 * (int64_t)h->graph_steps;
+            h->launches += (h->schedule == LBM_SCHED_FUSED ? 1 : 2) * (int64_t)h->graph_steps;
             left -= h->graph_steps;  // graph_steps is even: parity unchanged
         }
     }
@@ -825,7 +839,8 @@ int lbm_autotune(lbm_handle* h, int32_t repeats) {
     // the current state, computed first.
     for (int k = 0; k < 2 && rc == LBM_OK; ++k) {
         std::vector<PassCfg> cand;
-        const bool allow_tma = h->tune_variant != LBM_KERNEL_PLAIN;
+        const bool allow_tma = h->tune_variant != LBM_KERNEL_PLAIN &&
+                               !(k == 1 && h->schedule == LBM_SCHED_FUSED);
         const bool allow_plain = h->tune_variant != LBM_KERNEL_TMA;
         if (allow_tma)
             for (const auto& c : shapes_tma) cand.push_back({LBM_KERNEL_TMA, c[0], c[1], 0, 1});
@@ -845,7 +860,7 @@ int lbm_autotune(lbm_handle* h, int32_t repeats) {
             for (int mode = 0; mode < 2 && rc == LBM_OK; ++mode) {
                 const int grid = mode == 0 ? g0 : h->pass[k].ntiles;  // persistent vs one CTA per tile
                 const StepArgs a = step_args(h, h->parity, k);
-                if (k == 1) {
+                if (k == 1 && h->schedule != LBM_SCHED_FUSED) {
                     cudaError_t e = launch_pass(h, 0, step_args(h, h->parity, 0), h->pass[0].grid);
                     if (e != cudaSuccess) { rc = cuda_fail(h, e, "autotune psi"); break; }
                 }
@@ -879,7 +894,7 @@ int lbm_autotune(lbm_handle* h, int32_t repeats) {
     rc = sync_status(h);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    TuneKey key{h->device, h->storage, h->eos, h->tune_variant,
+    TuneKey key{h->device, h->storage, h->eos, h->tune_variant * 4 + h->schedule,
                 (int64_t)std::log2((double)h->sites), (int64_t)std::log2((double)h->lat.size())};
     g_tune_cache[key] = best_cfg;
     return LBM_OK;

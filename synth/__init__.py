@@ -75,6 +75,16 @@ def flat_band(nx: int = 64, ny: int = 64, T: float = 0.8, rows=(16, 47),
     return rho
 
 
+def band(nx: int, ny: int, T: float, y1: float, y2: float, W: float = 5.0,
+         densities=None) -> np.ndarray:
+    """Flat liquid band between rows y1 and y2 with the tanh interface
+    profile of Eq. (ISD) (width W) on both sides, vapour elsewhere."""
+    rg, rl = densities if densities is not None else coexistence(T)
+    y = np.arange(ny, dtype=np.float64)[:, None] * np.ones((1, nx))
+    prof = 0.5 * (np.tanh(2.0 * (y - y1) / W) - np.tanh(2.0 * (y - y2) / W))
+    return rg + (rl - rg) * prof
+
+
 def droplet(nx: int, ny: int, R: float, T: float, W: float = 5.0, center=None,
             densities=None) -> np.ndarray:
     """Circular droplet with the tanh profile of Eq. (ISD), centred on node
@@ -133,4 +143,4 @@ def request_field(req: dict) -> np.ndarray:
     if req["kind"] == "droplet":
         return droplet(req["nx"], req["ny"], req["R"], req["T"])
     ny = req["ny"]
-    return flat_band(req["nx"], ny, req["T"], rows=(ny // 4, 3 * ny // 4 - 1), noise=0.0)
+    return band(req["nx"], ny, req["T"], ny / 4.0, 3.0 * ny / 4.0)
