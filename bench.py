@@ -45,6 +45,8 @@ def parse():
                     help="served workload: number of requests of the Poisson stream")
     ap.add_argument("--step-scale", type=int, default=100,
                     help="served workload: divide each request's step count by this")
+    ap.add_argument("--target-sites", type=int, default=0,
+                    help="served workload: resident-site target of the server (0: default)")
     ap.add_argument("--eos", default="df", choices=["f64", "df", "f32"],
                     help="arithmetic of psi/EOS: float-float (default), native FP64 or FP32")
     ap.add_argument("--variant", default="auto", choices=["auto", "tma", "plain"])
@@ -501,6 +503,8 @@ def run_served(args):
 
     opts = P.lbm_server_opts_default(arena_bytes=64 << 30, chunk_steps=50, storage=storage,
                                      max_resident=1024)
+    if args.target_sites:
+        opts.target_resident_sites = args.target_sites
     srv = P.lbm_server_create(opts)
     tickets = [None] * len(reqs)
     t_start = time.perf_counter()
@@ -566,7 +570,8 @@ def run_served(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"served: {len(reqs)} requests, Poisson 200/s, sides U{{128..2048}}, "
                                   f"steps U{{1000..50000}}/{args.step_scale}, droplet/band 50/50",
-                      "storage": args.storage, "chunk_steps": 50, "site_steps": work},
+                      "storage": args.storage, "chunk_steps": 50, "site_steps": work,
+                      "target_resident_sites": opts.target_resident_sites},
            "served": {"MLUPS": round(served, 1), "p50_s": round(pct(lat, 50), 4),
                       "p99_s": round(pct(lat, 99), 4), "wall_s": round(wall, 3),
                       "gpu_busy_s": round(stats["busy_s"], 3),

@@ -129,8 +129,10 @@ void lbm_desc_default(lbm_lattice_desc* d, int32_t nx, int32_t ny);
 /* Create a handle over n_lattices independent lattices (n_lattices = 1: one
  * lattice; > 1: a batch stepped together in persistent launches over one tile
  * list).  All lattices of a handle share storage, eos_precision, collision
- * and m2_trace_variant; tau, G, eps, sigma, T, EOS constants and rho0 may
- * differ per lattice.  Allocates all device memory now.
+ * and m2_trace_variant; tau, G, eps, sigma, T, EOS constants, rho0 and the
+ * MRT rates may differ per lattice.  MRT runs in the plain-load kernels only
+ * (kernel_variant LBM_KERNEL_TMA with MRT is refused).  Allocates all device
+ * memory now.
  * Errors: LBM_ERR_ARG (bad sizes/params, mixed storage), LBM_ERR_OOM,
  * LBM_ERR_CUDA.  *out is NULL on error. */
 int lbm_create(const lbm_lattice_desc* descs, int32_t n_lattices,
@@ -225,8 +227,10 @@ int lbm_autotune(lbm_handle* h, int32_t repeats);
  * lattice (the same kernels as a batch handle).  Requests are admitted at
  * chunk boundaries, first come first served but skipping any that do not
  * fit yet, whenever a slot and arena space (HBM footprint: both population
- * buffers plus psi) are free; a finished lattice's moments are copied out and
- * its space is reused at once.  One native worker thread drives the GPU; the
+ * buffers plus psi) are free and the resident sites stay below a target; a
+ * chunk runs each lattice for min(chunk_steps, its remaining steps); a
+ * finished lattice's moments are copied out while the next chunk runs, and
+ * its space is then reused.  One native worker thread drives the GPU; the
  * submit and poll calls are thread-safe and never wait for the GPU.  The
  * numerics of a request do not depend on what else is resident. */
 typedef struct lbm_server lbm_server;
@@ -236,9 +240,13 @@ typedef struct {
     int32_t max_resident;     /* resident lattices at most (0: 1024)              */
     int32_t chunk_steps;      /* steps between admission points (0: 100)          */
     int64_t max_request_sites;/* largest nx*ny accepted (0: 2048*2048)            */
+    int64_t target_resident_sites; /* admit while resident sites stay below this
+                                 (0: 16 Mi); enough to keep the GPU busy,
+                                 small enough to keep latency close to FIFO      */
     int32_t storage;          /* LBM_STORE_* of every request                     */
     int32_t eos_precision;    /* LBM_EOS_* of every request                       */
-    int32_t kernel_variant;   /* LBM_KERNEL_* (AUTO: the measured defaults)       */
+    int32_t kernel_variant;   /* LBM_KERNEL_AUTO or LBM_KERNEL_PLAIN (the server's
+                                 chunks need the plain-load kernels)             */
     int32_t tile_x, tile_y;   /* 0: defaults; else both passes, one site/thread   */
 } lbm_server_opts;
 
@@ -258,8 +266,8 @@ void lbm_server_opts_default(lbm_server_opts* o);
  * Errors: LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA. */
 int lbm_server_create(const lbm_server_opts* opts, lbm_server** out);
 
-/* Queue one solve: a lattice `d` (its storage and eos_precision are replaced
- * by the server's), initial density rho (host [ny][nx] FP64, copied before
+/* Queue one solve: a BGK lattice `d` (its storage and eos_precision are
+ * replaced by the server's), initial density rho (host [ny][nx] FP64, copied before
  * return, u = 0), nsteps >= 1 time steps.  Thread-safe; never waits for the
  * GPU.  *ticket identifies the request.  Errors: LBM_ERR_ARG (bad desc or
  * nsteps), LBM_ERR_CAPACITY (the lattice can never fit: larger than the

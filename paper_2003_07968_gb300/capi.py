@@ -76,7 +76,7 @@ class ServerOpts(ctypes.Structure):
 
     _fields_ = [("arena_bytes", ctypes.c_size_t), ("max_resident", ctypes.c_int32),
                 ("chunk_steps", ctypes.c_int32), ("max_request_sites", ctypes.c_int64),
-                ("storage", ctypes.c_int32), ("eos_precision", ctypes.c_int32),
+                ("target_resident_sites", ctypes.c_int64), ("storage", ctypes.c_int32), ("eos_precision", ctypes.c_int32),
                 ("kernel_variant", ctypes.c_int32), ("tile_x", ctypes.c_int32),
                 ("tile_y", ctypes.c_int32)]
 

@@ -78,6 +78,10 @@ struct StepArgs {
     uint32_t* status;   // per-lattice fault bits: 1 psi undefined, 2 copy wait timed out,
                         // 4 a staging copy broke the alignment rules (skipped)
     int parity;         // which population buffer holds the current state
+    // optional per-lattice step quotas (server chunks): tiles of a lattice with
+    // step >= quota[lattice] are skipped; nullptr for handles
+    const int* quota;
+    int step;
 };
 
 // ---- storage traits ---------------------------------------------------------
@@ -341,6 +345,72 @@ __device__ __forceinline__ void collide_site(const SiteConsts& C, const float g[
     PPLBM_PAIR(6, 8, 1.f / 36.f, gd, uy - ux, F.y - F.x)
 #undef PPLBM_PAIR
     o[0] = drho - s1;
+}
+
+// MRT collision (Eq. MRTCO) with Guo forcing in moment space (Eq. GFSMRT),
+// for the Gram-Schmidt matrix M of Appendix A.  Same inputs and outputs as
+// collide_site.  Moments of the stored deviations: m(f) = M g + rho0 M w with
+// M w = (1, -2, 1, 0, ..., 0).  Post-collision moments
+//   m* = m - Lambda (m - m^eq) + (I - Lambda/2) M S
+// with m^eq and M S the vectors printed in Appendix A (rho u is the
+// force-shifted momentum of Eq. FMD).  Back to populations with
+// M^-1 = M^T D^-1, D = diag(9, 36, 36, 6, 12, 6, 12, 4, 4) (the rows of M
+// are orthogonal); the rest population again from mass conservation.
+__device__ __forceinline__ void collide_site_mrt(const SiteConsts& C, const float* s,
+                                                 const float g[9], const float p[9],
+                                                 float o[9]) {
+    const float drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    const float rho = drho + C.rho0;
+    const float jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+    const float jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+    LatDev dummy;
+    dummy.k_sc = C.k_sc;
+    dummy.k1 = C.k1;
+    dummy.k2 = C.k2;
+    dummy.m2_variant = C.m2v;
+    const Force F = site_force(dummy, p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], p[8]);
+    const float inv = __frcp_rn(rho);
+    const float rux = fmaf(0.5f, F.x, jx), ruy = fmaf(0.5f, F.y, jy);  // rho u, Eq. (FMD)
+    const float ux = rux * inv, uy = ruy * inv;
+    const float usq = ux * ux + uy * uy;
+    const float uF = ux * F.x + uy * F.y;
+    // moments of f (deviations shifted by rho0 M w)
+    const float sa = (g[1] + g[2]) + (g[3] + g[4]), sd = (g[5] + g[6]) + (g[7] + g[8]);
+    const float m1 = (-4.f * g[0] - sa + 2.f * sd) - 2.f * C.rho0;
+    const float m2 = (4.f * g[0] - 2.f * sa + sd) + C.rho0;
+    const float m4 = (-2.f * g[1] + 2.f * g[3]) + ((g[5] - g[6]) + (g[8] - g[7]));
+    const float m6 = (-2.f * g[2] + 2.f * g[4]) + ((g[5] + g[6]) - (g[7] + g[8]));
+    const float m7 = (g[1] - g[2]) + (g[3] - g[4]);
+    const float m8 = (g[5] - g[6]) + (g[7] - g[8]);
+    // m* = m - s (m - meq) + (1 - s/2) Sbar, component by component
+    const float r3u2 = 3.f * rho * usq;
+    const float p1 = m1 - s[1] * (m1 - (-2.f * rho + r3u2)) + (1.f - 0.5f * s[1]) * (6.f * uF);
+    const float p2 = m2 - s[2] * (m2 - (rho - r3u2)) + (1.f - 0.5f * s[2]) * (-6.f * uF);
+    const float p3 = jx - s[3] * (jx - rux) + (1.f - 0.5f * s[3]) * F.x;
+    const float p4 = m4 - s[4] * (m4 + rux) + (1.f - 0.5f * s[4]) * (-F.x);
+    const float p5 = jy - s[5] * (jy - ruy) + (1.f - 0.5f * s[5]) * F.y;
+    const float p6 = m6 - s[6] * (m6 + ruy) + (1.f - 0.5f * s[6]) * (-F.y);
+    const float p7 = m7 - s[7] * (m7 - rho * (ux * ux - uy * uy)) +
+                     (1.f - 0.5f * s[7]) * (2.f * (ux * F.x - uy * F.y));
+    const float p8 = m8 - s[8] * (m8 - rho * ux * uy) + (1.f - 0.5f * s[8]) * (ux * F.y + uy * F.x);
+    // back to deviations: subtract rho0 M w from the moments, then M^T D^-1
+    const float q0 = drho * (1.f / 9.f);
+    const float q1 = (p1 + 2.f * C.rho0) * (1.f / 36.f);
+    const float q2 = (p2 - C.rho0) * (1.f / 36.f);
+    const float q3 = p3 * (1.f / 6.f), q4 = p4 * (1.f / 12.f);
+    const float q5 = p5 * (1.f / 6.f), q6 = p6 * (1.f / 12.f);
+    const float q7 = p7 * 0.25f, q8 = p8 * 0.25f;
+    const float ax = q0 - q1 - 2.f * q2;  // common part of the axis directions
+    const float dg = q0 + 2.f * q1 + q2;  // common part of the diagonals
+    o[1] = ax + q3 - 2.f * q4 + q7;
+    o[2] = ax + q5 - 2.f * q6 - q7;
+    o[3] = ax - q3 + 2.f * q4 + q7;
+    o[4] = ax - q5 + 2.f * q6 - q7;
+    o[5] = dg + q3 + q4 + q5 + q6 + q8;
+    o[6] = dg - q3 - q4 + q5 + q6 - q8;
+    o[7] = dg - q3 - q4 - q5 - q6 + q8;
+    o[8] = dg + q3 + q4 - q5 - q6 - q8;
+    o[0] = drho - (((o[1] + o[2]) + (o[3] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
 }
 
 // Store the nine outputs of site (x, y): interior sites with plain stores,

@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(512) k_psi(StepArgs a) {
     using T = typename S::T;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const int4 tl = __ldg(&a.tiles[t]);
+        if (a.quota && a.step >= __ldg(&a.quota[tl.x])) continue;
         const LatDev& L = a.lats[tl.x];
         const int nx = L.nx, ny = L.ny;
         const int x = tl.y + threadIdx.x;
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(512) k_psi(StepArgs a) {
 }
 
 // --------------------------------------------- pass 2: force + collide + store
-template <class S, int SPT>
+template <class S, int SPT, bool MRT>
 __global__ void __launch_bounds__(512) k_collide(StepArgs a) {
     using T = typename S::T;
     extern __shared__ float sps[];
@@ -69,6 +70,7 @@ __global__ void __launch_bounds__(512) k_collide(StepArgs a) {
     const int tid = threadIdx.y * TX + threadIdx.x;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const int4 tl = __ldg(&a.tiles[t]);
+        if (a.quota && a.step >= __ldg(&a.quota[tl.x])) continue;  // uniform per block
         const LatDev& L = a.lats[tl.x];
         const int nx = L.nx, ny = L.ny;
         const int xend = min(tl.y + TX, nx);  // one past the last active column
@@ -125,21 +127,46 @@ __global__ void __launch_bounds__(512) k_collide(StepArgs a) {
             p[6] = c[W - 1];
             p[7] = c[-W - 1];
             p[8] = c[-W + 1];
-            collide_site(C, g[k], p, v);
+            if (MRT)
+                collide_site_mrt(C, L.mrt_s, g[k], p, v);
+            else
+                collide_site(C, g[k], p, v);
             store_site<S>(o, plane, pitch, L.gx, x, y, nx, ny, v);
         }
     }
 }
 
 // ------------------------------------------- single pass: psi rebuilt in the tile
-// One launch per step.  Phase A computes rho (Eq. FD) and psi (Eqs. DED,
-// CSEOS) for the tile and its one-site halo from the pulled populations
-// (reads reach two sites out, which the ghost frame holds), into shared
-// memory.  Phase B is the collision pass of k_collide.  Every psi is computed
-// by the same function of the same loaded values in the same order as the
-// psi pass, so the two schedules give identical numbers; DRAM sees each
-// population read once and written once (the halo reads hit L1/L2).
-template <class S, int EOSP, int SPT>
+// One launch per step.  Each thread pulls the populations of its own sites
+// (kept in registers for the collision), computes rho (Eq. FD) and psi
+// (Eqs. DED, CSEOS) from them and writes psi to shared memory; the first
+// threads of the block also compute psi on the one-site ring around the
+// tile (pulling from up to two sites out, which the ghost frame holds).
+// After one barrier the collision runs as in k_collide.  Every psi is the
+// same function of the same loaded values in the same order as in the psi
+// pass, so both schedules give the same numbers; DRAM sees each population
+// read once and written once.
+template <class S, int EOSP>
+__device__ __forceinline__ float ring_psi(const StepArgs& a, const LatDev& L,
+                                          const typename S::T* base, int x, int y) {
+    const int pitch = L.pitch;
+    const int64_t plane = L.plane;
+    const typename S::T* f = base + (int64_t)(y + GY) * pitch + x;
+    const float d = ((S::ld(f) + S::ld(f + 1 * plane - 1)) +
+                     (S::ld(f + 2 * plane - pitch) + S::ld(f + 3 * plane + 1))) +
+                    ((S::ld(f + 4 * plane + pitch) + S::ld(f + 5 * plane - pitch - 1)) +
+                     (S::ld(f + 6 * plane - pitch + 1) + S::ld(f + 7 * plane + pitch + 1))) +
+                    S::ld(f + 8 * plane + pitch - 1);
+    bool ok;
+    float psi = eval_psi<EOSP>(L, d + L.rho0, ok);
+    if (!ok) {
+        atomicOr(&a.status[L.lattice], 1u);
+        psi = __int_as_float(0x7fc00000);
+    }
+    return psi;
+}
+
+template <class S, int EOSP, int SPT, bool MRT>
 __global__ void __launch_bounds__(512) k_fused(StepArgs a) {
     using T = typename S::T;
     extern __shared__ float sps[];
@@ -147,8 +174,10 @@ __global__ void __launch_bounds__(512) k_fused(StepArgs a) {
     const int W = TX + 2;
     const int nthr = TX * BY;
     const int tid = threadIdx.y * TX + threadIdx.x;
+    const int nring = 2 * (TX + TY) + 4;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const int4 tl = __ldg(&a.tiles[t]);
+        if (a.quota && a.step >= __ldg(&a.quota[tl.x])) continue;  // uniform per block
         const LatDev& L = a.lats[tl.x];
         const int nx = L.nx, ny = L.ny;
         const int pitch = L.pitch;
@@ -157,28 +186,6 @@ __global__ void __launch_bounds__(512) k_fused(StepArgs a) {
         const int xend = min(tl.y + TX, nx);  // one past the last active column
         const int yend = min(tl.z + TY, ny);
         __syncthreads();  // the previous tile is done with sps
-        {
-            const int n = W * (TY + 2);
-            const float rho0 = L.rho0;
-            for (int k = tid; k < n; k += nthr) {
-                const int ly = k / W, lx = k - ly * W;
-                const int x = tl.y - 1 + lx, y = tl.z - 1 + ly;
-                if (x > xend || y > yend) continue;
-                const T* f = base + (int64_t)(y + GY) * pitch + x;
-                const float d = ((S::ld(f) + S::ld(f + 1 * plane - 1)) +
-                                 (S::ld(f + 2 * plane - pitch) + S::ld(f + 3 * plane + 1))) +
-                                ((S::ld(f + 4 * plane + pitch) + S::ld(f + 5 * plane - pitch - 1)) +
-                                 (S::ld(f + 6 * plane - pitch + 1) + S::ld(f + 7 * plane + pitch + 1))) +
-                                S::ld(f + 8 * plane + pitch - 1);
-                bool ok;
-                float psi = eval_psi<EOSP>(L, d + rho0, ok);
-                if (!ok) {
-                    atomicOr(&a.status[L.lattice], 1u);
-                    psi = __int_as_float(0x7fc00000);
-                }
-                sps[k] = psi;
-            }
-        }
         const int x = tl.y + threadIdx.x;
         float g[SPT][9];
         if (x < nx) {
@@ -195,6 +202,44 @@ __global__ void __launch_bounds__(512) k_fused(StepArgs a) {
                 g[k][6] = S::ld(f + 6 * plane - pitch + 1);
                 g[k][7] = S::ld(f + 7 * plane + pitch + 1);
                 g[k][8] = S::ld(f + 8 * plane + pitch - 1);
+            }
+        }
+        // the ring around the tile: (x0-1 .. xend) x {y0-1, yend} and
+        // {x0-1, xend} x (y0 .. yend-1), as far as the active region reaches
+        for (int r = tid; r < nring; r += nthr) {
+            int lx, ly;
+            if (r < W) {
+                lx = r;
+                ly = 0;
+            } else if (r < 2 * W) {
+                lx = r - W;
+                ly = TY + 1;
+            } else {
+                const int q = r - 2 * W;  // 2 * TY side cells
+                lx = (q & 1) ? TX + 1 : 0;
+                ly = 1 + (q >> 1);
+            }
+            int gx = tl.y - 1 + lx, gy = tl.z - 1 + ly;
+            // the right/bottom ring of a ragged tile sits at the active edge
+            if (lx == TX + 1) gx = xend;
+            if (ly == TY + 1) gy = yend;
+            if (gx > xend || gy > yend) continue;
+            sps[(gy - tl.z + 1) * W + (gx - tl.y + 1)] = ring_psi<S, EOSP>(a, L, base, gx, gy);
+        }
+        if (x < nx) {
+#pragma unroll
+            for (int k = 0; k < SPT; ++k) {
+                const int ly = (int)threadIdx.y + k * BY;
+                if (tl.z + ly >= ny) break;
+                const float d = ((g[k][0] + g[k][1]) + (g[k][2] + g[k][3])) +
+                                ((g[k][4] + g[k][5]) + (g[k][6] + g[k][7])) + g[k][8];
+                bool ok;
+                float psi = eval_psi<EOSP>(L, d + L.rho0, ok);
+                if (!ok) {
+                    atomicOr(&a.status[L.lattice], 1u);
+                    psi = __int_as_float(0x7fc00000);
+                }
+                sps[(ly + 1) * W + (threadIdx.x + 1)] = psi;
             }
         }
         __syncthreads();  // psi tile complete
@@ -217,15 +262,20 @@ __global__ void __launch_bounds__(512) k_fused(StepArgs a) {
             p[6] = c[W - 1];
             p[7] = c[-W - 1];
             p[8] = c[-W + 1];
-            collide_site(C, g[k], p, v);
+            if (MRT)
+                collide_site_mrt(C, L.mrt_s, g[k], p, v);
+            else
+                collide_site(C, g[k], p, v);
             store_site<S>(o, plane, pitch, L.gx, x, y, nx, ny, v);
         }
     }
 }
 
 // ------------------------------------------------------------------ init
-// Stores at site x the value f_i^eq(x + c_i) - w_i rho0, so that the next
-// pull f_i(x) = f*_i(x - c_i) yields f_i^eq(x).  Equilibrium in FP64.
+// The value f_i^eq(x) (FP64, then rounded to the storage type as a deviation
+// from w_i rho0) is stored at x - c_i, so that the next pull
+// f_i(x) = f*_i(x - c_i) yields f_i^eq(x).  Each thread computes the
+// equilibrium of its own site once and scatters the nine values.
 template <class S>
 __global__ void k_init(LatDev L, void* pop, int parity, const double* rho, const double* ux,
                        const double* uy) {
@@ -237,18 +287,18 @@ __global__ void k_init(LatDev L, void* pop, int parity, const double* rho, const
     T* o = reinterpret_cast<T*>(pop) + L.off_f[parity];
     const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
                          1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    const int64_t s = (int64_t)y * nx + x;
+    const double r = rho[s];
+    const double vx = ux ? ux[s] : 0.0, vy = uy ? uy[s] : 0.0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        int sx = x + kCx[i], sy = y + kCy[i];
-        sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
-        sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-        const int64_t s = (int64_t)sy * nx + sx;
-        const double r = rho[s];
-        const double vx = ux ? ux[s] : 0.0, vy = uy ? uy[s] : 0.0;
         const double cu = kCx[i] * vx + kCy[i] * vy;
         const double feq = w[i] * (r + r * (3.0 * cu + 4.5 * cu * cu - 1.5 * (vx * vx + vy * vy)));
         const double g = feq - w[i] * (double)L.rho0;
-        store_img(o + i * L.plane, L.pitch, L.gx, x, y, nx, ny, S::cv((float)g));
+        int tx = x - kCx[i], ty = y - kCy[i];
+        tx = tx < 0 ? tx + nx : (tx >= nx ? tx - nx : tx);
+        ty = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
+        store_img(o + i * L.plane, L.pitch, L.gx, tx, ty, nx, ny, S::cv((float)g));
     }
 }
 
@@ -348,13 +398,13 @@ cudaError_t psi_spt(int spt, int eos, const StepArgs& a, dim3 g, dim3 b, cudaStr
         default: return cudaErrorInvalidValue;
     }
 }
-template <class S>
+template <class S, bool MRT>
 cudaError_t collide_spt(int spt, const StepArgs& a, dim3 g, dim3 b, size_t smem,
                         cudaStream_t st) {
     switch (spt) {
-        case 1: k_collide<S, 1><<<g, b, smem, st>>>(a); break;
-        case 2: k_collide<S, 2><<<g, b, smem, st>>>(a); break;
-        case 4: k_collide<S, 4><<<g, b, smem, st>>>(a); break;
+        case 1: k_collide<S, 1, MRT><<<g, b, smem, st>>>(a); break;
+        case 2: k_collide<S, 2, MRT><<<g, b, smem, st>>>(a); break;
+        case 4: k_collide<S, 4, MRT><<<g, b, smem, st>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -372,44 +422,44 @@ const void* psi_fn(int spt, int eos) {
 #undef PPLBM_F
     return nullptr;
 }
-template <class S>
+template <class S, bool MRT>
 const void* collide_fn(int spt) {
-    return spt == 1 ? (const void*)k_collide<S, 1>
-         : spt == 2 ? (const void*)k_collide<S, 2>
-         : spt == 4 ? (const void*)k_collide<S, 4> : nullptr;
+    return spt == 1 ? (const void*)k_collide<S, 1, MRT>
+         : spt == 2 ? (const void*)k_collide<S, 2, MRT>
+         : spt == 4 ? (const void*)k_collide<S, 4, MRT> : nullptr;
 }
 }  // namespace
 
 bool plain_spt_supported(int spt) { return spt == 1 || spt == 2 || spt == 4; }
 
 namespace {
-template <class S, int SPT>
+template <class S, int SPT, bool MRT>
 cudaError_t fused_eos(int eos, const StepArgs& a, dim3 g, dim3 b, size_t smem, cudaStream_t st) {
     switch (eos) {
-        case EOS_F64: k_fused<S, EOS_F64, SPT><<<g, b, smem, st>>>(a); break;
-        case EOS_DF: k_fused<S, EOS_DF, SPT><<<g, b, smem, st>>>(a); break;
-        case EOS_F32: k_fused<S, EOS_F32, SPT><<<g, b, smem, st>>>(a); break;
+        case EOS_F64: k_fused<S, EOS_F64, SPT, MRT><<<g, b, smem, st>>>(a); break;
+        case EOS_DF: k_fused<S, EOS_DF, SPT, MRT><<<g, b, smem, st>>>(a); break;
+        case EOS_F32: k_fused<S, EOS_F32, SPT, MRT><<<g, b, smem, st>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
-template <class S>
+template <class S, bool MRT>
 cudaError_t fused_spt(int spt, int eos, const StepArgs& a, dim3 g, dim3 b, size_t smem,
                       cudaStream_t st) {
     switch (spt) {
-        case 1: return fused_eos<S, 1>(eos, a, g, b, smem, st);
-        case 2: return fused_eos<S, 2>(eos, a, g, b, smem, st);
-        case 4: return fused_eos<S, 4>(eos, a, g, b, smem, st);
+        case 1: return fused_eos<S, 1, MRT>(eos, a, g, b, smem, st);
+        case 2: return fused_eos<S, 2, MRT>(eos, a, g, b, smem, st);
+        case 4: return fused_eos<S, 4, MRT>(eos, a, g, b, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
-template <class S>
+template <class S, bool MRT>
 const void* fused_fn(int spt, int eos) {
 #define PPLBM_F(N)                                                                  \
     if (spt == N)                                                                   \
-        return eos == EOS_F64 ? (const void*)k_fused<S, EOS_F64, N>                 \
-             : eos == EOS_DF  ? (const void*)k_fused<S, EOS_DF, N>                  \
-                              : (const void*)k_fused<S, EOS_F32, N>;
+        return eos == EOS_F64 ? (const void*)k_fused<S, EOS_F64, N, MRT>            \
+             : eos == EOS_DF  ? (const void*)k_fused<S, EOS_DF, N, MRT>             \
+                              : (const void*)k_fused<S, EOS_F32, N, MRT>;
     PPLBM_F(1)
     PPLBM_F(2)
     PPLBM_F(4)
@@ -418,15 +468,21 @@ const void* fused_fn(int spt, int eos) {
 }
 }  // namespace
 
-cudaError_t launch_fused(int storage_f16, int eos, int spt, const StepArgs& a, dim3 g, dim3 b,
-                         size_t smem, cudaStream_t st) {
-    return storage_f16 ? fused_spt<StoreF16>(spt, eos, a, g, b, smem, st)
-                       : fused_spt<StoreF32>(spt, eos, a, g, b, smem, st);
+cudaError_t launch_fused(int storage_f16, int mrt, int eos, int spt, const StepArgs& a, dim3 g,
+                         dim3 b, size_t smem, cudaStream_t st) {
+    if (mrt)
+        return storage_f16 ? fused_spt<StoreF16, true>(spt, eos, a, g, b, smem, st)
+                           : fused_spt<StoreF32, true>(spt, eos, a, g, b, smem, st);
+    return storage_f16 ? fused_spt<StoreF16, false>(spt, eos, a, g, b, smem, st)
+                       : fused_spt<StoreF32, false>(spt, eos, a, g, b, smem, st);
 }
 
-int occupancy_fused(int storage_f16, int eos, int spt, int threads, size_t smem) {
+int occupancy_fused(int storage_f16, int mrt, int eos, int spt, int threads, size_t smem) {
     int n = 0;
-    const void* fn = storage_f16 ? fused_fn<StoreF16>(spt, eos) : fused_fn<StoreF32>(spt, eos);
+    const void* fn = mrt ? (storage_f16 ? fused_fn<StoreF16, true>(spt, eos)
+                                        : fused_fn<StoreF32, true>(spt, eos))
+                         : (storage_f16 ? fused_fn<StoreF16, false>(spt, eos)
+                                        : fused_fn<StoreF32, false>(spt, eos));
     if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
@@ -438,10 +494,13 @@ cudaError_t launch_psi(int storage_f16, int eos, int spt, const StepArgs& a, dim
                        : psi_spt<StoreF32>(spt, eos, a, g, b, st);
 }
 
-cudaError_t launch_collide(int storage_f16, int spt, const StepArgs& a, dim3 g, dim3 b,
-                           size_t smem, cudaStream_t st) {
-    return storage_f16 ? collide_spt<StoreF16>(spt, a, g, b, smem, st)
-                       : collide_spt<StoreF32>(spt, a, g, b, smem, st);
+cudaError_t launch_collide(int storage_f16, int mrt, int spt, const StepArgs& a, dim3 g,
+                           dim3 b, size_t smem, cudaStream_t st) {
+    if (mrt)
+        return storage_f16 ? collide_spt<StoreF16, true>(spt, a, g, b, smem, st)
+                           : collide_spt<StoreF32, true>(spt, a, g, b, smem, st);
+    return storage_f16 ? collide_spt<StoreF16, false>(spt, a, g, b, smem, st)
+                       : collide_spt<StoreF32, false>(spt, a, g, b, smem, st);
 }
 
 cudaError_t launch_init(int storage_f16, const LatDev& L, void* pop, int parity,
@@ -487,9 +546,12 @@ int occupancy_psi(int storage_f16, int eos, int spt, int threads) {
     return n > 0 ? n : 1;
 }
 
-int occupancy_collide(int storage_f16, int spt, int threads, size_t smem) {
+int occupancy_collide(int storage_f16, int mrt, int spt, int threads, size_t smem) {
     int n = 0;
-    const void* fn = storage_f16 ? collide_fn<StoreF16>(spt) : collide_fn<StoreF32>(spt);
+    const void* fn = mrt ? (storage_f16 ? collide_fn<StoreF16, true>(spt)
+                                        : collide_fn<StoreF32, true>(spt))
+                         : (storage_f16 ? collide_fn<StoreF16, false>(spt)
+                                        : collide_fn<StoreF32, false>(spt));
     if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;

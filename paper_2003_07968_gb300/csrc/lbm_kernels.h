@@ -8,8 +8,8 @@ namespace pplbm {
 bool plain_spt_supported(int spt);
 cudaError_t launch_psi(int storage_f16, int eos, int spt, const StepArgs& a, dim3 g, dim3 b,
                        cudaStream_t st);
-cudaError_t launch_collide(int storage_f16, int spt, const StepArgs& a, dim3 g, dim3 b,
-                           size_t smem, cudaStream_t st);
+cudaError_t launch_collide(int storage_f16, int mrt, int spt, const StepArgs& a, dim3 g,
+                           dim3 b, size_t smem, cudaStream_t st);
 cudaError_t launch_init(int storage_f16, const LatDev& L, void* pop, int parity,
                         const double* rho, const double* ux, const double* uy,
                         cudaStream_t st);
@@ -27,11 +27,11 @@ cudaError_t launch_collide_tma(int f16, int tx, int ty, const StepArgs& a, int g
                                cudaStream_t st);
 int occupancy_psi_tma(int f16, int eos, int tx, int ty);
 int occupancy_collide_tma(int f16, int tx, int ty);
-int occupancy_collide(int storage_f16, int spt, int threads, size_t smem);
+int occupancy_collide(int storage_f16, int mrt, int spt, int threads, size_t smem);
 // Single-pass step (psi rebuilt on the tile's halo): same block and shared
 // memory shape as the plain collision pass.
-cudaError_t launch_fused(int storage_f16, int eos, int spt, const StepArgs& a, dim3 g, dim3 b,
-                         size_t smem, cudaStream_t st);
-int occupancy_fused(int storage_f16, int eos, int spt, int threads, size_t smem);
+cudaError_t launch_fused(int storage_f16, int mrt, int eos, int spt, const StepArgs& a, dim3 g,
+                         dim3 b, size_t smem, cudaStream_t st);
+int occupancy_fused(int storage_f16, int mrt, int eos, int spt, int threads, size_t smem);
 
 }  // namespace pplbm

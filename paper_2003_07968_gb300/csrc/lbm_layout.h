@@ -77,7 +77,12 @@ inline int validate_desc(const lbm_lattice_desc& d, std::string& why) {
         return why = "unknown eos_precision", LBM_ERR_ARG;
     if (d.m2_trace_variant != 0 && d.m2_trace_variant != 1)
         return why = "m2_trace_variant must be 0 or 1", LBM_ERR_ARG;
-    if (d.collision != LBM_COLL_BGK) return why = "only BGK collision is built", LBM_ERR_ARG;
+    if (d.collision != LBM_COLL_BGK && d.collision != LBM_COLL_MRT)
+        return why = "unknown collision", LBM_ERR_ARG;
+    if (d.collision == LBM_COLL_MRT)
+        for (int i = 0; i < 9; ++i)
+            if (!(d.mrt_rates[i] > 0.0 && d.mrt_rates[i] < 2.0))
+                return why = "MRT rates must lie in (0, 2)", LBM_ERR_ARG;
     return LBM_OK;
 }
 

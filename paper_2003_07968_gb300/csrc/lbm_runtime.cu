@@ -212,11 +212,11 @@ void default_grid(lbm_handle* h, int k) {
         occ = k == 0 ? occupancy_psi_tma(h->f16, h->eos, P.tx, P.ty)
                      : occupancy_collide_tma(h->f16, P.tx, P.ty);
     else if (k == 1 && h->schedule == LBM_SCHED_FUSED)
-        occ = occupancy_fused(h->f16, h->eos, P.spt, P.tx * (P.ty / P.spt),
+        occ = occupancy_fused(h->f16, h->collision == LBM_COLL_MRT, h->eos, P.spt, P.tx * (P.ty / P.spt),
                               collide_smem(P.tx, P.ty));
     else
         occ = k == 0 ? occupancy_psi(h->f16, h->eos, P.spt, P.tx * (P.ty / P.spt))
-                     : occupancy_collide(h->f16, P.spt, P.tx * (P.ty / P.spt),
+                     : occupancy_collide(h->f16, h->collision == LBM_COLL_MRT, P.spt, P.tx * (P.ty / P.spt),
                                          collide_smem(P.tx, P.ty));
     P.grid = std::max(1, std::min(P.ntiles, h->sm_count * occ));
 }
@@ -238,6 +238,8 @@ StepArgs step_args(lbm_handle* h, int parity, int k) {
     a.psi = h->psi;
     a.status = h->status;
     a.parity = parity;
+    a.quota = nullptr;
+    a.step = 0;
     return a;
 }
 
@@ -249,11 +251,11 @@ cudaError_t launch_pass(lbm_handle* h, int k, const StepArgs& a, int grid) {
                    ? launch_psi_tma(h->f16, h->eos, P.tx, P.ty, a, grid, h->stream)
                    : launch_psi(h->f16, h->eos, P.spt, a, dim3(grid), block, h->stream);
     if (h->schedule == LBM_SCHED_FUSED)
-        return launch_fused(h->f16, h->eos, P.spt, a, dim3(grid), block, collide_smem(P.tx, P.ty),
+        return launch_fused(h->f16, h->collision == LBM_COLL_MRT, h->eos, P.spt, a, dim3(grid), block, collide_smem(P.tx, P.ty),
                             h->stream);
     return P.variant == LBM_KERNEL_TMA
                ? launch_collide_tma(h->f16, P.tx, P.ty, a, grid, h->stream)
-               : launch_collide(h->f16, P.spt, a, dim3(grid), block, collide_smem(P.tx, P.ty),
+               : launch_collide(h->f16, h->collision == LBM_COLL_MRT, P.spt, a, dim3(grid), block, collide_smem(P.tx, P.ty),
                                 h->stream);
 }
 
@@ -552,6 +554,8 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
         return LBM_ERR_ARG;
     if (opts && opts->schedule == LBM_SCHED_FUSED && opts->kernel_variant == LBM_KERNEL_TMA)
         return LBM_ERR_ARG;  // the single-pass step exists as a plain-load kernel only
+    if (descs[0].collision == LBM_COLL_MRT && opts && opts->kernel_variant == LBM_KERNEL_TMA)
+        return LBM_ERR_ARG;  // the MRT collision exists in the plain-load kernels only
 
     lbm_handle* h = new (std::nothrow) lbm_handle();
     if (!h) return LBM_ERR_OOM;
@@ -614,7 +618,8 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
         if (it != g_tune_cache.end() && !(opts && (opts->tile_x || opts->tile_y)))
             for (int q = 0; q < 2; ++q) cfg[q] = it->second.pass[q];
     }
-    if (h->schedule == LBM_SCHED_FUSED && cfg[1].variant == LBM_KERNEL_TMA)
+    if ((h->schedule == LBM_SCHED_FUSED || h->collision == LBM_COLL_MRT) &&
+        cfg[1].variant == LBM_KERNEL_TMA)
         cfg[1] = PassCfg{LBM_KERNEL_PLAIN, kPassDefaults[1].tx, kPassDefaults[1].ty, 0,
                          kPassDefaults[1].spt};
     for (int q = 0; q < 2; ++q) {
@@ -840,7 +845,8 @@ int lbm_autotune(lbm_handle* h, int32_t repeats) {
     for (int k = 0; k < 2 && rc == LBM_OK; ++k) {
         std::vector<PassCfg> cand;
         const bool allow_tma = h->tune_variant != LBM_KERNEL_PLAIN &&
-                               !(k == 1 && h->schedule == LBM_SCHED_FUSED);
+                               !(k == 1 && (h->schedule == LBM_SCHED_FUSED ||
+                                            h->collision == LBM_COLL_MRT));
         const bool allow_plain = h->tune_variant != LBM_KERNEL_TMA;
         if (allow_tma)
             for (const auto& c : shapes_tma) cand.push_back({LBM_KERNEL_TMA, c[0], c[1], 0, 1});

@@ -4,17 +4,23 @@
 //
 // One worker thread owns the GPU work.  Its loop:
 //   1. admit queued requests (first come first served, skipping those that
-//      do not fit yet) while a slot and arena space are free; initialise
-//      each at equilibrium in the current population buffer;
-//   2. if the resident set changed, rebuild the lattice table and both tile
-//      lists (lattice-major, so each lattice's tiles are one range);
-//   3. run k = min(chunk_steps, fewest steps left) steps for every resident
-//      lattice: two launches per step over the whole tile list;
-//   4. read the fault words; copy out the moments of lattices that finished
-//      (psi pass over their tiles, moments kernel, device-to-host) and free
-//      their space.
-// All resident lattices share the buffer parity (each step flips it), so a
-// newly admitted lattice is initialised into the buffer the next step reads.
+//      do not fit yet) while a slot, arena space and the resident-site
+//      target allow; initialise each at equilibrium in the current buffer;
+//   2. rebuild one of two alternating table sets (lattice table, tile list
+//      per pass, per-lattice step quotas) from the resident requests;
+//   3. launch a chunk of up to chunk_steps steps for every resident lattice:
+//      two launches per step over the whole tile list, each lattice running
+//      min(chunk_steps, its remaining steps) of them (the kernels skip the
+//      tiles of a lattice whose quota is used up);
+//   4. while that chunk runs, copy out the lattices that finished in the
+//      previous chunk (psi pass over their tiles, moments kernel,
+//      device-to-host, on a side stream with the previous table set) and
+//      free their space;
+//   5. wait for the chunk, read the fault words, note which lattices finished.
+// Every lattice still resident after a chunk has run all of its steps, so all
+// resident lattices share the buffer parity; a lattice that stops early
+// keeps its own final parity for the copy-out.  Bounding the resident sites
+// keeps the GPU saturated without stretching every request's latency.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -100,11 +106,21 @@ struct Request {
 };
 
 struct PassState {
-    int variant = LBM_KERNEL_PLAIN, tx = 64, ty = 4, spt = 2;
-    int4* tiles = nullptr;
-    size_t cap = 0;
-    int ntiles = 0;
-    std::vector<int> begin, count;
+    int tx = 64, ty = 4, spt = 2;
+};
+
+// One set of device tables (lattice table, tile list per pass, quotas,
+// fault words).  Two sets alternate between chunks so that the copy-out of
+// lattices that finished in chunk n (on the side stream, with set n % 2)
+// overlaps chunk n + 1 (main stream, the other set).
+struct TableSet {
+    LatDev* lat = nullptr;
+    int* quota = nullptr;
+    uint32_t* status = nullptr;
+    int4* tiles[2] = {nullptr, nullptr};
+    size_t cap[2] = {0, 0};
+    int ntiles[2] = {0, 0};
+    std::vector<int> begin[2], count[2];
 };
 
 }  // namespace
@@ -112,13 +128,14 @@ struct PassState {
 struct lbm_server {
     lbm_server_opts o{};
     int device = 0, sm_count = 0, f16 = 0, es = 4;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr, side = nullptr;
+    cudaEvent_t chunk_end = nullptr;
     void* arena = nullptr;
-    double* staging = nullptr;  // rho, ux, uy of one request
-    LatDev* lat_dev = nullptr;  // max_resident entries
-    uint32_t* status = nullptr; // max_resident words
+    double* staging = nullptr;  // rho of one admitted request (main stream)
+    double* outbuf = nullptr;   // rho, ux, uy of one finished request (side stream)
     uint32_t* status_host = nullptr;
     PassState pass[2];
+    TableSet set[2];
     ArenaAlloc alloc;
     int parity = 0;
     // shared with the API threads
@@ -126,7 +143,6 @@ struct lbm_server {
     std::condition_variable cv;
     std::deque<uint64_t> queue;
     std::map<uint64_t, Request> reqs;
-    std::vector<uint64_t> resident;
     uint64_t next_ticket = 1;
     bool stop = false;
     lbm_server_stats st{};
@@ -136,118 +152,130 @@ struct lbm_server {
 namespace {
 
 void free_server(lbm_server* S) {
-    for (auto& P : S->pass)
-        if (P.tiles) cudaFree(P.tiles);
+    for (auto& T : S->set) {
+        for (auto& t : T.tiles)
+            if (t) cudaFree(t);
+        if (T.lat) cudaFree(T.lat);
+        if (T.quota) cudaFree(T.quota);
+        if (T.status) cudaFree(T.status);
+    }
     if (S->status_host) cudaFreeHost(S->status_host);
-    if (S->status) cudaFree(S->status);
-    if (S->lat_dev) cudaFree(S->lat_dev);
+    if (S->outbuf) cudaFree(S->outbuf);
     if (S->staging) cudaFree(S->staging);
     if (S->arena) cudaFree(S->arena);
+    if (S->chunk_end) cudaEventDestroy(S->chunk_end);
+    if (S->side) cudaStreamDestroy(S->side);
     if (S->stream) cudaStreamDestroy(S->stream);
 }
 
-int pass_grid(lbm_server* S, int k) {
+size_t smem_of(const PassState& P) { return (size_t)(P.tx + 2) * (P.ty + 2) * sizeof(float); }
+
+int pass_grid(lbm_server* S, int k, int ntiles) {
     const PassState& P = S->pass[k];
-    int occ;
-    if (P.variant == LBM_KERNEL_TMA)
-        occ = k == 0 ? occupancy_psi_tma(S->f16, S->o.eos_precision, P.tx, P.ty)
-                     : occupancy_collide_tma(S->f16, P.tx, P.ty);
-    else
-        occ = k == 0 ? occupancy_psi(S->f16, S->o.eos_precision, P.spt, P.tx * (P.ty / P.spt))
-                     : occupancy_collide(S->f16, P.spt, P.tx * (P.ty / P.spt),
-                                         (size_t)(P.tx + 2) * (P.ty + 2) * sizeof(float));
-    return std::max(1, std::min(P.ntiles, S->sm_count * occ));
+    const int thr = P.tx * (P.ty / P.spt);
+    const int occ = k == 0 ? occupancy_psi(S->f16, S->o.eos_precision, P.spt, thr)
+                           : occupancy_collide(S->f16, 0, P.spt, thr, smem_of(P));
+    return std::max(1, std::min(ntiles, S->sm_count * occ));
 }
 
-cudaError_t launch(lbm_server* S, int k, const StepArgs& a, int grid) {
+cudaError_t launch(lbm_server* S, int k, const StepArgs& a, int grid, cudaStream_t st) {
     const PassState& P = S->pass[k];
     const dim3 block(P.tx, P.ty / P.spt);
-    if (k == 0)
-        return P.variant == LBM_KERNEL_TMA
-                   ? launch_psi_tma(S->f16, S->o.eos_precision, P.tx, P.ty, a, grid, S->stream)
-                   : launch_psi(S->f16, S->o.eos_precision, P.spt, a, dim3(grid), block, S->stream);
-    return P.variant == LBM_KERNEL_TMA
-               ? launch_collide_tma(S->f16, P.tx, P.ty, a, grid, S->stream)
-               : launch_collide(S->f16, P.spt, a, dim3(grid), block,
-                                (size_t)(P.tx + 2) * (P.ty + 2) * sizeof(float), S->stream);
+    if (k == 0) return launch_psi(S->f16, S->o.eos_precision, P.spt, a, dim3(grid), block, st);
+    return launch_collide(S->f16, 0, P.spt, a, dim3(grid), block, smem_of(P), st);
 }
 
-StepArgs args(lbm_server* S, int k) {
+StepArgs args(lbm_server* S, const TableSet& T, int k, int parity) {
     StepArgs a;
-    a.lats = S->lat_dev;
-    a.tiles = S->pass[k].tiles;
-    a.ntiles = S->pass[k].ntiles;
+    a.lats = T.lat;
+    a.tiles = T.tiles[k];
+    a.ntiles = T.ntiles[k];
     a.pop = S->arena;
     a.psi = static_cast<float*>(S->arena);
-    a.status = S->status;
-    a.parity = S->parity;
+    a.status = T.status;
+    a.parity = parity;
+    a.quota = T.quota;
+    a.step = 0;
     return a;
 }
 
-// Rebuild the lattice table and tile lists from the resident requests.
-cudaError_t rebuild(lbm_server* S, std::vector<Request*>& res) {
+// Fill table set T from the resident requests with their chunk quotas.
+cudaError_t rebuild(lbm_server* S, TableSet& T, std::vector<Request*>& res,
+                    const std::vector<int>& quota) {
     std::vector<LatDev> lats(res.size());
     for (size_t i = 0; i < res.size(); ++i) {
         res[i]->L.lattice = (int)i;
         lats[i] = res[i]->L;
     }
     cudaError_t e = cudaSuccess;
-    if (!lats.empty())
-        e = cudaMemcpyAsync(S->lat_dev, lats.data(), lats.size() * sizeof(LatDev),
+    if (!lats.empty()) {
+        e = cudaMemcpyAsync(T.lat, lats.data(), lats.size() * sizeof(LatDev),
                             cudaMemcpyHostToDevice, S->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(T.quota, quota.data(), quota.size() * sizeof(int),
+                                cudaMemcpyHostToDevice, S->stream);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(T.status, 0, res.size() * sizeof(uint32_t), S->stream);
+    }
     if (e != cudaSuccess) return e;
-    for (auto& P : S->pass) {
+    for (int k = 0; k < 2; ++k) {
+        const PassState& P = S->pass[k];
         std::vector<int4> t;
-        P.begin.assign(res.size(), 0);
-        P.count.assign(res.size(), 0);
+        T.begin[k].assign(res.size(), 0);
+        T.count[k].assign(res.size(), 0);
         for (size_t l = 0; l < res.size(); ++l) {
-            P.begin[l] = (int)t.size();
+            T.begin[k][l] = (int)t.size();
             for (int y0 = 0; y0 < lats[l].ny; y0 += P.ty)
-                for (int x0 = 0; x0 < lats[l].nx; x0 += P.tx)
-                    t.push_back(make_int4((int)l, x0, y0, 0));
-            P.count[l] = (int)t.size() - P.begin[l];
+                for (int x0 = 0; x0 < lats[l].nx; x0 += P.tx) t.push_back(make_int4((int)l, x0, y0, 0));
+            T.count[k][l] = (int)t.size() - T.begin[k][l];
         }
         const size_t bytes = t.size() * sizeof(int4);
-        if (bytes > P.cap) {
-            if (P.tiles) {
-                cudaStreamSynchronize(S->stream);
-                cudaFree(P.tiles);
+        if (bytes > T.cap[k]) {
+            if (T.tiles[k]) {
+                cudaDeviceSynchronize();
+                cudaFree(T.tiles[k]);
             }
-            P.tiles = nullptr;
-            P.cap = 0;
-            e = cudaMalloc(&P.tiles, std::max<size_t>(bytes * 2, 4096));
+            T.tiles[k] = nullptr;
+            T.cap[k] = 0;
+            const size_t cap = std::max<size_t>(bytes * 2, 4096);
+            e = cudaMalloc(&T.tiles[k], cap);
             if (e != cudaSuccess) return e;
-            P.cap = std::max<size_t>(bytes * 2, 4096);
+            T.cap[k] = cap;
         }
-        if (bytes) e = cudaMemcpyAsync(P.tiles, t.data(), bytes, cudaMemcpyHostToDevice, S->stream);
+        // pageable source: the copy has finished reading `t` when the call returns
+        if (bytes) e = cudaMemcpyAsync(T.tiles[k], t.data(), bytes, cudaMemcpyHostToDevice, S->stream);
         if (e != cudaSuccess) return e;
-        P.ntiles = (int)t.size();
+        T.ntiles[k] = (int)t.size();
     }
-    // the host staging vectors go out of scope: finish the copies first
-    return cudaStreamSynchronize(S->stream);
+    return cudaSuccess;
 }
 
-// Moments of resident lattice `l` (index in the current table) into R.
-cudaError_t copy_out(lbm_server* S, Request& R, int l) {
-    StepArgs a = args(S, 0);
-    a.tiles = S->pass[0].tiles + S->pass[0].begin[l];
-    a.ntiles = S->pass[0].count[l];
-    cudaError_t e = launch(S, 0, a, std::min(pass_grid(S, 0), a.ntiles));
+// Moments of lattice l of set T (final parity `par`) into R, on the side
+// stream after the chunk that finished it.
+cudaError_t copy_out(lbm_server* S, const TableSet& T, Request& R, int l, int par) {
+    StepArgs a = args(S, T, 0, par);
+    a.tiles = T.tiles[0] + T.begin[0][l];
+    a.ntiles = T.count[0][l];
+    a.quota = nullptr;
+    cudaError_t e = launch(S, 0, a, pass_grid(S, 0, a.ntiles), S->side);
     if (e != cudaSuccess) return e;
     const size_t n = (size_t)R.L.nx * R.L.ny;
-    double* dr = S->staging;
+    double* dr = S->outbuf;
     double* dx = dr + S->o.max_request_sites;
     double* dy = dx + S->o.max_request_sites;
-    e = launch_moments(S->f16, R.L, S->arena, S->parity, static_cast<float*>(S->arena), dr, dx,
-                       dy, S->stream);
+    e = launch_moments(S->f16, R.L, S->arena, par, static_cast<float*>(S->arena), dr, dx, dy,
+                       S->side);
     if (e != cudaSuccess) return e;
     R.rho.resize(n);
     R.ux.resize(n);
     R.uy.resize(n);
-    cudaMemcpyAsync(R.rho.data(), dr, n * sizeof(double), cudaMemcpyDeviceToHost, S->stream);
-    cudaMemcpyAsync(R.ux.data(), dx, n * sizeof(double), cudaMemcpyDeviceToHost, S->stream);
-    cudaMemcpyAsync(R.uy.data(), dy, n * sizeof(double), cudaMemcpyDeviceToHost, S->stream);
-    return cudaStreamSynchronize(S->stream);
+    e = cudaMemcpyAsync(R.rho.data(), dr, n * sizeof(double), cudaMemcpyDeviceToHost, S->side);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(R.ux.data(), dx, n * sizeof(double), cudaMemcpyDeviceToHost, S->side);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(R.uy.data(), dy, n * sizeof(double), cudaMemcpyDeviceToHost, S->side);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->side);
+    return e;
 }
 
 void fail_all(lbm_server* S, int status) {
@@ -260,25 +288,40 @@ void fail_all(lbm_server* S, int status) {
             S->st.failed++;
         }
     S->queue.clear();
-    S->resident.clear();
+    S->st.queued = 0;
+    S->st.resident = 0;
 }
+
+struct Finished {
+    Request* R;
+    int l, par, status;
+};
 
 void worker_main(lbm_server* S) {
     cudaSetDevice(S->device);
-    std::vector<Request*> res;  // resident requests in table order (worker's view)
-    bool changed = false;
+    std::vector<Request*> res;  // resident requests (worker's view)
+    int64_t res_sites = 0;
+    std::vector<Finished> pending;  // finished in the last chunk, to copy out
+    int pending_set = 0;
+    int64_t chunk_no = 0;
     for (;;) {
         std::vector<Request*> admitted;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             if (S->stop) break;
-            if (res.empty() && S->queue.empty()) {
+            if (res.empty() && S->queue.empty() && pending.empty()) {
                 S->cv.wait_for(lk, std::chrono::milliseconds(20));
                 continue;
             }
+            // admission: first come first served, skipping requests that do
+            // not fit yet, while slots, arena space and the resident-site
+            // target allow (one request is always admitted into an idle GPU)
             for (auto it = S->queue.begin(); it != S->queue.end();) {
                 if ((int)(res.size() + admitted.size()) >= S->o.max_resident) break;
                 Request& R = S->reqs[*it];
+                const int64_t n = (int64_t)R.L.nx * R.L.ny;
+                if (res_sites + n > S->o.target_resident_sites && (res_sites > 0 || !admitted.empty()))
+                    break;
                 size_t po = 0, qo = 0;
                 if (S->alloc.alloc(R.pop_bytes, &po)) {
                     if (S->alloc.alloc(R.psi_bytes, &qo)) {
@@ -286,13 +329,13 @@ void worker_main(lbm_server* S) {
                         R.psi_off = qo;
                         R.state = ST_RESIDENT;
                         admitted.push_back(&R);
-                        S->resident.push_back(R.ticket);
+                        res_sites += n;
                         it = S->queue.erase(it);
                         continue;
                     }
                     S->alloc.release(po, R.pop_bytes);
                 }
-                ++it;  // does not fit yet: smaller requests behind it may
+                ++it;
             }
             S->st.queued = (int)S->queue.size();
             S->st.arena_in_use = (int64_t)S->alloc.in_use();
@@ -306,52 +349,73 @@ void worker_main(lbm_server* S) {
             const size_t n = (size_t)R->L.nx * R->L.ny;
             if (R->d.storage != LBM_STORE_F32 && R->d.rho0 < 0.0)
                 R->L.rho0 = auto_rho0(R->rho.data(), n);
+            // pageable source: the copy has read R->rho when the call returns;
+            // the next request's copy into the staging follows this init in stream order
             e = cudaMemcpyAsync(S->staging, R->rho.data(), n * sizeof(double),
                                 cudaMemcpyHostToDevice, S->stream);
             if (e == cudaSuccess)
                 e = launch_init(S->f16, R->L, S->arena, S->parity, S->staging, nullptr, nullptr,
                                 S->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);  // staging reused next
             if (e != cudaSuccess) break;
             std::vector<double>().swap(R->rho);
             res.push_back(R);
-            changed = true;
         }
-        if (e == cudaSuccess && changed) {
-            e = rebuild(S, res);
+        // launch the next chunk (if anything is resident) before copying out
+        // the lattices that finished in the previous one
+        const int cur = (int)(chunk_no & 1);
+        std::vector<int> quota(res.size());
+        int64_t k = 0;
+        for (size_t l = 0; l < res.size(); ++l) {
+            quota[l] = (int)std::min<int64_t>(S->o.chunk_steps, res[l]->remaining);
+            k = std::max<int64_t>(k, quota[l]);
+        }
+        const int p0 = S->parity;
+        if (e == cudaSuccess && !res.empty()) {
+            TableSet& T = S->set[cur];
+            e = rebuild(S, T, res, quota);
+            const int g0 = pass_grid(S, 0, T.ntiles[0]), g1 = pass_grid(S, 1, T.ntiles[1]);
+            for (int64_t s = 0; s < k && e == cudaSuccess; ++s) {
+                StepArgs a0 = args(S, T, 0, S->parity), a1 = args(S, T, 1, S->parity);
+                a0.step = a1.step = (int)s;
+                e = launch(S, 0, a0, g0, S->stream);
+                if (e == cudaSuccess) e = launch(S, 1, a1, g1, S->stream);
+                S->parity ^= 1;
+            }
             if (e == cudaSuccess)
-                e = cudaMemsetAsync(S->status, 0, std::max<size_t>(res.size(), 1) * 4, S->stream);
-            changed = false;
+                e = cudaMemcpyAsync(S->status_host, T.status, res.size() * sizeof(uint32_t),
+                                    cudaMemcpyDeviceToHost, S->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(S->chunk_end, S->stream);
         }
+        // copy out the previous chunk's finished lattices while this chunk runs
+        for (Finished& f : pending) {
+            int status = f.status;
+            if (status == LBM_OK && e == cudaSuccess &&
+                copy_out(S, S->set[pending_set], *f.R, f.l, f.par) != cudaSuccess)
+                status = LBM_ERR_CUDA;
+            std::lock_guard<std::mutex> lk(S->mu);
+            f.R->status = status;
+            f.R->state = ST_DONE;
+            f.R->t_done = Clock::now();
+            S->alloc.release(f.R->pop_off, f.R->pop_bytes);
+            S->alloc.release(f.R->psi_off, f.R->psi_bytes);
+            if (status == LBM_OK) S->st.completed++;
+            else S->st.failed++;
+        }
+        pending.clear();
+        if (e == cudaSuccess && !res.empty()) e = cudaEventSynchronize(S->chunk_end);
         if (e != cudaSuccess) {
             fail_all(S, LBM_ERR_CUDA);
             res.clear();
+            res_sites = 0;
             continue;
         }
         if (res.empty()) continue;
-        int64_t k = S->o.chunk_steps;
-        for (Request* R : res) k = std::min(k, R->remaining);
-        const int g0 = pass_grid(S, 0), g1 = pass_grid(S, 1);
-        for (int64_t s = 0; s < k && e == cudaSuccess; ++s) {
-            e = launch(S, 0, args(S, 0), g0);
-            if (e == cudaSuccess) e = launch(S, 1, args(S, 1), g1);
-            S->parity ^= 1;
-        }
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(S->status_host, S->status, res.size() * sizeof(uint32_t),
-                                cudaMemcpyDeviceToHost, S->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-        if (e != cudaSuccess) {
-            fail_all(S, LBM_ERR_CUDA);
-            res.clear();
-            continue;
-        }
         int64_t done_sites = 0;
         std::vector<Request*> keep;
         for (size_t l = 0; l < res.size(); ++l) {
             Request* R = res[l];
-            R->remaining -= k;
-            done_sites += (int64_t)R->L.nx * R->L.ny * k;
+            R->remaining -= quota[l];
+            done_sites += (int64_t)R->L.nx * R->L.ny * quota[l];
             const uint32_t bits = S->status_host[l];
             if (R->remaining > 0 && !bits) {
                 keep.push_back(R);
@@ -360,19 +424,12 @@ void worker_main(lbm_server* S) {
             int status = LBM_OK;
             if (bits & 2u) status = LBM_ERR_TIMEOUT;
             else if (bits) status = LBM_ERR_NUMERIC;
-            if (status == LBM_OK && copy_out(S, *R, (int)l) != cudaSuccess) status = LBM_ERR_CUDA;
-            std::lock_guard<std::mutex> lk(S->mu);
-            R->status = status;
-            R->state = ST_DONE;
-            R->t_done = Clock::now();
-            S->alloc.release(R->pop_off, R->pop_bytes);
-            S->alloc.release(R->psi_off, R->psi_bytes);
-            S->resident.erase(std::find(S->resident.begin(), S->resident.end(), R->ticket));
-            if (status == LBM_OK) S->st.completed++;
-            else S->st.failed++;
-            changed = true;
+            pending.push_back(Finished{R, (int)l, (p0 + quota[l]) & 1, status});
+            res_sites -= (int64_t)R->L.nx * R->L.ny;
         }
+        pending_set = cur;
         res.swap(keep);
+        ++chunk_no;
         std::lock_guard<std::mutex> lk(S->mu);
         S->st.site_steps += done_sites;
         S->st.busy_s += std::chrono::duration<double>(Clock::now() - t0).count();
@@ -392,6 +449,7 @@ void lbm_server_opts_default(lbm_server_opts* o) {
     o->max_resident = 1024;
     o->chunk_steps = 100;
     o->max_request_sites = (int64_t)2048 * 2048;
+    o->target_resident_sites = (int64_t)16 << 20;
     o->storage = LBM_STORE_F32_DEV;
     o->eos_precision = LBM_EOS_DF;
     o->kernel_variant = LBM_KERNEL_AUTO;
@@ -403,17 +461,18 @@ int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
     lbm_server_opts o;
     lbm_server_opts_default(&o);
     if (opts) {
+        lbm_server_opts d = o;
         o = *opts;
-        lbm_server_opts d;
-        lbm_server_opts_default(&d);
         if (!o.arena_bytes) o.arena_bytes = d.arena_bytes;
         if (!o.max_resident) o.max_resident = d.max_resident;
         if (!o.chunk_steps) o.chunk_steps = d.chunk_steps;
         if (!o.max_request_sites) o.max_request_sites = d.max_request_sites;
+        if (!o.target_resident_sites) o.target_resident_sites = d.target_resident_sites;
     }
     if (o.max_resident < 1 || o.chunk_steps < 1 || o.max_request_sites < 4 ||
-        o.storage < LBM_STORE_F32 || o.storage > LBM_STORE_F16_DEV ||
-        o.eos_precision < LBM_EOS_F64 || o.eos_precision > LBM_EOS_F32)
+        o.target_resident_sites < 1 || o.storage < LBM_STORE_F32 ||
+        o.storage > LBM_STORE_F16_DEV || o.eos_precision < LBM_EOS_F64 ||
+        o.eos_precision > LBM_EOS_F32 || o.kernel_variant == LBM_KERNEL_TMA)
         return LBM_ERR_ARG;
     lbm_server* S = new (std::nothrow) lbm_server();
     if (!S) return LBM_ERR_OOM;
@@ -422,28 +481,15 @@ int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
     S->es = S->f16 ? 2 : 4;
     for (int k = 0; k < 2; ++k) {
         PassState& P = S->pass[k];
-        P.variant = kPassDefaults[k].variant;
         P.tx = kPassDefaults[k].tx;
         P.ty = kPassDefaults[k].ty;
         P.spt = kPassDefaults[k].spt;
-        if (o.kernel_variant == LBM_KERNEL_TMA) {
-            P.variant = LBM_KERNEL_TMA;
-            P.tx = 64;
-            P.ty = 8;
-            P.spt = 1;
-        } else if (o.kernel_variant == LBM_KERNEL_PLAIN) {
-            P.variant = LBM_KERNEL_PLAIN;
-        }
         if (o.tile_x || o.tile_y) {
             P.tx = o.tile_x ? o.tile_x : 64;
             P.ty = o.tile_y ? o.tile_y : 8;
             P.spt = 1;
         }
-        const bool ok = P.variant == LBM_KERNEL_TMA
-                            ? tma_shape_supported(P.tx, P.ty)
-                            : (P.tx % 32 == 0 && P.ty > 0 && P.tx * P.ty <= 512 * P.spt &&
-                               P.ty % P.spt == 0);
-        if (!ok) {
+        if (P.tx % 32 || P.ty < 1 || P.tx * (P.ty / P.spt) > 512 || P.ty % P.spt) {
             delete S;
             return LBM_ERR_ARG;
         }
@@ -456,13 +502,21 @@ int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
     if (cudaGetDevice(&S->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&S->sm_count, cudaDevAttrMultiProcessorCount, S->device) !=
             cudaSuccess ||
-        cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess)
+        cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&S->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S->chunk_end, cudaEventDisableTiming) != cudaSuccess)
         return fail(LBM_ERR_CUDA);
-    if (cudaMalloc(&S->arena, o.arena_bytes) != cudaSuccess ||
-        cudaMalloc(&S->staging, 3 * (size_t)o.max_request_sites * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&S->lat_dev, (size_t)o.max_resident * sizeof(LatDev)) != cudaSuccess ||
-        cudaMalloc(&S->status, (size_t)o.max_resident * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMallocHost(&S->status_host, (size_t)o.max_resident * sizeof(uint32_t)) != cudaSuccess) {
+    const size_t nmax = (size_t)o.max_request_sites;
+    bool ok = cudaMalloc(&S->arena, o.arena_bytes) == cudaSuccess &&
+              cudaMalloc(&S->staging, nmax * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&S->outbuf, 3 * nmax * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost(&S->status_host, (size_t)o.max_resident * sizeof(uint32_t)) ==
+                  cudaSuccess;
+    for (auto& T : S->set)
+        ok = ok && cudaMalloc(&T.lat, (size_t)o.max_resident * sizeof(LatDev)) == cudaSuccess &&
+             cudaMalloc(&T.quota, (size_t)o.max_resident * sizeof(int)) == cudaSuccess &&
+             cudaMalloc(&T.status, (size_t)o.max_resident * sizeof(uint32_t)) == cudaSuccess;
+    if (!ok) {
         cudaGetLastError();
         return fail(LBM_ERR_OOM);
     }
@@ -486,7 +540,7 @@ int lbm_submit(lbm_server* S, const lbm_lattice_desc* d, const double* rho, int6
     R.d.storage = S->o.storage;
     R.d.eos_precision = S->o.eos_precision;
     std::string why;
-    if (validate_desc(R.d, why) != LBM_OK) return LBM_ERR_ARG;
+    if (validate_desc(R.d, why) != LBM_OK || R.d.collision != LBM_COLL_BGK) return LBM_ERR_ARG;
     const size_t n = (size_t)R.d.nx * R.d.ny;
     if ((int64_t)n > S->o.max_request_sites) return LBM_ERR_CAPACITY;
     for (size_t i = 0; i < n; ++i)
@@ -548,6 +602,7 @@ void lbm_server_destroy(lbm_server* S) {
     S->cv.notify_all();
     if (S->worker.joinable()) S->worker.join();
     cudaStreamSynchronize(S->stream);
+    cudaStreamSynchronize(S->side);
     free_server(S);
     delete S;
 }
