@@ -50,11 +50,12 @@ def parse():
     ap.add_argument("--eos", default="df", choices=["f64", "df", "f32"],
                     help="arithmetic of psi/EOS: float-float (default), native FP64 or FP32")
     ap.add_argument("--variant", default="auto", choices=["auto", "tma", "plain"])
-    ap.add_argument("--schedule", default="two_pass", choices=["two_pass", "fused"],
-                    help="two_pass: psi pass + collision pass; fused: one pass per step")
+    ap.add_argument("--schedule", default="fused", choices=["two_pass", "fused"],
+                    help="fused: one pass per step (default); two_pass: psi pass + collision pass")
     ap.add_argument("--storage", default="f32dev", choices=["f32", "f32dev", "f16dev"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="skip lbm_autotune (tile shapes, sites per thread, grid) before timing")
     ap.add_argument("--size", type=int, default=8192,
                     help="lattice side of the droplet workload (8192 is the benchmark; "
                          "smaller sides are for profiler captures)")

@@ -39,8 +39,9 @@ LBM_COLL_MRT = 1
 LBM_KERNEL_AUTO = 0
 LBM_KERNEL_PLAIN = 1
 LBM_KERNEL_TMA = 2
-LBM_SCHED_TWO_PASS = 0
-LBM_SCHED_FUSED = 1
+LBM_SCHED_AUTO = 0
+LBM_SCHED_TWO_PASS = 1
+LBM_SCHED_FUSED = 2
 
 
 class LatticeDesc(ctypes.Structure):
@@ -77,8 +78,8 @@ class ServerOpts(ctypes.Structure):
     _fields_ = [("arena_bytes", ctypes.c_size_t), ("max_resident", ctypes.c_int32),
                 ("chunk_steps", ctypes.c_int32), ("max_request_sites", ctypes.c_int64),
                 ("target_resident_sites", ctypes.c_int64), ("storage", ctypes.c_int32), ("eos_precision", ctypes.c_int32),
-                ("kernel_variant", ctypes.c_int32), ("tile_x", ctypes.c_int32),
-                ("tile_y", ctypes.c_int32)]
+                ("kernel_variant", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -242,7 +243,7 @@ def lbm_desc_default(nx: int, ny: int, **kw) -> LatticeDesc:
     return d
 
 
-def lbm_create(descs, tile=None, grid_ctas=0, schedule=LBM_SCHED_TWO_PASS, graph_steps=0,
+def lbm_create(descs, tile=None, grid_ctas=0, schedule=LBM_SCHED_AUTO, graph_steps=0,
                stream=None, device=None, kernel_variant=LBM_KERNEL_AUTO) -> Handle:
     """Create a handle over one descriptor or a list of them."""
     import torch

@@ -74,7 +74,7 @@ struct lbm_handle {
     int f16 = 0;
     int eos = LBM_EOS_F64;
     int collision = LBM_COLL_BGK;
-    int schedule = LBM_SCHED_TWO_PASS;
+    int schedule = LBM_SCHED_FUSED;
     // device memory
     void* pop = nullptr;
     size_t pop_bytes = 0;
@@ -550,7 +550,8 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
             if (!shape_ok(c.variant, c.tx, c.ty, c.spt)) return LBM_ERR_ARG;
         }
     }
-    if (opts && opts->schedule != LBM_SCHED_TWO_PASS && opts->schedule != LBM_SCHED_FUSED)
+    if (opts && opts->schedule != LBM_SCHED_AUTO && opts->schedule != LBM_SCHED_TWO_PASS &&
+        opts->schedule != LBM_SCHED_FUSED)
         return LBM_ERR_ARG;
     if (opts && opts->schedule == LBM_SCHED_FUSED && opts->kernel_variant == LBM_KERNEL_TMA)
         return LBM_ERR_ARG;  // the single-pass step exists as a plain-load kernel only
@@ -563,7 +564,10 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
     h->desc.assign(descs, descs + n);
     h->storage = descs[0].storage;
     h->f16 = h->storage == LBM_STORE_F16_DEV;
-    h->schedule = opts ? opts->schedule : LBM_SCHED_TWO_PASS;
+    // LBM_SCHED_AUTO: the single pass unless a TMA kernel was asked for
+    h->schedule = opts ? opts->schedule : LBM_SCHED_AUTO;
+    if (h->schedule == LBM_SCHED_AUTO)
+        h->schedule = variant == LBM_KERNEL_TMA ? LBM_SCHED_TWO_PASS : LBM_SCHED_FUSED;
     h->eos = descs[0].eos_precision;
     h->collision = descs[0].collision;
     h->graph_steps = (opts && opts->graph_steps != 0) ? opts->graph_steps : 32;

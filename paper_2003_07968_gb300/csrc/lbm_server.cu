@@ -128,6 +128,7 @@ struct TableSet {
 struct lbm_server {
     lbm_server_opts o{};
     int device = 0, sm_count = 0, f16 = 0, es = 4;
+    int fused = 1;  // one launch per step (LBM_SCHED_FUSED)
     cudaStream_t stream = nullptr, side = nullptr;
     cudaEvent_t chunk_end = nullptr;
     void* arena = nullptr;
@@ -170,11 +171,15 @@ void free_server(lbm_server* S) {
 
 size_t smem_of(const PassState& P) { return (size_t)(P.tx + 2) * (P.ty + 2) * sizeof(float); }
 
+// Pass 0: psi pass (used by the copy-out; and by the two-pass schedule);
+// pass 1: the collision pass, or the single-pass step when fused.
 int pass_grid(lbm_server* S, int k, int ntiles) {
     const PassState& P = S->pass[k];
     const int thr = P.tx * (P.ty / P.spt);
-    const int occ = k == 0 ? occupancy_psi(S->f16, S->o.eos_precision, P.spt, thr)
-                           : occupancy_collide(S->f16, 0, P.spt, thr, smem_of(P));
+    const int occ =
+        k == 0 ? occupancy_psi(S->f16, S->o.eos_precision, P.spt, thr)
+        : S->fused ? occupancy_fused(S->f16, 0, S->o.eos_precision, P.spt, thr, smem_of(P))
+                   : occupancy_collide(S->f16, 0, P.spt, thr, smem_of(P));
     return std::max(1, std::min(ntiles, S->sm_count * occ));
 }
 
@@ -182,6 +187,9 @@ cudaError_t launch(lbm_server* S, int k, const StepArgs& a, int grid, cudaStream
     const PassState& P = S->pass[k];
     const dim3 block(P.tx, P.ty / P.spt);
     if (k == 0) return launch_psi(S->f16, S->o.eos_precision, P.spt, a, dim3(grid), block, st);
+    if (S->fused)
+        return launch_fused(S->f16, 0, S->o.eos_precision, P.spt, a, dim3(grid), block, smem_of(P),
+                            st);
     return launch_collide(S->f16, 0, P.spt, a, dim3(grid), block, smem_of(P), st);
 }
 
@@ -377,7 +385,7 @@ void worker_main(lbm_server* S) {
             for (int64_t s = 0; s < k && e == cudaSuccess; ++s) {
                 StepArgs a0 = args(S, T, 0, S->parity), a1 = args(S, T, 1, S->parity);
                 a0.step = a1.step = (int)s;
-                e = launch(S, 0, a0, g0, S->stream);
+                if (!S->fused) e = launch(S, 0, a0, g0, S->stream);
                 if (e == cudaSuccess) e = launch(S, 1, a1, g1, S->stream);
                 S->parity ^= 1;
             }
@@ -400,6 +408,7 @@ void worker_main(lbm_server* S) {
             S->alloc.release(f.R->psi_off, f.R->psi_bytes);
             if (status == LBM_OK) S->st.completed++;
             else S->st.failed++;
+            S->st.arena_in_use = (int64_t)S->alloc.in_use();
         }
         pending.clear();
         if (e == cudaSuccess && !res.empty()) e = cudaEventSynchronize(S->chunk_end);
@@ -472,11 +481,14 @@ int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
     if (o.max_resident < 1 || o.chunk_steps < 1 || o.max_request_sites < 4 ||
         o.target_resident_sites < 1 || o.storage < LBM_STORE_F32 ||
         o.storage > LBM_STORE_F16_DEV || o.eos_precision < LBM_EOS_F64 ||
-        o.eos_precision > LBM_EOS_F32 || o.kernel_variant == LBM_KERNEL_TMA)
+        o.eos_precision > LBM_EOS_F32 || o.kernel_variant == LBM_KERNEL_TMA ||
+        (o.schedule != LBM_SCHED_AUTO && o.schedule != LBM_SCHED_TWO_PASS &&
+         o.schedule != LBM_SCHED_FUSED))
         return LBM_ERR_ARG;
     lbm_server* S = new (std::nothrow) lbm_server();
     if (!S) return LBM_ERR_OOM;
     S->o = o;
+    S->fused = o.schedule != LBM_SCHED_TWO_PASS;
     S->f16 = o.storage == LBM_STORE_F16_DEV;
     S->es = S->f16 ? 2 : 4;
     for (int k = 0; k < 2; ++k) {
