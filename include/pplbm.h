@@ -61,7 +61,7 @@ extern "C" {
 
 /* ---- arithmetic of psi / Eq. (CSEOS) ------------------------------------- */
 #define LBM_EOS_F64 0 /* native FP64                                             */
-#define LBM_EOS_DF 1  /* float-float pairs (about 48 significant bits)           */
+#define LBM_EOS_DF 1  /* float-float pairs (about 43 significant bits)           */
 #define LBM_EOS_F32 2 /* FP32                                                    */
 
 /* ---- collision operator -------------------------------------------------- */
@@ -71,10 +71,11 @@ extern "C" {
 /* ---- kernel variant ------------------------------------------------------ */
 #define LBM_KERNEL_AUTO 0  /* per pass, the variant and tile measured fastest
                               on GB300 (or found by lbm_autotune)            */
-#define LBM_KERNEL_PLAIN 1 /* plain global loads, 1, 2 or 4 sites per thread;
-                              tile_x a multiple of 32, tile_x*tile_y <= 512
-                              (tiles given through lbm_runtime_opts use one
-                              site per thread)                               */
+#define LBM_KERNEL_PLAIN 1 /* plain global loads, 1, 2 or 4 sites per thread
+                              (with 2 or 4, site pairs share the paired FP32
+                              instructions); tile_x a multiple of 32,
+                              tile_y a multiple of the sites per thread,
+                              tile_x*tile_y/sites_per_thread <= 512          */
 #define LBM_KERNEL_TMA 2   /* tiles staged by TMA bulk copies through a
                               warp-specialised mbarrier pipeline; tile shapes
                               64x8, 64x16, 128x4, 128x8, 32x16               */
@@ -122,6 +123,7 @@ typedef struct {
     int32_t schedule;  /* LBM_SCHED_*                                          */
     int32_t graph_steps; /* steps per captured CUDA graph (0: default, <0: off) */
     int32_t kernel_variant; /* LBM_KERNEL_*                                   */
+    int32_t sites_per_thread; /* with tile_x/tile_y: 1, 2 or 4 (0: 1)          */
 } lbm_runtime_opts;
 
 typedef struct lbm_handle lbm_handle;
@@ -212,6 +214,7 @@ typedef struct {
     int32_t psi_variant, collide_variant;                       /* LBM_KERNEL_*   */
     int32_t schedule;
     int32_t n_lattices;
+    int32_t spt, psi_spt;     /* sites per thread, collision / psi pass         */
 } lbm_info_t;
 int lbm_info(lbm_handle* h, lbm_info_t* out);
 
@@ -251,7 +254,8 @@ typedef struct {
     int32_t kernel_variant;   /* LBM_KERNEL_AUTO or LBM_KERNEL_PLAIN (the server's
                                  chunks need the plain-load kernels)             */
     int32_t schedule;         /* LBM_SCHED_* (AUTO: single pass)                  */
-    int32_t tile_x, tile_y;   /* 0: defaults; else both passes, one site/thread   */
+    int32_t tile_x, tile_y;   /* 0: defaults; else both passes                    */
+    int32_t sites_per_thread; /* with tile_x/tile_y: 1, 2 or 4 (0: 1)              */
 } lbm_server_opts;
 
 typedef struct {
@@ -260,6 +264,7 @@ typedef struct {
     int64_t site_steps;       /* lattice-site updates done                       */
     double busy_s;            /* time the worker spent in GPU chunks             */
     int64_t arena_bytes, arena_in_use;
+    int64_t launches;         /* kernels launched by the worker                  */
 } lbm_server_stats;
 
 /* Fill *o with the defaults above (FP32 deviation storage, float-float EOS). */

@@ -69,7 +69,7 @@ class RuntimeOpts(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("tile_x", ctypes.c_int32),
                 ("tile_y", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
-                ("kernel_variant", ctypes.c_int32)]
+                ("kernel_variant", ctypes.c_int32), ("sites_per_thread", ctypes.c_int32)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -79,7 +79,8 @@ class ServerOpts(ctypes.Structure):
                 ("chunk_steps", ctypes.c_int32), ("max_request_sites", ctypes.c_int64),
                 ("target_resident_sites", ctypes.c_int64), ("storage", ctypes.c_int32), ("eos_precision", ctypes.c_int32),
                 ("kernel_variant", ctypes.c_int32), ("schedule", ctypes.c_int32),
-                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32)]
+                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
+                ("sites_per_thread", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -89,7 +90,7 @@ class ServerStats(ctypes.Structure):
                 ("failed", ctypes.c_int64), ("queued", ctypes.c_int32),
                 ("resident", ctypes.c_int32), ("site_steps", ctypes.c_int64),
                 ("busy_s", ctypes.c_double), ("arena_bytes", ctypes.c_int64),
-                ("arena_in_use", ctypes.c_int64)]
+                ("arena_in_use", ctypes.c_int64), ("launches", ctypes.c_int64)]
 
 
 class KernelStat(ctypes.Structure):
@@ -108,7 +109,8 @@ class Info(ctypes.Structure):
                 ("psi_tile_x", ctypes.c_int32), ("psi_tile_y", ctypes.c_int32),
                 ("psi_n_tiles", ctypes.c_int32), ("psi_grid_ctas", ctypes.c_int32),
                 ("psi_variant", ctypes.c_int32), ("collide_variant", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("n_lattices", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("n_lattices", ctypes.c_int32),
+                ("spt", ctypes.c_int32), ("psi_spt", ctypes.c_int32)]
 
 
 # Every symbol include/pplbm.h declares, with (restype, argtypes).
@@ -244,8 +246,10 @@ def lbm_desc_default(nx: int, ny: int, **kw) -> LatticeDesc:
 
 
 def lbm_create(descs, tile=None, grid_ctas=0, schedule=LBM_SCHED_AUTO, graph_steps=0,
-               stream=None, device=None, kernel_variant=LBM_KERNEL_AUTO) -> Handle:
-    """Create a handle over one descriptor or a list of them."""
+               stream=None, device=None, kernel_variant=LBM_KERNEL_AUTO,
+               sites_per_thread=0) -> Handle:
+    """Create a handle over one descriptor or a list of them.  ``tile`` =
+    (tile_x, tile_y) fixes both passes' tiles, with ``sites_per_thread``."""
     import torch
 
     if isinstance(descs, LatticeDesc):
@@ -262,6 +266,7 @@ def lbm_create(descs, tile=None, grid_ctas=0, schedule=LBM_SCHED_AUTO, graph_ste
     o.tile_x, o.tile_y = (tile or (0, 0))
     o.grid_ctas, o.schedule, o.graph_steps = grid_ctas, schedule, graph_steps
     o.kernel_variant = kernel_variant
+    o.sites_per_thread = sites_per_thread
     out = ctypes.c_void_p()
     with torch.cuda.device(dev):
         rc = load().lbm_create(arr, n, ctypes.byref(o), ctypes.byref(out))

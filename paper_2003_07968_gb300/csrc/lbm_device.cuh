@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace pplbm {
 
 constexpr int GW = 2;  // depth of the periodic images kept around the interior
@@ -57,14 +59,24 @@ struct LatDev {
     float k_sc;         // -2 G / c_s^2                  = -6 G
     float k1;           // (-3/4 eps c_s^2 G)(-2 / c_s^6) = 13.5 eps G
     float k2;           // (sigma - 1) c_s^2 G / c_s^6    = 9 (sigma - 1) G
+    // ... with the scale factors of the integer stencils folded in (site_force)
+    float fsc, fk2, fkd;  // k_sc / 36, k2 / 1944, (k1 - k2) / 1944
+    // BGK + Guo per weight class, axis w = 1/9 (a) and diagonal w = 1/36 (d),
+    // as collide_bgk uses them
+    float om1;          // 1 - omega
+    float wa, wd;       // omega w
+    float ra, rd;       // 9/2 omega w
+    float sa, sd;       // 3 omega w
+    float ga9, gd9;     // 9 guo w
+    float ga3, gd3;     // 3 guo w
     float rho0;         // deviation reference (0 for plain FP32 storage)
     int32_t m2_variant; // 0: direct trace; 1: 2 c_s^2 (M0 - psi)
     int32_t lattice;    // index for the status word
     // psi(rho)^2 = (P_EOS - c_s^2 rho)/G = rho (e1 q(rho) - e2 rho - e3),
     // q = (1 + eta + eta^2 - eta^3)/(1 - eta)^3, eta = b rho      Eqs. (DED), (CSEOS)
     double eb, e1, e2, e3;
-    df2 fb, f1, f2, f3;  // the same constants as float-float pairs
-    float sb, s1, s2, s3; // ... and as floats
+    df2 fb, f2, fc0, fC1;  // b, e2, c0 = e1 - e3, C1 = 2 b e1 as float-float pairs
+    float sb, s1, s2, s3;  // b, e1, e2, e3 as floats
     // MRT relaxation rates (Eq. RelaxationMatrix), used by the MRT kernels
     float mrt_s[9];
 };
@@ -137,289 +149,466 @@ __device__ __forceinline__ void store_img(T* plane, int pitch, int gx, int x, in
     }
 }
 
-// ---- float-float arithmetic (error-free transformations) ---------------------
-// TwoSum: Knuth, TAOCP vol. 2; FastTwoSum: Dekker 1971; TwoProd via FMA.
-// Intrinsics (__fadd_rn etc.) are never contracted or reordered by nvcc.
-__device__ __forceinline__ df2 two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    float bb = __fsub_rn(s, a);
-    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return {s, e};
+// ---- lane-parallel FP32 -------------------------------------------------------
+// The site arithmetic below is written once over V = float (one site) or
+// V = float2 (two sites).  For float2 every operation is one of the paired
+// FP32 instructions of sm_100 and later (add/sub/mul/fma .f32x2: two lanes per
+// issue slot); for float it is the scalar instruction.  Both are written as
+// PTX with an explicit .rn rounding modifier, which the compiler's optimiser
+// cannot see through.  Two facts measured on sm_103a shape the code:
+//  - the code generator keeps scalar .rn operations as written, but fuses a
+//    paired multiply into a following paired add or subtract even with .rn;
+//    so no product ever feeds a paired add here (products only enter FMAs
+//    as multiplicands or addends), and the float-float EOS, whose error-free
+//    transformations need every rounding as written, runs lane by lane on
+//    the scalar instructions;
+//  - the CUDA rounding intrinsics (__fadd_rn ...) are not enough either:
+//    a TwoSum error term built from them folded to zero.
+// Every operation is then one IEEE round-to-nearest step per lane, in the
+// order written, and a site gets bitwise the same result whichever lane
+// count, tile or kernel computes it.
+__device__ __forceinline__ float vadd(float a, float b) {
+    float d;
+    asm("add.rn.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
 }
-__device__ __forceinline__ df2 fast_two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+__device__ __forceinline__ float vsub(float a, float b) {
+    float d;
+    asm("sub.rn.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
 }
-__device__ __forceinline__ df2 df_add(df2 a, df2 b) {
-    df2 s = two_sum(a.hi, b.hi);
-    df2 t = two_sum(a.lo, b.lo);
-    s.lo = __fadd_rn(s.lo, t.hi);
-    s = fast_two_sum(s.hi, s.lo);
-    s.lo = __fadd_rn(s.lo, t.lo);
-    return fast_two_sum(s.hi, s.lo);
+__device__ __forceinline__ float vmul(float a, float b) {
+    float d;
+    asm("mul.rn.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
 }
-__device__ __forceinline__ df2 df_neg(df2 a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ df2 df_mul(df2 a, df2 b) {
-    float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-    return fast_two_sum(p, e);
+__device__ __forceinline__ float vfma(float a, float b, float c) {
+    float d;
+    asm("fma.rn.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
 }
-__device__ __forceinline__ df2 df_mul_f(df2 a, float b) {
-    float p = __fmul_rn(a.hi, b);
-    float e = __fmaf_rn(a.hi, b, -p);
-    e = __fmaf_rn(a.lo, b, e);
-    return fast_two_sum(p, e);
+#define PPLBM_F32X2_BINARY(NAME, OP)                                                       \
+    __device__ __forceinline__ float2 NAME(float2 a, float2 b) {                          \
+        float2 d;                                                                          \
+        asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t" \
+            OP " rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"                                  \
+            : "=f"(d.x), "=f"(d.y)                                                         \
+            : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                     \
+        return d;                                                                          \
+    }
+PPLBM_F32X2_BINARY(vadd, "add.rn.f32x2")
+PPLBM_F32X2_BINARY(vsub, "sub.rn.f32x2")
+PPLBM_F32X2_BINARY(vmul, "mul.rn.f32x2")
+#undef PPLBM_F32X2_BINARY
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
 }
-// Long division with two correction quotients (Bailey's double-double scheme).
-__device__ __forceinline__ df2 df_div(df2 a, df2 b) {
-    float q1 = __fdiv_rn(a.hi, b.hi);
-    df2 r = df_add(a, df_neg(df_mul_f(b, q1)));
-    float q2 = __fdiv_rn(r.hi, b.hi);
-    r = df_add(r, df_neg(df_mul_f(b, q2)));
-    float q3 = __fdiv_rn(r.hi, b.hi);
-    df2 q = fast_two_sum(q1, q2);
-    return df_add(q, df2{q3, 0.f});
+
+template <class V> struct Lanes;
+template <> struct Lanes<float> {
+    static constexpr int n = 1;
+    static __device__ __forceinline__ float set(float c) { return c; }
+    static __device__ __forceinline__ float get(float v, int) { return v; }
+    static __device__ __forceinline__ void put(float& v, int, float c) { v = c; }
+};
+template <> struct Lanes<float2> {
+    static constexpr int n = 2;
+    static __device__ __forceinline__ float2 set(float c) { return make_float2(c, c); }
+    static __device__ __forceinline__ float get(float2 v, int k) { return k ? v.y : v.x; }
+    static __device__ __forceinline__ void put(float2& v, int k, float c) {
+        if (k)
+            v.y = c;
+        else
+            v.x = c;
+    }
+};
+// vector type of a thread that handles SPT sites: pairs when SPT is even
+template <int SPT> struct LaneOf { using V = typename std::conditional<SPT % 2 == 0, float2, float>::type; };
+
+// Density deviation of nine populations, in the one summation order that
+// every kernel uses.
+template <class V>
+__device__ __forceinline__ V sum9(const V g[9]) {
+    return vadd(vadd(vadd(vadd(g[0], g[1]), vadd(g[2], g[3])), vadd(vadd(g[4], g[5]), vadd(g[6], g[7]))),
+                g[8]);
+}
+
+// 1/x correctly rounded (PTX rcp.rn.f32): a unique result.  (The one-ulp
+// rcp.approx leaves the code generator free to produce different results in
+// different contexts, measured on sm_103a, which would make a site's result
+// depend on the kernel that computes it.)
+__device__ __forceinline__ float rcp_rn(float x) {
+    float r;
+    asm("rcp.rn.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+template <class V>
+__device__ __forceinline__ V vrcp(V x) {
+    V r;
+#pragma unroll
+    for (int k = 0; k < Lanes<V>::n; ++k) Lanes<V>::put(r, k, rcp_rn(Lanes<V>::get(x, k)));
+    return r;
 }
 
 // ---- psi(rho), Eqs. (DED) and (CSEOS) --------------------------------------
 // psi^2 = (P_EOS - c_s^2 rho)/G = rho (e1 q - e2 rho - e3) with
-// q = (1 + eta + eta^2 - eta^3)/(1 - eta)^3, eta = b rho.  Writing
-// r = 1/(1 - eta) turns q into the polynomial 1 - 2r + 2r^3 (exact algebra:
-// the numerator is 2 - 2s^2 + s^3 in s = 1 - eta), which needs one
-// reciprocal instead of a division of two cubics.
-// Returns psi and sets ok = false where psi is undefined (rho <= 0 or not
-// finite, b rho >= 1, negative radicand).
+// q = (1 + eta + eta^2 - eta^3)/(1 - eta)^3, eta = b rho.  With r = 1/(1 - eta)
+// one has eta r = r - 1 and (2 - eta) r = 1 + r, so q = 1 - 2r + 2r^3 =
+// 1 + 2 eta r^2 (1 + r) exactly, and
+//   psi^2 / rho = c0 + rho (C1 r^2 (1 + r) - e2),   c0 = e1 - e3,  C1 = 2 b e1.
+// For the Carnahan-Starling constants at 0.55 <= T_r <= 1 and rho <= 3.6 no sum
+// here cancels by more than a factor of about 8, and the float-float version
+// (below) keeps about 43 significant bits of the radicand.
+// A lane is valid when rho > 0, b rho < 1 and the radicand is finite and
+// >= 0; an invalid lane gets psi = NaN and raises status bit 1 of its lattice.
 enum { EOS_F64 = 0, EOS_DF = 1, EOS_F32 = 2 };
 
+template <class V>
+__device__ __forceinline__ V psi_finish(const LatDev& L, V rho, V s, V arg, uint32_t* status) {
+    V psi;
+#pragma unroll
+    for (int k = 0; k < Lanes<V>::n; ++k) {
+        const float r = Lanes<V>::get(rho, k), a = Lanes<V>::get(arg, k);
+        const bool ok = (r > 0.f) && (Lanes<V>::get(s, k) > 0.f) && (a >= 0.f) && (a < INFINITY);
+        if (!ok) atomicOr(status + L.lattice, 1u);
+        Lanes<V>::put(psi, k, ok ? __fsqrt_rn(a) : __int_as_float(0x7fc00000));
+    }
+    return psi;
+}
+
 template <int P>
-__device__ __forceinline__ float eval_psi(const LatDev& L, float rho, bool& ok);
+struct Eos;
 
+// Native FP64, lane by lane (the FP64 pipe has no paired form).
 template <>
-__device__ __forceinline__ float eval_psi<EOS_F64>(const LatDev& L, float rho, bool& ok) {
-    const double r = (double)rho;
-    const double s = fma(-L.eb, r, 1.0);
-    const double rr = 1.0 / s;
-    const double q = fma(2.0 * rr, rr * rr, fma(-2.0, rr, 1.0));
-    const double arg = r * fma(L.e1, q, -fma(L.e2, r, L.e3));
-    ok = (rho > 0.f) && (s > 0.0) && (arg >= 0.0) && isfinite(arg);
-    return sqrtf((float)arg);
-}
+struct Eos<EOS_F64> {
+    template <class V>
+    static __device__ __forceinline__ V psi(const LatDev& L, V rho, uint32_t* status) {
+        V s, arg;
+#pragma unroll
+        for (int k = 0; k < Lanes<V>::n; ++k) {
+            const double r = (double)Lanes<V>::get(rho, k);
+            const double sd = fma(-L.eb, r, 1.0);
+            const double rr = 1.0 / sd;
+            const double q = fma(2.0 * rr, rr * rr, fma(-2.0, rr, 1.0));
+            const double a = r * fma(L.e1, q, -fma(L.e2, r, L.e3));
+            Lanes<V>::put(s, k, sd > 0.0 ? 1.f : -1.f);
+            Lanes<V>::put(arg, k, (float)a);
+        }
+        return psi_finish(L, rho, s, arg, status);
+    }
+};
 
-// 1/s in float-float: one Newton step on the rounded reciprocal.
-__device__ __forceinline__ df2 df_rcp(df2 s) {
-    const float q = __frcp_rn(s.hi);
-    const float e = __fmaf_rn(-s.lo, q, __fmaf_rn(-s.hi, q, 1.f));  // 1 - s q
-    return fast_two_sum(q, __fmul_rn(q, e));
-}
-
+// Float-float: TwoProd by FMA, TwoSum where signs may differ, FastTwoSum where
+// the larger operand is known, one Newton step on the rounded reciprocal.
+// Computed lane by lane with the scalar instructions: the code generator
+// fuses a paired multiply into a following paired add even when both carry
+// .rn (measured on sm_103a), which would break the error-free
+// transformations, while the scalar .rn forms are kept as written.
 template <>
-__device__ __forceinline__ float eval_psi<EOS_DF>(const LatDev& L, float rho, bool& ok) {
-    const df2 br = df_mul_f(L.fb, rho);
-    df2 s = two_sum(1.f, -br.hi);  // 1 - b rho
-    s = fast_two_sum(s.hi, __fsub_rn(s.lo, br.lo));
-    const df2 r = df_rcp(s);
-    const df2 r3 = df_mul(df_mul(r, r), r);
-    // q = 1 - 2 r + 2 r^3 (doubling is exact)
-    const df2 q = df_add(df_add(df2{1.f, 0.f}, df2{-2.f * r.hi, -2.f * r.lo}),
-                         df2{2.f * r3.hi, 2.f * r3.lo});
-    const df2 t = df_add(df_mul_f(L.f2, rho), L.f3);
-    const df2 inner = df_add(df_mul(L.f1, q), df_neg(t));
-    const df2 arg = df_mul_f(inner, rho);
-    ok = (rho > 0.f) && (s.hi > 0.f) && (arg.hi >= 0.f) && isfinite(arg.hi);
-    return sqrtf(arg.hi);
-}
+struct Eos<EOS_DF> {
+    static __device__ __forceinline__ float lane(const LatDev& L, float rho, float& s) {
+        using V = float;
+        using Ln = Lanes<V>;
+        const V one = Ln::set(1.f), mone = Ln::set(-1.f);
+        // b rho = p - en
+        const V p = vmul(Ln::set(L.fb.hi), rho);
+        V en = vfma(Ln::set(-L.fb.hi), rho, p);
+        en = vfma(Ln::set(-L.fb.lo), rho, en);
+        // s = 1 - b rho = sh + sl  (FastTwoSum, 1 > b rho)
+        const V sh = vsub(one, p);
+        const V sl = vadd(vsub(vsub(one, sh), p), en);
+        // r = 1/s = q - rl  (q the rounded 1/sh, one Newton step)
+        const V q = vrcp(sh);
+        V t = vfma(sh, q, mone);
+        t = vfma(sl, q, t);
+        const V rl = vmul(q, t);
+        // 1 + r = oh + ol  (FastTwoSum, q >= 1)
+        const V oh = vadd(q, one);
+        const V ol = vsub(vadd(vsub(q, oh), one), rl);
+        // r^2 = r2h + r2l
+        const V nq = vmul(q, mone);
+        const V r2h = vmul(q, q), nr2h = vmul(nq, q);
+        const V r2l = vfma(vmul(q, Ln::set(-2.f)), rl, vfma(q, q, nr2h));
+        // A = r^2 (1 + r) = Ah + Ae
+        const V Ah = vmul(r2h, oh);
+        V Ae = vfma(r2h, oh, vmul(nr2h, oh));
+        Ae = vfma(r2h, ol, Ae);
+        Ae = vfma(r2l, oh, Ae);
+        // C1 A = Bh - nBl
+        const V Bh = vmul(Ln::set(L.fC1.hi), Ah);
+        V nBl = vfma(Ln::set(-L.fC1.hi), Ah, Bh);
+        nBl = vfma(Ln::set(-L.fC1.hi), Ae, nBl);
+        nBl = vfma(Ln::set(-L.fC1.lo), Ah, nBl);
+        // v = C1 A - e2 = vh + vl  (TwoSum on the leading parts: they may cancel)
+        const V ne2h = Ln::set(-L.f2.hi);
+        const V vh = vadd(Bh, ne2h);
+        const V bb = vsub(vh, Bh);
+        const V ve = vadd(vsub(Bh, vsub(vh, bb)), vsub(ne2h, bb));
+        const V vl = vadd(vsub(ve, nBl), Ln::set(-L.f2.lo));
+        // w = rho v = wh + we
+        const V wh = vmul(vh, rho);
+        V we = vfma(vh, rho, vmul(vh, vmul(rho, mone)));
+        we = vfma(vl, rho, we);
+        // c0 + w = hh + hl  (FastTwoSum, |c0| >= |w| wherever psi is defined)
+        const V c0h = Ln::set(L.fc0.hi);
+        const V hh = vadd(c0h, wh);
+        const V hl = vadd(vadd(vsub(c0h, hh), wh), vadd(Ln::set(L.fc0.lo), we));
+        s = sh;
+        return vfma(rho, hh, vmul(rho, hl));
+    }
+    template <class V>
+    static __device__ __forceinline__ V psi(const LatDev& L, V rho, uint32_t* status) {
+        V s, arg;
+#pragma unroll
+        for (int k = 0; k < Lanes<V>::n; ++k) {
+            float sk;
+            Lanes<V>::put(arg, k, lane(L, Lanes<V>::get(rho, k), sk));
+            Lanes<V>::put(s, k, sk);
+        }
+        return psi_finish(L, rho, s, arg, status);
+    }
+};
 
+// Plain FP32 (selectable; no extended precision).
 template <>
-__device__ __forceinline__ float eval_psi<EOS_F32>(const LatDev& L, float rho, bool& ok) {
-    const float s = fmaf(-L.sb, rho, 1.f);
-    const float rr = 1.f / s;
-    const float q = fmaf(2.f * rr, rr * rr, fmaf(-2.f, rr, 1.f));
-    const float arg = rho * fmaf(L.s1, q, -fmaf(L.s2, rho, L.s3));
-    ok = (rho > 0.f) && (s > 0.f) && (arg >= 0.f) && isfinite(arg);
-    return sqrtf(arg);
-}
+struct Eos<EOS_F32> {
+    template <class V>
+    static __device__ __forceinline__ V psi(const LatDev& L, V rho, uint32_t* status) {
+        using Ln = Lanes<V>;
+        const V one = Ln::set(1.f);
+        const V s = vfma(Ln::set(-L.sb), rho, one);
+        V rr;
+#pragma unroll
+        for (int k = 0; k < Ln::n; ++k) Ln::put(rr, k, __frcp_rn(Ln::get(s, k)));
+        const V q = vfma(vadd(rr, rr), vmul(rr, rr), vfma(Ln::set(-2.f), rr, one));
+        const V inner = vfma(Ln::set(L.s1), q, vfma(Ln::set(-L.s2), rho, Ln::set(-L.s3)));
+        return psi_finish(L, rho, s, vmul(rho, inner), status);
+    }
+};
 
 // ---- force of Eq. (IFT) from the nine psi values around a site ------------
-// p[0] = psi(x); p[i] = psi(x + c_i).
-// M1 and M2 (Eqs. FOMED, SOMED) with the D2Q9 weights multiplied out.
-struct Force {
-    float x, y;
-};
-__device__ __forceinline__ Force site_force(const LatDev& L, float p0, float pE, float pN,
-                                            float pW, float pS, float pNE, float pNW,
-                                            float pSW, float pSE) {
-    const float m1x = (4.f * (pE - pW) + (pNE - pNW) + (pSE - pSW)) * (1.f / 36.f);
-    const float m1y = (4.f * (pN - pS) + (pNE + pNW) - (pSW + pSE)) * (1.f / 36.f);
-    const float sd = (pNE + pNW) + (pSW + pSE);
-    const float sx = pE + pW, sy = pN + pS;
-    const float m2xx = (-8.f * p0 + 4.f * sx - 2.f * sy + sd) * (1.f / 54.f);
-    const float m2yy = (-8.f * p0 + 4.f * sy - 2.f * sx + sd) * (1.f / 54.f);
-    const float m2xy = ((pNE - pNW) + (pSW - pSE)) * (1.f / 36.f);
-    const float tr = L.m2_variant ? (-20.f * p0 + 4.f * (sx + sy) + sd) * (1.f / 54.f)
-                                  : (m2xx + m2yy);
-    const float ax = m1x * m2xx + m1y * m2xy;  // M1_b M2_ab
-    const float ay = m1x * m2xy + m1y * m2yy;
-    Force F;
-    F.x = L.k_sc * p0 * m1x + L.k1 * ax + L.k2 * (m1x * tr - ax);
-    F.y = L.k_sc * p0 * m1y + L.k1 * ay + L.k2 * (m1y * tr - ay);
-    return F;
-}
-
-// ---- BGK collision with Guo forcing for direction I ------------------------
-// g: stored (deviation) population; returns the post-collision value.
-// f^eq - w rho0 = w (drho + rho (3 cu + 9/2 cu^2 - 3/2 u^2))          Eq. (SEDF)
-// S = (1 - 1/2tau) w (3 cF + 9 cF cu - 3 F.u)                          Eqs. (GFS), (GFSBGK)
-template <int I>
-__device__ __forceinline__ float bgk_guo(float g, float drho, float rho, float ux, float uy,
-                                         float usq, float Fx, float Fy, float Fu, float omega,
-                                         float guo) {
-    constexpr float w = Vel<I>::w;
-    const float cu = (float)Vel<I>::x * ux + (float)Vel<I>::y * uy;
-    const float cF = (float)Vel<I>::x * Fx + (float)Vel<I>::y * Fy;
-    const float feq = w * (drho + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * usq));
-    const float src = guo * w * (3.f * cF + 9.f * cF * cu - 3.f * Fu);
-    return g + omega * (feq - g) + src;
-}
-
-// Per-lattice constants of one site update, held in registers for a tile.
+// p[0] = psi(x); p[i] = psi(x + c_i), i = E, N, W, S, NE, NW, SW, SE.
+// With M1 and M2 of Eqs. (FOMED), (SOMED) written as integer stencils
+// m1' = 36 M1, m2'_xx = 54 M2_xx, m2'_yy = 54 M2_yy, m2''_xy = 54 M2_xy,
+// tr' = 54 tr M2 (either trace variant), the force
+//   F = k_sc psi M1 + k1 M1.M2 + k2 (M1 tr M2 - M1.M2)
+// becomes F = m1' (fsc psi + fk2 tr') + fkd (m1'.m2'), with fsc = k_sc/36,
+// fk2 = k2/1944, fkd = (k1 - k2)/1944 (LatDev).
 struct SiteConsts {
-    float omega, guo, rho0, k_sc, k1, k2;
+    float rho0, om1, wa, wd, ra, rd, sa, sd, ga9, gd9, ga3, gd3, fsc, fk2, fkd;
     int m2v;
 };
-__device__ __forceinline__ SiteConsts site_consts(const LatDev& L) {
-    return SiteConsts{L.omega, L.guo, L.rho0, L.k_sc, L.k1, L.k2, L.m2_variant};
+
+template <class V>
+__device__ __forceinline__ void site_force(const SiteConsts& C, const V p[9], V& Fx, V& Fy) {
+    using Ln = Lanes<V>;
+    const V four = Ln::set(4.f);
+    const V dEW = vsub(p[1], p[3]), dNS = vsub(p[2], p[4]);
+    const V a = vsub(p[5], p[7]), b = vsub(p[6], p[8]);
+    const V m1x = vfma(four, dEW, vsub(a, b));
+    const V m1y = vfma(four, dNS, vadd(a, b));
+    const V sx = vadd(p[1], p[3]), sy = vadd(p[2], p[4]);
+    const V s1 = vadd(p[5], p[7]), s2 = vadd(p[6], p[8]);
+    const V sd = vadd(s1, s2);
+    const V base = vfma(Ln::set(-8.f), p[0], sd);
+    const V m2xx = vfma(four, sx, vfma(Ln::set(-2.f), sy, base));
+    const V m2yy = vfma(four, sy, vfma(Ln::set(-2.f), sx, base));
+    const V m2xy = vmul(Ln::set(1.5f), vsub(s1, s2));
+    const V tr = C.m2v ? vfma(Ln::set(-20.f), p[0], vfma(four, vadd(sx, sy), sd))
+                       : vadd(m2xx, m2yy);
+    const V ax = vfma(m1x, m2xx, vmul(m1y, m2xy));
+    const V ay = vfma(m1x, m2xy, vmul(m1y, m2yy));
+    const V cp = vfma(Ln::set(C.fsc), p[0], vmul(Ln::set(C.fk2), tr));
+    const V kd = Ln::set(C.fkd);
+    Fx = vfma(m1x, cp, vmul(kd, ax));
+    Fy = vfma(m1y, cp, vmul(kd, ay));
 }
 
-// One site of the collision pass: pulled (deviation) populations g[0..8]
-// and psi at x + c_i (p[0] = psi(x), then E, N, W, S, NE, NW, SW, SE) in,
-// post-collision deviations o[0..8] out.
-//   rho, j     Eqs. (FD), (FMD)
-//   F          Eq. (IFT) via site_force
-//   f*_i       Eqs. (BGKCO), (SEDF), (GFS), (GFSBGK), with opposite
-//              directions sharing their terms: for c and -c,
-//              f^eq = w (base + rho cu (3 +- 9/2 cu)) with base = drho - 3/2 rho u^2,
-//              S    = gu w (9 cF cu +- 3 cF - 3 F.u);
-// the rest population f*_0 takes what mass conservation leaves (in exact
+__device__ __forceinline__ SiteConsts site_consts(const LatDev& L) {
+    return SiteConsts{L.rho0, L.om1, L.wa, L.wd, L.ra, L.rd, L.sa, L.sd, L.ga9, L.gd9,
+                      L.ga3, L.gd3, L.fsc, L.fk2, L.fkd, L.m2_variant};
+}
+
+// ---- BGK collision with Guo forcing -------------------------------------------
+// Pulled (deviation) populations g[0..8], their sum drho (sum9) and psi
+// around the site p[0..8] in, post-collision deviations o[0..8] out.
+//   rho, j     Eqs. (FD), (FMD);  u = (j + F/2)/rho
+//   f*_i = f_i - omega (f_i - f^eq_i) + (1 - 1/2tau) S_i       Eqs. (BGKCO), (GFSBGK)
+//   f^eq_i - w_i rho0 = w_i (drho + rho (3 cu + 9/2 cu^2 - 3/2 u^2))   Eq. (SEDF)
+//   S_i = w_i (3 cF + 9 cF cu - 3 F.u)                          Eq. (GFS)
+// For a pair of opposite directions c, -c of weight w this is
+//   f*_{+-} = (1 - omega) g_{+-} + P +- Q,
+//   P = omega w base - 3 guo w F.u + cu (9/2 omega w rho cu + 9 guo w cF),
+//   Q = 3 omega w rho cu + 3 guo w cF,   base = drho - 3/2 rho u^2,
+// with the per-class constants of LatDev (axis w = 1/9, diagonal w = 1/36).
+// The rest population f*_0 takes what mass conservation leaves (in exact
 // arithmetic the same number; it keeps the FP32 weights, whose sum is not
 // exactly 1, from adding a biased mass error every step).
-__device__ __forceinline__ void collide_site(const SiteConsts& C, const float g[9],
-                                             const float p[9], float o[9]) {
-    const float drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-    const float rho = drho + C.rho0;
-    const float jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
-    const float jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
-    LatDev dummy;  // site_force reads only the force coefficients and the trace flag
-    dummy.k_sc = C.k_sc;
-    dummy.k1 = C.k1;
-    dummy.k2 = C.k2;
-    dummy.m2_variant = C.m2v;
-    const Force F = site_force(dummy, p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], p[8]);
-    const float inv = __frcp_rn(rho);
-    const float ux = fmaf(0.5f, F.x, jx) * inv;  // Eq. (FMD)
-    const float uy = fmaf(0.5f, F.y, jy) * inv;
-    const float usq = ux * ux + uy * uy;
-    const float f3u = 3.f * (F.x * ux + F.y * uy);
-    const float base = drho - 1.5f * rho * usq;
-    const float om = C.omega;
-    const float ga = C.guo * (1.f / 9.f), gd = C.guo * (1.f / 36.f);
-    float s1 = 0.f;
-    // one pair of opposite directions (I, J = opposite of I), weight w, guo weight gw
-#define PPLBM_PAIR(I, J, W, GW, CU, CF)                                             \
-    {                                                                               \
-        const float cu = (CU), cF = (CF);                                           \
-        const float t = rho * cu;                                                   \
-        const float a = 4.5f * t * cu, b = 3.f * t;                                 \
-        const float s2 = 9.f * cF * cu - f3u, s3 = 3.f * cF;                        \
-        const float fi = (W) * (base + a + b), fj = (W) * (base + a - b);          \
-        const float oi = fmaf(om, fi - g[I], g[I]) + (GW) * (s2 + s3);              \
-        const float oj = fmaf(om, fj - g[J], g[J]) + (GW) * (s2 - s3);              \
-        o[I] = oi;                                                                  \
-        o[J] = oj;                                                                  \
-        s1 += oi + oj;                                                              \
+template <class V>
+__device__ __forceinline__ void collide_bgk(const SiteConsts& C, V drho, const V g[9],
+                                            const V p[9], V o[9]) {
+    using Ln = Lanes<V>;
+    const V rho = vadd(drho, Ln::set(C.rho0));
+    const V jx = vadd(vadd(vsub(g[1], g[3]), vsub(g[5], g[6])), vsub(g[8], g[7]));
+    const V jy = vsub(vadd(vsub(g[2], g[4]), vadd(g[5], g[6])), vadd(g[7], g[8]));
+    V Fx, Fy;
+    site_force(C, p, Fx, Fy);
+    const V inv = vrcp(rho);
+    const V half = Ln::set(0.5f);
+    const V ux = vmul(vfma(half, Fx, jx), inv);  // Eq. (FMD)
+    const V uy = vmul(vfma(half, Fy, jy), inv);
+    const V usq = vfma(ux, ux, vmul(uy, uy));
+    const V Fu = vfma(Fx, ux, vmul(Fy, uy));
+    const V base = vfma(vmul(Ln::set(-1.5f), rho), usq, drho);
+    const V Pa = vfma(Ln::set(C.wa), base, vmul(Ln::set(-C.ga3), Fu));
+    const V Pd = vfma(Ln::set(C.wd), base, vmul(Ln::set(-C.gd3), Fu));
+    const V Ra = vmul(Ln::set(C.ra), rho), Rd = vmul(Ln::set(C.rd), rho);
+    const V Sa = vmul(Ln::set(C.sa), rho), Sd = vmul(Ln::set(C.sd), rho);
+    const V om1 = Ln::set(C.om1);
+#define PPLBM_PAIR(I, J, CU, CF, R, S, P, G9, G3)                          \
+    {                                                                      \
+        const V cu = (CU), cF = (CF);                                      \
+        const V z = vfma(R, cu, vmul(Ln::set(G9), cF));                    \
+        const V pp = vfma(cu, z, P);                                       \
+        const V qq = vfma(S, cu, vmul(Ln::set(G3), cF));                   \
+        o[I] = vadd(vfma(om1, g[I], pp), qq);                              \
+        o[J] = vsub(vfma(om1, g[J], pp), qq);                              \
     }
-    PPLBM_PAIR(1, 3, 1.f / 9.f, ga, ux, F.x)
-    PPLBM_PAIR(2, 4, 1.f / 9.f, ga, uy, F.y)
-    PPLBM_PAIR(5, 7, 1.f / 36.f, gd, ux + uy, F.x + F.y)
-    PPLBM_PAIR(6, 8, 1.f / 36.f, gd, uy - ux, F.y - F.x)
+    PPLBM_PAIR(1, 3, ux, Fx, Ra, Sa, Pa, C.ga9, C.ga3)
+    PPLBM_PAIR(2, 4, uy, Fy, Ra, Sa, Pa, C.ga9, C.ga3)
+    // the diagonal projections u.c = (j.c + F.c/2)/rho are products of their
+    // own: no product ever feeds a paired add (see Eos<EOS_DF>)
+    {
+        const V F5 = vadd(Fx, Fy), F6 = vsub(Fy, Fx);
+        const V cu5 = vmul(vfma(half, F5, vadd(jx, jy)), inv);
+        const V cu6 = vmul(vfma(half, F6, vsub(jy, jx)), inv);
+        PPLBM_PAIR(5, 7, cu5, F5, Rd, Sd, Pd, C.gd9, C.gd3)
+        PPLBM_PAIR(6, 8, cu6, F6, Rd, Sd, Pd, C.gd9, C.gd3)
+    }
 #undef PPLBM_PAIR
-    o[0] = drho - s1;
+    o[0] = vsub(drho, vadd(vadd(vadd(o[1], o[2]), vadd(o[3], o[4])),
+                           vadd(vadd(o[5], o[6]), vadd(o[7], o[8]))));
 }
 
 // MRT collision (Eq. MRTCO) with Guo forcing in moment space (Eq. GFSMRT),
-// for the Gram-Schmidt matrix M of Appendix A.  Same inputs and outputs as
-// collide_site.  Moments of the stored deviations: m(f) = M g + rho0 M w with
-// M w = (1, -2, 1, 0, ..., 0).  Post-collision moments
-//   m* = m - Lambda (m - m^eq) + (I - Lambda/2) M S
-// with m^eq and M S the vectors printed in Appendix A (rho u is the
-// force-shifted momentum of Eq. FMD).  Back to populations with
-// M^-1 = M^T D^-1, D = diag(9, 36, 36, 6, 12, 6, 12, 4, 4) (the rows of M
-// are orthogonal); the rest population again from mass conservation.
-__device__ __forceinline__ void collide_site_mrt(const SiteConsts& C, const float* s,
+// for the Gram-Schmidt matrix M of Appendix A, one site.  Written on the
+// non-equilibrium part n = f - f^eq, which is small, so rounding scales with
+// it and not with rho:
+//   f* = f^eq + M^-1 [ (I - Lambda) M n + (I - Lambda/2) M S ],
+// the same update as f - M^-1 Lambda M (f - f^eq) + M^-1 (I - Lambda/2) M S.
+// f^eq is the equilibrium of Eq. (SEDF); M S is the vector printed in
+// Appendix A; the conserved moments of n are exact: (M n)_0 = 0,
+// (M n)_3 = -F_x/2, (M n)_5 = -F_y/2 (Eq. FMD).  Back to populations with
+// M^-1 = M^T D^-1, D = diag(9, 36, 36, 6, 12, 6, 12, 4, 4) (the rows of M are
+// orthogonal); the rest population from mass conservation.
+__device__ __forceinline__ void collide_mrt_site(const SiteConsts& C, const float* s,
                                                  const float g[9], const float p[9],
                                                  float o[9]) {
     const float drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
     const float rho = drho + C.rho0;
     const float jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
     const float jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
-    LatDev dummy;
-    dummy.k_sc = C.k_sc;
-    dummy.k1 = C.k1;
-    dummy.k2 = C.k2;
-    dummy.m2_variant = C.m2v;
-    const Force F = site_force(dummy, p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], p[8]);
-    const float inv = __frcp_rn(rho);
-    const float rux = fmaf(0.5f, F.x, jx), ruy = fmaf(0.5f, F.y, jy);  // rho u, Eq. (FMD)
-    const float ux = rux * inv, uy = ruy * inv;
+    float Fx, Fy;
+    site_force(C, p, Fx, Fy);
+    const float inv = rcp_rn(rho);
+    const float ux = fmaf(0.5f, Fx, jx) * inv;  // Eq. (FMD)
+    const float uy = fmaf(0.5f, Fy, jy) * inv;
     const float usq = ux * ux + uy * uy;
-    const float uF = ux * F.x + uy * F.y;
-    // moments of f (deviations shifted by rho0 M w)
-    const float sa = (g[1] + g[2]) + (g[3] + g[4]), sd = (g[5] + g[6]) + (g[7] + g[8]);
-    const float m1 = (-4.f * g[0] - sa + 2.f * sd) - 2.f * C.rho0;
-    const float m2 = (4.f * g[0] - 2.f * sa + sd) + C.rho0;
-    const float m4 = (-2.f * g[1] + 2.f * g[3]) + ((g[5] - g[6]) + (g[8] - g[7]));
-    const float m6 = (-2.f * g[2] + 2.f * g[4]) + ((g[5] + g[6]) - (g[7] + g[8]));
-    const float m7 = (g[1] - g[2]) + (g[3] - g[4]);
-    const float m8 = (g[5] - g[6]) + (g[7] - g[8]);
-    // m* = m - s (m - meq) + (1 - s/2) Sbar, component by component
-    const float r3u2 = 3.f * rho * usq;
-    const float p1 = m1 - s[1] * (m1 - (-2.f * rho + r3u2)) + (1.f - 0.5f * s[1]) * (6.f * uF);
-    const float p2 = m2 - s[2] * (m2 - (rho - r3u2)) + (1.f - 0.5f * s[2]) * (-6.f * uF);
-    const float p3 = jx - s[3] * (jx - rux) + (1.f - 0.5f * s[3]) * F.x;
-    const float p4 = m4 - s[4] * (m4 + rux) + (1.f - 0.5f * s[4]) * (-F.x);
-    const float p5 = jy - s[5] * (jy - ruy) + (1.f - 0.5f * s[5]) * F.y;
-    const float p6 = m6 - s[6] * (m6 + ruy) + (1.f - 0.5f * s[6]) * (-F.y);
-    const float p7 = m7 - s[7] * (m7 - rho * (ux * ux - uy * uy)) +
-                     (1.f - 0.5f * s[7]) * (2.f * (ux * F.x - uy * F.y));
-    const float p8 = m8 - s[8] * (m8 - rho * ux * uy) + (1.f - 0.5f * s[8]) * (ux * F.y + uy * F.x);
-    // back to deviations: subtract rho0 M w from the moments, then M^T D^-1
-    const float q0 = drho * (1.f / 9.f);
-    const float q1 = (p1 + 2.f * C.rho0) * (1.f / 36.f);
-    const float q2 = (p2 - C.rho0) * (1.f / 36.f);
+    const float uF = ux * Fx + uy * Fy;
+    const float base = drho - 1.5f * rho * usq;
+    // equilibrium deviations f^eq_i - w_i rho0
+    float e[9];
+    {
+        const float a1 = 4.5f * rho * ux * ux, b1 = 3.f * rho * ux;
+        const float a2 = 4.5f * rho * uy * uy, b2 = 3.f * rho * uy;
+        const float c5 = ux + uy, c6 = uy - ux;
+        const float a5 = 4.5f * rho * c5 * c5, b5 = 3.f * rho * c5;
+        const float a6 = 4.5f * rho * c6 * c6, b6 = 3.f * rho * c6;
+        e[1] = (1.f / 9.f) * (base + a1 + b1);
+        e[3] = (1.f / 9.f) * (base + a1 - b1);
+        e[2] = (1.f / 9.f) * (base + a2 + b2);
+        e[4] = (1.f / 9.f) * (base + a2 - b2);
+        e[5] = (1.f / 36.f) * (base + a5 + b5);
+        e[7] = (1.f / 36.f) * (base + a5 - b5);
+        e[6] = (1.f / 36.f) * (base + a6 + b6);
+        e[8] = (1.f / 36.f) * (base + a6 - b6);
+        e[0] = (4.f / 9.f) * base;
+    }
+    float n[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) n[i] = g[i] - e[i];
+    // non-conserved moments of n
+    const float sa = (n[1] + n[2]) + (n[3] + n[4]), sd = (n[5] + n[6]) + (n[7] + n[8]);
+    const float m1 = -4.f * n[0] - sa + 2.f * sd;
+    const float m2 = 4.f * n[0] - 2.f * sa + sd;
+    const float m4 = (-2.f * n[1] + 2.f * n[3]) + ((n[5] - n[6]) + (n[8] - n[7]));
+    const float m6 = (-2.f * n[2] + 2.f * n[4]) + ((n[5] + n[6]) - (n[7] + n[8]));
+    const float m7 = (n[1] - n[2]) + (n[3] - n[4]);
+    const float m8 = (n[5] - n[6]) + (n[7] - n[8]);
+    // (I - Lambda) M n + (I - Lambda/2) M S, moment by moment
+    const float p1 = (1.f - s[1]) * m1 + (1.f - 0.5f * s[1]) * (6.f * uF);
+    const float p2 = (1.f - s[2]) * m2 + (1.f - 0.5f * s[2]) * (-6.f * uF);
+    const float p3 = (1.f - s[3]) * (-0.5f * Fx) + (1.f - 0.5f * s[3]) * Fx;
+    const float p4 = (1.f - s[4]) * m4 + (1.f - 0.5f * s[4]) * (-Fx);
+    const float p5 = (1.f - s[5]) * (-0.5f * Fy) + (1.f - 0.5f * s[5]) * Fy;
+    const float p6 = (1.f - s[6]) * m6 + (1.f - 0.5f * s[6]) * (-Fy);
+    const float p7 = (1.f - s[7]) * m7 + (1.f - 0.5f * s[7]) * (2.f * (ux * Fx - uy * Fy));
+    const float p8 = (1.f - s[8]) * m8 + (1.f - 0.5f * s[8]) * (ux * Fy + uy * Fx);
+    // M^T D^-1 (the mass moment of the update is zero)
+    const float q1 = p1 * (1.f / 36.f), q2 = p2 * (1.f / 36.f);
     const float q3 = p3 * (1.f / 6.f), q4 = p4 * (1.f / 12.f);
     const float q5 = p5 * (1.f / 6.f), q6 = p6 * (1.f / 12.f);
     const float q7 = p7 * 0.25f, q8 = p8 * 0.25f;
-    const float ax = q0 - q1 - 2.f * q2;  // common part of the axis directions
-    const float dg = q0 + 2.f * q1 + q2;  // common part of the diagonals
-    o[1] = ax + q3 - 2.f * q4 + q7;
-    o[2] = ax + q5 - 2.f * q6 - q7;
-    o[3] = ax - q3 + 2.f * q4 + q7;
-    o[4] = ax - q5 + 2.f * q6 - q7;
-    o[5] = dg + q3 + q4 + q5 + q6 + q8;
-    o[6] = dg - q3 - q4 + q5 + q6 - q8;
-    o[7] = dg - q3 - q4 - q5 - q6 + q8;
-    o[8] = dg + q3 + q4 - q5 - q6 - q8;
+    const float ax = -q1 - 2.f * q2;  // common part of the axis directions
+    const float dg = 2.f * q1 + q2;   // common part of the diagonals
+    o[1] = e[1] + (ax + q3 - 2.f * q4 + q7);
+    o[2] = e[2] + (ax + q5 - 2.f * q6 - q7);
+    o[3] = e[3] + (ax - q3 + 2.f * q4 + q7);
+    o[4] = e[4] + (ax - q5 + 2.f * q6 - q7);
+    o[5] = e[5] + (dg + q3 + q4 + q5 + q6 + q8);
+    o[6] = e[6] + (dg - q3 - q4 + q5 + q6 - q8);
+    o[7] = e[7] + (dg - q3 - q4 - q5 - q6 + q8);
+    o[8] = e[8] + (dg + q3 + q4 - q5 - q6 - q8);
     o[0] = drho - (((o[1] + o[2]) + (o[3] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
 }
 
+// One collision (BGK or MRT) of the sites held in the lanes of V.
+template <bool MRT, class V>
+__device__ __forceinline__ void collide(const SiteConsts& C, const float* mrt_s, V drho,
+                                        const V g[9], const V p[9], V o[9]) {
+    if (!MRT) {
+        collide_bgk(C, drho, g, p, o);
+    } else {
+#pragma unroll
+        for (int k = 0; k < Lanes<V>::n; ++k) {
+            float gs[9], ps[9], os[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                gs[i] = Lanes<V>::get(g[i], k);
+                ps[i] = Lanes<V>::get(p[i], k);
+            }
+            collide_mrt_site(C, mrt_s, gs, ps, os);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Lanes<V>::put(o[i], k, os[i]);
+        }
+    }
+}
+
 // Store the nine outputs of site (x, y): interior sites with plain stores,
-// sites within GW of an edge also into their periodic images.
+// sites within GW of an edge also into their periodic images.  `tile_in`
+// says the whole tile is interior (uniform per block), which skips the
+// per-site test.
 template <class S>
 __device__ __forceinline__ void store_site(typename S::T* o, int64_t plane, int pitch, int gx,
-                                           int x, int y, int nx, int ny, const float v[9]) {
-    const bool interior = (x >= GW) & (x < nx - GW) & (y >= GW) & (y < ny - GW);
-    if (interior) {
+                                           int x, int y, int nx, int ny, const float v[9],
+                                           bool tile_in = false) {
+    if (tile_in || ((x >= GW) & (x < nx - GW) & (y >= GW) & (y < ny - GW))) {
         typename S::T* q = o + (int64_t)(y + GY) * pitch + (x + gx);
 #pragma unroll
         for (int i = 0; i < 9; ++i) q[i * plane] = S::cv(v[i]);

@@ -14,14 +14,36 @@
 
 namespace pplbm {
 
-// Both plain passes give each thread SPT sites of one column (rows
+// Each plain pass gives a thread SPT sites of one column (rows
 // threadIdx.y + k blockDim.y): all SPT x 9 loads are issued before any of
-// them is used, which keeps more bytes in flight per thread.
+// them is used, which keeps more bytes in flight per thread.  With SPT even,
+// sites k and k+1 share the lanes of one float2 and go through the EOS and
+// the collision together on the paired FP32 instructions.
+
+// Pulled density deviation at (x, y): f_i(x) = f*_i(x - c_i) summed in the
+// fixed order of sum9.  `f` points at (x, y) of plane 0 of the buffer.
+template <class S>
+__device__ __forceinline__ float pulled_drho(const typename S::T* f, int64_t plane, int pitch) {
+    float v[9];
+    v[0] = S::ld(f);
+    v[1] = S::ld(f + 1 * plane - 1);
+    v[2] = S::ld(f + 2 * plane - pitch);
+    v[3] = S::ld(f + 3 * plane + 1);
+    v[4] = S::ld(f + 4 * plane + pitch);
+    v[5] = S::ld(f + 5 * plane - pitch - 1);
+    v[6] = S::ld(f + 6 * plane - pitch + 1);
+    v[7] = S::ld(f + 7 * plane + pitch + 1);
+    v[8] = S::ld(f + 8 * plane + pitch - 1);
+    return sum9(v);
+}
 
 // ---------------------------------------------------------------- pass 1: psi
 template <class S, int EOSP, int SPT>
 __global__ void __launch_bounds__(512) k_psi(StepArgs a) {
     using T = typename S::T;
+    using V = typename LaneOf<SPT>::V;
+    using Ln = Lanes<V>;
+    constexpr int NV = SPT / Ln::n;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const int4 tl = __ldg(&a.tiles[t]);
         if (a.quota && a.step >= __ldg(&a.quota[tl.x])) continue;
@@ -32,29 +54,92 @@ __global__ void __launch_bounds__(512) k_psi(StepArgs a) {
         const int pitch = L.pitch;
         const int64_t plane = L.plane;
         const T* base = reinterpret_cast<const T*>(a.pop) + L.off_f[a.parity] + (x + L.gx);
-        float d[SPT];
+        V d[NV];
 #pragma unroll
         for (int k = 0; k < SPT; ++k) {
             const int y = min(tl.z + (int)threadIdx.y + k * (int)blockDim.y, ny - 1);
-            const T* f = base + (int64_t)(y + GY) * pitch;
-            // pull f_i(x) = f*_i(x - c_i)
-            d[k] = ((S::ld(f) + S::ld(f + 1 * plane - 1)) +
-                    (S::ld(f + 2 * plane - pitch) + S::ld(f + 3 * plane + 1))) +
-                   ((S::ld(f + 4 * plane + pitch) + S::ld(f + 5 * plane - pitch - 1)) +
-                    (S::ld(f + 6 * plane - pitch + 1) + S::ld(f + 7 * plane + pitch + 1))) +
-                   S::ld(f + 8 * plane + pitch - 1);
+            Ln::put(d[k / Ln::n], k % Ln::n,
+                    pulled_drho<S>(base + (int64_t)(y + GY) * pitch, plane, pitch));
         }
+        const V rho0 = Ln::set(L.rho0);
 #pragma unroll
-        for (int k = 0; k < SPT; ++k) {
-            const int y = tl.z + (int)threadIdx.y + k * (int)blockDim.y;
-            if (y >= ny) break;
-            bool ok;
-            float psi = eval_psi<EOSP>(L, d[k] + L.rho0, ok);
-            if (!ok) {
-                atomicOr(&a.status[L.lattice], 1u);
-                psi = __int_as_float(0x7fc00000);
+        for (int j = 0; j < NV; ++j) {
+            const V psi = Eos<EOSP>::psi(L, vadd(d[j], rho0), a.status);
+#pragma unroll
+            for (int l = 0; l < Ln::n; ++l) {
+                const int y = tl.z + (int)threadIdx.y + (j * Ln::n + l) * (int)blockDim.y;
+                if (y < ny)
+                    store_img(a.psi + L.off_psi, L.pitch_psi, L.gx_psi, x, y, nx, ny,
+                              Ln::get(psi, l));
             }
-            store_img(a.psi + L.off_psi, L.pitch_psi, L.gx_psi, x, y, nx, ny, psi);
+        }
+    }
+}
+
+// Loads the nine pulled populations of SPT sites of one column into lanes.
+template <class S, int SPT, class V>
+__device__ __forceinline__ void load_sites(const typename S::T* base, int64_t plane, int pitch,
+                                           int y0, int by, int ny, V (*g)[9]) {
+    using Ln = Lanes<V>;
+#pragma unroll
+    for (int k = 0; k < SPT; ++k) {
+        const int y = min(y0 + k * by, ny - 1);
+        const typename S::T* f = base + (int64_t)(y + GY) * pitch;
+        V* gk = g[k / Ln::n];
+        const int l = k % Ln::n;
+        Ln::put(gk[0], l, S::ld(f));
+        Ln::put(gk[1], l, S::ld(f + 1 * plane - 1));
+        Ln::put(gk[2], l, S::ld(f + 2 * plane - pitch));
+        Ln::put(gk[3], l, S::ld(f + 3 * plane + 1));
+        Ln::put(gk[4], l, S::ld(f + 4 * plane + pitch));
+        Ln::put(gk[5], l, S::ld(f + 5 * plane - pitch - 1));
+        Ln::put(gk[6], l, S::ld(f + 6 * plane - pitch + 1));
+        Ln::put(gk[7], l, S::ld(f + 7 * plane + pitch + 1));
+        Ln::put(gk[8], l, S::ld(f + 8 * plane + pitch - 1));
+    }
+}
+
+// Whether every site of the tile at (x0, y0) lies at least GW from each edge
+// (then no site of it has periodic images to write).
+__device__ __forceinline__ bool tile_interior(int x0, int y0, int TX, int TY, int nx, int ny) {
+    return x0 >= GW && y0 >= GW && x0 + TX <= nx - GW && y0 + TY <= ny - GW;
+}
+
+// Collision of the SPT sites of a thread from the psi tile in shared memory
+// (row stride W, the thread's column at offset tx + 1) and their stores.
+template <class S, int SPT, bool MRT, class V>
+__device__ __forceinline__ void collide_store(const LatDev& L, const float* sps, int W, int tx,
+                                              int ly0, int by, int x, int y0, const V* drho,
+                                              V (*g)[9], typename S::T* o, bool tile_in) {
+    using Ln = Lanes<V>;
+    constexpr int NV = SPT / Ln::n;
+    const SiteConsts C = site_consts(L);
+    const int nx = L.nx, ny = L.ny;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        V p[9], v[9];
+#pragma unroll
+        for (int l = 0; l < Ln::n; ++l) {
+            const float* c = sps + (ly0 + (j * Ln::n + l) * by + 1) * W + (tx + 1);
+            Ln::put(p[0], l, c[0]);
+            Ln::put(p[1], l, c[1]);
+            Ln::put(p[2], l, c[W]);
+            Ln::put(p[3], l, c[-1]);
+            Ln::put(p[4], l, c[-W]);
+            Ln::put(p[5], l, c[W + 1]);
+            Ln::put(p[6], l, c[W - 1]);
+            Ln::put(p[7], l, c[-W - 1]);
+            Ln::put(p[8], l, c[-W + 1]);
+        }
+        collide<MRT>(C, L.mrt_s, drho[j], g[j], p, v);
+#pragma unroll
+        for (int l = 0; l < Ln::n; ++l) {
+            const int y = y0 + (j * Ln::n + l) * by;
+            if (y >= ny) break;
+            float vs[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) vs[i] = Ln::get(v[i], l);
+            store_site<S>(o, L.plane, L.pitch, L.gx, x, y, nx, ny, vs, tile_in);
         }
     }
 }
@@ -63,6 +148,8 @@ __global__ void __launch_bounds__(512) k_psi(StepArgs a) {
 template <class S, int SPT, bool MRT>
 __global__ void __launch_bounds__(512) k_collide(StepArgs a) {
     using T = typename S::T;
+    using V = typename LaneOf<SPT>::V;
+    constexpr int NV = SPT / Lanes<V>::n;
     extern __shared__ float sps[];
     const int TX = blockDim.x, BY = blockDim.y, TY = BY * SPT;
     const int W = TX + 2;
@@ -87,52 +174,18 @@ __global__ void __launch_bounds__(512) k_collide(StepArgs a) {
             }
         }
         const int x = tl.y + threadIdx.x;
-        const int pitch = L.pitch;
-        const int64_t plane = L.plane;
         const T* base = reinterpret_cast<const T*>(a.pop) + L.off_f[a.parity] + (x + L.gx);
-        float g[SPT][9];
-        if (x < nx) {
-#pragma unroll
-            for (int k = 0; k < SPT; ++k) {
-                const int y = min(tl.z + (int)threadIdx.y + k * BY, ny - 1);
-                const T* f = base + (int64_t)(y + GY) * pitch;
-                g[k][0] = S::ld(f);
-                g[k][1] = S::ld(f + 1 * plane - 1);
-                g[k][2] = S::ld(f + 2 * plane - pitch);
-                g[k][3] = S::ld(f + 3 * plane + 1);
-                g[k][4] = S::ld(f + 4 * plane + pitch);
-                g[k][5] = S::ld(f + 5 * plane - pitch - 1);
-                g[k][6] = S::ld(f + 6 * plane - pitch + 1);
-                g[k][7] = S::ld(f + 7 * plane + pitch + 1);
-                g[k][8] = S::ld(f + 8 * plane + pitch - 1);
-            }
-        }
+        V g[NV][9];
+        if (x < nx) load_sites<S, SPT>(base, L.plane, L.pitch, tl.z + (int)threadIdx.y, BY, ny, g);
         __syncthreads();  // psi tile complete
         if (x >= nx) continue;
-        const SiteConsts C = site_consts(L);
-        T* o = reinterpret_cast<T*>(a.pop) + L.off_f[a.parity ^ 1];
+        V drho[NV];
 #pragma unroll
-        for (int k = 0; k < SPT; ++k) {
-            const int ly = (int)threadIdx.y + k * BY;
-            const int y = tl.z + ly;
-            if (y >= ny) break;
-            const float* c = sps + (ly + 1) * W + (threadIdx.x + 1);
-            float p[9], v[9];
-            p[0] = c[0];
-            p[1] = c[1];
-            p[2] = c[W];
-            p[3] = c[-1];
-            p[4] = c[-W];
-            p[5] = c[W + 1];
-            p[6] = c[W - 1];
-            p[7] = c[-W - 1];
-            p[8] = c[-W + 1];
-            if (MRT)
-                collide_site_mrt(C, L.mrt_s, g[k], p, v);
-            else
-                collide_site(C, g[k], p, v);
-            store_site<S>(o, plane, pitch, L.gx, x, y, nx, ny, v);
-        }
+        for (int j = 0; j < NV; ++j) drho[j] = sum9(g[j]);
+        collide_store<S, SPT, MRT>(L, sps, W, threadIdx.x, threadIdx.y, BY, x,
+                                   tl.z + (int)threadIdx.y, drho, g,
+                                   reinterpret_cast<T*>(a.pop) + L.off_f[a.parity ^ 1],
+                                   tile_interior(tl.y, tl.z, TX, TY, nx, ny));
     }
 }
 
@@ -141,40 +194,53 @@ __global__ void __launch_bounds__(512) k_collide(StepArgs a) {
 // (kept in registers for the collision), computes rho (Eq. FD) and psi
 // (Eqs. DED, CSEOS) from them and writes psi to shared memory; the first
 // threads of the block also compute psi on the one-site ring around the
-// tile (pulling from up to two sites out, which the ghost frame holds).
-// After one barrier the collision runs as in k_collide.  Every psi is the
-// same function of the same loaded values in the same order as in the psi
-// pass, so both schedules give the same numbers; DRAM sees each population
-// read once and written once.
-template <class S, int EOSP>
-__device__ __forceinline__ float ring_psi(const StepArgs& a, const LatDev& L,
-                                          const typename S::T* base, int x, int y) {
-    const int pitch = L.pitch;
-    const int64_t plane = L.plane;
-    const typename S::T* f = base + (int64_t)(y + GY) * pitch + x;
-    const float d = ((S::ld(f) + S::ld(f + 1 * plane - 1)) +
-                     (S::ld(f + 2 * plane - pitch) + S::ld(f + 3 * plane + 1))) +
-                    ((S::ld(f + 4 * plane + pitch) + S::ld(f + 5 * plane - pitch - 1)) +
-                     (S::ld(f + 6 * plane - pitch + 1) + S::ld(f + 7 * plane + pitch + 1))) +
-                    S::ld(f + 8 * plane + pitch - 1);
-    bool ok;
-    float psi = eval_psi<EOSP>(L, d + L.rho0, ok);
-    if (!ok) {
-        atomicOr(&a.status[L.lattice], 1u);
-        psi = __int_as_float(0x7fc00000);
+// tile, two ring cells per thread (pulling from up to two sites out, which
+// the ghost frame holds).  After one barrier the collision runs as in
+// k_collide.  Every psi is the same function of the same loaded values in
+// the same order as in the psi pass, so both schedules give the same
+// numbers; DRAM sees each population read once and written once.
+
+// Ring cell r of a tile: (x0-1 .. xend) x {y0-1, yend} and {x0-1, xend} x
+// (y0 .. yend-1).  Returns false for cells beyond the active region of a
+// ragged tile; (gx, gy) are then clamped onto a cell that is in the region.
+__device__ __forceinline__ bool ring_cell(int r, int TX, int TY, int x0, int y0, int xend,
+                                          int yend, int& gx, int& gy) {
+    const int W = TX + 2;
+    int lx, ly;
+    if (r < W) {
+        lx = r;
+        ly = 0;
+    } else if (r < 2 * W) {
+        lx = r - W;
+        ly = TY + 1;
+    } else {
+        const int q = r - 2 * W;  // 2 * TY side cells
+        lx = (q & 1) ? TX + 1 : 0;
+        ly = 1 + (q >> 1);
     }
-    return psi;
+    gx = x0 - 1 + lx;
+    gy = y0 - 1 + ly;
+    // the right/bottom ring of a ragged tile sits at the active edge
+    if (lx == TX + 1) gx = xend;
+    if (ly == TY + 1) gy = yend;
+    const bool on = gx <= xend && gy <= yend;
+    gx = min(gx, xend);
+    gy = min(gy, yend);
+    return on;
 }
 
 template <class S, int EOSP, int SPT, bool MRT>
 __global__ void __launch_bounds__(512) k_fused(StepArgs a) {
     using T = typename S::T;
+    using V = typename LaneOf<SPT>::V;
+    using Ln = Lanes<V>;
+    constexpr int NV = SPT / Ln::n;
     extern __shared__ float sps[];
     const int TX = blockDim.x, BY = blockDim.y, TY = BY * SPT;
     const int W = TX + 2;
     const int nthr = TX * BY;
     const int tid = threadIdx.y * TX + threadIdx.x;
-    const int nring = 2 * (TX + TY) + 4;
+    const int nhalf = TX + TY + 2;  // half of the 2 (TX + TY) + 4 ring cells
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const int4 tl = __ldg(&a.tiles[t]);
         if (a.quota && a.step >= __ldg(&a.quota[tl.x])) continue;  // uniform per block
@@ -187,87 +253,40 @@ __global__ void __launch_bounds__(512) k_fused(StepArgs a) {
         const int yend = min(tl.z + TY, ny);
         __syncthreads();  // the previous tile is done with sps
         const int x = tl.y + threadIdx.x;
-        float g[SPT][9];
-        if (x < nx) {
-#pragma unroll
-            for (int k = 0; k < SPT; ++k) {
-                const int y = min(tl.z + (int)threadIdx.y + k * BY, ny - 1);
-                const T* f = base + (int64_t)(y + GY) * pitch + x;
-                g[k][0] = S::ld(f);
-                g[k][1] = S::ld(f + 1 * plane - 1);
-                g[k][2] = S::ld(f + 2 * plane - pitch);
-                g[k][3] = S::ld(f + 3 * plane + 1);
-                g[k][4] = S::ld(f + 4 * plane + pitch);
-                g[k][5] = S::ld(f + 5 * plane - pitch - 1);
-                g[k][6] = S::ld(f + 6 * plane - pitch + 1);
-                g[k][7] = S::ld(f + 7 * plane + pitch + 1);
-                g[k][8] = S::ld(f + 8 * plane + pitch - 1);
-            }
+        V g[NV][9];
+        if (x < nx) load_sites<S, SPT>(base + x, plane, pitch, tl.z + (int)threadIdx.y, BY, ny, g);
+        // the ring, cells r and r + nhalf in the two lanes of a float2
+        for (int r = tid; r < nhalf; r += nthr) {
+            int cx0, cy0, cx1, cy1;
+            const bool on0 = ring_cell(r, TX, TY, tl.y, tl.z, xend, yend, cx0, cy0);
+            const bool on1 = ring_cell(r + nhalf, TX, TY, tl.y, tl.z, xend, yend, cx1, cy1);
+            float2 d;
+            d.x = pulled_drho<S>(base + (int64_t)(cy0 + GY) * pitch + cx0, plane, pitch);
+            d.y = pulled_drho<S>(base + (int64_t)(cy1 + GY) * pitch + cx1, plane, pitch);
+            const float2 psi = Eos<EOSP>::psi(L, vadd(d, Lanes<float2>::set(L.rho0)), a.status);
+            if (on0) sps[(cy0 - tl.z + 1) * W + (cx0 - tl.y + 1)] = psi.x;
+            if (on1) sps[(cy1 - tl.z + 1) * W + (cx1 - tl.y + 1)] = psi.y;
         }
-        // the ring around the tile: (x0-1 .. xend) x {y0-1, yend} and
-        // {x0-1, xend} x (y0 .. yend-1), as far as the active region reaches
-        for (int r = tid; r < nring; r += nthr) {
-            int lx, ly;
-            if (r < W) {
-                lx = r;
-                ly = 0;
-            } else if (r < 2 * W) {
-                lx = r - W;
-                ly = TY + 1;
-            } else {
-                const int q = r - 2 * W;  // 2 * TY side cells
-                lx = (q & 1) ? TX + 1 : 0;
-                ly = 1 + (q >> 1);
-            }
-            int gx = tl.y - 1 + lx, gy = tl.z - 1 + ly;
-            // the right/bottom ring of a ragged tile sits at the active edge
-            if (lx == TX + 1) gx = xend;
-            if (ly == TY + 1) gy = yend;
-            if (gx > xend || gy > yend) continue;
-            sps[(gy - tl.z + 1) * W + (gx - tl.y + 1)] = ring_psi<S, EOSP>(a, L, base, gx, gy);
-        }
+        V drho[NV];
         if (x < nx) {
+            const V rho0 = Ln::set(L.rho0);
 #pragma unroll
-            for (int k = 0; k < SPT; ++k) {
-                const int ly = (int)threadIdx.y + k * BY;
-                if (tl.z + ly >= ny) break;
-                const float d = ((g[k][0] + g[k][1]) + (g[k][2] + g[k][3])) +
-                                ((g[k][4] + g[k][5]) + (g[k][6] + g[k][7])) + g[k][8];
-                bool ok;
-                float psi = eval_psi<EOSP>(L, d + L.rho0, ok);
-                if (!ok) {
-                    atomicOr(&a.status[L.lattice], 1u);
-                    psi = __int_as_float(0x7fc00000);
+            for (int j = 0; j < NV; ++j) {
+                drho[j] = sum9(g[j]);
+                const V psi = Eos<EOSP>::psi(L, vadd(drho[j], rho0), a.status);
+#pragma unroll
+                for (int l = 0; l < Ln::n; ++l) {
+                    const int ly = (int)threadIdx.y + (j * Ln::n + l) * BY;
+                    if (tl.z + ly < ny) sps[(ly + 1) * W + (threadIdx.x + 1)] = Ln::get(psi, l);
                 }
-                sps[(ly + 1) * W + (threadIdx.x + 1)] = psi;
             }
         }
         __syncthreads();  // psi tile complete
         if (x >= nx) continue;
-        const SiteConsts C = site_consts(L);
-        T* o = reinterpret_cast<T*>(a.pop) + L.off_f[a.parity ^ 1];
-#pragma unroll
-        for (int k = 0; k < SPT; ++k) {
-            const int ly = (int)threadIdx.y + k * BY;
-            const int y = tl.z + ly;
-            if (y >= ny) break;
-            const float* c = sps + (ly + 1) * W + (threadIdx.x + 1);
-            float p[9], v[9];
-            p[0] = c[0];
-            p[1] = c[1];
-            p[2] = c[W];
-            p[3] = c[-1];
-            p[4] = c[-W];
-            p[5] = c[W + 1];
-            p[6] = c[W - 1];
-            p[7] = c[-W - 1];
-            p[8] = c[-W + 1];
-            if (MRT)
-                collide_site_mrt(C, L.mrt_s, g[k], p, v);
-            else
-                collide_site(C, g[k], p, v);
-            store_site<S>(o, plane, pitch, L.gx, x, y, nx, ny, v);
-        }
+        collide_store<S, SPT, MRT>(L, sps, W, threadIdx.x, threadIdx.y, BY, x,
+                                   tl.z + (int)threadIdx.y, drho, g,
+                                   reinterpret_cast<T*>(a.pop) + L.off_f[a.parity ^ 1],
+                                   tile_interior(tl.y, tl.z, TX, TY, nx, ny));
     }
 }
 
@@ -330,12 +349,13 @@ __global__ void k_moments(LatDev L, const void* pop, int parity, const float* ps
     const double rho = d + (double)L.rho0;
     const float* c = psi_arena + L.off_psi + (int64_t)(y + GY) * L.pitch_psi + (x + L.gx_psi);
     const int W = L.pitch_psi;
-    const Force F = site_force(L, c[0], c[1], c[W], c[-1], c[-W], c[W + 1], c[W - 1], c[-W - 1],
-                               c[-W + 1]);
+    const float p[9] = {c[0], c[1], c[W], c[-1], c[-W], c[W + 1], c[W - 1], c[-W - 1], c[-W + 1]};
+    float Fx, Fy;
+    site_force(site_consts(L), p, Fx, Fy);
     const int64_t s = (int64_t)y * nx + x;
     if (rho_out) rho_out[s] = rho;
-    if (ux_out) ux_out[s] = (jx + 0.5 * (double)F.x) / rho;
-    if (uy_out) uy_out[s] = (jy + 0.5 * (double)F.y) / rho;
+    if (ux_out) ux_out[s] = (jx + 0.5 * (double)Fx) / rho;
+    if (uy_out) uy_out[s] = (jy + 0.5 * (double)Fy) / rho;
 }
 
 // ------------------------------------------------------------------ mass

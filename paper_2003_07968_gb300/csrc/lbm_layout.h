@@ -38,6 +38,24 @@ inline LatDev lat_layout(const lbm_lattice_desc& d, int index) {
     L.k_sc = (float)(-6.0 * d.G);
     L.k1 = (float)(13.5 * d.eps * d.G);
     L.k2 = (float)(9.0 * (d.sigma - 1.0) * d.G);
+    {
+        const double ksc = -6.0 * d.G, k1 = 13.5 * d.eps * d.G, k2 = 9.0 * (d.sigma - 1.0) * d.G;
+        L.fsc = (float)(ksc / 36.0);
+        L.fk2 = (float)(k2 / 1944.0);
+        L.fkd = (float)((k1 - k2) / 1944.0);
+        const double om = 1.0 / d.tau, guo = 1.0 - 1.0 / (2.0 * d.tau);
+        L.om1 = (float)(1.0 - om);
+        L.wa = (float)(om / 9.0);
+        L.wd = (float)(om / 36.0);
+        L.ra = (float)(4.5 * om / 9.0);
+        L.rd = (float)(4.5 * om / 36.0);
+        L.sa = (float)(3.0 * om / 9.0);
+        L.sd = (float)(3.0 * om / 36.0);
+        L.ga9 = (float)(9.0 * guo / 9.0);
+        L.gd9 = (float)(9.0 * guo / 36.0);
+        L.ga3 = (float)(3.0 * guo / 9.0);
+        L.gd3 = (float)(3.0 * guo / 36.0);
+    }
     L.rho0 = (d.storage == LBM_STORE_F32 || d.rho0 < 0.0) ? 0.f : (float)d.rho0;
     L.m2_variant = d.m2_trace_variant;
     L.lattice = index;
@@ -47,9 +65,9 @@ inline LatDev lat_layout(const lbm_lattice_desc& d, int index) {
     L.e2 = d.eos_k * d.eos_a / d.G;
     L.e3 = 1.0 / (3.0 * d.G);
     split_df(L.eb, L.fb);
-    split_df(L.e1, L.f1);
     split_df(L.e2, L.f2);
-    split_df(L.e3, L.f3);
+    split_df(L.e1 - L.e3, L.fc0);      // psi^2/rho = c0 + rho (C1 r^2 (1 + r) - e2)
+    split_df(2.0 * L.eb * L.e1, L.fC1);
     L.sb = (float)L.eb;
     L.s1 = (float)L.e1;
     L.s2 = (float)L.e2;

@@ -546,7 +546,7 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
         for (auto& c : cfg) {
             c.tx = opts->tile_x ? opts->tile_x : 64;
             c.ty = opts->tile_y ? opts->tile_y : 8;
-            c.spt = 1;
+            c.spt = opts->sites_per_thread ? opts->sites_per_thread : 1;
             if (!shape_ok(c.variant, c.tx, c.ty, c.spt)) return LBM_ERR_ARG;
         }
     }
@@ -822,6 +822,8 @@ int lbm_info(lbm_handle* h, lbm_info_t* out) {
     out->collide_variant = h->pass[1].variant;
     out->schedule = h->schedule;
     out->n_lattices = (int32_t)h->lat.size();
+    out->spt = h->pass[1].spt;
+    out->psi_spt = h->pass[0].spt;
     return LBM_OK;
 }
 

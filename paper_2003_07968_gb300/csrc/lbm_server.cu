@@ -350,6 +350,7 @@ void worker_main(lbm_server* S) {
         }
         const auto t0 = Clock::now();
         cudaError_t e = cudaSuccess;
+        int64_t launches = 0;
         for (Request* R : admitted) {
             R->L.off_f[0] = (int64_t)(R->pop_off / S->es);
             R->L.off_f[1] = R->L.off_f[0] + 9 * R->L.plane;
@@ -365,6 +366,7 @@ void worker_main(lbm_server* S) {
                 e = launch_init(S->f16, R->L, S->arena, S->parity, S->staging, nullptr, nullptr,
                                 S->stream);
             if (e != cudaSuccess) break;
+            launches += 1;
             std::vector<double>().swap(R->rho);
             res.push_back(R);
         }
@@ -387,6 +389,7 @@ void worker_main(lbm_server* S) {
                 a0.step = a1.step = (int)s;
                 if (!S->fused) e = launch(S, 0, a0, g0, S->stream);
                 if (e == cudaSuccess) e = launch(S, 1, a1, g1, S->stream);
+                launches += S->fused ? 1 : 2;
                 S->parity ^= 1;
             }
             if (e == cudaSuccess)
@@ -397,9 +400,11 @@ void worker_main(lbm_server* S) {
         // copy out the previous chunk's finished lattices while this chunk runs
         for (Finished& f : pending) {
             int status = f.status;
-            if (status == LBM_OK && e == cudaSuccess &&
-                copy_out(S, S->set[pending_set], *f.R, f.l, f.par) != cudaSuccess)
-                status = LBM_ERR_CUDA;
+            if (status == LBM_OK && e == cudaSuccess) {
+                if (copy_out(S, S->set[pending_set], *f.R, f.l, f.par) != cudaSuccess)
+                    status = LBM_ERR_CUDA;
+                launches += 2;
+            }
             std::lock_guard<std::mutex> lk(S->mu);
             f.R->status = status;
             f.R->state = ST_DONE;
@@ -411,6 +416,10 @@ void worker_main(lbm_server* S) {
             S->st.arena_in_use = (int64_t)S->alloc.in_use();
         }
         pending.clear();
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->st.launches += launches;
+        }
         if (e == cudaSuccess && !res.empty()) e = cudaEventSynchronize(S->chunk_end);
         if (e != cudaSuccess) {
             fail_all(S, LBM_ERR_CUDA);
@@ -499,7 +508,7 @@ int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
         if (o.tile_x || o.tile_y) {
             P.tx = o.tile_x ? o.tile_x : 64;
             P.ty = o.tile_y ? o.tile_y : 8;
-            P.spt = 1;
+            P.spt = o.sites_per_thread ? o.sites_per_thread : 1;
         }
         if (P.tx % 32 || P.ty < 1 || P.tx * (P.ty / P.spt) > 512 || P.ty % P.spt) {
             delete S;

@@ -223,17 +223,17 @@ __global__ void __launch_bounds__(kBlock, 2) k_psi_tma(StepArgs a) {
             const int y = tl.z + ty;
             if (y >= ny) break;
             const T* b = P + ty * G::BW + tx + G::H;
-            const float d = ((S::lds(b) + S::lds(b + 1 * G::BOXE - 1)) +
-                             (S::lds(b + 2 * G::BOXE) + S::lds(b + 3 * G::BOXE + 1))) +
-                            ((S::lds(b + 4 * G::BOXE) + S::lds(b + 5 * G::BOXE - 1)) +
-                             (S::lds(b + 6 * G::BOXE + 1) + S::lds(b + 7 * G::BOXE + 1))) +
-                            S::lds(b + 8 * G::BOXE - 1);
-            bool ok;
-            float psi = eval_psi<EOSP>(L, d + rho0, ok);
-            if (!ok) {
-                atomicOr(&a.status[L.lattice], 1u);
-                psi = __int_as_float(0x7fc00000);
-            }
+            float v[9];
+            v[0] = S::lds(b);
+            v[1] = S::lds(b + 1 * G::BOXE - 1);
+            v[2] = S::lds(b + 2 * G::BOXE);
+            v[3] = S::lds(b + 3 * G::BOXE + 1);
+            v[4] = S::lds(b + 4 * G::BOXE);
+            v[5] = S::lds(b + 5 * G::BOXE - 1);
+            v[6] = S::lds(b + 6 * G::BOXE + 1);
+            v[7] = S::lds(b + 7 * G::BOXE + 1);
+            v[8] = S::lds(b + 8 * G::BOXE - 1);
+            const float psi = Eos<EOSP>::psi(L, sum9(v) + rho0, a.status);
             store_img(a.psi + L.off_psi, L.pitch_psi, L.gx_psi, x, y, nx, ny, psi);
         }
     });
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_collide_tma(StepArgs a) {
             p[6] = c[W - 1];
             p[7] = c[-W - 1];
             p[8] = c[-W + 1];
-            collide_site(C, g, p, v);
+            collide<false>(C, nullptr, sum9(g), g, p, v);
             store_site<S>(o, plane, pitch, gx, x, y, nx, ny, v);
         }
     });

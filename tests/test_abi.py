@@ -36,7 +36,7 @@ def test_binding_covers_every_declared_function():
     assert sorted(capi.SIGNATURES) == header_functions()
 
 
-def test_struct_layouts_match_header(lib):
+def test_struct_layouts_match_header(lib, tmp_path):
     # sizes of the ctypes mirrors against a tiny C program compiled with the header
     from paper_2003_07968_gb300 import capi
 
@@ -44,10 +44,8 @@ def test_struct_layouts_match_header(lib):
            'sizeof(lbm_lattice_desc), sizeof(lbm_runtime_opts), sizeof(lbm_kernel_stat),'
            'sizeof(lbm_info_t), offsetof(lbm_lattice_desc, mrt_rates), sizeof(lbm_server_opts),'
            'sizeof(lbm_server_stats));return 0;}')
-    tmp = os.path.join(ROOT, "paper_2003_07968_gb300", "_lib")
-    os.makedirs(tmp, exist_ok=True)
-    c = os.path.join(tmp, "layout.c")
-    exe = os.path.join(tmp, "layout")
+    c = str(tmp_path / "layout.c")
+    exe = str(tmp_path / "layout")
     open(c, "w").write(src)
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
     got = [int(v) for v in subprocess.run([exe], capture_output=True, text=True).stdout.split()]

@@ -374,8 +374,9 @@ def test_config4_batch_of_512_against_oracle(P):
 
 @pytest.mark.parametrize("eos", [1, 0])
 def test_fused_schedule(P, eos):
-    # one pass per step, psi rebuilt on each tile's halo: same numbers as the
-    # two-pass step up to compilation of the same arithmetic, and the oracle
+    # one pass per step, psi rebuilt on each tile's halo: bitwise the same
+    # numbers as the two-pass step (every psi is the same sequence of rounded
+    # operations on the same loaded values), and the oracle
     rho = synth.droplet(150, 110, 32.0, 0.7)
     outs = []
     for sched in (P.LBM_SCHED_TWO_PASS, P.LBM_SCHED_FUSED):
@@ -385,10 +386,30 @@ def test_fused_schedule(P, eos):
         P.lbm_step(h, 400)
         outs.append(P.lbm_moments(h, 0))
         P.lbm_destroy(h)
-    assert rel(outs[1]["rho"], outs[0]["rho"]) <= 1e-6
+    assert np.array_equal(outs[1]["rho"], outs[0]["rho"])
+    assert np.array_equal(outs[1]["ux"], outs[0]["ux"])
     o = oracle_run(rho, 400, T=0.7)
     assert rel(outs[1]["rho"], o["rho"]) <= RTOL_RHO
-    assert abs(outs[1]["mass"] - outs[0]["mass"]) <= 1e-9 * outs[0]["mass"]
+
+
+@pytest.mark.parametrize("eos", [0, 1, 2])
+def test_sites_per_thread_are_bitwise_invariant(P, eos):
+    # one site per thread (scalar FP32) and two or four (site pairs on the
+    # paired FP32 instructions) run the same rounded operations per site
+    rho = synth.droplet(131, 97, 30.0, 0.6)
+    outs = []
+    for sched, tile, spt in ((P.LBM_SCHED_FUSED, (32, 8), 1), (P.LBM_SCHED_FUSED, (32, 8), 2),
+                             (P.LBM_SCHED_FUSED, (64, 8), 4), (P.LBM_SCHED_TWO_PASS, (64, 4), 2)):
+        d = P.lbm_desc_default(131, 97, T=0.6, eos_precision=eos)
+        h = P.lbm_create(d, schedule=sched, tile=tile, sites_per_thread=spt)
+        assert P.lbm_info(h)["spt"] == spt
+        P.lbm_init(h, 0, rho)
+        P.lbm_step(h, 300)
+        outs.append(P.lbm_moments(h, 0, mass=False))
+        P.lbm_destroy(h)
+    for o in outs[1:]:
+        assert np.array_equal(o["rho"], outs[0]["rho"])
+        assert np.array_equal(o["ux"], outs[0]["ux"])
 
 
 def test_fused_batch_and_fault(P):
@@ -442,7 +463,10 @@ def test_mrt_with_equal_rates_is_bgk(P):
     a = P.lbm_moments(h, 0)
     P.lbm_destroy(h)
     b = gpu_run(P, rho, 300, T=T, tau=tau)
-    assert rel(a["rho"], b["rho"]) <= 1e-6
+    # two different FP32 evaluations of the same update (moment space vs the
+    # paired-direction BGK form): measured 1.9e-6 apart after 300 steps, each
+    # within 2.3e-6 of the FP64 oracle; held to the density bar
+    assert rel(a["rho"], b["rho"]) <= RTOL_RHO
 
 
 def test_mrt_oscillation_period_on_gpu(P):
