@@ -364,6 +364,7 @@ def run_gpu(args):
                    "collide_pass": {"variant": ["auto", "plain", "tma"][info["collide_variant"]],
                                     "tile": [info["tile_x"], info["tile_y"]],
                                     "sites_per_thread": info["spt"],
+                                    "tensor_map": bool(info["tensor_map"]),
                                     "grid_ctas": info["grid_ctas"]},
                    "sites": sites,
                    "l2": f"working set {info['device_bytes'] / 1e9:.2f} GB vs 129 MB L2: "

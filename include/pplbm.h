@@ -76,12 +76,16 @@ extern "C" {
                               instructions); tile_x a multiple of 32,
                               tile_y a multiple of the sites per thread,
                               tile_x*tile_y/sites_per_thread <= 512          */
-#define LBM_KERNEL_TMA 2   /* tiles staged by TMA bulk copies through a
-                              warp-specialised mbarrier pipeline; tile shapes
-                              64x8, 64x16, 128x4, 128x8, 32x16               */
+#define LBM_KERNEL_TMA 2   /* tiles staged in shared memory by TMA bulk copies
+                              through a warp-specialised mbarrier pipeline
+                              (one producer warp, eight consumer warps);
+                              single pass: tiles 64x8, 32x16, 64x16, 128x8;
+                              two-pass: 64x8, 64x16, 128x4, 128x8, 32x16   */
 
 /* ---- step schedule ------------------------------------------------------- */
-#define LBM_SCHED_AUTO 0     /* the faster schedule on GB300: LBM_SCHED_FUSED   */
+#define LBM_SCHED_AUTO 0     /* the faster schedule on GB300: LBM_SCHED_FUSED
+                                (two-pass for TMA tiles of a two-pass-only
+                                shape)                                         */
 #define LBM_SCHED_TWO_PASS 1 /* psi pass, then fused force+collide+pull pass    */
 #define LBM_SCHED_FUSED 2    /* one pass per step: each tile rebuilds psi on a
                                 one-site ring from populations pulled up to two
@@ -135,8 +139,9 @@ void lbm_desc_default(lbm_lattice_desc* d, int32_t nx, int32_t ny);
  * lattice; > 1: a batch stepped together in persistent launches over one tile
  * list).  All lattices of a handle share storage, eos_precision, collision
  * and m2_trace_variant; tau, G, eps, sigma, T, EOS constants, rho0 and the
- * MRT rates may differ per lattice.  MRT runs in the plain-load kernels only
- * (kernel_variant LBM_KERNEL_TMA with MRT is refused).  Allocates all device
+ * MRT rates may differ per lattice.  MRT runs in the plain-load kernels and
+ * in the single-pass TMA kernel (the two-pass schedule with
+ * kernel_variant LBM_KERNEL_TMA and MRT is refused).  Allocates all device
  * memory now.
  * Errors: LBM_ERR_ARG (bad sizes/params, mixed storage), LBM_ERR_OOM,
  * LBM_ERR_CUDA.  *out is NULL on error. */
@@ -215,6 +220,8 @@ typedef struct {
     int32_t schedule;
     int32_t n_lattices;
     int32_t spt, psi_spt;     /* sites per thread, collision / psi pass         */
+    int32_t tensor_map;       /* 1: the single-pass TMA kernel fills each stage
+                                 with one tensor copy per tile (else row copies) */
 } lbm_info_t;
 int lbm_info(lbm_handle* h, lbm_info_t* out);
 
@@ -326,11 +333,12 @@ int lbm_mass_noalloc(const float* values, int64_t count, double offset, double* 
                      void* stream);
 
 /* Host-only consistency proof of the shared-memory staging used by the
- * LBM_KERNEL_TMA passes: for a set of lattice shapes, every tile shape, both
- * storages and both population buffers, each bulk copy is 16-byte aligned
+ * LBM_KERNEL_TMA passes (two-pass and single-pass plans): for a set of
+ * lattice shapes, every tile shape, both storages and both population
+ * buffers, each bulk copy is 16-byte aligned
  * on both sides, has a size that is a multiple of 16 bytes, stays inside
  * its lattice's allocation and its shared-memory box, and the copies cover
- * every value an active site reads.  Writes a one-line report.  Needs no GPU.
+ * every value an active site (and, single pass, a ring cell) reads.  Writes a one-line report.  Needs no GPU.
  * Returns LBM_OK, or LBM_ERR_STATE with the first violation in the report. */
 int lbm_selfcheck(char* report, int32_t report_len);
 

@@ -110,7 +110,8 @@ class Info(ctypes.Structure):
                 ("psi_n_tiles", ctypes.c_int32), ("psi_grid_ctas", ctypes.c_int32),
                 ("psi_variant", ctypes.c_int32), ("collide_variant", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("n_lattices", ctypes.c_int32),
-                ("spt", ctypes.c_int32), ("psi_spt", ctypes.c_int32)]
+                ("spt", ctypes.c_int32), ("psi_spt", ctypes.c_int32),
+                ("tensor_map", ctypes.c_int32)]
 
 
 # Every symbol include/pplbm.h declares, with (restype, argtypes).

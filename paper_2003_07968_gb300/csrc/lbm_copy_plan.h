@@ -79,4 +79,72 @@ __host__ __device__ inline bool plan_copy(const LatDev& L, int parity, int x0, i
     return true;
 }
 
+// ---- single-pass (fused) step --------------------------------------------
+// Stage layout (bytes): nine population boxes of BOXB bytes.  Box i holds
+// ROWS = TY + 2 rows: box row rr is lattice row y0 - 1 - c_iy + rr, so the
+// value a cell (x, y) of the tile or of its one-site ring pulls,
+// f*_i(x - c_ix, y - c_iy), sits in box row y - y0 + 1 at column
+// x - c_ix - x0 + H; columns [x0 - H, x0 + TX + H) of the lattice row.
+template <int ES, int TX, int TY>
+struct FusedGeo {
+    static constexpr int H = 16 / ES;        // halo columns per side (16 bytes)
+    static constexpr int BW = TX + 2 * H;    // box width (elements)
+    static constexpr int ROWS = TY + 2;      // box rows
+    static constexpr int BOXB = align128(ROWS * BW * ES);
+    static constexpr int STAGEB = 9 * BOXB;
+    static constexpr int NCOPY = 9 * ROWS;
+};
+
+// Copy q of the fused tile with origin (x0, y0) of lattice L, reading
+// population buffer `parity`.  Rows outside the lattice allocation (beyond
+// the ghost frame of a ragged last tile) are not copied; no active cell
+// reads them.
+template <int ES, int TX, int TY>
+__host__ __device__ inline bool plan_copy_fused(const LatDev& L, int parity, int x0, int y0, int q,
+                                                CopyOp& op) {
+    using G = FusedGeo<ES, TX, TY>;
+    const int i = q / G::ROWS, rr = q - (q / G::ROWS) * G::ROWS;
+    const int y = y0 - 1 - plane_cy(i) + rr;  // lattice row held by box row rr
+    if (y < -GY || y > L.ny + GY - 1) return false;
+    const int avail = L.pitch - (x0 - G::H + L.gx);  // columns left in the row
+    const int cols = avail < G::BW ? avail : G::BW;
+    op.src = (L.off_f[parity] + (int64_t)i * L.plane + (int64_t)(y + GY) * L.pitch +
+              (x0 - G::H + L.gx)) *
+             ES;
+    op.dst = i * G::BOXB + rr * G::BW * ES;
+    op.bytes = cols * ES;
+    op.psi = false;
+    return true;
+}
+
+// Cell r of the one-site ring around a tile with active extent up to
+// (xend, yend): (x0-1 .. xend) x {y0-1, yend} and {x0-1, xend} x (y0 .. yend-1),
+// r < 2 (TX + TY) + 4.  Returns false for cells beyond the active region of
+// a ragged tile; (gx, gy) are then clamped onto a cell of the region.
+__host__ __device__ inline bool ring_cell(int r, int TX, int TY, int x0, int y0, int xend,
+                                          int yend, int& gx, int& gy) {
+    const int W = TX + 2;
+    int lx, ly;
+    if (r < W) {
+        lx = r;
+        ly = 0;
+    } else if (r < 2 * W) {
+        lx = r - W;
+        ly = TY + 1;
+    } else {
+        const int q = r - 2 * W;  // 2 * TY side cells
+        lx = (q & 1) ? TX + 1 : 0;
+        ly = 1 + (q >> 1);
+    }
+    gx = x0 - 1 + lx;
+    gy = y0 - 1 + ly;
+    // the right/bottom ring of a ragged tile sits at the active edge
+    if (lx == TX + 1) gx = xend;
+    if (ly == TY + 1) gy = yend;
+    const bool on = gx <= xend && gy <= yend;
+    gx = gx < xend ? gx : xend;
+    gy = gy < yend ? gy : yend;
+    return on;
+}
+
 }  // namespace pplbm

@@ -77,6 +77,7 @@ struct LatDev {
     double eb, e1, e2, e3;
     df2 fb, f2, fc0, fC1;  // b, e2, c0 = e1 - e3, C1 = 2 b e1 as float-float pairs
     float sb, s1, s2, s3;  // b, e1, e2, e3 as floats
+    float zero;            // 0, as a value the compiler cannot see (Eos<EOS_DF>)
     // MRT relaxation rates (Eq. RelaxationMatrix), used by the MRT kernels
     float mrt_s[9];
 };
@@ -158,10 +159,10 @@ __device__ __forceinline__ void store_img(T* plane, int pitch, int gx, int x, in
 // cannot see through.  Two facts measured on sm_103a shape the code:
 //  - the code generator keeps scalar .rn operations as written, but fuses a
 //    paired multiply into a following paired add or subtract even with .rn;
-//    so no product ever feeds a paired add here (products only enter FMAs
-//    as multiplicands or addends), and the float-float EOS, whose error-free
-//    transformations need every rounding as written, runs lane by lane on
-//    the scalar instructions;
+//    so no product of a paired multiply ever feeds a paired add here:
+//    products enter FMAs as multiplicands or addends, and a product that
+//    must be added is formed as an FMA with a zero addend the compiler
+//    cannot see (the float-float EOS);
 //  - the CUDA rounding intrinsics (__fadd_rn ...) are not enough either:
 //    a TwoSum error term built from them folded to zero.
 // Every operation is then one IEEE round-to-nearest step per lane, in the
@@ -265,17 +266,19 @@ __device__ __forceinline__ V vrcp(V x) {
 // here cancels by more than a factor of about 8, and the float-float version
 // (below) keeps about 43 significant bits of the radicand.
 // A lane is valid when rho > 0, b rho < 1 and the radicand is finite and
-// >= 0; an invalid lane gets psi = NaN and raises status bit 1 of its lattice.
+// >= 0; an invalid lane gets psi = NaN and, if its bit in `live` is set,
+// raises status bit 1 of its lattice (lanes without a site are not live).
 enum { EOS_F64 = 0, EOS_DF = 1, EOS_F32 = 2 };
 
 template <class V>
-__device__ __forceinline__ V psi_finish(const LatDev& L, V rho, V s, V arg, uint32_t* status) {
+__device__ __forceinline__ V psi_finish(const LatDev& L, V rho, V s, V arg, uint32_t* status,
+                                        unsigned live) {
     V psi;
 #pragma unroll
     for (int k = 0; k < Lanes<V>::n; ++k) {
         const float r = Lanes<V>::get(rho, k), a = Lanes<V>::get(arg, k);
         const bool ok = (r > 0.f) && (Lanes<V>::get(s, k) > 0.f) && (a >= 0.f) && (a < INFINITY);
-        if (!ok) atomicOr(status + L.lattice, 1u);
+        if (!ok && ((live >> k) & 1u)) atomicOr(status + L.lattice, 1u);
         Lanes<V>::put(psi, k, ok ? __fsqrt_rn(a) : __int_as_float(0x7fc00000));
     }
     return psi;
@@ -288,7 +291,8 @@ struct Eos;
 template <>
 struct Eos<EOS_F64> {
     template <class V>
-    static __device__ __forceinline__ V psi(const LatDev& L, V rho, uint32_t* status) {
+    static __device__ __forceinline__ V psi(const LatDev& L, V rho, uint32_t* status,
+                                            unsigned live = ~0u) {
         V s, arg;
 #pragma unroll
         for (int k = 0; k < Lanes<V>::n; ++k) {
@@ -300,24 +304,27 @@ struct Eos<EOS_F64> {
             Lanes<V>::put(s, k, sd > 0.0 ? 1.f : -1.f);
             Lanes<V>::put(arg, k, (float)a);
         }
-        return psi_finish(L, rho, s, arg, status);
+        return psi_finish(L, rho, s, arg, status, live);
     }
 };
 
 // Float-float: TwoProd by FMA, TwoSum where signs may differ, FastTwoSum where
 // the larger operand is known, one Newton step on the rounded reciprocal.
-// Computed lane by lane with the scalar instructions: the code generator
-// fuses a paired multiply into a following paired add even when both carry
-// .rn (measured on sm_103a), which would break the error-free
-// transformations, while the scalar .rn forms are kept as written.
+// Runtime negations are explicit products by -1 (there is no paired negate).
+// Every product that feeds an add (p, rl, Bh, wh) is formed as an FMA with a
+// zero addend the compiler cannot see (LatDev::zero): the code generator
+// fuses a paired multiply into a following paired add even with .rn
+// (measured on sm_103a), which would break the error-free transformations,
+// but it cannot fuse an FMA.
 template <>
 struct Eos<EOS_DF> {
-    static __device__ __forceinline__ float lane(const LatDev& L, float rho, float& s) {
-        using V = float;
+    template <class V>
+    static __device__ __forceinline__ V psi(const LatDev& L, V rho, uint32_t* status,
+                                            unsigned live = ~0u) {
         using Ln = Lanes<V>;
-        const V one = Ln::set(1.f), mone = Ln::set(-1.f);
+        const V one = Ln::set(1.f), mone = Ln::set(-1.f), z0 = Ln::set(L.zero);
         // b rho = p - en
-        const V p = vmul(Ln::set(L.fb.hi), rho);
+        const V p = vfma(Ln::set(L.fb.hi), rho, z0);
         V en = vfma(Ln::set(-L.fb.hi), rho, p);
         en = vfma(Ln::set(-L.fb.lo), rho, en);
         // s = 1 - b rho = sh + sl  (FastTwoSum, 1 > b rho)
@@ -327,7 +334,7 @@ struct Eos<EOS_DF> {
         const V q = vrcp(sh);
         V t = vfma(sh, q, mone);
         t = vfma(sl, q, t);
-        const V rl = vmul(q, t);
+        const V rl = vfma(q, t, z0);
         // 1 + r = oh + ol  (FastTwoSum, q >= 1)
         const V oh = vadd(q, one);
         const V ol = vsub(vadd(vsub(q, oh), one), rl);
@@ -341,7 +348,7 @@ struct Eos<EOS_DF> {
         Ae = vfma(r2h, ol, Ae);
         Ae = vfma(r2l, oh, Ae);
         // C1 A = Bh - nBl
-        const V Bh = vmul(Ln::set(L.fC1.hi), Ah);
+        const V Bh = vfma(Ln::set(L.fC1.hi), Ah, z0);
         V nBl = vfma(Ln::set(-L.fC1.hi), Ah, Bh);
         nBl = vfma(Ln::set(-L.fC1.hi), Ae, nBl);
         nBl = vfma(Ln::set(-L.fC1.lo), Ah, nBl);
@@ -352,26 +359,14 @@ struct Eos<EOS_DF> {
         const V ve = vadd(vsub(Bh, vsub(vh, bb)), vsub(ne2h, bb));
         const V vl = vadd(vsub(ve, nBl), Ln::set(-L.f2.lo));
         // w = rho v = wh + we
-        const V wh = vmul(vh, rho);
+        const V wh = vfma(vh, rho, z0);
         V we = vfma(vh, rho, vmul(vh, vmul(rho, mone)));
         we = vfma(vl, rho, we);
         // c0 + w = hh + hl  (FastTwoSum, |c0| >= |w| wherever psi is defined)
         const V c0h = Ln::set(L.fc0.hi);
         const V hh = vadd(c0h, wh);
         const V hl = vadd(vadd(vsub(c0h, hh), wh), vadd(Ln::set(L.fc0.lo), we));
-        s = sh;
-        return vfma(rho, hh, vmul(rho, hl));
-    }
-    template <class V>
-    static __device__ __forceinline__ V psi(const LatDev& L, V rho, uint32_t* status) {
-        V s, arg;
-#pragma unroll
-        for (int k = 0; k < Lanes<V>::n; ++k) {
-            float sk;
-            Lanes<V>::put(arg, k, lane(L, Lanes<V>::get(rho, k), sk));
-            Lanes<V>::put(s, k, sk);
-        }
-        return psi_finish(L, rho, s, arg, status);
+        return psi_finish(L, rho, sh, vfma(rho, hh, vmul(rho, hl)), status, live);
     }
 };
 
@@ -379,7 +374,8 @@ struct Eos<EOS_DF> {
 template <>
 struct Eos<EOS_F32> {
     template <class V>
-    static __device__ __forceinline__ V psi(const LatDev& L, V rho, uint32_t* status) {
+    static __device__ __forceinline__ V psi(const LatDev& L, V rho, uint32_t* status,
+                                            unsigned live = ~0u) {
         using Ln = Lanes<V>;
         const V one = Ln::set(1.f);
         const V s = vfma(Ln::set(-L.sb), rho, one);
@@ -388,7 +384,7 @@ struct Eos<EOS_F32> {
         for (int k = 0; k < Ln::n; ++k) Ln::put(rr, k, __frcp_rn(Ln::get(s, k)));
         const V q = vfma(vadd(rr, rr), vmul(rr, rr), vfma(Ln::set(-2.f), rr, one));
         const V inner = vfma(Ln::set(L.s1), q, vfma(Ln::set(-L.s2), rho, Ln::set(-L.s3)));
-        return psi_finish(L, rho, s, vmul(rho, inner), status);
+        return psi_finish(L, rho, s, vmul(rho, inner), status, live);
     }
 };
 

@@ -10,6 +10,7 @@
 //
 // Both passes walk a global tile list with a persistent grid, so one launch
 // covers one lattice or a batch of uneven lattices alike.
+#include "lbm_copy_plan.h"
 #include "lbm_kernels.h"
 
 namespace pplbm {
@@ -199,35 +200,6 @@ __global__ void __launch_bounds__(512) k_collide(StepArgs a) {
 // k_collide.  Every psi is the same function of the same loaded values in
 // the same order as in the psi pass, so both schedules give the same
 // numbers; DRAM sees each population read once and written once.
-
-// Ring cell r of a tile: (x0-1 .. xend) x {y0-1, yend} and {x0-1, xend} x
-// (y0 .. yend-1).  Returns false for cells beyond the active region of a
-// ragged tile; (gx, gy) are then clamped onto a cell that is in the region.
-__device__ __forceinline__ bool ring_cell(int r, int TX, int TY, int x0, int y0, int xend,
-                                          int yend, int& gx, int& gy) {
-    const int W = TX + 2;
-    int lx, ly;
-    if (r < W) {
-        lx = r;
-        ly = 0;
-    } else if (r < 2 * W) {
-        lx = r - W;
-        ly = TY + 1;
-    } else {
-        const int q = r - 2 * W;  // 2 * TY side cells
-        lx = (q & 1) ? TX + 1 : 0;
-        ly = 1 + (q >> 1);
-    }
-    gx = x0 - 1 + lx;
-    gy = y0 - 1 + ly;
-    // the right/bottom ring of a ragged tile sits at the active edge
-    if (lx == TX + 1) gx = xend;
-    if (ly == TY + 1) gy = yend;
-    const bool on = gx <= xend && gy <= yend;
-    gx = min(gx, xend);
-    gy = min(gy, yend);
-    return on;
-}
 
 template <class S, int EOSP, int SPT, bool MRT>
 __global__ void __launch_bounds__(512) k_fused(StepArgs a) {

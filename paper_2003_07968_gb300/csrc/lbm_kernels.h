@@ -1,5 +1,7 @@
 // lbm_kernels.h -- host launchers of the kernels in lbm_kernels.cu.
 #pragma once
+#include <cuda.h>
+
 #include "lbm_device.cuh"
 
 namespace pplbm {
@@ -33,5 +35,16 @@ int occupancy_collide(int storage_f16, int mrt, int spt, int threads, size_t sme
 cudaError_t launch_fused(int storage_f16, int mrt, int eos, int spt, const StepArgs& a, dim3 g,
                          dim3 b, size_t smem, cudaStream_t st);
 int occupancy_fused(int storage_f16, int mrt, int eos, int spt, int threads, size_t smem);
+// Single-pass step with TMA-staged tiles (lbm_fused_tma.cu): 288 threads
+// (eight consumer warps and a producer warp), persistent over the tile list.
+// With a tensor map (fused_tma_make_map: single lattice, rows at least a
+// box wide) each tile is one 3-D tensor copy and the lattice's constants
+// travel by value (lat0); without, bulk row copies and a.lats.
+bool fused_tma_shape_supported(int tx, int ty);
+bool fused_tma_make_map(int f16, int tx, int ty, const LatDev& L, void* pop, CUtensorMap* map);
+cudaError_t launch_fused_tma(int f16, int mrt, int eos, int tx, int ty, const StepArgs& a,
+                             const CUtensorMap* map, const LatDev* lat0, int grid,
+                             cudaStream_t st);
+int occupancy_fused_tma(int f16, int mrt, int eos, int tx, int ty, bool with_map);
 
 }  // namespace pplbm

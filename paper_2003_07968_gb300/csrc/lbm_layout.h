@@ -72,6 +72,7 @@ inline LatDev lat_layout(const lbm_lattice_desc& d, int index) {
     L.s1 = (float)L.e1;
     L.s2 = (float)L.e2;
     L.s3 = (float)L.e3;
+    L.zero = 0.f;
     for (int i = 0; i < 9; ++i) L.mrt_s[i] = (float)d.mrt_rates[i];
     return L;
 }

@@ -101,6 +101,10 @@ struct lbm_handle {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by starting parity
     int graph_steps = 32;
     int tune_variant = LBM_KERNEL_AUTO;  // the kernel_variant the handle was created with
+    // tensor map of the population buffers for the single-pass TMA kernel
+    // (single lattice, rows at least a box wide); else that kernel uses row copies
+    CUtensorMap tmap{};
+    bool has_tmap = false;
     // profiling
     bool prof = false;
     ProfRec rec[2];
@@ -166,8 +170,12 @@ LatDev make_lat(const lbm_lattice_desc& d, int index, int64_t& pop_cursor,
 void drop_graph(lbm_handle* h);
 
 int build_tiles(lbm_handle* h, int k, int tx, int ty) {
-    drop_graph(h);  // captured launches embed the tile lists and grids
+    drop_graph(h);  // captured launches embed the tile lists, grids and tensor map
     Pass& P = h->pass[k];
+    if (k == 1)
+        h->has_tmap = h->schedule == LBM_SCHED_FUSED && P.variant == LBM_KERNEL_TMA &&
+                      h->lat.size() == 1 &&
+                      fused_tma_make_map(h->f16, tx, ty, h->lat[0], h->pop, &h->tmap);
     std::vector<int4> t;
     P.begin.assign(h->lat.size(), 0);
     P.count.assign(h->lat.size(), 0);
@@ -196,8 +204,9 @@ int build_tiles(lbm_handle* h, int k, int tx, int ty) {
     return LBM_OK;
 }
 
-bool shape_ok(int variant, int tx, int ty, int spt) {
-    if (variant == LBM_KERNEL_TMA) return tma_shape_supported(tx, ty);
+bool shape_ok(int variant, int tx, int ty, int spt, bool fused = false) {
+    if (variant == LBM_KERNEL_TMA)
+        return fused ? fused_tma_shape_supported(tx, ty) : tma_shape_supported(tx, ty);
     return tx > 0 && ty > 0 && (tx % 32) == 0 && plain_spt_supported(spt) && ty % spt == 0 &&
            tx * (ty / spt) <= 512;
 }
@@ -208,7 +217,10 @@ size_t collide_smem(int tx, int ty) { return (size_t)(tx + 2) * (ty + 2) * sizeo
 void default_grid(lbm_handle* h, int k) {
     Pass& P = h->pass[k];
     int occ;
-    if (P.variant == LBM_KERNEL_TMA)
+    if (P.variant == LBM_KERNEL_TMA && k == 1 && h->schedule == LBM_SCHED_FUSED)
+        occ = occupancy_fused_tma(h->f16, h->collision == LBM_COLL_MRT, h->eos, P.tx, P.ty,
+                                  h->has_tmap);
+    else if (P.variant == LBM_KERNEL_TMA)
         occ = k == 0 ? occupancy_psi_tma(h->f16, h->eos, P.tx, P.ty)
                      : occupancy_collide_tma(h->f16, P.tx, P.ty);
     else if (k == 1 && h->schedule == LBM_SCHED_FUSED)
@@ -250,6 +262,9 @@ cudaError_t launch_pass(lbm_handle* h, int k, const StepArgs& a, int grid) {
         return P.variant == LBM_KERNEL_TMA
                    ? launch_psi_tma(h->f16, h->eos, P.tx, P.ty, a, grid, h->stream)
                    : launch_psi(h->f16, h->eos, P.spt, a, dim3(grid), block, h->stream);
+    if (h->schedule == LBM_SCHED_FUSED && P.variant == LBM_KERNEL_TMA)
+        return launch_fused_tma(h->f16, h->collision == LBM_COLL_MRT, h->eos, P.tx, P.ty, a,
+                                h->has_tmap ? &h->tmap : nullptr, &h->lat[0], grid, h->stream);
     if (h->schedule == LBM_SCHED_FUSED)
         return launch_fused(h->f16, h->collision == LBM_COLL_MRT, h->eos, P.spt, a, dim3(grid), block, collide_smem(P.tx, P.ty),
                             h->stream);
@@ -450,6 +465,70 @@ std::string check_plan_t(const LatDev& L, int par, int x0, int y0, int64_t lo, i
     return "";
 }
 
+// Host proof of one fused tile's copy plan (FusedGeo): every copy aligned,
+// inside the lattice allocation and inside its own box, and every pulled
+// value that an active site or a ring cell (clamped or not) reads covered.
+template <int ES, int TX, int TY>
+std::string check_fused_t(const LatDev& L, int par, int x0, int y0, int64_t lo, int64_t hi) {
+    using G = FusedGeo<ES, TX, TY>;
+    char buf[256];
+    std::vector<char> cov(G::STAGEB, 0);
+    for (int q = 0; q < G::NCOPY; ++q) {
+        CopyOp op;
+        if (!plan_copy_fused<ES, TX, TY>(L, par, x0, y0, q, op)) continue;
+        const int box = op.dst / G::BOXB;
+        if (op.src % 16 || op.dst % 16 || op.bytes % 16 || op.bytes <= 0 || op.src < lo ||
+            op.src + op.bytes > hi || op.dst < 0 ||
+            op.dst + op.bytes > box * G::BOXB + G::ROWS * G::BW * ES) {
+            std::snprintf(buf, sizeof buf,
+                          "bad fused copy: es=%d tile=%dx%d lattice %dx%d x0=%d y0=%d q=%d src=%lld "
+                          "dst=%d bytes=%d range=[%lld,%lld)",
+                          ES, TX, TY, L.nx, L.ny, x0, y0, q, (long long)op.src, op.dst, op.bytes,
+                          (long long)lo, (long long)hi);
+            return buf;
+        }
+        for (int k = 0; k < op.bytes; ++k) cov[op.dst + k] = 1;
+    }
+    const int xend = std::min(x0 + TX, L.nx), yend = std::min(y0 + TY, L.ny);
+    auto covered = [&](int gx, int gy) {
+        for (int i = 0; i < 9; ++i) {
+            const int off =
+                i * G::BOXB + ((gy - y0 + 1) * G::BW + (gx - x0 + G::H - plane_cx(i))) * ES;
+            if (off < 0 || off + ES > G::STAGEB) return false;
+            for (int k = 0; k < ES; ++k)
+                if (!cov[off + k]) return false;
+        }
+        return true;
+    };
+    for (int y = y0; y < yend; ++y)
+        for (int x = x0; x < xend; ++x)
+            if (!covered(x, y)) {
+                std::snprintf(buf, sizeof buf, "uncovered fused read: site (%d,%d) of %dx%d", x, y,
+                              L.nx, L.ny);
+                return buf;
+            }
+    for (int r = 0; r < 2 * (TX + TY) + 4; ++r) {
+        int gx, gy;
+        ring_cell(r, TX, TY, x0, y0, xend, yend, gx, gy);
+        if (!covered(gx, gy)) {
+            std::snprintf(buf, sizeof buf, "uncovered fused read: ring cell %d (%d,%d) of %dx%d", r,
+                          gx, gy, L.nx, L.ny);
+            return buf;
+        }
+    }
+    return "";
+}
+
+template <int ES>
+std::string check_fused_shape(int tx, int ty, const LatDev& L, int par, int x0, int y0,
+                              int64_t lo, int64_t hi) {
+    if (tx == 64 && ty == 8) return check_fused_t<ES, 64, 8>(L, par, x0, y0, lo, hi);
+    if (tx == 32 && ty == 16) return check_fused_t<ES, 32, 16>(L, par, x0, y0, lo, hi);
+    if (tx == 64 && ty == 16) return check_fused_t<ES, 64, 16>(L, par, x0, y0, lo, hi);
+    if (tx == 128 && ty == 8) return check_fused_t<ES, 128, 8>(L, par, x0, y0, lo, hi);
+    return "unknown fused tile shape";
+}
+
 template <int ES, bool P>
 std::string check_shape(int tx, int ty, const LatDev& L, int par, int x0, int y0, int64_t lo,
                         int64_t hi, int64_t plo, int64_t phi) {
@@ -540,23 +619,30 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
     for (int q = 0; q < 2; ++q)
         cfg[q] = PassCfg{kPassDefaults[q].variant, kPassDefaults[q].tx, kPassDefaults[q].ty, 0,
                          kPassDefaults[q].spt};
-    if (variant == LBM_KERNEL_TMA)
-        for (auto& c : cfg) c = PassCfg{variant, 64, 8, 0, 1};
-    if (opts && (opts->tile_x || opts->tile_y)) {
-        for (auto& c : cfg) {
-            c.tx = opts->tile_x ? opts->tile_x : 64;
-            c.ty = opts->tile_y ? opts->tile_y : 8;
-            c.spt = opts->sites_per_thread ? opts->sites_per_thread : 1;
-            if (!shape_ok(c.variant, c.tx, c.ty, c.spt)) return LBM_ERR_ARG;
-        }
-    }
     if (opts && opts->schedule != LBM_SCHED_AUTO && opts->schedule != LBM_SCHED_TWO_PASS &&
         opts->schedule != LBM_SCHED_FUSED)
         return LBM_ERR_ARG;
-    if (opts && opts->schedule == LBM_SCHED_FUSED && opts->kernel_variant == LBM_KERNEL_TMA)
-        return LBM_ERR_ARG;  // the single-pass step exists as a plain-load kernel only
-    if (descs[0].collision == LBM_COLL_MRT && opts && opts->kernel_variant == LBM_KERNEL_TMA)
-        return LBM_ERR_ARG;  // the MRT collision exists in the plain-load kernels only
+    // LBM_SCHED_AUTO: the single pass, unless TMA tiles were asked for in a
+    // shape that only the two-pass kernels have
+    int schedule = (opts && opts->schedule != LBM_SCHED_AUTO) ? opts->schedule : LBM_SCHED_FUSED;
+    if (!(opts && opts->schedule != LBM_SCHED_AUTO) && variant == LBM_KERNEL_TMA && opts &&
+        (opts->tile_x || opts->tile_y) &&
+        !fused_tma_shape_supported(opts->tile_x ? opts->tile_x : 64, opts->tile_y ? opts->tile_y : 8))
+        schedule = LBM_SCHED_TWO_PASS;
+    const bool fused = schedule == LBM_SCHED_FUSED;
+    if (variant == LBM_KERNEL_TMA)
+        for (auto& c : cfg) c = PassCfg{variant, 64, 8, 0, 1};
+    if (opts && (opts->tile_x || opts->tile_y)) {
+        for (int q = 0; q < 2; ++q) {
+            PassCfg& c = cfg[q];
+            c.tx = opts->tile_x ? opts->tile_x : 64;
+            c.ty = opts->tile_y ? opts->tile_y : 8;
+            c.spt = opts->sites_per_thread ? opts->sites_per_thread : 1;
+            if (!shape_ok(c.variant, c.tx, c.ty, c.spt, fused && q == 1)) return LBM_ERR_ARG;
+        }
+    }
+    if (!fused && descs[0].collision == LBM_COLL_MRT && variant == LBM_KERNEL_TMA)
+        return LBM_ERR_ARG;  // the two-pass MRT collision exists as a plain-load kernel only
 
     lbm_handle* h = new (std::nothrow) lbm_handle();
     if (!h) return LBM_ERR_OOM;
@@ -564,10 +650,7 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
     h->desc.assign(descs, descs + n);
     h->storage = descs[0].storage;
     h->f16 = h->storage == LBM_STORE_F16_DEV;
-    // LBM_SCHED_AUTO: the single pass unless a TMA kernel was asked for
-    h->schedule = opts ? opts->schedule : LBM_SCHED_AUTO;
-    if (h->schedule == LBM_SCHED_AUTO)
-        h->schedule = variant == LBM_KERNEL_TMA ? LBM_SCHED_TWO_PASS : LBM_SCHED_FUSED;
+    h->schedule = schedule;
     h->eos = descs[0].eos_precision;
     h->collision = descs[0].collision;
     h->graph_steps = (opts && opts->graph_steps != 0) ? opts->graph_steps : 32;
@@ -622,13 +705,18 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
         if (it != g_tune_cache.end() && !(opts && (opts->tile_x || opts->tile_y)))
             for (int q = 0; q < 2; ++q) cfg[q] = it->second.pass[q];
     }
-    if ((h->schedule == LBM_SCHED_FUSED || h->collision == LBM_COLL_MRT) &&
-        cfg[1].variant == LBM_KERNEL_TMA)
+    if (cfg[1].variant == LBM_KERNEL_TMA &&
+        !shape_ok(LBM_KERNEL_TMA, cfg[1].tx, cfg[1].ty, 1, fused))
+        cfg[1] = PassCfg{LBM_KERNEL_PLAIN, kPassDefaults[1].tx, kPassDefaults[1].ty, 0,
+                         kPassDefaults[1].spt};
+    if (!fused && h->collision == LBM_COLL_MRT && cfg[1].variant == LBM_KERNEL_TMA)
         cfg[1] = PassCfg{LBM_KERNEL_PLAIN, kPassDefaults[1].tx, kPassDefaults[1].ty, 0,
                          kPassDefaults[1].spt};
     for (int q = 0; q < 2; ++q) {
         h->pass[q].variant = cfg[q].variant;
-        h->pass[q].spt = cfg[q].variant == LBM_KERNEL_TMA ? 1 : cfg[q].spt;
+        h->pass[q].spt = cfg[q].variant != LBM_KERNEL_TMA ? cfg[q].spt
+                         : (fused && q == 1)              ? cfg[q].tx * cfg[q].ty / 256
+                                                          : 1;
         int rc = build_tiles(h, q, cfg[q].tx, cfg[q].ty);
         if (rc) return fail(rc);
         default_grid(h, q);
@@ -660,7 +748,9 @@ int lbm_init(lbm_handle* h, int32_t lattice, const double* rho, const double* ux
         double m = rho[0];
         for (size_t i = 1; i < n; ++i) m = std::min(m, rho[i]);
         if (!std::isfinite(m)) return LBM_ERR_ARG;
-        L.rho0 = (float)std::max(m, 0.0);
+        const float r0 = (float)std::max(m, 0.0);
+        if (r0 != L.rho0) drop_graph(h);  // captured launches may carry the lattice by value
+        L.rho0 = r0;
         CK(h, cudaMemcpyAsync(h->lat_dev + lattice, &L, sizeof(LatDev), cudaMemcpyHostToDevice,
                               h->stream));
     }
@@ -824,6 +914,7 @@ int lbm_info(lbm_handle* h, lbm_info_t* out) {
     out->n_lattices = (int32_t)h->lat.size();
     out->spt = h->pass[1].spt;
     out->psi_spt = h->pass[0].spt;
+    out->tensor_map = h->has_tmap ? 1 : 0;
     return LBM_OK;
 }
 
@@ -831,6 +922,7 @@ int lbm_autotune(lbm_handle* h, int32_t repeats) {
     if (!h || repeats < 1) return LBM_ERR_ARG;
     CK(h, cudaStreamSynchronize(h->stream));
     static const int shapes_tma[][2] = {{64, 8}, {64, 16}, {128, 4}, {128, 8}, {32, 16}};
+    static const int shapes_fused_tma[][2] = {{64, 8}, {32, 16}, {64, 16}, {128, 8}};
     // plain: tile width, tile height, sites per thread
     static const int shapes_plain[][3] = {{32, 4, 1}, {32, 8, 1}, {64, 2, 1}, {64, 4, 1},
                                           {128, 2, 1}, {32, 8, 2}, {32, 16, 2}, {64, 4, 2},
@@ -850,11 +942,14 @@ int lbm_autotune(lbm_handle* h, int32_t repeats) {
     // the current state, computed first.
     for (int k = 0; k < 2 && rc == LBM_OK; ++k) {
         std::vector<PassCfg> cand;
+        const bool fused = k == 1 && h->schedule == LBM_SCHED_FUSED;
         const bool allow_tma = h->tune_variant != LBM_KERNEL_PLAIN &&
-                               !(k == 1 && (h->schedule == LBM_SCHED_FUSED ||
-                                            h->collision == LBM_COLL_MRT));
+                               !(k == 1 && !fused && h->collision == LBM_COLL_MRT);
         const bool allow_plain = h->tune_variant != LBM_KERNEL_TMA;
-        if (allow_tma)
+        if (allow_tma && fused)
+            for (const auto& c : shapes_fused_tma)
+                cand.push_back({LBM_KERNEL_TMA, c[0], c[1], 0, c[0] * c[1] / 256});
+        else if (allow_tma)
             for (const auto& c : shapes_tma) cand.push_back({LBM_KERNEL_TMA, c[0], c[1], 0, 1});
         if (allow_plain)
             for (const auto& c : shapes_plain)
@@ -951,6 +1046,38 @@ int lbm_selfcheck(char* report, int32_t report_len) {
                 }
             }
         }
+    }
+    {
+        // the single-pass step's plans
+        const int ftiles[][2] = {{64, 8}, {32, 16}, {64, 16}, {128, 8}};
+        for (int f16 = 0; f16 < 2 && msg.empty(); ++f16)
+            for (const auto& tt : ftiles) {
+                int64_t pc = 0, qc = 0;
+                std::vector<LatDev> lats;
+                int idx = 0;
+                for (const auto& sh : shapes) {
+                    lbm_lattice_desc d;
+                    lbm_desc_default(&d, sh[0], sh[1]);
+                    d.storage = f16 ? LBM_STORE_F16_DEV : LBM_STORE_F32_DEV;
+                    lats.push_back(make_lat(d, idx++, pc, qc));
+                }
+                const int es = f16 ? 2 : 4;
+                for (const LatDev& L : lats) {
+                    const int64_t lo = L.off_f[0] * es, hi = (L.off_f[1] + 9 * L.plane) * es;
+                    for (int y0 = 0; y0 < L.ny; y0 += tt[1])
+                        for (int x0 = 0; x0 < L.nx; x0 += tt[0])
+                            for (int par = 0; par < 2; ++par) {
+                                std::string e =
+                                    f16 ? check_fused_shape<2>(tt[0], tt[1], L, par, x0, y0, lo, hi)
+                                        : check_fused_shape<4>(tt[0], tt[1], L, par, x0, y0, lo, hi);
+                                ++checked;
+                                if (!e.empty()) {
+                                    msg = e;
+                                    goto done;
+                                }
+                            }
+                }
+            }
     }
 done:
     if (msg.empty()) msg = "ok: " + std::to_string(checked) + " tile plans checked";

@@ -493,3 +493,62 @@ def test_mrt_oscillation_period_on_gpu(P):
     period = -b / (2 * a)
     print(f"MRT oscillation period on the GPU: {period:.0f} steps (paper: 3200)")
     assert abs(period - 3200) <= 100
+
+
+@pytest.mark.parametrize("tile", [(64, 8), (32, 16), (64, 16), (128, 8)])
+def test_fused_tma_equals_plain_fused_bitwise(P, tile):
+    # the TMA-staged single pass runs the same per-site arithmetic on the same
+    # values as the plain-load single pass: bitwise equal results, on ragged
+    # lattices of a batch (tiles crossing the right and bottom edges)
+    rec = synth.batch_recipe(n=4, side=(37, 150))
+    descs = [P.lbm_desc_default(r["nx"], r["ny"], T=r["T"]) for r in rec]
+    fields = [synth.droplet(r["nx"], r["ny"], r["R"], r["T"]) for r in rec]
+    outs = []
+    for variant, sp in ((P.LBM_KERNEL_PLAIN, 2), (P.LBM_KERNEL_TMA, 0)):
+        h = P.lbm_create(descs, schedule=P.LBM_SCHED_FUSED, kernel_variant=variant, tile=tile,
+                         sites_per_thread=sp if variant == P.LBM_KERNEL_PLAIN else 0)
+        assert P.lbm_info(h)["collide_variant"] == variant
+        for i, f in enumerate(fields):
+            P.lbm_init(h, i, f)
+        P.lbm_step(h, 150)
+        outs.append([P.lbm_moments(h, i, mass=False) for i in range(len(descs))])
+        P.lbm_destroy(h)
+    for a, b in zip(*outs):
+        assert np.array_equal(a["rho"], b["rho"]) and np.array_equal(a["ux"], b["ux"])
+    o = oracle_run(fields[0], 150, T=rec[0]["T"])
+    assert rel(outs[1][0]["rho"], o["rho"]) <= RTOL_RHO
+    # a single ragged lattice takes the tensor-map path (one 3-D copy per tile)
+    nx, ny = 203, 77
+    rho = synth.droplet(nx, ny, 25.0, 0.7)
+    single = []
+    for variant, sp in ((P.LBM_KERNEL_PLAIN, 2), (P.LBM_KERNEL_TMA, 0)):
+        h = P.lbm_create(P.lbm_desc_default(nx, ny, T=0.7), schedule=P.LBM_SCHED_FUSED,
+                         kernel_variant=variant, tile=tile,
+                         sites_per_thread=sp if variant == P.LBM_KERNEL_PLAIN else 0)
+        if variant == P.LBM_KERNEL_TMA:
+            assert P.lbm_info(h)["tensor_map"] == 1
+        P.lbm_init(h, 0, rho)
+        P.lbm_step(h, 150)
+        single.append(P.lbm_moments(h, 0, mass=False))
+        P.lbm_destroy(h)
+    assert np.array_equal(single[0]["rho"], single[1]["rho"])
+    assert np.array_equal(single[0]["ux"], single[1]["ux"])
+
+
+@pytest.mark.parametrize("storage,mrt", [(2, False), (1, True)])
+def test_fused_tma_storage_and_mrt(P, storage, mrt):
+    n, T = 100, 0.7
+    rho = synth.droplet(n, n, 24.0, T)
+    kw = dict(T=T, storage=storage)
+    if mrt:
+        kw.update(collision=P.LBM_COLL_MRT, tau=0.8, mrt_rates=[1.0] * 7 + [1 / 0.8] * 2)
+    outs = []
+    for variant in (P.LBM_KERNEL_PLAIN, P.LBM_KERNEL_TMA):
+        h = P.lbm_create(P.lbm_desc_default(n, n, **kw), schedule=P.LBM_SCHED_FUSED,
+                         kernel_variant=variant, tile=(64, 8),
+                         sites_per_thread=2 if variant == P.LBM_KERNEL_PLAIN else 0)
+        P.lbm_init(h, 0, rho)
+        P.lbm_step(h, 200)
+        outs.append(P.lbm_moments(h, 0, mass=False))
+        P.lbm_destroy(h)
+    assert np.array_equal(outs[0]["rho"], outs[1]["rho"])
