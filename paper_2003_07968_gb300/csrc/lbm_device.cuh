@@ -596,6 +596,29 @@ __device__ __forceinline__ void collide(const SiteConsts& C, const float* mrt_s,
     }
 }
 
+// The periodic images of site (x, y) within GW of the interior, without the
+// site itself (which a bulk tile store writes).
+template <class T>
+__device__ __forceinline__ void store_images(T* plane, int pitch, int gx, int x, int y, int nx,
+                                             int ny, T v) {
+    T* const row = plane + (int64_t)(y + GY) * pitch + gx;
+    const bool xl = x < GW, xh = x >= nx - GW, yl = y < GW, yh = y >= ny - GW;
+    if (xl) row[x + nx] = v;
+    if (xh) row[x - nx] = v;
+    if (yl) {
+        T* const r = row + (int64_t)ny * pitch;
+        r[x] = v;
+        if (xl) r[x + nx] = v;
+        if (xh) r[x - nx] = v;
+    }
+    if (yh) {
+        T* const r = row - (int64_t)ny * pitch;
+        r[x] = v;
+        if (xl) r[x + nx] = v;
+        if (xh) r[x - nx] = v;
+    }
+}
+
 // Store the nine outputs of site (x, y): interior sites with plain stores,
 // sites within GW of an edge also into their periodic images.  `tile_in`
 // says the whole tile is interior (uniform per block), which skips the

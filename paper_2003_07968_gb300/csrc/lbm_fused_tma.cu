@@ -87,6 +87,17 @@ __device__ __forceinline__ void tensor_g2s(void* dst, const CUtensorMap* map, in
         : "memory");
 }
 
+// 3-D tensor store shared -> global of a box at (x, y, z) (x a multiple of 16
+// bytes, all coordinates >= 0); parts outside the tensor are not written.
+__device__ __forceinline__ void tensor_s2g(const CUtensorMap* map, const void* src, int x, int y,
+                                           int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
 __device__ __forceinline__ bool tile_skipped(const StepArgs& a, int t) {
     return a.quota && a.step >= __ldg(&a.quota[__ldg(&a.tiles[t]).x]);
 }
@@ -128,7 +139,7 @@ __device__ __forceinline__ void issue_fused(const StepArgs& a, int4 tl, unsigned
 template <class S, int EOSP, int TX, int TY, bool MRT, bool TMAP>
 __global__ void __launch_bounds__(kBlockF, 2)
     k_fused_tma(StepArgs a, const __grid_constant__ CUtensorMap tmap,
-                const __grid_constant__ LatDev lat0) {
+                const __grid_constant__ CUtensorMap smap, const __grid_constant__ LatDev lat0) {
     using G = FGeo<S, TX, TY, TMAP>;
     using T = typename S::T;
     using V = typename LaneOf<G::SPT>::V;
@@ -144,7 +155,10 @@ __global__ void __launch_bounds__(kBlockF, 2)
     if (threadIdx.x == 0) {
         for (int s = 0; s < G::STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kConsumers / 32);
+            // row copies: each consumer warp releases a stage after reading it;
+            // tensor path: the consumer that stores the tile releases it once
+            // the tile store has read it
+            mbar_init(&empty[s], TMAP ? 1 : kConsumers / 32);
         }
         *abort_flag = 0;
         mbar_fence_init();
@@ -193,6 +207,7 @@ __global__ void __launch_bounds__(kBlockF, 2)
     const int tx = tid % TX, ty0 = tid / TX;
     constexpr int nhalf = TX + TY + 2;  // half of the 2 (TX + TY) + 4 ring cells
     int k = 0;
+    int prev_s = -1;  // tensor path: stage of the tile whose store is in flight
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         if (tile_skipped(a, t)) continue;
         const int s = k % G::STAGES;
@@ -256,9 +271,11 @@ __global__ void __launch_bounds__(kBlockF, 2)
                 if (live & 1u) ps[(gy[0] - y0 + 1) * PW + (gx[0] - x0 + 1)] = psi.x;
                 if (live & 2u) ps[(gy[1] - y0 + 1) * PW + (gx[1] - x0 + 1)] = psi.y;
             }
-            // every read of the stage is done: hand it back to the producer
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);
+            // row copies: every read of the stage is done, hand it back
+            if (!TMAP) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+            }
         }
         // psi tile complete; a warp whose wait ran out makes every consumer leave
         uint32_t failed;
@@ -272,15 +289,23 @@ __global__ void __launch_bounds__(kBlockF, 2)
             if (tid == 0) {
                 *abort_flag = 1;
                 atomicOr(&a.status[tl.x], 2u);
+                if (TMAP) bulk_wait_all();  // tile stores already issued complete on their own
             }
             return;
         }
         ++k;
-        if (x >= nx) continue;
+        if (!TMAP && x >= nx) continue;
         // force, collision, stores
         const SiteConsts C = site_consts(L);
         T* o = reinterpret_cast<T*>(a.pop) + L.off_f[a.parity ^ 1];
         const bool tile_in = x0 >= GW && y0 >= GW && x0 + TX <= nx - GW && y0 + TY <= ny - GW;
+        // tensor path, tiles inside the lattice: f* of the tile goes to the
+        // stage just consumed, laid out as the store box [plane][TY][TX], and
+        // leaves in one tensor store.  A ragged edge tile uses plain stores:
+        // the store unit clips a box at 16-byte granularity in x (measured), so
+        // a partial box would also write the ghost columns just past nx.
+        const bool bulk_out = TMAP && x0 + TX <= nx && y0 + TY <= ny;
+        T* out = reinterpret_cast<T*>(smem + s * G::STAGEB);
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
             V p[9], v[9];
@@ -300,14 +325,52 @@ __global__ void __launch_bounds__(kBlockF, 2)
             collide<MRT>(C, L.mrt_s, drho[j], g[j], p, v);
 #pragma unroll
             for (int l = 0; l < Ln::n; ++l) {
-                const int y = y0 + ty0 + (j * Ln::n + l) * G::RPB;
-                if (y >= ny) break;
-                float vs[9];
+                const int ly = ty0 + (j * Ln::n + l) * G::RPB;
+                const int y = y0 + ly;
+                if (bulk_out) {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) vs[i] = Ln::get(v[i], l);
-                store_site<S>(o, L.plane, L.pitch, L.gx, x, y, nx, ny, vs, tile_in);
+                    for (int i = 0; i < 9; ++i) out[(i * TY + ly) * TX + tx] = S::cv(Ln::get(v[i], l));
+                    if (!tile_in)
+#pragma unroll
+                        for (int i = 0; i < 9; ++i)
+                            store_images(o + i * L.plane, L.pitch, L.gx, x, y, nx, ny,
+                                         S::cv(Ln::get(v[i], l)));
+                } else {
+                    if (x >= nx || y >= ny) continue;
+                    float vs[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) vs[i] = Ln::get(v[i], l);
+                    store_site<S>(o, L.plane, L.pitch, L.gx, x, y, nx, ny, vs, tile_in);
+                }
             }
         }
+        if (TMAP) {
+            // the tile's f* in shared memory -> one tensor store; a stage goes
+            // back to the producer once the store of its tile has read it
+            if (bulk_out) fence_proxy_async_smem();
+            named_sync(2, kConsumers);
+            if (tid == 0) {
+                if (bulk_out) {
+                    tensor_s2g(&smap, smem + s * G::STAGEB, x0 + L.gx, y0 + GY,
+                               9 * (a.parity ^ 1));
+                    bulk_commit();
+                    if (prev_s >= 0) {
+                        bulk_wait_read<1>();
+                        mbar_arrive(&empty[prev_s]);
+                    }
+                } else {
+                    // no store reads this stage: release it, and the previous one
+                    bulk_wait_read<0>();
+                    if (prev_s >= 0) mbar_arrive(&empty[prev_s]);
+                    mbar_arrive(&empty[s]);
+                }
+            }
+            prev_s = bulk_out ? s : -1;
+        }
+    }
+    if (TMAP && tid == 0) {
+        bulk_wait_all();
+        if (prev_s >= 0) mbar_arrive(&empty[prev_s]);
     }
 }
 
@@ -315,6 +378,7 @@ __global__ void __launch_bounds__(kBlockF, 2)
 template <class S, int EOSP, int TX, int TY, bool MRT, bool TMAP>
 cudaError_t fused_inst(const StepArgs& a, const CUtensorMap* map, const LatDev* lat0, int grid,
                        cudaStream_t st, bool query, int* occ) {
+    // map[0]: load map, map[1]: store map (tensor path)
     using G = FGeo<S, TX, TY, TMAP>;
     const void* fn = (const void*)k_fused_tma<S, EOSP, TX, TY, MRT, TMAP>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
@@ -324,7 +388,7 @@ cudaError_t fused_inst(const StepArgs& a, const CUtensorMap* map, const LatDev* 
     std::memset(&none, 0, sizeof none);
     const LatDev nolat{};
     k_fused_tma<S, EOSP, TX, TY, MRT, TMAP><<<grid, dim3(kBlockF), G::SMEM, st>>>(
-        a, map ? *map : none, lat0 ? *lat0 : nolat);
+        a, map ? map[0] : none, map ? map[1] : none, lat0 ? *lat0 : nolat);
     return cudaGetLastError();
 }
 
@@ -389,23 +453,35 @@ bool fused_tma_shape_supported(int tx, int ty) {
 
 bool fused_tma_make_map(int f16, int tx, int ty, const LatDev& L, void* pop, CUtensorMap* map) {
     const int es = f16 ? 2 : 4, h = 16 / es, bw = tx + 2 * h;
-    // the box must lie inside the tensor: rows at least a box wide, and
+    // every box must lie inside its tensor: rows at least a box wide and
     // enough rows; the row and plane strides are multiples of 16 bytes
-    if (!fused_tma_shape_supported(tx, ty) || L.pitch < bw || L.ny + 2 * GY < ty + 4) return false;
+    if (!fused_tma_shape_supported(tx, ty) || L.pitch < bw || L.ny + 2 * GY < ty + 4 ||
+        L.gx + L.nx < tx || GY + L.ny < ty)
+        return false;
     if ((L.pitch * es) % 16 || (L.plane * es) % 16) return false;
     char* base = reinterpret_cast<char*>(pop) + L.off_f[0] * es;
     if (reinterpret_cast<uintptr_t>(base) % 16 || L.off_f[1] != L.off_f[0] + 9 * L.plane)
         return false;
     EncodeTiled enc = encode_fn();
     if (!enc) return false;
-    // both population buffers as 18 planes: x (row elements), y (rows), z (plane)
-    const cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)(L.ny + 2 * GY), 18};
+    const CUtensorMapDataType dt = f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * es, (cuuint64_t)L.plane * es};
-    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)(ty + 4), 9};
     const cuuint32_t estr[3] = {1, 1, 1};
-    return enc(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-               base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    // loads: both population buffers as 18 planes of whole rows, ghost frame
+    // included: x (row elements), y (rows), z (plane)
+    const cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)(L.ny + 2 * GY), 18};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)(ty + 4), 9};
+    if (enc(&map[0], dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    // stores: the same planes, clipped after the last interior column and row
+    // (x < gx + nx, y < GY + ny), so a ragged tile writes no ghost or pad
+    // element; boxes of one tile
+    const cuuint64_t sdims[3] = {(cuuint64_t)(L.gx + L.nx), (cuuint64_t)(GY + L.ny), 18};
+    const cuuint32_t sbox[3] = {(cuuint32_t)tx, (cuuint32_t)ty, 9};
+    return enc(&map[1], dt, 3, base, sdims, strides, sbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -420,9 +496,9 @@ cudaError_t launch_fused_tma(int f16, int mrt, int eos, int tx, int ty, const St
 int occupancy_fused_tma(int f16, int mrt, int eos, int tx, int ty, bool with_map) {
     int occ = 0;
     StepArgs a{};
-    CUtensorMap m;
-    std::memset(&m, 0, sizeof m);
-    const CUtensorMap* mp = with_map ? &m : nullptr;
+    CUtensorMap m[2];
+    std::memset(m, 0, sizeof m);
+    const CUtensorMap* mp = with_map ? m : nullptr;
     const LatDev lat{};
     cudaError_t e =
         f16 ? fused_any<StoreF16>(tx, ty, mrt, eos, a, mp, &lat, 0, nullptr, true, &occ)

@@ -103,7 +103,7 @@ struct lbm_handle {
     int tune_variant = LBM_KERNEL_AUTO;  // the kernel_variant the handle was created with
     // tensor map of the population buffers for the single-pass TMA kernel
     // (single lattice, rows at least a box wide); else that kernel uses row copies
-    CUtensorMap tmap{};
+    CUtensorMap tmap[2]{};  // loads, stores
     bool has_tmap = false;
     // profiling
     bool prof = false;
@@ -175,7 +175,7 @@ int build_tiles(lbm_handle* h, int k, int tx, int ty) {
     if (k == 1)
         h->has_tmap = h->schedule == LBM_SCHED_FUSED && P.variant == LBM_KERNEL_TMA &&
                       h->lat.size() == 1 &&
-                      fused_tma_make_map(h->f16, tx, ty, h->lat[0], h->pop, &h->tmap);
+                      fused_tma_make_map(h->f16, tx, ty, h->lat[0], h->pop, h->tmap);
     std::vector<int4> t;
     P.begin.assign(h->lat.size(), 0);
     P.count.assign(h->lat.size(), 0);
@@ -264,7 +264,7 @@ cudaError_t launch_pass(lbm_handle* h, int k, const StepArgs& a, int grid) {
                    : launch_psi(h->f16, h->eos, P.spt, a, dim3(grid), block, h->stream);
     if (h->schedule == LBM_SCHED_FUSED && P.variant == LBM_KERNEL_TMA)
         return launch_fused_tma(h->f16, h->collision == LBM_COLL_MRT, h->eos, P.tx, P.ty, a,
-                                h->has_tmap ? &h->tmap : nullptr, &h->lat[0], grid, h->stream);
+                                h->has_tmap ? h->tmap : nullptr, &h->lat[0], grid, h->stream);
     if (h->schedule == LBM_SCHED_FUSED)
         return launch_fused(h->f16, h->collision == LBM_COLL_MRT, h->eos, P.spt, a, dim3(grid), block, collide_smem(P.tx, P.ty),
                             h->stream);
