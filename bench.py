@@ -47,6 +47,8 @@ def parse():
                     help="served workload: divide each request's step count by this")
     ap.add_argument("--target-sites", type=int, default=0,
                     help="served workload: resident-site target of the server (0: default)")
+    ap.add_argument("--chunk", type=int, default=100,
+                    help="served workload: steps per server chunk")
     ap.add_argument("--eos", default="df", choices=["f64", "df", "f32"],
                     help="arithmetic of psi/EOS: float-float (default), native FP64 or FP32")
     ap.add_argument("--variant", default="auto", choices=["auto", "tma", "plain"])
@@ -514,8 +516,9 @@ def run_served(args):
     P.lbm_sync(h)
     P.lbm_destroy(h)
 
-    opts = P.lbm_server_opts_default(arena_bytes=64 << 30, chunk_steps=50, storage=storage,
-                                     max_resident=1024)
+    # results carry rho only, as the sequential runs below read rho only
+    opts = P.lbm_server_opts_default(arena_bytes=64 << 30, chunk_steps=args.chunk, storage=storage,
+                                     max_resident=1024, with_velocity=0)
     if args.target_sites:
         opts.target_resident_sites = args.target_sites
     srv = P.lbm_server_create(opts)
@@ -583,7 +586,7 @@ def run_served(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"served: {len(reqs)} requests, Poisson 200/s, sides U{{128..2048}}, "
                                   f"steps U{{1000..50000}}/{args.step_scale}, droplet/band 50/50",
-                      "storage": args.storage, "chunk_steps": 50, "site_steps": work,
+                      "storage": args.storage, "chunk_steps": args.chunk, "site_steps": work,
                       "target_resident_sites": opts.target_resident_sites},
            "served": {"MLUPS": round(served, 1), "p50_s": round(pct(lat, 50), 4),
                       "p99_s": round(pct(lat, 99), 4), "wall_s": round(wall, 3),

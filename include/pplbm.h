@@ -241,11 +241,14 @@ int lbm_autotune(lbm_handle* h, int32_t repeats);
  * chunk boundaries, first come first served but skipping any that do not
  * fit yet, whenever a slot and arena space (HBM footprint: both population
  * buffers plus psi) are free and the resident sites stay below a target; a
- * chunk runs each lattice for min(chunk_steps, its remaining steps); a
- * finished lattice's moments are copied out while the next chunk runs, and
- * its space is then reused.  One native worker thread drives the GPU; the
- * submit and poll calls are thread-safe and never wait for the GPU.  The
- * numerics of a request do not depend on what else is resident. */
+ * chunk runs each lattice for min(chunk_steps, its remaining steps).  The
+ * worker keeps two chunks in flight: new requests' fields are uploaded
+ * through pinned memory on their own stream while a chunk runs, the next
+ * chunk is queued before the previous one is retired, and a finished
+ * lattice's moments are copied out (through pinned memory) while the next
+ * chunk runs; its space is then reused.  One native worker thread drives
+ * the GPU; the submit and poll calls are thread-safe and never wait for the
+ * GPU.  The numerics of a request do not depend on what else is resident. */
 typedef struct lbm_server lbm_server;
 
 typedef struct {
@@ -263,6 +266,8 @@ typedef struct {
     int32_t schedule;         /* LBM_SCHED_* (AUTO: single pass)                  */
     int32_t tile_x, tile_y;   /* 0: defaults; else both passes                    */
     int32_t sites_per_thread; /* with tile_x/tile_y: 1, 2 or 4 (0: 1)              */
+    int32_t with_velocity;    /* 1 (default): results carry ux, uy; 0: rho only
+                                 (lbm_poll then fills ux, uy with NaN)           */
 } lbm_server_opts;
 
 typedef struct {

@@ -1,23 +1,28 @@
 // lbm_server.cu -- continuous-batching server of the C ABI (lbm_server_*,
 // lbm_submit, lbm_poll): many independent lattices resident in one device
-// arena, stepped together by the same two passes as a batch handle.
+// arena, stepped together by the same kernels as a batch handle.
 //
-// One worker thread owns the GPU work.  Its loop:
+// One worker thread owns the GPU work and keeps two chunks in flight.  Each
+// turn of its loop:
 //   1. admit queued requests (first come first served, skipping those that
 //      do not fit yet) while a slot, arena space and the resident-site
-//      target allow; initialise each at equilibrium in the current buffer;
-//   2. rebuild one of two alternating table sets (lattice table, tile list
-//      per pass, per-lattice step quotas) from the resident requests;
-//   3. launch a chunk of up to chunk_steps steps for every resident lattice:
-//      two launches per step over the whole tile list, each lattice running
-//      min(chunk_steps, its remaining steps) of them (the kernels skip the
-//      tiles of a lattice whose quota is used up);
-//   4. while that chunk runs, copy out the lattices that finished in the
-//      previous chunk (psi pass over their tiles, moments kernel,
-//      device-to-host, on a side stream with the previous table set) and
-//      free their space;
-//   5. wait for the chunk, read the fault words, note which lattices finished.
-// Every lattice still resident after a chunk has run all of its steps, so all
+//      target allow; their initial fields go through a pinned upload buffer
+//      on the upload stream (overlapping the chunk in flight) and are
+//      initialised at equilibrium on the main stream;
+//   2. launch chunk n: rebuild one of two alternating table sets (lattice
+//      table, tile lists, per-lattice step quotas), one launch per step over
+//      the tile list of every resident lattice, each lattice running
+//      min(chunk_steps, its remaining steps) (the kernels skip the tiles of a
+//      lattice whose quota is used up).  Quotas are known on the host, so the
+//      lattices that finish in chunk n are known when it is launched and are
+//      not part of chunk n + 1;
+//   3. retire chunk n - 1 (which ran while the host did 1 and 2): read its
+//      fault words, copy out the lattices that finished in it (psi pass,
+//      moments, device to pinned host memory, on the side stream, while
+//      chunk n runs) and free their space.
+// A lattice whose fault bit shows up is dropped one chunk later than it
+// faulted (its extra chunk computes garbage that nobody reads).  Every
+// lattice still resident after a chunk has run all of its steps, so all
 // resident lattices share the buffer parity; a lattice that stops early
 // keeps its own final parity for the copy-out.  Bounding the resident sites
 // keeps the GPU saturated without stretching every request's latency.
@@ -28,6 +33,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <limits>
 #include <map>
 #include <mutex>
 #include <new>
@@ -101,6 +107,8 @@ struct Request {
     int state = ST_QUEUED;
     int status = LBM_OK;
     size_t pop_off = 0, psi_off = 0, pop_bytes = 0, psi_bytes = 0;
+    size_t stage_off = 0;  // doubles into the upload buffers while being admitted
+    bool dropped = false;  // faulted: no further chunks, released once its last chunk is done
     LatDev L{};
     Clock::time_point t_submit, t_done;
 };
@@ -129,12 +137,17 @@ struct lbm_server {
     lbm_server_opts o{};
     int device = 0, sm_count = 0, f16 = 0, es = 4;
     int fused = 1;  // one launch per step (LBM_SCHED_FUSED)
-    cudaStream_t stream = nullptr, side = nullptr;
-    cudaEvent_t chunk_end = nullptr;
+    cudaStream_t stream = nullptr, side = nullptr, up = nullptr;
+    cudaEvent_t chunk_end[2] = {nullptr, nullptr};  // per table set: its last chunk is done
+    cudaEvent_t up_done = nullptr;    // the last uploads have read up_host
+    cudaEvent_t init_done = nullptr;  // the last inits have read staging
     void* arena = nullptr;
-    double* staging = nullptr;  // rho of one admitted request (main stream)
-    double* outbuf = nullptr;   // rho, ux, uy of one finished request (side stream)
-    uint32_t* status_host = nullptr;
+    size_t up_cap = 0;            // doubles of the upload buffers
+    double* staging = nullptr;    // rho of the requests admitted in one turn (device)
+    double* up_host = nullptr;    // ... their pinned host copy
+    double* outbuf = nullptr;     // rho, ux, uy of one finished request (side stream)
+    double* down_host = nullptr;  // ... their pinned host copy
+    uint32_t* status_host = nullptr;  // fault words of both table sets (pinned)
     PassState pass[2];
     TableSet set[2];
     ArenaAlloc alloc;
@@ -161,10 +174,16 @@ void free_server(lbm_server* S) {
         if (T.status) cudaFree(T.status);
     }
     if (S->status_host) cudaFreeHost(S->status_host);
+    if (S->down_host) cudaFreeHost(S->down_host);
+    if (S->up_host) cudaFreeHost(S->up_host);
     if (S->outbuf) cudaFree(S->outbuf);
     if (S->staging) cudaFree(S->staging);
     if (S->arena) cudaFree(S->arena);
-    if (S->chunk_end) cudaEventDestroy(S->chunk_end);
+    for (auto& e : S->chunk_end)
+        if (e) cudaEventDestroy(e);
+    if (S->up_done) cudaEventDestroy(S->up_done);
+    if (S->init_done) cudaEventDestroy(S->init_done);
+    if (S->up) cudaStreamDestroy(S->up);
     if (S->side) cudaStreamDestroy(S->side);
     if (S->stream) cudaStreamDestroy(S->stream);
 }
@@ -259,7 +278,8 @@ cudaError_t rebuild(lbm_server* S, TableSet& T, std::vector<Request*>& res,
 }
 
 // Moments of lattice l of set T (final parity `par`) into R, on the side
-// stream after the chunk that finished it.
+// stream after the chunk that finished it: device -> pinned host buffer ->
+// R (velocities only with the server's with_velocity option).
 cudaError_t copy_out(lbm_server* S, const TableSet& T, Request& R, int l, int par) {
     StepArgs a = args(S, T, 0, par);
     a.tiles = T.tiles[0] + T.begin[0][l];
@@ -268,22 +288,29 @@ cudaError_t copy_out(lbm_server* S, const TableSet& T, Request& R, int l, int pa
     cudaError_t e = launch(S, 0, a, pass_grid(S, 0, a.ntiles), S->side);
     if (e != cudaSuccess) return e;
     const size_t n = (size_t)R.L.nx * R.L.ny;
+    const bool vel = S->o.with_velocity != 0;
     double* dr = S->outbuf;
     double* dx = dr + S->o.max_request_sites;
     double* dy = dx + S->o.max_request_sites;
-    e = launch_moments(S->f16, R.L, S->arena, par, static_cast<float*>(S->arena), dr, dx, dy,
-                       S->side);
+    e = launch_moments(S->f16, R.L, S->arena, par, static_cast<float*>(S->arena), dr,
+                       vel ? dx : nullptr, vel ? dy : nullptr, S->side);
     if (e != cudaSuccess) return e;
-    R.rho.resize(n);
-    R.ux.resize(n);
-    R.uy.resize(n);
-    e = cudaMemcpyAsync(R.rho.data(), dr, n * sizeof(double), cudaMemcpyDeviceToHost, S->side);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(R.ux.data(), dx, n * sizeof(double), cudaMemcpyDeviceToHost, S->side);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(R.uy.data(), dy, n * sizeof(double), cudaMemcpyDeviceToHost, S->side);
+    double* hr = S->down_host;
+    double* hx = hr + S->o.max_request_sites;
+    double* hy = hx + S->o.max_request_sites;
+    e = cudaMemcpyAsync(hr, dr, n * sizeof(double), cudaMemcpyDeviceToHost, S->side);
+    if (e == cudaSuccess && vel)
+        e = cudaMemcpyAsync(hx, dx, n * sizeof(double), cudaMemcpyDeviceToHost, S->side);
+    if (e == cudaSuccess && vel)
+        e = cudaMemcpyAsync(hy, dy, n * sizeof(double), cudaMemcpyDeviceToHost, S->side);
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->side);
-    return e;
+    if (e != cudaSuccess) return e;
+    R.rho.assign(hr, hr + n);
+    if (vel) {
+        R.ux.assign(hx, hx + n);
+        R.uy.assign(hy, hy + n);
+    }
+    return cudaSuccess;
 }
 
 void fail_all(lbm_server* S, int status) {
@@ -305,39 +332,69 @@ struct Finished {
     int l, par, status;
 };
 
+// What the worker remembers of a chunk in flight until it retires it.
+struct Chunk {
+    bool live = false;
+    std::vector<Request*> res;       // lattices of the chunk, in table order
+    std::vector<int> quota;
+    int p0 = 0;                      // buffer parity at its start
+    std::vector<Finished> finished;  // ran their last steps in it
+    std::vector<Request*> dropped;   // faulted earlier, still part of it: free once it is done
+    Clock::time_point t0;
+};
+
+void finish(lbm_server* S, Request* R, int status) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    R->status = status;
+    R->state = ST_DONE;
+    R->t_done = Clock::now();
+    S->alloc.release(R->pop_off, R->pop_bytes);
+    S->alloc.release(R->psi_off, R->psi_bytes);
+    if (status == LBM_OK)
+        S->st.completed++;
+    else
+        S->st.failed++;
+    S->st.arena_in_use = (int64_t)S->alloc.in_use();
+}
+
 void worker_main(lbm_server* S) {
     cudaSetDevice(S->device);
-    std::vector<Request*> res;  // resident requests (worker's view)
-    int64_t res_sites = 0;
-    std::vector<Finished> pending;  // finished in the last chunk, to copy out
-    int pending_set = 0;
-    int64_t chunk_no = 0;
+    std::vector<Request*> res;  // resident and still to run (host view)
+    int64_t res_sites = 0;      // sites held in the arena by resident lattices
+    Chunk chunk[2];
+    int64_t n = 0;              // chunks launched
     for (;;) {
+        // ------------------------------------------------------------ admission
         std::vector<Request*> admitted;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             if (S->stop) break;
-            if (res.empty() && S->queue.empty() && pending.empty()) {
+            if (res.empty() && S->queue.empty() && !chunk[0].live && !chunk[1].live) {
                 S->cv.wait_for(lk, std::chrono::milliseconds(20));
                 continue;
             }
-            // admission: first come first served, skipping requests that do
-            // not fit yet, while slots, arena space and the resident-site
-            // target allow (one request is always admitted into an idle GPU)
+            // first come first served, skipping requests that do not fit yet,
+            // while slots, arena space, the resident-site target and the upload
+            // buffer allow (one request is always admitted into an idle GPU)
+            size_t up_used = 0;
             for (auto it = S->queue.begin(); it != S->queue.end();) {
                 if ((int)(res.size() + admitted.size()) >= S->o.max_resident) break;
                 Request& R = S->reqs[*it];
-                const int64_t n = (int64_t)R.L.nx * R.L.ny;
-                if (res_sites + n > S->o.target_resident_sites && (res_sites > 0 || !admitted.empty()))
+                const int64_t ns = (int64_t)R.L.nx * R.L.ny;
+                const size_t nup = (size_t)round_up(ns, 32);
+                if (res_sites + ns > S->o.target_resident_sites && (res_sites > 0 || !admitted.empty()))
                     break;
+                if (up_used + nup > S->up_cap) break;
                 size_t po = 0, qo = 0;
                 if (S->alloc.alloc(R.pop_bytes, &po)) {
                     if (S->alloc.alloc(R.psi_bytes, &qo)) {
                         R.pop_off = po;
                         R.psi_off = qo;
+                        R.stage_off = up_used;
+                        up_used += nup;
                         R.state = ST_RESIDENT;
                         admitted.push_back(&R);
-                        res_sites += n;
+                        res_sites += ns;
                         it = S->queue.erase(it);
                         continue;
                     }
@@ -348,41 +405,64 @@ void worker_main(lbm_server* S) {
             S->st.queued = (int)S->queue.size();
             S->st.arena_in_use = (int64_t)S->alloc.in_use();
         }
-        const auto t0 = Clock::now();
         cudaError_t e = cudaSuccess;
         int64_t launches = 0;
-        for (Request* R : admitted) {
-            R->L.off_f[0] = (int64_t)(R->pop_off / S->es);
-            R->L.off_f[1] = R->L.off_f[0] + 9 * R->L.plane;
-            R->L.off_psi = (int64_t)(R->psi_off / 4);
-            const size_t n = (size_t)R->L.nx * R->L.ny;
-            if (R->d.storage != LBM_STORE_F32 && R->d.rho0 < 0.0)
-                R->L.rho0 = auto_rho0(R->rho.data(), n);
-            // pageable source: the copy has read R->rho when the call returns;
-            // the next request's copy into the staging follows this init in stream order
-            e = cudaMemcpyAsync(S->staging, R->rho.data(), n * sizeof(double),
-                                cudaMemcpyHostToDevice, S->stream);
+        if (!admitted.empty()) {
+            // the previous uploads have read up_host, the previous inits staging
+            e = cudaEventSynchronize(S->up_done);
+            size_t total = 0;
+            for (Request* R : admitted) {
+                const size_t ns = (size_t)R->L.nx * R->L.ny;
+                std::memcpy(S->up_host + R->stage_off, R->rho.data(), ns * sizeof(double));
+                total = std::max(total, R->stage_off + ns);
+            }
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(S->up, S->init_done, 0);
             if (e == cudaSuccess)
-                e = launch_init(S->f16, R->L, S->arena, S->parity, S->staging, nullptr, nullptr,
-                                S->stream);
-            if (e != cudaSuccess) break;
-            launches += 1;
-            std::vector<double>().swap(R->rho);
-            res.push_back(R);
+                e = cudaMemcpyAsync(S->staging, S->up_host, total * sizeof(double),
+                                    cudaMemcpyHostToDevice, S->up);
+            if (e == cudaSuccess) e = cudaEventRecord(S->up_done, S->up);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(S->stream, S->up_done, 0);
+            for (Request* R : admitted) {
+                if (e != cudaSuccess) break;
+                R->L.off_f[0] = (int64_t)(R->pop_off / S->es);
+                R->L.off_f[1] = R->L.off_f[0] + 9 * R->L.plane;
+                R->L.off_psi = (int64_t)(R->psi_off / 4);
+                const size_t ns = (size_t)R->L.nx * R->L.ny;
+                if (R->d.storage != LBM_STORE_F32 && R->d.rho0 < 0.0)
+                    R->L.rho0 = auto_rho0(R->rho.data(), ns);
+                e = launch_init(S->f16, R->L, S->arena, S->parity, S->staging + R->stage_off,
+                                nullptr, nullptr, S->stream);
+                launches += 1;
+                std::vector<double>().swap(R->rho);
+                res.push_back(R);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(S->init_done, S->stream);
         }
-        // launch the next chunk (if anything is resident) before copying out
-        // the lattices that finished in the previous one
-        const int cur = (int)(chunk_no & 1);
-        std::vector<int> quota(res.size());
-        int64_t k = 0;
-        for (size_t l = 0; l < res.size(); ++l) {
-            quota[l] = (int)std::min<int64_t>(S->o.chunk_steps, res[l]->remaining);
-            k = std::max<int64_t>(k, quota[l]);
-        }
-        const int p0 = S->parity;
+        // ------------------------------------------------------------ chunk n
+        const int cur = (int)(n & 1);
         if (e == cudaSuccess && !res.empty()) {
+            Chunk& C = chunk[cur];
+            // the table set's previous chunk (n - 2) and its copy-outs are done
+            e = cudaEventSynchronize(S->chunk_end[cur]);
+            C = Chunk{};
+            C.live = true;
+            C.res = res;
+            C.p0 = S->parity;
+            C.t0 = Clock::now();
+            C.quota.resize(res.size());
+            int64_t k = 0;
+            std::vector<Request*> keep;
+            for (size_t l = 0; l < res.size(); ++l) {
+                C.quota[l] = (int)std::min<int64_t>(S->o.chunk_steps, res[l]->remaining);
+                k = std::max<int64_t>(k, C.quota[l]);
+                res[l]->remaining -= C.quota[l];
+                if (res[l]->remaining > 0)
+                    keep.push_back(res[l]);
+                else
+                    C.finished.push_back(Finished{res[l], (int)l, (C.p0 + C.quota[l]) & 1, LBM_OK});
+            }
             TableSet& T = S->set[cur];
-            e = rebuild(S, T, res, quota);
+            if (e == cudaSuccess) e = rebuild(S, T, C.res, C.quota);
             const int g0 = pass_grid(S, 0, T.ntiles[0]), g1 = pass_grid(S, 1, T.ntiles[1]);
             for (int64_t s = 0; s < k && e == cudaSuccess; ++s) {
                 StepArgs a0 = args(S, T, 0, S->parity), a1 = args(S, T, 1, S->parity);
@@ -393,66 +473,88 @@ void worker_main(lbm_server* S) {
                 S->parity ^= 1;
             }
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(S->status_host, T.status, res.size() * sizeof(uint32_t),
-                                    cudaMemcpyDeviceToHost, S->stream);
-            if (e == cudaSuccess) e = cudaEventRecord(S->chunk_end, S->stream);
+                e = cudaMemcpyAsync(S->status_host + cur * S->o.max_resident, T.status,
+                                    C.res.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                    S->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(S->chunk_end[cur], S->stream);
+            res.swap(keep);
+            ++n;
         }
-        // copy out the previous chunk's finished lattices while this chunk runs
-        for (Finished& f : pending) {
-            int status = f.status;
-            if (status == LBM_OK && e == cudaSuccess) {
-                if (copy_out(S, S->set[pending_set], *f.R, f.l, f.par) != cudaSuccess)
-                    status = LBM_ERR_CUDA;
-                launches += 2;
+        // ------------------------------------------------------------ retire n - 1
+        Chunk& P = chunk[cur ^ 1];
+        if (e == cudaSuccess && P.live) {
+            e = cudaEventSynchronize(S->chunk_end[cur ^ 1]);
+            const uint32_t* bits = S->status_host + (cur ^ 1) * S->o.max_resident;
+            int64_t done_sites = 0;
+            std::vector<Request*> failed_now;
+            for (size_t l = 0; l < P.res.size() && e == cudaSuccess; ++l) {
+                Request* R = P.res[l];
+                done_sites += (int64_t)R->L.nx * R->L.ny * P.quota[l];
+                if (!bits[l] || R->dropped) continue;
+                const int status = (bits[l] & 2u) ? LBM_ERR_TIMEOUT : LBM_ERR_NUMERIC;
+                R->status = status;
+                bool fin = false;
+                for (Finished& f : P.finished)
+                    if (f.R == R) {
+                        f.status = status;  // finishes (with the error) below
+                        fin = true;
+                    }
+                if (fin) continue;
+                // it went on into chunk n: fail it there
+                R->dropped = true;
+                Chunk& Cn = chunk[cur];
+                bool fin_n = false;
+                if (Cn.live)
+                    for (Finished& f : Cn.finished)
+                        if (f.R == R) {
+                            f.status = status;
+                            fin_n = true;
+                        }
+                if (fin_n) continue;
+                res.erase(std::remove(res.begin(), res.end(), R), res.end());
+                if (Cn.live)
+                    Cn.dropped.push_back(R);  // freed once chunk n is done
+                else
+                    failed_now.push_back(R);
+            }
+            for (Finished& f : P.finished) {
+                int status = f.status;
+                if (status == LBM_OK && e == cudaSuccess) {
+                    e = copy_out(S, S->set[cur ^ 1], *f.R, f.l, f.par);
+                    if (e != cudaSuccess) status = LBM_ERR_CUDA;
+                    launches += 2;
+                }
+                res_sites -= (int64_t)f.R->L.nx * f.R->L.ny;
+                finish(S, f.R, status);
+            }
+            for (Request* R : P.dropped) {
+                res_sites -= (int64_t)R->L.nx * R->L.ny;
+                finish(S, R, R->status);
+            }
+            for (Request* R : failed_now) {
+                res_sites -= (int64_t)R->L.nx * R->L.ny;
+                finish(S, R, R->status);
             }
             std::lock_guard<std::mutex> lk(S->mu);
-            f.R->status = status;
-            f.R->state = ST_DONE;
-            f.R->t_done = Clock::now();
-            S->alloc.release(f.R->pop_off, f.R->pop_bytes);
-            S->alloc.release(f.R->psi_off, f.R->psi_bytes);
-            if (status == LBM_OK) S->st.completed++;
-            else S->st.failed++;
-            S->st.arena_in_use = (int64_t)S->alloc.in_use();
+            S->st.site_steps += done_sites;
+            S->st.busy_s += std::chrono::duration<double>(Clock::now() - P.t0).count();
+            S->st.resident = (int)res.size();
+            P.live = false;
         }
-        pending.clear();
         {
             std::lock_guard<std::mutex> lk(S->mu);
             S->st.launches += launches;
         }
-        if (e == cudaSuccess && !res.empty()) e = cudaEventSynchronize(S->chunk_end);
         if (e != cudaSuccess) {
+            cudaStreamSynchronize(S->stream);
+            cudaStreamSynchronize(S->side);
             fail_all(S, LBM_ERR_CUDA);
             res.clear();
             res_sites = 0;
+            chunk[0] = Chunk{};
+            chunk[1] = Chunk{};
             continue;
         }
-        if (res.empty()) continue;
-        int64_t done_sites = 0;
-        std::vector<Request*> keep;
-        for (size_t l = 0; l < res.size(); ++l) {
-            Request* R = res[l];
-            R->remaining -= quota[l];
-            done_sites += (int64_t)R->L.nx * R->L.ny * quota[l];
-            const uint32_t bits = S->status_host[l];
-            if (R->remaining > 0 && !bits) {
-                keep.push_back(R);
-                continue;
-            }
-            int status = LBM_OK;
-            if (bits & 2u) status = LBM_ERR_TIMEOUT;
-            else if (bits) status = LBM_ERR_NUMERIC;
-            pending.push_back(Finished{R, (int)l, (p0 + quota[l]) & 1, status});
-            res_sites -= (int64_t)R->L.nx * R->L.ny;
-        }
-        pending_set = cur;
-        res.swap(keep);
-        ++chunk_no;
-        std::lock_guard<std::mutex> lk(S->mu);
-        S->st.site_steps += done_sites;
-        S->st.busy_s += std::chrono::duration<double>(Clock::now() - t0).count();
-        S->st.resident = (int)res.size();
-        S->st.arena_in_use = (int64_t)S->alloc.in_use();
     }
 }
 
@@ -471,6 +573,7 @@ void lbm_server_opts_default(lbm_server_opts* o) {
     o->storage = LBM_STORE_F32_DEV;
     o->eos_precision = LBM_EOS_DF;
     o->kernel_variant = LBM_KERNEL_AUTO;
+    o->with_velocity = 1;
 }
 
 int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
@@ -525,13 +628,21 @@ int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
             cudaSuccess ||
         cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&S->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&S->chunk_end, cudaEventDisableTiming) != cudaSuccess)
+        cudaStreamCreateWithFlags(&S->up, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S->chunk_end[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S->chunk_end[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S->up_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S->init_done, cudaEventDisableTiming) != cudaSuccess)
         return fail(LBM_ERR_CUDA);
     const size_t nmax = (size_t)o.max_request_sites;
+    // one turn admits at most the resident-site target plus one request
+    S->up_cap = (size_t)round_up(o.target_resident_sites, 32) + (size_t)round_up((int64_t)nmax, 32);
     bool ok = cudaMalloc(&S->arena, o.arena_bytes) == cudaSuccess &&
-              cudaMalloc(&S->staging, nmax * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&S->staging, S->up_cap * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost(&S->up_host, S->up_cap * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&S->outbuf, 3 * nmax * sizeof(double)) == cudaSuccess &&
-              cudaMallocHost(&S->status_host, (size_t)o.max_resident * sizeof(uint32_t)) ==
+              cudaMallocHost(&S->down_host, 3 * nmax * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost(&S->status_host, 2 * (size_t)o.max_resident * sizeof(uint32_t)) ==
                   cudaSuccess;
     for (auto& T : S->set)
         ok = ok && cudaMalloc(&T.lat, (size_t)o.max_resident * sizeof(LatDev)) == cudaSuccess &&
@@ -599,8 +710,16 @@ int lbm_poll(lbm_server* S, uint64_t ticket, double* rho, double* ux, double* uy
     if (status == LBM_OK) {
         const size_t n = R.rho.size();
         if (rho) std::memcpy(rho, R.rho.data(), n * sizeof(double));
-        if (ux) std::memcpy(ux, R.ux.data(), n * sizeof(double));
-        if (uy) std::memcpy(uy, R.uy.data(), n * sizeof(double));
+        // without with_velocity the server keeps no velocities: NaN
+        for (int c = 0; c < 2; ++c) {
+            double* dst = c ? uy : ux;
+            const std::vector<double>& src = c ? R.uy : R.ux;
+            if (!dst) continue;
+            if (src.size() == n)
+                std::memcpy(dst, src.data(), n * sizeof(double));
+            else
+                std::fill(dst, dst + n, std::numeric_limits<double>::quiet_NaN());
+        }
     }
     if (latency_s) *latency_s = std::chrono::duration<double>(R.t_done - R.t_submit).count();
     S->reqs.erase(it);
@@ -624,6 +743,7 @@ void lbm_server_destroy(lbm_server* S) {
     if (S->worker.joinable()) S->worker.join();
     cudaStreamSynchronize(S->stream);
     cudaStreamSynchronize(S->side);
+    cudaStreamSynchronize(S->up);
     free_server(S);
     delete S;
 }

@@ -113,3 +113,24 @@ def test_server_admission_capacity_and_failures(P):
     st = P.lbm_server_get_stats(srv)
     assert st["completed"] == 6 and st["failed"] == 1 and st["arena_in_use"] == 0
     P.lbm_server_destroy(srv)
+
+
+def test_rho_only_results_without_velocity(P):
+    # with_velocity = 0: results carry rho only (equal to the alone run); ux, uy are NaN
+    opts = P.lbm_server_opts_default(arena_bytes=1 << 28, chunk_steps=25, with_velocity=0,
+                                     kernel_variant=P.LBM_KERNEL_PLAIN, tile_x=TILE[0],
+                                     tile_y=TILE[1])
+    srv = P.lbm_server_create(opts)
+    specs = [(64, 48, 14.0, 0.8, 60), (90, 90, 25.0, 0.7, 110), (40, 72, 10.0, 0.75, 35)]
+    tickets, jobs = [], []
+    for nx, ny, R, T, n in specs:
+        d = P.lbm_desc_default(nx, ny, T=T)
+        rho = synth.droplet(nx, ny, R, T)
+        tickets.append(P.lbm_submit(srv, d, rho, n))
+        jobs.append((d, rho, n))
+    res = wait(P, srv, tickets)
+    P.lbm_server_destroy(srv)
+    for t, (d, rho, n) in zip(tickets, jobs):
+        a = alone(P, d, rho, n)
+        assert np.array_equal(res[t]["rho"], a["rho"])
+        assert np.isnan(res[t]["ux"]).all() and np.isnan(res[t]["uy"]).all()
