@@ -85,10 +85,15 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback (6.8 TB/s)"
 
 
+KERNEL_SOURCES = ("lbm_device.cuh", "lbm_async.cuh", "lbm_copy_plan.h", "lbm_layout.h",
+                  "lbm_kernels.h", "lbm_kernels.cu", "lbm_tma.cu", "lbm_fused_tma.cu")
+
+
 def kernel_source_hash():
+    """Hash of the files that define the step kernels (not the host runtime)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2003_07968_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]

@@ -288,23 +288,26 @@ cudaEvent_t take_event(lbm_handle* h) {
 // Launch the two passes of one step on parity p (state in buffer p, result
 // in buffer p^1).  Records events around each launch when profiling.
 int launch_step(lbm_handle* h, int p) {
+    const bool fused = h->schedule == LBM_SCHED_FUSED;
     cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
     if (h->prof) {
-        e0 = take_event(h);
         e1 = take_event(h);
         e2 = take_event(h);
-        CK(h, cudaEventRecord(e0, h->stream));
+        if (!fused) {
+            e0 = take_event(h);
+            CK(h, cudaEventRecord(e0, h->stream));
+        }
     }
-    if (h->schedule != LBM_SCHED_FUSED) CK(h, launch_pass(h, 0, step_args(h, p, 0), h->pass[0].grid));
+    if (!fused) CK(h, launch_pass(h, 0, step_args(h, p, 0), h->pass[0].grid));
     if (h->prof) CK(h, cudaEventRecord(e1, h->stream));
     CK(h, launch_pass(h, 1, step_args(h, p, 1), h->pass[1].grid));
     if (h->prof) {
         CK(h, cudaEventRecord(e2, h->stream));
-        h->rec[0].pending.emplace_back(e0, e1);
+        // the psi pair owns e0, the step pair owns e1 and e2
+        if (!fused) h->rec[0].pending.emplace_back(e0, e1);
         h->rec[1].pending.emplace_back(e1, e2);
-        // e1 is shared: keep it out of the pool until both pairs are read
     }
-    h->launches += h->schedule == LBM_SCHED_FUSED ? 1 : 2;
+    h->launches += fused ? 1 : 2;
     return LBM_OK;
 }
 
@@ -388,12 +391,12 @@ int ensure_staging(lbm_handle* h, size_t elems) {
 void release(lbm_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graph(h);
-    // kernel-0 pairs own (e0, e1); kernel-1 pairs share e1 and own e2
-    for (auto& pr : h->rec[0].pending) {
+    // psi pairs own e0; step pairs own (e1, e2)
+    for (auto& pr : h->rec[0].pending) cudaEventDestroy(pr.first);
+    for (auto& pr : h->rec[1].pending) {
         cudaEventDestroy(pr.first);
         cudaEventDestroy(pr.second);
     }
-    for (auto& pr : h->rec[1].pending) cudaEventDestroy(pr.second);
     h->rec[0].pending.clear();
     h->rec[1].pending.clear();
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -874,12 +877,12 @@ int lbm_profile_read(lbm_handle* h, lbm_kernel_stat* out, int32_t max, int32_t* 
             r.launches += 1;
         }
     }
-    // return events to the pool: kernel 0 pairs own (e0, e1), kernel 1 pairs own e2
-    for (auto& pr : h->rec[0].pending) {
+    // return events to the pool: psi pairs own e0, step pairs own (e1, e2)
+    for (auto& pr : h->rec[0].pending) h->ev_pool.push_back(pr.first);
+    for (auto& pr : h->rec[1].pending) {
         h->ev_pool.push_back(pr.first);
         h->ev_pool.push_back(pr.second);
     }
-    for (auto& pr : h->rec[1].pending) h->ev_pool.push_back(pr.second);
     h->rec[0].pending.clear();
     h->rec[1].pending.clear();
     const int cnt = 2;
