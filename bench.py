@@ -86,11 +86,11 @@ def measured_hbm_peak():
 
 
 KERNEL_SOURCES = ("lbm_device.cuh", "lbm_async.cuh", "lbm_copy_plan.h", "lbm_layout.h",
-                  "lbm_kernels.h", "lbm_kernels.cu", "lbm_tma.cu", "lbm_fused_tma.cu")
+                  "lbm_kernels.h", "lbm_fused_tma.cuh")
 
 
 def kernel_source_hash():
-    """Hash of the files that define the step kernels (not the host runtime)."""
+    """Hash of the files that define the single-pass step kernel (not the host runtime)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2003_07968_gb300", "csrc")
     for f in KERNEL_SOURCES:

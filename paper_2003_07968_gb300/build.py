@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libpplbm.so")
-SOURCES = ["lbm_kernels.cu", "lbm_tma.cu", "lbm_fused_tma.cu", "lbm_runtime.cu", "lbm_server.cu", "lbm_noalloc.cu"]
+SOURCES = ["lbm_kernels.cu", "lbm_tma.cu", "lbm_fused_tma.cu", "lbm_fused_tma_f32_bgk.cu", "lbm_fused_tma_f32_mrt.cu",
+           "lbm_fused_tma_f16_bgk.cu", "lbm_fused_tma_f16_mrt.cu", "lbm_runtime.cu", "lbm_server.cu", "lbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]

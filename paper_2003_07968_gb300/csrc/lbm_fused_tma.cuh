@@ -1,0 +1,430 @@
+// lbm_fused_tma.cuh -- the single-pass step with tiles staged by TMA bulk copies.
+//
+// Kernel and launch templates; the instances are compiled in four units
+// (lbm_fused_tma_{f32,f16}_{bgk,mrt}.cu) and dispatched by lbm_fused_tma.cu.
+//
+// One launch per step, persistent CTAs over the global tile list.  Per CTA:
+//   - one producer warp streams, for each of its tiles, the nine population
+//     planes into a ring of shared-memory stages with cp.async.bulk row
+//     copies (lbm_copy_plan.h, FusedGeo): per plane the TY + 2 rows the tile
+//     and its one-site ring pull from, already shifted by -c_iy, with 16
+//     bytes of halo columns on each side;
+//   - eight consumer warps (1, 2 or 4 sites per thread, site pairs on the
+//     paired FP32 instructions) compute, from shared memory, rho (Eq. FD)
+//     and psi (Eqs. DED, CSEOS) of their own sites, keeping the pulled
+//     populations in registers, and psi of the ring cells; they release the
+//     stage to the producer right after these reads, meet at one named
+//     barrier (psi tile complete), then run the force (Eq. IFT) and the
+//     collision (Eqs. BGKCO, GFSBGK, or MRTCO) and store f* with coalesced
+//     plain stores (plus the periodic images of edge sites).
+// Two ways to fill a stage: for a single lattice whose rows are at least a
+// box wide, one 3-D tensor copy per tile (cp.async.bulk.tensor over a tensor
+// map of both population buffers, passed as a __grid_constant__ parameter:
+// box = (TX + 2H) columns x (TY + 4) rows x 9 planes, rows y0 - 2 .. y0 + TY + 1
+// unshifted, parts outside the tensor zero-filled); otherwise (batches,
+// narrow lattices) one bulk row copy per plane and row as above.  One tensor
+// copy replaces 9 (TY + 2) row copies, whose issue cost is what limits the
+// row-copy form (measured about 32 SM cycles per copy on GB300).
+// The stage ring decouples DRAM latency from the arithmetic: the producer
+// runs up to STAGES tiles ahead, and the bytes in flight cost no registers.
+// The psi tile is double-buffered, so one barrier per tile suffices.
+//
+// Every mbarrier wait is bounded (lbm_async.cuh).  A consumer warp whose wait
+// runs out does not release its stage; the consumers agree on the failure at
+// the named barrier (an OR reduction) and all leave together, after raising
+// status bit 2 of the tile's lattice; the producer's own waits then run out,
+// it drains (bounded) the copies it issued and leaves.  No wait is unbounded
+// and no copy lands after its CTA has exited.
+#pragma once
+#include <cuda.h>
+
+#include <cstring>
+
+#include "lbm_async.cuh"
+#include "lbm_copy_plan.h"
+#include "lbm_kernels.h"
+
+namespace pplbm {
+namespace {
+
+constexpr int kConsumers = 256;             // eight consumer warps
+constexpr int kBlockF = kConsumers + 32;    // plus one producer warp
+constexpr int kStageBudget = 100 * 1024;    // bytes of stages per CTA (two CTAs per SM)
+
+template <class S, int TX, int TY, bool TMAP>
+struct FGeo : FusedGeo<(int)sizeof(typename S::T), TX, TY> {
+    using B = FusedGeo<(int)sizeof(typename S::T), TX, TY>;
+    static constexpr int ES = (int)sizeof(typename S::T);
+    static constexpr int SPT = TX * TY / kConsumers;  // sites per consumer thread
+    static constexpr int RPB = kConsumers / TX;       // tile rows per pass of the block
+    static constexpr int PW = TX + 2;                 // psi tile width (with the ring)
+    static constexpr int PSIB = align128(PW * (TY + 2) * 4);
+    // tensor box: rows y0 - 2 .. y0 + TY + 1 of all nine planes, dense
+    static constexpr int TROWS = TY + 4;
+    static constexpr int TBYTES = 9 * TROWS * B::BW * ES;
+    static constexpr int STAGEB = TMAP ? align128(TBYTES) : B::STAGEB;
+    static constexpr int BOXE = TMAP ? TROWS * B::BW : B::BOXB / ES;  // plane stride (elements)
+    static constexpr int STAGES = kStageBudget / STAGEB >= 4   ? 4
+                                  : kStageBudget / STAGEB >= 3 ? 3
+                                                               : 2;
+    static constexpr int BAR = STAGES * STAGEB + 2 * PSIB;  // mbarriers after stages + psi
+    // element offset, inside a stage, of the value that cell (lx, ly) of the
+    // tile (lx, ly in -1 .. TX, -1 .. TY) pulls from plane i
+    static __host__ __device__ constexpr int pull(int i, int lx, int ly) {
+        return TMAP ? i * BOXE + (ly + 2 - plane_cy(i)) * B::BW + lx + B::H - plane_cx(i)
+                    : i * BOXE + (ly + 1) * B::BW + lx + B::H - plane_cx(i);
+    }
+    static constexpr int SMEM = BAR + 2 * STAGES * 8 + 16;
+    static_assert(SPT == 1 || SPT == 2 || SPT == 4, "a tile holds 256, 512 or 1024 sites");
+    static_assert(TX % 32 == 0 && kConsumers % TX == 0, "tile width: 32, 64, 128 or 256");
+    static_assert(!TMAP || (B::BW <= 256 && TROWS <= 256), "tensor box dimensions");
+};
+
+// 3-D tensor copy global -> shared completing on *bar: box at element
+// coordinates (x, y, z) of the tensor map (x a multiple of 16 bytes).
+__device__ __forceinline__ void tensor_g2s(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                           uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+// 3-D tensor store shared -> global of a box at (x, y, z) (x a multiple of 16
+// bytes, all coordinates >= 0); parts outside the tensor are not written.
+__device__ __forceinline__ void tensor_s2g(const CUtensorMap* map, const void* src, int x, int y,
+                                           int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+__device__ __forceinline__ bool tile_skipped(const StepArgs& a, int t) {
+    return a.quota && a.step >= __ldg(&a.quota[__ldg(&a.tiles[t]).x]);
+}
+
+// Copies of one tile into `stage`, issued by the 32 lanes of the producer warp.
+template <class S, int TX, int TY>
+__device__ __forceinline__ void issue_fused(const StepArgs& a, int4 tl, unsigned char* stage,
+                                            uint64_t* bar) {
+    using G = FGeo<S, TX, TY, false>;
+    constexpr int ES = (int)sizeof(typename S::T);
+    constexpr int PER = (G::NCOPY + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    const LatDev& L = a.lats[tl.x];
+    CopyOp op[PER];
+    bool on[PER];
+    uint32_t bytes = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int q = lane + 32 * k;
+        on[k] = q < G::NCOPY && plan_copy_fused<ES, TX, TY>(L, a.parity, tl.y, tl.z, q, op[k]);
+        // the plan is proven on the host (lbm_selfcheck); a copy that still broke
+        // the bulk-copy rules would be skipped and flagged, never issued
+        if (on[k] && ((op[k].src | op[k].dst | op[k].bytes) & 15)) {
+            atomicOr(&a.status[tl.x], 4u);
+            on[k] = false;
+        }
+        if (on[k]) bytes += (uint32_t)op[k].bytes;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+    if (lane == 0) mbar_expect_tx(bar, bytes);
+    __syncwarp();
+    const char* pop = reinterpret_cast<const char*>(a.pop);
+#pragma unroll
+    for (int k = 0; k < PER; ++k)
+        if (on[k]) bulk_g2s(stage + op[k].dst, pop + op[k].src, (uint32_t)op[k].bytes, bar);
+}
+
+template <class S, int EOSP, int TX, int TY, bool MRT, bool TMAP>
+__global__ void __launch_bounds__(kBlockF, 2)
+    k_fused_tma(StepArgs a, const __grid_constant__ CUtensorMap tmap,
+                const __grid_constant__ CUtensorMap smap, const __grid_constant__ LatDev lat0) {
+    using G = FGeo<S, TX, TY, TMAP>;
+    using T = typename S::T;
+    using V = typename LaneOf<G::SPT>::V;
+    using Ln = Lanes<V>;
+    constexpr int NV = G::SPT / Ln::n;
+    constexpr int PW = G::PW;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + G::BAR);
+    uint64_t* empty = full + G::STAGES;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + G::STAGES);
+    float* psi_buf = reinterpret_cast<float*>(smem + G::STAGES * G::STAGEB);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < G::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            // row copies: each consumer warp releases a stage after reading it;
+            // tensor path: the consumer that stores the tile releases it once
+            // the tile store has read it
+            mbar_init(&empty[s], TMAP ? 1 : kConsumers / 32);
+        }
+        *abort_flag = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    if (warp == kConsumers / 32) {
+        // ------------------------------------------------------------ producer
+        int k = 0;
+        for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+            if (tile_skipped(a, t)) continue;
+            if (*abort_flag) break;
+            const int s = k % G::STAGES;
+            if (k >= G::STAGES) {
+                const bool ok = mbar_wait_bounded(&empty[s], (uint32_t)(k / G::STAGES - 1) & 1u);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    if (lane == 0) atomicOr(&a.status[__ldg(&a.tiles[t]).x], 2u);
+                    break;
+                }
+                // the consumers' generic-proxy reads of the stage come before the refill
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            }
+            if (TMAP) {
+                // one tensor copy: columns from x0 - H (element x0 of the row, a
+                // multiple of 32), rows from y0 - 2 (buffer row y0), planes of the
+                // current buffer
+                if (lane == 0) {
+                    const int4 tl = __ldg(&a.tiles[t]);
+                    mbar_expect_tx(&full[s], (uint32_t)G::TBYTES);
+                    tensor_g2s(smem + s * G::STAGEB, &tmap, tl.y, tl.z, 9 * a.parity, &full[s]);
+                }
+                __syncwarp();
+            } else {
+                issue_fused<S, TX, TY>(a, __ldg(&a.tiles[t]), smem + s * G::STAGEB, &full[s]);
+            }
+            ++k;
+        }
+        // drain: the last issue into each stage must have landed before exit
+        for (int j = (k > G::STAGES ? k - G::STAGES : 0); j < k; ++j)
+            mbar_wait_bounded(&full[j % G::STAGES], (uint32_t)(j / G::STAGES) & 1u);
+        return;
+    }
+
+    // ---------------------------------------------------------------- consumers
+    const int tid = threadIdx.x;  // 0 .. kConsumers-1
+    const int tx = tid % TX, ty0 = tid / TX;
+    constexpr int nhalf = TX + TY + 2;  // half of the 2 (TX + TY) + 4 ring cells
+    int k = 0;
+    int prev_s = -1;  // tensor path: stage of the tile whose store is in flight
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        if (tile_skipped(a, t)) continue;
+        const int s = k % G::STAGES;
+        const int4 tl = __ldg(&a.tiles[t]);
+        // one lattice: its constants are kernel parameters (constant-bank operands)
+        const LatDev& L = TMAP ? lat0 : a.lats[tl.x];
+        const int nx = L.nx, ny = L.ny, x0 = tl.y, y0 = tl.z;
+        const int xend = min(x0 + TX, nx), yend = min(y0 + TY, ny);
+        const int x = x0 + tx;
+        float* ps = psi_buf + (k & 1) * (G::PSIB / 4);
+        const bool ok = __all_sync(0xffffffffu,
+                                   mbar_wait_bounded(&full[s], (uint32_t)(k / G::STAGES) & 1u));
+        V g[NV][9];
+        V drho[NV];
+        if (ok) {
+            const T* st = reinterpret_cast<const T*>(smem + s * G::STAGEB);
+            // own sites: pulled populations into registers, rho, psi
+#pragma unroll
+            for (int kk = 0; kk < G::SPT; ++kk) {
+                const int ly = ty0 + kk * G::RPB;
+                const T* b = st + G::pull(0, tx, ly);  // the other planes at constant offsets
+                V* gk = g[kk / Ln::n];
+                const int l = kk % Ln::n;
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    Ln::put(gk[i], l, S::lds(b + (G::pull(i, 0, 0) - G::pull(0, 0, 0))));
+            }
+            const V rho0 = Ln::set(L.rho0);
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                unsigned live = 0;
+#pragma unroll
+                for (int l = 0; l < Ln::n; ++l)
+                    live |= (unsigned)(x < nx && y0 + ty0 + (j * Ln::n + l) * G::RPB < ny) << l;
+                drho[j] = sum9(g[j]);
+                const V psi = Eos<EOSP>::psi(L, vadd(drho[j], rho0), a.status, live);
+#pragma unroll
+                for (int l = 0; l < Ln::n; ++l)
+                    if ((live >> l) & 1u)
+                        ps[(ty0 + (j * Ln::n + l) * G::RPB + 1) * PW + tx + 1] = Ln::get(psi, l);
+            }
+            // the ring, cells r and r + nhalf in the two lanes of a float2
+            for (int r = tid; r < nhalf; r += kConsumers) {
+                int gx[2], gy[2];
+                unsigned live = 0;
+                float2 d;
+#pragma unroll
+                for (int l = 0; l < 2; ++l) {
+                    live |= (unsigned)ring_cell(r + l * nhalf, TX, TY, x0, y0, xend, yend, gx[l],
+                                                gy[l])
+                            << l;
+                    const T* b = st + G::pull(0, gx[l] - x0, gy[l] - y0);
+                    float v[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i)
+                        v[i] = S::lds(b + (G::pull(i, 0, 0) - G::pull(0, 0, 0)));
+                    Lanes<float2>::put(d, l, sum9(v));
+                }
+                const float2 psi =
+                    Eos<EOSP>::psi(L, vadd(d, Lanes<float2>::set(L.rho0)), a.status, live);
+                if (live & 1u) ps[(gy[0] - y0 + 1) * PW + (gx[0] - x0 + 1)] = psi.x;
+                if (live & 2u) ps[(gy[1] - y0 + 1) * PW + (gx[1] - x0 + 1)] = psi.y;
+            }
+            // row copies: every read of the stage is done, hand it back
+            if (!TMAP) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+            }
+        }
+        // psi tile complete; a warp whose wait ran out makes every consumer leave
+        uint32_t failed;
+        asm volatile(
+            "{\n\t.reg .pred p, q;\n\tsetp.eq.u32 p, %1, 0;\n\t"
+            "bar.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+            : "=r"(failed)
+            : "r"((uint32_t)ok), "n"(kConsumers)
+            : "memory");
+        if (failed) {
+            if (tid == 0) {
+                *abort_flag = 1;
+                atomicOr(&a.status[tl.x], 2u);
+                if (TMAP) bulk_wait_all();  // tile stores already issued complete on their own
+            }
+            return;
+        }
+        ++k;
+        if (!TMAP && x >= nx) continue;
+        // force, collision, stores
+        const SiteConsts C = site_consts(L);
+        T* o = reinterpret_cast<T*>(a.pop) + L.off_f[a.parity ^ 1];
+        const bool tile_in = x0 >= GW && y0 >= GW && x0 + TX <= nx - GW && y0 + TY <= ny - GW;
+        // tensor path, tiles inside the lattice: f* of the tile goes to the
+        // stage just consumed, laid out as the store box [plane][TY][TX], and
+        // leaves in one tensor store.  A ragged edge tile uses plain stores:
+        // the store unit clips a box at 16-byte granularity in x (measured), so
+        // a partial box would also write the ghost columns just past nx.
+        const bool bulk_out = TMAP && x0 + TX <= nx && y0 + TY <= ny;
+        T* out = reinterpret_cast<T*>(smem + s * G::STAGEB);
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            V p[9], v[9];
+#pragma unroll
+            for (int l = 0; l < Ln::n; ++l) {
+                const float* c = ps + (ty0 + (j * Ln::n + l) * G::RPB + 1) * PW + (tx + 1);
+                Ln::put(p[0], l, c[0]);
+                Ln::put(p[1], l, c[1]);
+                Ln::put(p[2], l, c[PW]);
+                Ln::put(p[3], l, c[-1]);
+                Ln::put(p[4], l, c[-PW]);
+                Ln::put(p[5], l, c[PW + 1]);
+                Ln::put(p[6], l, c[PW - 1]);
+                Ln::put(p[7], l, c[-PW - 1]);
+                Ln::put(p[8], l, c[-PW + 1]);
+            }
+            collide<MRT>(C, L.mrt_s, drho[j], g[j], p, v);
+#pragma unroll
+            for (int l = 0; l < Ln::n; ++l) {
+                const int ly = ty0 + (j * Ln::n + l) * G::RPB;
+                const int y = y0 + ly;
+                if (bulk_out) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) out[(i * TY + ly) * TX + tx] = S::cv(Ln::get(v[i], l));
+                    if (!tile_in)
+#pragma unroll
+                        for (int i = 0; i < 9; ++i)
+                            store_images(o + i * L.plane, L.pitch, L.gx, x, y, nx, ny,
+                                         S::cv(Ln::get(v[i], l)));
+                } else {
+                    if (x >= nx || y >= ny) continue;
+                    float vs[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) vs[i] = Ln::get(v[i], l);
+                    store_site<S>(o, L.plane, L.pitch, L.gx, x, y, nx, ny, vs, tile_in);
+                }
+            }
+        }
+        if (TMAP) {
+            // the tile's f* in shared memory -> one tensor store; a stage goes
+            // back to the producer once the store of its tile has read it
+            if (bulk_out) fence_proxy_async_smem();
+            named_sync(2, kConsumers);
+            if (tid == 0) {
+                if (bulk_out) {
+                    tensor_s2g(&smap, smem + s * G::STAGEB, x0 + L.gx, y0 + GY,
+                               9 * (a.parity ^ 1));
+                    bulk_commit();
+                    if (prev_s >= 0) {
+                        bulk_wait_read<1>();
+                        mbar_arrive(&empty[prev_s]);
+                    }
+                } else {
+                    // no store reads this stage: release it, and the previous one
+                    bulk_wait_read<0>();
+                    if (prev_s >= 0) mbar_arrive(&empty[prev_s]);
+                    mbar_arrive(&empty[s]);
+                }
+            }
+            prev_s = bulk_out ? s : -1;
+        }
+    }
+    if (TMAP && tid == 0) {
+        bulk_wait_all();
+        if (prev_s >= 0) mbar_arrive(&empty[prev_s]);
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+template <class S, int EOSP, int TX, int TY, bool MRT, bool TMAP>
+cudaError_t fused_inst(const StepArgs& a, const CUtensorMap* map, const LatDev* lat0, int grid,
+                       cudaStream_t st, bool query, int* occ) {
+    // map[0]: load map, map[1]: store map (tensor path)
+    using G = FGeo<S, TX, TY, TMAP>;
+    const void* fn = (const void*)k_fused_tma<S, EOSP, TX, TY, MRT, TMAP>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    if (e != cudaSuccess) return e;
+    if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fn, kBlockF, G::SMEM);
+    CUtensorMap none;
+    std::memset(&none, 0, sizeof none);
+    const LatDev nolat{};
+    k_fused_tma<S, EOSP, TX, TY, MRT, TMAP><<<grid, dim3(kBlockF), G::SMEM, st>>>(
+        a, map ? map[0] : none, map ? map[1] : none, lat0 ? *lat0 : nolat);
+    return cudaGetLastError();
+}
+
+template <class S, bool MRT, int TX, int TY, bool TMAP>
+cudaError_t fused_eos(int eos, const StepArgs& a, const CUtensorMap* map, const LatDev* lat0,
+                      int grid, cudaStream_t st, bool q, int* occ) {
+    switch (eos) {
+        case EOS_F64: return fused_inst<S, EOS_F64, TX, TY, MRT, TMAP>(a, map, lat0, grid, st, q, occ);
+        case EOS_DF: return fused_inst<S, EOS_DF, TX, TY, MRT, TMAP>(a, map, lat0, grid, st, q, occ);
+        default: return fused_inst<S, EOS_F32, TX, TY, MRT, TMAP>(a, map, lat0, grid, st, q, occ);
+    }
+}
+
+template <class S, bool MRT, int TX, int TY>
+cudaError_t fused_map(int eos, const StepArgs& a, const CUtensorMap* map, const LatDev* lat0,
+                      int grid, cudaStream_t st, bool q, int* occ) {
+    return map ? fused_eos<S, MRT, TX, TY, true>(eos, a, map, lat0, grid, st, q, occ)
+               : fused_eos<S, MRT, TX, TY, false>(eos, a, nullptr, nullptr, grid, st, q, occ);
+}
+
+}  // namespace
+
+// One storage type and collision: every tile shape, EOS arithmetic and
+// staging form (the body of the four instance units).
+template <class S, bool MRT>
+cudaError_t fused_tma_any(int tx, int ty, int eos, const StepArgs& a, const CUtensorMap* map,
+                          const LatDev* lat0, int grid, cudaStream_t st, bool q, int* occ) {
+    if (tx == 64 && ty == 8) return fused_map<S, MRT, 64, 8>(eos, a, map, lat0, grid, st, q, occ);
+    if (tx == 32 && ty == 16) return fused_map<S, MRT, 32, 16>(eos, a, map, lat0, grid, st, q, occ);
+    if (tx == 64 && ty == 16) return fused_map<S, MRT, 64, 16>(eos, a, map, lat0, grid, st, q, occ);
+    if (tx == 128 && ty == 8) return fused_map<S, MRT, 128, 8>(eos, a, map, lat0, grid, st, q, occ);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace pplbm

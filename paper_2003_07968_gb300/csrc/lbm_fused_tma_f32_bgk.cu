@@ -1,0 +1,12 @@
+// lbm_fused_tma_f32_bgk.cu -- instances of the single-pass TMA step:
+// FP32 storage, BGK collision.
+#include "lbm_fused_tma.cuh"
+
+namespace pplbm {
+
+cudaError_t fused_tma_f32_bgk(int tx, int ty, int eos, const StepArgs& a, const CUtensorMap* map,
+                             const LatDev* lat0, int grid, cudaStream_t st, bool q, int* occ) {
+    return fused_tma_any<StoreF32, false>(tx, ty, eos, a, map, lat0, grid, st, q, occ);
+}
+
+}  // namespace pplbm
