@@ -72,6 +72,8 @@ struct LatDev {
     float rho0;         // deviation reference (0 for plain FP32 storage)
     int32_t m2_variant; // 0: direct trace; 1: 2 c_s^2 (M0 - psi)
     int32_t lattice;    // index for the status word
+    int32_t row0;       // row of the arena's row space where this lattice's ghost
+                        // row -GY starts (off_f[0] = row0 * pitch), or -1
     // psi(rho)^2 = (P_EOS - c_s^2 rho)/G = rho (e1 q(rho) - e2 rho - e3),
     // q = (1 + eta + eta^2 - eta^3)/(1 - eta)^3, eta = b rho      Eqs. (DED), (CSEOS)
     double eb, e1, e2, e3;

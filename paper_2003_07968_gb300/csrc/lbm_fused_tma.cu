@@ -55,34 +55,48 @@ bool fused_tma_shape_supported(int tx, int ty) {
            (tx == 128 && ty == 8);
 }
 
-bool fused_tma_make_map(int f16, int tx, int ty, const LatDev& L, void* pop, CUtensorMap* map) {
+bool fused_tma_make_map(int f16, int tx, int ty, const LatDev* lats, int n, void* pop,
+                        CUtensorMap map[2]) {
+    if (n < 1 || !fused_tma_shape_supported(tx, ty)) return false;
     const int es = f16 ? 2 : 4, h = 16 / es, bw = tx + 2 * h;
+    const LatDev& L = lats[0];
+    // one lattice, or a batch in one row space (common pitch and planes,
+    // off_f[0] = row0 * pitch, buffer B nine planes after A)
+    int64_t rows = 0;
+    for (int i = 0; i < n; ++i) {
+        const LatDev& M = lats[i];
+        if (M.row0 != (int32_t)rows || M.pitch != L.pitch || M.plane != L.plane ||
+            M.off_f[0] != (int64_t)M.row0 * M.pitch || M.off_f[1] != M.off_f[0] + 9 * M.plane)
+            return false;
+        rows += M.ny + 2 * GY;
+    }
     // every box must lie inside its tensor: rows at least a box wide and
     // enough rows; the row and plane strides are multiples of 16 bytes
-    if (!fused_tma_shape_supported(tx, ty) || L.pitch < bw || L.ny + 2 * GY < ty + 4 ||
-        L.gx + L.nx < tx || GY + L.ny < ty)
+    if (L.pitch < bw || rows < ty + 4 || (n == 1 && (L.gx + L.nx < tx || GY + L.ny < ty)))
         return false;
-    if ((L.pitch * es) % 16 || (L.plane * es) % 16) return false;
-    char* base = reinterpret_cast<char*>(pop) + L.off_f[0] * es;
-    if (reinterpret_cast<uintptr_t>(base) % 16 || L.off_f[1] != L.off_f[0] + 9 * L.plane)
+    if ((L.pitch * es) % 16 || (L.plane * es) % 16 || (int64_t)L.pitch * rows > L.plane)
         return false;
+    char* base = reinterpret_cast<char*>(pop);
+    if (reinterpret_cast<uintptr_t>(base) % 16) return false;
     EncodeTiled enc = encode_fn();
     if (!enc) return false;
     const CUtensorMapDataType dt = f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * es, (cuuint64_t)L.plane * es};
     const cuuint32_t estr[3] = {1, 1, 1};
-    // loads: both population buffers as 18 planes of whole rows, ghost frame
-    // included: x (row elements), y (rows), z (plane)
-    const cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)(L.ny + 2 * GY), 18};
+    // loads: both population buffers as 18 planes of whole rows, ghost frames
+    // included: x (row elements), y (rows of the row space), z (plane)
+    const cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)rows, 18};
     const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)(ty + 4), 9};
     if (enc(&map[0], dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
-    // stores: the same planes, clipped after the last interior column and row
-    // (x < gx + nx, y < GY + ny), so a ragged tile writes no ghost or pad
-    // element; boxes of one tile
-    const cuuint64_t sdims[3] = {(cuuint64_t)(L.gx + L.nx), (cuuint64_t)(GY + L.ny), 18};
+    // stores, boxes of one tile: one lattice, clipped after its last interior
+    // column and row (x < gx + nx, y < GY + ny); a batch, the whole row space
+    // (only tiles inside their lattice are stored this way)
+    const cuuint64_t sdims[3] = {
+        n == 1 ? (cuuint64_t)(L.gx + L.nx) : (cuuint64_t)L.pitch,
+        n == 1 ? (cuuint64_t)(GY + L.ny) : (cuuint64_t)rows, 18};
     const cuuint32_t sbox[3] = {(cuuint32_t)tx, (cuuint32_t)ty, 9};
     return enc(&map[1], dt, 3, base, sdims, strides, sbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
@@ -96,14 +110,15 @@ cudaError_t launch_fused_tma(int f16, int mrt, int eos, int tx, int ty, const St
     return fused_any(f16, mrt, tx, ty, eos, a, map, lat0, grid, st, false, &occ);
 }
 
-int occupancy_fused_tma(int f16, int mrt, int eos, int tx, int ty, bool with_map) {
+int occupancy_fused_tma(int f16, int mrt, int eos, int tx, int ty, bool with_map, bool single) {
     int occ = 0;
     StepArgs a{};
     CUtensorMap m[2];
     std::memset(m, 0, sizeof m);
     const CUtensorMap* mp = with_map ? m : nullptr;
     const LatDev lat{};
-    cudaError_t e = fused_any(f16, mrt, tx, ty, eos, a, mp, &lat, 0, nullptr, true, &occ);
+    cudaError_t e =
+        fused_any(f16, mrt, tx, ty, eos, a, mp, single ? &lat : nullptr, 0, nullptr, true, &occ);
     return (e == cudaSuccess && occ > 0) ? occ : 1;
 }
 

@@ -140,10 +140,14 @@ __device__ __forceinline__ void issue_fused(const StepArgs& a, int4 tl, unsigned
         if (on[k]) bulk_g2s(stage + op[k].dst, pop + op[k].src, (uint32_t)op[k].bytes, bar);
 }
 
-template <class S, int EOSP, int TX, int TY, bool MRT, bool TMAP>
+// MODE 0: row copies, lattice constants from a.lats; 1: tensor copies, one
+// lattice whose constants are the parameter lat0; 2: tensor copies, a batch
+// in one row space, constants from a.lats.
+template <class S, int EOSP, int TX, int TY, bool MRT, int MODE>
 __global__ void __launch_bounds__(kBlockF, 2)
     k_fused_tma(StepArgs a, const __grid_constant__ CUtensorMap tmap,
                 const __grid_constant__ CUtensorMap smap, const __grid_constant__ LatDev lat0) {
+    constexpr bool TMAP = MODE != 0;
     using G = FGeo<S, TX, TY, TMAP>;
     using T = typename S::T;
     using V = typename LaneOf<G::SPT>::V;
@@ -187,12 +191,14 @@ __global__ void __launch_bounds__(kBlockF, 2)
             }
             if (TMAP) {
                 // one tensor copy: columns from x0 - H (element x0 of the row, a
-                // multiple of 32), rows from y0 - 2 (buffer row y0), planes of the
-                // current buffer
+                // multiple of 32), rows from y0 - 2 (row row0 + y0 of the row
+                // space), planes of the current buffer
                 if (lane == 0) {
                     const int4 tl = __ldg(&a.tiles[t]);
+                    const int row0 = MODE == 1 ? lat0.row0 : a.lats[tl.x].row0;
                     mbar_expect_tx(&full[s], (uint32_t)G::TBYTES);
-                    tensor_g2s(smem + s * G::STAGEB, &tmap, tl.y, tl.z, 9 * a.parity, &full[s]);
+                    tensor_g2s(smem + s * G::STAGEB, &tmap, tl.y, row0 + tl.z, 9 * a.parity,
+                               &full[s]);
                 }
                 __syncwarp();
             } else {
@@ -217,7 +223,7 @@ __global__ void __launch_bounds__(kBlockF, 2)
         const int s = k % G::STAGES;
         const int4 tl = __ldg(&a.tiles[t]);
         // one lattice: its constants are kernel parameters (constant-bank operands)
-        const LatDev& L = TMAP ? lat0 : a.lats[tl.x];
+        const LatDev& L = MODE == 1 ? lat0 : a.lats[tl.x];
         const int nx = L.nx, ny = L.ny, x0 = tl.y, y0 = tl.z;
         const int xend = min(x0 + TX, nx), yend = min(y0 + TY, ny);
         const int x = x0 + tx;
@@ -355,7 +361,7 @@ __global__ void __launch_bounds__(kBlockF, 2)
             named_sync(2, kConsumers);
             if (tid == 0) {
                 if (bulk_out) {
-                    tensor_s2g(&smap, smem + s * G::STAGEB, x0 + L.gx, y0 + GY,
+                    tensor_s2g(&smap, smem + s * G::STAGEB, x0 + L.gx, L.row0 + y0 + GY,
                                9 * (a.parity ^ 1));
                     bulk_commit();
                     if (prev_s >= 0) {
@@ -379,38 +385,40 @@ __global__ void __launch_bounds__(kBlockF, 2)
 }
 
 // ---------------------------------------------------------------- launchers
-template <class S, int EOSP, int TX, int TY, bool MRT, bool TMAP>
+template <class S, int EOSP, int TX, int TY, bool MRT, int MODE>
 cudaError_t fused_inst(const StepArgs& a, const CUtensorMap* map, const LatDev* lat0, int grid,
                        cudaStream_t st, bool query, int* occ) {
     // map[0]: load map, map[1]: store map (tensor path)
-    using G = FGeo<S, TX, TY, TMAP>;
-    const void* fn = (const void*)k_fused_tma<S, EOSP, TX, TY, MRT, TMAP>;
+    using G = FGeo<S, TX, TY, MODE != 0>;
+    const void* fn = (const void*)k_fused_tma<S, EOSP, TX, TY, MRT, MODE>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
     if (e != cudaSuccess) return e;
     if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fn, kBlockF, G::SMEM);
     CUtensorMap none;
     std::memset(&none, 0, sizeof none);
     const LatDev nolat{};
-    k_fused_tma<S, EOSP, TX, TY, MRT, TMAP><<<grid, dim3(kBlockF), G::SMEM, st>>>(
+    k_fused_tma<S, EOSP, TX, TY, MRT, MODE><<<grid, dim3(kBlockF), G::SMEM, st>>>(
         a, map ? map[0] : none, map ? map[1] : none, lat0 ? *lat0 : nolat);
     return cudaGetLastError();
 }
 
-template <class S, bool MRT, int TX, int TY, bool TMAP>
+template <class S, bool MRT, int TX, int TY, int MODE>
 cudaError_t fused_eos(int eos, const StepArgs& a, const CUtensorMap* map, const LatDev* lat0,
                       int grid, cudaStream_t st, bool q, int* occ) {
     switch (eos) {
-        case EOS_F64: return fused_inst<S, EOS_F64, TX, TY, MRT, TMAP>(a, map, lat0, grid, st, q, occ);
-        case EOS_DF: return fused_inst<S, EOS_DF, TX, TY, MRT, TMAP>(a, map, lat0, grid, st, q, occ);
-        default: return fused_inst<S, EOS_F32, TX, TY, MRT, TMAP>(a, map, lat0, grid, st, q, occ);
+        case EOS_F64: return fused_inst<S, EOS_F64, TX, TY, MRT, MODE>(a, map, lat0, grid, st, q, occ);
+        case EOS_DF: return fused_inst<S, EOS_DF, TX, TY, MRT, MODE>(a, map, lat0, grid, st, q, occ);
+        default: return fused_inst<S, EOS_F32, TX, TY, MRT, MODE>(a, map, lat0, grid, st, q, occ);
     }
 }
 
 template <class S, bool MRT, int TX, int TY>
 cudaError_t fused_map(int eos, const StepArgs& a, const CUtensorMap* map, const LatDev* lat0,
                       int grid, cudaStream_t st, bool q, int* occ) {
-    return map ? fused_eos<S, MRT, TX, TY, true>(eos, a, map, lat0, grid, st, q, occ)
-               : fused_eos<S, MRT, TX, TY, false>(eos, a, nullptr, nullptr, grid, st, q, occ);
+    // tensor maps with lat0: one lattice; tensor maps alone: a batch in one row space
+    return !map ? fused_eos<S, MRT, TX, TY, 0>(eos, a, nullptr, nullptr, grid, st, q, occ)
+           : lat0 ? fused_eos<S, MRT, TX, TY, 1>(eos, a, map, lat0, grid, st, q, occ)
+                  : fused_eos<S, MRT, TX, TY, 2>(eos, a, map, nullptr, grid, st, q, occ);
 }
 
 }  // namespace

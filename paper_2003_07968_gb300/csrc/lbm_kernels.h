@@ -37,15 +37,17 @@ cudaError_t launch_fused(int storage_f16, int mrt, int eos, int spt, const StepA
 int occupancy_fused(int storage_f16, int mrt, int eos, int spt, int threads, size_t smem);
 // Single-pass step with TMA-staged tiles (lbm_fused_tma.cu): 288 threads
 // (eight consumer warps and a producer warp), persistent over the tile list.
-// With tensor maps (fused_tma_make_map: single lattice, rows at least a box
-// wide; map[0] loads, map[1] stores) each tile is one 3-D tensor copy in and
-// one out, and the lattice's constants travel by value (lat0); without,
-// bulk row copies in, plain stores out, and a.lats.
+// With tensor maps (fused_tma_make_map: one lattice, or a batch in one row
+// space (row_space_layout), rows at least a box wide; map[0] loads, map[1]
+// stores) each tile is one 3-D tensor copy in and, inside its lattice, one
+// out; one lattice's constants travel by value (lat0), a batch's come from
+// a.lats (lat0 null).  Without maps: bulk row copies in, plain stores out.
 bool fused_tma_shape_supported(int tx, int ty);
-bool fused_tma_make_map(int f16, int tx, int ty, const LatDev& L, void* pop, CUtensorMap map[2]);
+bool fused_tma_make_map(int f16, int tx, int ty, const LatDev* lats, int n, void* pop,
+                        CUtensorMap map[2]);
 cudaError_t launch_fused_tma(int f16, int mrt, int eos, int tx, int ty, const StepArgs& a,
                              const CUtensorMap* map, const LatDev* lat0, int grid,
                              cudaStream_t st);
-int occupancy_fused_tma(int f16, int mrt, int eos, int tx, int ty, bool with_map);
+int occupancy_fused_tma(int f16, int mrt, int eos, int tx, int ty, bool with_map, bool single);
 
 }  // namespace pplbm

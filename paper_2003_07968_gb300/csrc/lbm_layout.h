@@ -3,6 +3,7 @@
 #pragma once
 #include <cmath>
 #include <string>
+#include <vector>
 
 #include "../../include/pplbm.h"
 #include "lbm_device.cuh"
@@ -59,6 +60,7 @@ inline LatDev lat_layout(const lbm_lattice_desc& d, int index) {
     L.rho0 = (d.storage == LBM_STORE_F32 || d.rho0 < 0.0) ? 0.f : (float)d.rho0;
     L.m2_variant = d.m2_trace_variant;
     L.lattice = index;
+    L.row0 = -1;
     // psi^2 = rho (e1 q - e2 rho - e3): e1 = k c T / G, e2 = k a / G, e3 = 1/(3G)
     L.eb = d.eos_b;
     L.e1 = d.eos_k * d.eos_c * d.T / d.G;
@@ -119,6 +121,35 @@ inline float auto_rho0(const double* rho, size_t n) {
     double m = rho[0];
     for (size_t i = 1; i < n; ++i) m = m < rho[i] ? m : rho[i];
     return (float)(m > 0.0 ? m : 0.0);
+}
+
+// Row-space layout of a batch: every lattice with the same pitch P (the
+// widest lattice's) and its nx + 2 GY rows stacked, lattice after lattice,
+// inside each of the 18 planes (buffer A's nine, then B's), so that one 3-D
+// tensor map (x: P, y: all rows, z: 18 planes) covers every lattice.  Sets
+// pitch, plane, off_f and row0 of each lattice and returns the population
+// elements of the arena; returns -1 (and changes nothing) when the common
+// pitch would cost more than `max_waste` times the compact layout's memory.
+inline int64_t row_space_layout(std::vector<LatDev>& lats, int es, double max_waste) {
+    int P = 0;
+    int64_t rows = 0, compact = 0;
+    for (const LatDev& L : lats) {
+        P = P > L.pitch ? P : L.pitch;
+        rows += L.ny + 2 * GY;
+        compact += 18 * L.plane;
+    }
+    const int64_t plane = round_up((int64_t)P * rows, 256 / es);
+    if ((double)(18 * plane) > max_waste * (double)compact) return -1;
+    int64_t r = 0;
+    for (LatDev& L : lats) {
+        L.pitch = P;
+        L.plane = plane;
+        L.row0 = (int32_t)r;
+        L.off_f[0] = r * P;
+        L.off_f[1] = L.off_f[0] + 9 * plane;
+        r += L.ny + 2 * GY;
+    }
+    return 18 * plane;
 }
 
 // Elements of the two population buffers (A then B, nine planes each).

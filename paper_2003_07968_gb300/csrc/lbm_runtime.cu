@@ -101,8 +101,9 @@ struct lbm_handle {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by starting parity
     int graph_steps = 32;
     int tune_variant = LBM_KERNEL_AUTO;  // the kernel_variant the handle was created with
-    // tensor map of the population buffers for the single-pass TMA kernel
-    // (single lattice, rows at least a box wide); else that kernel uses row copies
+    // tensor maps (loads, stores) of the population arena for the single-pass
+    // TMA kernel (one lattice, or a batch in one row space; rows at least a box
+    // wide); else that kernel uses row copies
     CUtensorMap tmap[2]{};  // loads, stores
     bool has_tmap = false;
     // profiling
@@ -174,8 +175,8 @@ int build_tiles(lbm_handle* h, int k, int tx, int ty) {
     Pass& P = h->pass[k];
     if (k == 1)
         h->has_tmap = h->schedule == LBM_SCHED_FUSED && P.variant == LBM_KERNEL_TMA &&
-                      h->lat.size() == 1 &&
-                      fused_tma_make_map(h->f16, tx, ty, h->lat[0], h->pop, h->tmap);
+                      fused_tma_make_map(h->f16, tx, ty, h->lat.data(), (int)h->lat.size(),
+                                         h->pop, h->tmap);
     std::vector<int4> t;
     P.begin.assign(h->lat.size(), 0);
     P.count.assign(h->lat.size(), 0);
@@ -219,7 +220,7 @@ void default_grid(lbm_handle* h, int k) {
     int occ;
     if (P.variant == LBM_KERNEL_TMA && k == 1 && h->schedule == LBM_SCHED_FUSED)
         occ = occupancy_fused_tma(h->f16, h->collision == LBM_COLL_MRT, h->eos, P.tx, P.ty,
-                                  h->has_tmap);
+                                  h->has_tmap, h->lat.size() == 1);
     else if (P.variant == LBM_KERNEL_TMA)
         occ = k == 0 ? occupancy_psi_tma(h->f16, h->eos, P.tx, P.ty)
                      : occupancy_collide_tma(h->f16, P.tx, P.ty);
@@ -264,7 +265,8 @@ cudaError_t launch_pass(lbm_handle* h, int k, const StepArgs& a, int grid) {
                    : launch_psi(h->f16, h->eos, P.spt, a, dim3(grid), block, h->stream);
     if (h->schedule == LBM_SCHED_FUSED && P.variant == LBM_KERNEL_TMA)
         return launch_fused_tma(h->f16, h->collision == LBM_COLL_MRT, h->eos, P.tx, P.ty, a,
-                                h->has_tmap ? h->tmap : nullptr, &h->lat[0], grid, h->stream);
+                                h->has_tmap ? h->tmap : nullptr,
+                                h->lat.size() == 1 ? &h->lat[0] : nullptr, grid, h->stream);
     if (h->schedule == LBM_SCHED_FUSED)
         return launch_fused(h->f16, h->collision == LBM_COLL_MRT, h->eos, P.spt, a, dim3(grid), block, collide_smem(P.tx, P.ty),
                             h->stream);
@@ -681,6 +683,14 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
         h->sites += (int64_t)descs[i].nx * descs[i].ny;
     }
     const size_t es = h->f16 ? 2 : 4;
+    if (n == 1) {
+        h->lat[0].row0 = 0;  // the lattice is the whole row space
+    } else {
+        // a batch in one row space (one tensor map for all lattices) unless the
+        // common pitch costs more than 2.5x the memory of the compact layout
+        const int64_t rs = row_space_layout(h->lat, (int)es, 2.5);
+        if (rs > 0) pc = rs;
+    }
     h->pop_bytes = (size_t)pc * es;
     h->psi_bytes = (size_t)qc * sizeof(float);
     h->pop = dev_alloc(h, h->pop_bytes);

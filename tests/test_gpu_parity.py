@@ -503,20 +503,35 @@ def test_fused_tma_equals_plain_fused_bitwise(P, tile):
     rec = synth.batch_recipe(n=4, side=(37, 150))
     descs = [P.lbm_desc_default(r["nx"], r["ny"], T=r["T"]) for r in rec]
     fields = [synth.droplet(r["nx"], r["ny"], r["R"], r["T"]) for r in rec]
-    outs = []
-    for variant, sp in ((P.LBM_KERNEL_PLAIN, 2), (P.LBM_KERNEL_TMA, 0)):
-        h = P.lbm_create(descs, schedule=P.LBM_SCHED_FUSED, kernel_variant=variant, tile=tile,
-                         sites_per_thread=sp if variant == P.LBM_KERNEL_PLAIN else 0)
-        assert P.lbm_info(h)["collide_variant"] == variant
-        for i, f in enumerate(fields):
-            P.lbm_init(h, i, f)
-        P.lbm_step(h, 150)
-        outs.append([P.lbm_moments(h, i, mass=False) for i in range(len(descs))])
-        P.lbm_destroy(h)
-    for a, b in zip(*outs):
-        assert np.array_equal(a["rho"], b["rho"]) and np.array_equal(a["ux"], b["ux"])
+    # a batch of similar widths shares one row space (one tensor map); a
+    # lopsided batch keeps the compact layout (bulk row copies)
+    lop = [(600, 40), (40, 600), (64, 64)]
+    cases = [(descs, fields, 1),
+             ([P.lbm_desc_default(nx, ny, T=0.7) for nx, ny in lop],
+              [synth.droplet(nx, ny, min(nx, ny) / 3.0, 0.7) for nx, ny in lop], 0)]
+    for dd, ff, tensor in cases:
+        outs = []
+        for variant, sp in ((P.LBM_KERNEL_PLAIN, 2), (P.LBM_KERNEL_TMA, 0)):
+            h = P.lbm_create(dd, schedule=P.LBM_SCHED_FUSED, kernel_variant=variant, tile=tile,
+                             sites_per_thread=sp if variant == P.LBM_KERNEL_PLAIN else 0)
+            info = P.lbm_info(h)
+            assert info["collide_variant"] == variant
+            if variant == P.LBM_KERNEL_TMA:
+                assert info["tensor_map"] == tensor
+            for i, f in enumerate(ff):
+                P.lbm_init(h, i, f)
+            P.lbm_step(h, 150)
+            outs.append([P.lbm_moments(h, i, mass=False) for i in range(len(dd))])
+            P.lbm_destroy(h)
+        for a, b in zip(*outs):
+            assert np.array_equal(a["rho"], b["rho"]) and np.array_equal(a["ux"], b["ux"])
     o = oracle_run(fields[0], 150, T=rec[0]["T"])
-    assert rel(outs[1][0]["rho"], o["rho"]) <= RTOL_RHO
+    h = P.lbm_create(descs, schedule=P.LBM_SCHED_FUSED, kernel_variant=P.LBM_KERNEL_TMA, tile=tile)
+    for i, f in enumerate(fields):
+        P.lbm_init(h, i, f)
+    P.lbm_step(h, 150)
+    assert rel(P.lbm_moments(h, 0, mass=False)["rho"], o["rho"]) <= RTOL_RHO
+    P.lbm_destroy(h)
     # a single ragged lattice takes the tensor-map path (one 3-D copy per tile)
     nx, ny = 203, 77
     rho = synth.droplet(nx, ny, 25.0, 0.7)
