@@ -70,7 +70,11 @@ extern "C" {
 
 /* ---- kernel variant ------------------------------------------------------ */
 #define LBM_KERNEL_AUTO 0  /* per pass, the variant and tile measured fastest
-                              on GB300 (or found by lbm_autotune)            */
+                              on GB300 (or found by lbm_autotune): the single
+                              pass uses the TMA kernel with 32x16 tiles where
+                              the population arena can be one tensor (one
+                              lattice, or a batch in one row space), else
+                              plain loads with 32x8 tiles                    */
 #define LBM_KERNEL_PLAIN 1 /* plain global loads, 1, 2 or 4 sites per thread
                               (with 2 or 4, site pairs share the paired FP32
                               instructions); tile_x a multiple of 32,
@@ -240,7 +244,8 @@ int lbm_autotune(lbm_handle* h, int32_t repeats);
  * lattice (the same kernels as a batch handle).  Requests are admitted at
  * chunk boundaries, first come first served but skipping any that do not
  * fit yet, whenever a slot and arena space (HBM footprint: both population
- * buffers plus psi) are free and the resident sites stay below a target; a
+ * buffers at the arena's common pitch, plus psi) are free and the resident
+ * sites stay below a target; a
  * chunk runs each lattice for min(chunk_steps, its remaining steps).  The
  * worker keeps two chunks in flight: new requests' fields are uploaded
  * through pinned memory on their own stream while a chunk runs, the next
@@ -261,13 +266,18 @@ typedef struct {
                                  small enough to keep latency close to FIFO      */
     int32_t storage;          /* LBM_STORE_* of every request                     */
     int32_t eos_precision;    /* LBM_EOS_* of every request                       */
-    int32_t kernel_variant;   /* LBM_KERNEL_AUTO or LBM_KERNEL_PLAIN (the server's
-                                 chunks need the plain-load kernels)             */
+    int32_t kernel_variant;   /* LBM_KERNEL_AUTO (single pass: the TMA kernel,
+                                 32x16 tiles), LBM_KERNEL_TMA or LBM_KERNEL_PLAIN */
     int32_t schedule;         /* LBM_SCHED_* (AUTO: single pass)                  */
     int32_t tile_x, tile_y;   /* 0: defaults; else both passes                    */
     int32_t sites_per_thread; /* with tile_x/tile_y: 1, 2 or 4 (0: 1)              */
     int32_t with_velocity;    /* 1 (default): results carry ux, uy; 0: rho only
                                  (lbm_poll then fills ux, uy with NaN)           */
+    int32_t max_width;        /* widest nx accepted (0: 2048).  The arena holds
+                                 every resident lattice at the pitch of this
+                                 width (its ny + 4 rows in each of 18 planes, a
+                                 ninth of the arena for psi), so that one tensor
+                                 map covers them all for the TMA single pass    */
 } lbm_server_opts;
 
 typedef struct {

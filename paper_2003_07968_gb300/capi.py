@@ -80,7 +80,8 @@ class ServerOpts(ctypes.Structure):
                 ("target_resident_sites", ctypes.c_int64), ("storage", ctypes.c_int32), ("eos_precision", ctypes.c_int32),
                 ("kernel_variant", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
-                ("sites_per_thread", ctypes.c_int32), ("with_velocity", ctypes.c_int32)]
+                ("sites_per_thread", ctypes.c_int32), ("with_velocity", ctypes.c_int32),
+                ("max_width", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):

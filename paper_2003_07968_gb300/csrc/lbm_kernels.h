@@ -45,6 +45,10 @@ int occupancy_fused(int storage_f16, int mrt, int eos, int spt, int threads, siz
 bool fused_tma_shape_supported(int tx, int ty);
 bool fused_tma_make_map(int f16, int tx, int ty, const LatDev* lats, int n, void* pop,
                         CUtensorMap map[2]);
+// Maps over a whole row space of `rows` rows (the server's arena, whose
+// lattices come and go): stores unclipped.
+bool fused_tma_make_space_map(int f16, int tx, int ty, int64_t pitch, int64_t plane,
+                              int64_t rows, void* pop, CUtensorMap map[2]);
 cudaError_t launch_fused_tma(int f16, int mrt, int eos, int tx, int ty, const StepArgs& a,
                              const CUtensorMap* map, const LatDev* lat0, int grid,
                              cudaStream_t st);

@@ -107,9 +107,10 @@ inline int validate_desc(const lbm_lattice_desc& d, std::string& why) {
     return LBM_OK;
 }
 
-// Per-pass defaults of LBM_KERNEL_AUTO, measured fastest on GB300 for the
-// 8192^2 droplet: psi pass plain 64 x 4 tiles, collision pass plain 32 x 8
-// tiles, both with two sites per thread.
+// Per-pass defaults of LBM_KERNEL_AUTO for the plain-load kernels: psi pass
+// 64 x 4 tiles, collision (or single) pass 32 x 8 tiles, both with two sites
+// per thread.  (The single pass defaults to the TMA kernel with 32 x 16 tiles
+// wherever the arena can be one tensor; see lbm_create.)
 struct PassDefault {
     int variant, tx, ty, spt;
 };

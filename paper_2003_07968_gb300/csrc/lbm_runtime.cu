@@ -710,6 +710,14 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
         cudaMemcpyAsync(h->lat_dev, h->lat.data(), n * sizeof(LatDev), cudaMemcpyHostToDevice,
                         h->stream) != cudaSuccess)
         return fail(LBM_ERR_CUDA);
+    // LBM_KERNEL_AUTO, single pass: the TMA kernel with 32 x 16 tiles wherever
+    // the population arena can be one tensor (one lattice, or a batch in one
+    // row space, rows at least a box wide); measured fastest on GB300
+    if (fused && variant == LBM_KERNEL_AUTO && !(opts && (opts->tile_x || opts->tile_y))) {
+        CUtensorMap probe[2];
+        if (fused_tma_make_map(h->f16, 32, 16, h->lat.data(), n, h->pop, probe))
+            cfg[1] = PassCfg{LBM_KERNEL_TMA, 32, 16, 0, 2};
+    }
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         TuneKey k{h->device, h->storage, h->eos, variant * 4 + h->schedule,

@@ -1,6 +1,10 @@
 // lbm_server.cu -- continuous-batching server of the C ABI (lbm_server_*,
 // lbm_submit, lbm_poll): many independent lattices resident in one device
-// arena, stepped together by the same kernels as a batch handle.
+// arena, stepped together by the same kernels as a batch handle.  The
+// arena's population part is one row space: every lattice at the common
+// pitch of the widest accepted request, its ny + 2 GY rows (allocated first
+// fit) in each of 18 planes, so that one tensor map covers all resident
+// lattices and the single pass runs on the TMA kernel.
 //
 // One worker thread owns the GPU work and keeps two chunks in flight.  Each
 // turn of its loop:
@@ -51,16 +55,18 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-// First-fit allocator over [0, size) in 256-byte units, coalescing on release.
+// First-fit allocator over [0, size) in units of `granule`, coalescing on
+// release (bytes of the psi arena; rows of the population row space).
 class ArenaAlloc {
   public:
-    void reset(size_t n) {
+    void reset(size_t n, size_t granule = 256) {
         free_.clear();
         if (n) free_[0] = n;
         in_use_ = 0;
+        granule_ = granule;
     }
     bool alloc(size_t n, size_t* off) {
-        n = (size_t)round_up((int64_t)n, 256);
+        n = (size_t)round_up((int64_t)n, (int64_t)granule_);
         for (auto it = free_.begin(); it != free_.end(); ++it) {
             if (it->second < n) continue;
             *off = it->first;
@@ -73,7 +79,7 @@ class ArenaAlloc {
         return false;
     }
     void release(size_t off, size_t n) {
-        n = (size_t)round_up((int64_t)n, 256);
+        n = (size_t)round_up((int64_t)n, (int64_t)granule_);
         in_use_ -= n;
         auto it = free_.emplace(off, n).first;
         auto nx = std::next(it);
@@ -94,6 +100,7 @@ class ArenaAlloc {
   private:
     std::map<size_t, size_t> free_;
     size_t in_use_ = 0;
+    size_t granule_ = 256;
 };
 
 enum { ST_QUEUED = 0, ST_RESIDENT = 1, ST_DONE = 2 };
@@ -106,7 +113,7 @@ struct Request {
     int64_t nsteps = 0, remaining = 0;
     int state = ST_QUEUED;
     int status = LBM_OK;
-    size_t pop_off = 0, psi_off = 0, pop_bytes = 0, psi_bytes = 0;
+    size_t row_off = 0, psi_off = 0, rows = 0, psi_bytes = 0;  // rows of the row space
     size_t stage_off = 0;  // doubles into the upload buffers while being admitted
     bool dropped = false;  // faulted: no further chunks, released once its last chunk is done
     LatDev L{};
@@ -141,7 +148,14 @@ struct lbm_server {
     cudaEvent_t chunk_end[2] = {nullptr, nullptr};  // per table set: its last chunk is done
     cudaEvent_t up_done = nullptr;    // the last uploads have read up_host
     cudaEvent_t init_done = nullptr;  // the last inits have read staging
+    // device arena: the population row space (every resident lattice with the
+    // common pitch, its ny + 2 GY rows in each of 18 planes), then psi
     void* arena = nullptr;
+    float* psi_arena = nullptr;
+    int64_t pitch = 0, plane = 0, row_cap = 0;  // of the row space (elements, rows)
+    size_t pop_bytes = 0, psi_region = 0;
+    bool tma = false;      // single pass on the TMA kernel (one tensor map for the arena)
+    CUtensorMap tmap[2]{};  // loads, stores
     size_t up_cap = 0;            // doubles of the upload buffers
     double* staging = nullptr;    // rho of the requests admitted in one turn (device)
     double* up_host = nullptr;    // ... their pinned host copy
@@ -150,7 +164,7 @@ struct lbm_server {
     uint32_t* status_host = nullptr;  // fault words of both table sets (pinned)
     PassState pass[2];
     TableSet set[2];
-    ArenaAlloc alloc;
+    ArenaAlloc rows_alloc, psi_alloc;
     int parity = 0;
     // shared with the API threads
     std::mutex mu;
@@ -196,7 +210,8 @@ int pass_grid(lbm_server* S, int k, int ntiles) {
     const PassState& P = S->pass[k];
     const int thr = P.tx * (P.ty / P.spt);
     const int occ =
-        k == 0 ? occupancy_psi(S->f16, S->o.eos_precision, P.spt, thr)
+        k == 0   ? occupancy_psi(S->f16, S->o.eos_precision, P.spt, thr)
+        : S->tma ? occupancy_fused_tma(S->f16, 0, S->o.eos_precision, P.tx, P.ty, true, false)
         : S->fused ? occupancy_fused(S->f16, 0, S->o.eos_precision, P.spt, thr, smem_of(P))
                    : occupancy_collide(S->f16, 0, P.spt, thr, smem_of(P));
     return std::max(1, std::min(ntiles, S->sm_count * occ));
@@ -206,6 +221,9 @@ cudaError_t launch(lbm_server* S, int k, const StepArgs& a, int grid, cudaStream
     const PassState& P = S->pass[k];
     const dim3 block(P.tx, P.ty / P.spt);
     if (k == 0) return launch_psi(S->f16, S->o.eos_precision, P.spt, a, dim3(grid), block, st);
+    if (S->tma)
+        return launch_fused_tma(S->f16, 0, S->o.eos_precision, P.tx, P.ty, a, S->tmap, nullptr,
+                                grid, st);
     if (S->fused)
         return launch_fused(S->f16, 0, S->o.eos_precision, P.spt, a, dim3(grid), block, smem_of(P),
                             st);
@@ -218,7 +236,7 @@ StepArgs args(lbm_server* S, const TableSet& T, int k, int parity) {
     a.tiles = T.tiles[k];
     a.ntiles = T.ntiles[k];
     a.pop = S->arena;
-    a.psi = static_cast<float*>(S->arena);
+    a.psi = S->psi_arena;
     a.status = T.status;
     a.parity = parity;
     a.quota = T.quota;
@@ -292,7 +310,7 @@ cudaError_t copy_out(lbm_server* S, const TableSet& T, Request& R, int l, int pa
     double* dr = S->outbuf;
     double* dx = dr + S->o.max_request_sites;
     double* dy = dx + S->o.max_request_sites;
-    e = launch_moments(S->f16, R.L, S->arena, par, static_cast<float*>(S->arena), dr,
+    e = launch_moments(S->f16, R.L, S->arena, par, S->psi_arena, dr,
                        vel ? dx : nullptr, vel ? dy : nullptr, S->side);
     if (e != cudaSuccess) return e;
     double* hr = S->down_host;
@@ -343,18 +361,23 @@ struct Chunk {
     Clock::time_point t0;
 };
 
+int64_t arena_in_use(const lbm_server* S) {
+    return (int64_t)(S->rows_alloc.in_use() * (size_t)(18 * S->pitch * S->es) +
+                     S->psi_alloc.in_use());
+}
+
 void finish(lbm_server* S, Request* R, int status) {
     std::lock_guard<std::mutex> lk(S->mu);
     R->status = status;
     R->state = ST_DONE;
     R->t_done = Clock::now();
-    S->alloc.release(R->pop_off, R->pop_bytes);
-    S->alloc.release(R->psi_off, R->psi_bytes);
+    S->rows_alloc.release(R->row_off, R->rows);
+    S->psi_alloc.release(R->psi_off, R->psi_bytes);
     if (status == LBM_OK)
         S->st.completed++;
     else
         S->st.failed++;
-    S->st.arena_in_use = (int64_t)S->alloc.in_use();
+    S->st.arena_in_use = arena_in_use(S);
 }
 
 void worker_main(lbm_server* S) {
@@ -386,9 +409,9 @@ void worker_main(lbm_server* S) {
                     break;
                 if (up_used + nup > S->up_cap) break;
                 size_t po = 0, qo = 0;
-                if (S->alloc.alloc(R.pop_bytes, &po)) {
-                    if (S->alloc.alloc(R.psi_bytes, &qo)) {
-                        R.pop_off = po;
+                if (S->rows_alloc.alloc(R.rows, &po)) {
+                    if (S->psi_alloc.alloc(R.psi_bytes, &qo)) {
+                        R.row_off = po;
                         R.psi_off = qo;
                         R.stage_off = up_used;
                         up_used += nup;
@@ -398,12 +421,12 @@ void worker_main(lbm_server* S) {
                         it = S->queue.erase(it);
                         continue;
                     }
-                    S->alloc.release(po, R.pop_bytes);
+                    S->rows_alloc.release(po, R.rows);
                 }
                 ++it;
             }
             S->st.queued = (int)S->queue.size();
-            S->st.arena_in_use = (int64_t)S->alloc.in_use();
+            S->st.arena_in_use = arena_in_use(S);
         }
         cudaError_t e = cudaSuccess;
         int64_t launches = 0;
@@ -424,8 +447,11 @@ void worker_main(lbm_server* S) {
             if (e == cudaSuccess) e = cudaStreamWaitEvent(S->stream, S->up_done, 0);
             for (Request* R : admitted) {
                 if (e != cudaSuccess) break;
-                R->L.off_f[0] = (int64_t)(R->pop_off / S->es);
-                R->L.off_f[1] = R->L.off_f[0] + 9 * R->L.plane;
+                R->L.pitch = (int32_t)S->pitch;
+                R->L.plane = S->plane;
+                R->L.row0 = (int32_t)R->row_off;
+                R->L.off_f[0] = (int64_t)R->row_off * S->pitch;
+                R->L.off_f[1] = R->L.off_f[0] + 9 * S->plane;
                 R->L.off_psi = (int64_t)(R->psi_off / 4);
                 const size_t ns = (size_t)R->L.nx * R->L.ny;
                 if (R->d.storage != LBM_STORE_F32 && R->d.rho0 < 0.0)
@@ -574,6 +600,7 @@ void lbm_server_opts_default(lbm_server_opts* o) {
     o->eos_precision = LBM_EOS_DF;
     o->kernel_variant = LBM_KERNEL_AUTO;
     o->with_velocity = 1;
+    o->max_width = 2048;
 }
 
 int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
@@ -589,13 +616,17 @@ int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
         if (!o.chunk_steps) o.chunk_steps = d.chunk_steps;
         if (!o.max_request_sites) o.max_request_sites = d.max_request_sites;
         if (!o.target_resident_sites) o.target_resident_sites = d.target_resident_sites;
+        if (!o.max_width) o.max_width = d.max_width;
     }
     if (o.max_resident < 1 || o.chunk_steps < 1 || o.max_request_sites < 4 ||
         o.target_resident_sites < 1 || o.storage < LBM_STORE_F32 ||
         o.storage > LBM_STORE_F16_DEV || o.eos_precision < LBM_EOS_F64 ||
-        o.eos_precision > LBM_EOS_F32 || o.kernel_variant == LBM_KERNEL_TMA ||
+        o.eos_precision > LBM_EOS_F32 || o.max_width < 2 ||
+        (o.kernel_variant != LBM_KERNEL_AUTO && o.kernel_variant != LBM_KERNEL_PLAIN &&
+         o.kernel_variant != LBM_KERNEL_TMA) ||
         (o.schedule != LBM_SCHED_AUTO && o.schedule != LBM_SCHED_TWO_PASS &&
-         o.schedule != LBM_SCHED_FUSED))
+         o.schedule != LBM_SCHED_FUSED) ||
+        (o.kernel_variant == LBM_KERNEL_TMA && o.schedule == LBM_SCHED_TWO_PASS))
         return LBM_ERR_ARG;
     lbm_server* S = new (std::nothrow) lbm_server();
     if (!S) return LBM_ERR_OOM;
@@ -603,17 +634,28 @@ int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
     S->fused = o.schedule != LBM_SCHED_TWO_PASS;
     S->f16 = o.storage == LBM_STORE_F16_DEV;
     S->es = S->f16 ? 2 : 4;
+    // the single pass on the TMA kernel unless plain loads were asked for
+    const bool want_tma = S->fused && o.kernel_variant != LBM_KERNEL_PLAIN;
     for (int k = 0; k < 2; ++k) {
         PassState& P = S->pass[k];
         P.tx = kPassDefaults[k].tx;
         P.ty = kPassDefaults[k].ty;
         P.spt = kPassDefaults[k].spt;
+        if (k == 1 && want_tma) {
+            P.tx = 32;
+            P.ty = 16;
+            P.spt = 2;
+        }
         if (o.tile_x || o.tile_y) {
             P.tx = o.tile_x ? o.tile_x : 64;
             P.ty = o.tile_y ? o.tile_y : 8;
             P.spt = o.sites_per_thread ? o.sites_per_thread : 1;
+            if (k == 1 && want_tma) P.spt = P.tx * P.ty / 256;
         }
-        if (P.tx % 32 || P.ty < 1 || P.tx * (P.ty / P.spt) > 512 || P.ty % P.spt) {
+        const bool bad = (k == 1 && want_tma) ? !fused_tma_shape_supported(P.tx, P.ty)
+                                              : (P.tx % 32 || P.ty < 1 || P.spt < 1 ||
+                                                 P.tx * (P.ty / P.spt) > 512 || P.ty % P.spt);
+        if (bad) {
             delete S;
             return LBM_ERR_ARG;
         }
@@ -637,6 +679,22 @@ int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
     const size_t nmax = (size_t)o.max_request_sites;
     // one turn admits at most the resident-site target plus one request
     S->up_cap = (size_t)round_up(o.target_resident_sites, 32) + (size_t)round_up((int64_t)nmax, 32);
+    // the arena: a population row space with the common pitch of the widest
+    // request, then a psi region (a ninth of the arena)
+    {
+        const int64_t gx = 16 / S->es;
+        S->pitch = round_up(o.max_width + 2 * gx, 32 / S->es);
+        S->psi_region = (size_t)round_up((int64_t)(o.arena_bytes / 9), 256);
+        const size_t pop_budget = o.arena_bytes - S->psi_region;
+        S->row_cap = (int64_t)(pop_budget / (size_t)(18 * S->pitch * S->es));
+        S->plane = round_up(S->row_cap * S->pitch, 256 / S->es);
+        while (S->row_cap > 0 && (size_t)(18 * S->plane * S->es) > pop_budget) {
+            --S->row_cap;
+            S->plane = round_up(S->row_cap * S->pitch, 256 / S->es);
+        }
+        if (S->row_cap < 1) return fail(LBM_ERR_ARG);
+        S->pop_bytes = (size_t)(18 * S->plane * S->es);
+    }
     bool ok = cudaMalloc(&S->arena, o.arena_bytes) == cudaSuccess &&
               cudaMalloc(&S->staging, S->up_cap * sizeof(double)) == cudaSuccess &&
               cudaMallocHost(&S->up_host, S->up_cap * sizeof(double)) == cudaSuccess &&
@@ -653,7 +711,19 @@ int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
         return fail(LBM_ERR_OOM);
     }
     if (cudaMemset(S->arena, 0, o.arena_bytes) != cudaSuccess) return fail(LBM_ERR_CUDA);
-    S->alloc.reset(o.arena_bytes);
+    S->psi_arena = reinterpret_cast<float*>(static_cast<char*>(S->arena) + S->pop_bytes);
+    S->rows_alloc.reset((size_t)S->row_cap, 1);
+    S->psi_alloc.reset(o.arena_bytes - S->pop_bytes);
+    // one tensor map for the whole row space (all resident requests)
+    if (want_tma)
+        S->tma = fused_tma_make_space_map(S->f16, S->pass[1].tx, S->pass[1].ty, S->pitch,
+                                          S->plane, S->row_cap, S->arena, S->tmap);
+    if (want_tma && !S->tma) {
+        if (o.kernel_variant == LBM_KERNEL_TMA) return fail(LBM_ERR_ARG);
+        S->pass[1].tx = kPassDefaults[1].tx;  // plain loads instead
+        S->pass[1].ty = kPassDefaults[1].ty;
+        S->pass[1].spt = kPassDefaults[1].spt;
+    }
     S->st.arena_bytes = (int64_t)o.arena_bytes;
     try {
         S->worker = std::thread(worker_main, S);
@@ -677,11 +747,12 @@ int lbm_submit(lbm_server* S, const lbm_lattice_desc* d, const double* rho, int6
     if ((int64_t)n > S->o.max_request_sites) return LBM_ERR_CAPACITY;
     for (size_t i = 0; i < n; ++i)
         if (!std::isfinite(rho[i])) return LBM_ERR_ARG;
+    if (R.d.nx > S->o.max_width) return LBM_ERR_CAPACITY;
     R.L = lat_layout(R.d, 0);
-    R.pop_bytes = (size_t)lat_pop_elems(R.L) * S->es;
+    R.rows = (size_t)(R.d.ny + 2 * GY);  // of the row space, at the common pitch
     R.psi_bytes = (size_t)lat_psi_elems(R.L) * 4;
-    if ((size_t)round_up((int64_t)R.pop_bytes, 256) + (size_t)round_up((int64_t)R.psi_bytes, 256) >
-        S->o.arena_bytes)
+    if ((int64_t)R.rows > S->row_cap ||
+        (size_t)round_up((int64_t)R.psi_bytes, 256) > S->o.arena_bytes - S->pop_bytes)
         return LBM_ERR_CAPACITY;
     R.rho.assign(rho, rho + n);
     R.nsteps = R.remaining = nsteps;

@@ -85,7 +85,8 @@ def test_served_results_equal_alone_runs(P):
 
 def test_server_admission_capacity_and_failures(P):
     # a small arena: requests wait for space, one never fits, one fails alone
-    opts = P.lbm_server_opts_default(arena_bytes=8 << 20, chunk_steps=20, max_resident=3)
+    opts = P.lbm_server_opts_default(arena_bytes=8 << 20, chunk_steps=20, max_resident=3,
+                                     max_width=128)
     srv = P.lbm_server_create(opts)
     with pytest.raises(P.LbmError) as ei:
         big = P.lbm_desc_default(1024, 1024)
@@ -134,3 +135,25 @@ def test_rho_only_results_without_velocity(P):
         a = alone(P, d, rho, n)
         assert np.array_equal(res[t]["rho"], a["rho"])
         assert np.isnan(res[t]["ux"]).all() and np.isnan(res[t]["uy"]).all()
+
+
+def test_tma_server_results_equal_plain_alone_runs(P):
+    # the default server runs the single pass on the TMA kernel over its row
+    # space (one tensor map for every resident lattice); its results equal
+    # plain-kernel handles stepped alone, bitwise
+    opts = P.lbm_server_opts_default(arena_bytes=1 << 30, chunk_steps=29, max_width=256)
+    srv = P.lbm_server_create(opts)
+    specs = [(200, 150, 40.0, 0.75, 130), (96, 96, 24.0, 0.65, 90), (130, 97, 30.0, 0.7, 61),
+             (48, 40, 12.0, 0.8, 45), (256, 64, 20.0, 0.7, 70)]
+    tickets, jobs = [], []
+    for nx, ny, R, T, n in specs:
+        d = P.lbm_desc_default(nx, ny, T=T)
+        rho = synth.droplet(nx, ny, R, T)
+        tickets.append(P.lbm_submit(srv, d, rho, n))
+        jobs.append((d, rho, n))
+    res = wait(P, srv, tickets)
+    P.lbm_server_destroy(srv)
+    for t, (d, rho, n) in zip(tickets, jobs):
+        a = alone(P, d, rho, n)
+        assert np.array_equal(res[t]["rho"], a["rho"]), (d.nx, d.ny)
+        assert np.array_equal(res[t]["ux"], a["ux"])
