@@ -75,6 +75,21 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def job_rate(dist, units, seconds, device=None):
+    """Whole-job rate of replicas: the units every rank processed divided by
+    the slowest rank's time.  Returns (rate, slowest seconds); one process
+    without a process group: units / seconds."""
+    if dist is None:
+        return units / seconds, seconds
+    import torch
+
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item())
+
+
 def measured_hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -313,12 +328,9 @@ def run_gpu(args):
     stats = {s["name"]: s for s in P.lbm_profile_read(h)}
     P.lbm_profile(h, False)
     P.lbm_sync(h)
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = sites * args.steps * world / (ms_max * 1e-3) / 1e6
+    rate, s_max = job_rate(dist, sites * args.steps, ms * 1e-3, device="cuda")
+    ms_max = s_max * 1e3
+    value = rate / 1e6
 
     # ---- end-to-end through the C ABI with host buffers (pinned)
     host_rho = torch.from_numpy(rho).pin_memory().numpy()
@@ -330,12 +342,8 @@ def run_gpu(args):
     P.lbm_init(h, 0, host_rho)
     P.lbm_step(h, args.steps)
     m = P.lbm_moments(h, 0, rho=True, u=False, mass=True, out={"rho": host_out})
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": round(sites * args.steps * world / e2e_s / 1e6, 3), "unit": "MLUPS",
+    e2e_rate, _ = job_rate(dist, sites * args.steps, time.perf_counter() - t0, device="cuda")
+    e2e = {"value": round(e2e_rate / 1e6, 3), "unit": "MLUPS",
            "h2d_bytes_per_step": round(host_rho.nbytes / args.steps, 1),
            "d2h_bytes_per_step": round((host_out.nbytes + 8) / args.steps, 1),
            "mass_rel_drift": abs(m["mass"] - float(rho.sum())) / float(rho.sum())}
