@@ -123,6 +123,8 @@ cudaError_t launch_fused_tma(int f16, int mrt, int eos, int tx, int ty, const St
                              const CUtensorMap* map, const LatDev* lat0, int grid,
                              cudaStream_t st) {
     int occ = 0;
+    // a batch on the tensor path bulk-copies LatDev rows: 16-byte aligned array
+    if (map && !lat0 && (reinterpret_cast<uintptr_t>(a.lats) & 15u)) return cudaErrorInvalidValue;
     return fused_any(f16, mrt, tx, ty, eos, a, map, lat0, grid, st, false, &occ);
 }
 

@@ -25,9 +25,14 @@
 // narrow lattices) one bulk row copy per plane and row as above.  One tensor
 // copy replaces 9 (TY + 2) row copies, whose issue cost is what limits the
 // row-copy form (measured about 32 SM cycles per copy on GB300).
+// On the tensor path the consumers write the f* of a tile inside the lattice
+// back into its stage, laid out as the store box, and arrive on the stage's
+// mbarrier; the producer sends it out with one 3-D tensor store, waits until
+// the store has read the stage and refills it (edge tiles: plain stores).
 // The stage ring decouples DRAM latency from the arithmetic: the producer
-// runs up to STAGES tiles ahead, and the bytes in flight cost no registers.
-// The psi tile is double-buffered, so one barrier per tile suffices.
+// runs up to STAGES - 1 tiles ahead, and the bytes in flight cost no
+// registers.  The psi tile is double-buffered, so one barrier per tile
+// suffices.
 //
 // Every mbarrier wait is bounded (lbm_async.cuh).  A consumer warp whose wait
 // runs out does not release its stage; the consumers agree on the failure at
@@ -67,7 +72,11 @@ struct FGeo : FusedGeo<(int)sizeof(typename S::T), TX, TY> {
     static constexpr int STAGES = kStageBudget / STAGEB >= 4   ? 4
                                   : kStageBudget / STAGEB >= 3 ? 3
                                                                : 2;
-    static constexpr int BAR = STAGES * STAGEB + 2 * PSIB;  // mbarriers after stages + psi
+    // constants of the tile's lattice, copied in beside each stage (batches
+    // on the tensor path)
+    static constexpr int LATB = (int)((sizeof(LatDev) + 15) & ~size_t(15));
+    static constexpr int LATOFF = STAGES * STAGEB + 2 * PSIB;
+    static constexpr int BAR = LATOFF + STAGES * LATB;  // mbarriers after stages, psi, constants
     // element offset, inside a stage, of the value that cell (lx, ly) of the
     // tile (lx, ly in -1 .. TX, -1 .. TY) pulls from plane i
     static __host__ __device__ constexpr int pull(int i, int lx, int ly) {
@@ -105,6 +114,8 @@ __device__ __forceinline__ void tensor_s2g(const CUtensorMap* map, const void* s
 __device__ __forceinline__ bool tile_skipped(const StepArgs& a, int t) {
     return a.quota && a.step >= __ldg(&a.quota[__ldg(&a.tiles[t]).x]);
 }
+
+static_assert(sizeof(LatDev) % 16 == 0, "LatDev rows are bulk-copied (16-byte granules)");
 
 // Copies of one tile into `stage`, issued by the 32 lanes of the producer warp.
 template <class S, int TX, int TY>
@@ -164,9 +175,9 @@ __global__ void __launch_bounds__(kBlockF, 2)
         for (int s = 0; s < G::STAGES; ++s) {
             mbar_init(&full[s], 1);
             // row copies: each consumer warp releases a stage after reading it;
-            // tensor path: the consumer that stores the tile releases it once
-            // the tile store has read it
-            mbar_init(&empty[s], TMAP ? 1 : kConsumers / 32);
+            // tensor path: every consumer arrives once the tile's f* is in the
+            // stage (the producer stores it, then refills the stage)
+            mbar_init(&empty[s], TMAP ? kConsumers : kConsumers / 32);
         }
         *abort_flag = 0;
         mbar_fence_init();
@@ -175,16 +186,43 @@ __global__ void __launch_bounds__(kBlockF, 2)
 
     if (warp == kConsumers / 32) {
         // ------------------------------------------------------------ producer
+        // Tensor path: a stage comes back when its tile is done; the producer
+        // then sends the tile's f* out with one tensor store (tiles inside the
+        // lattice; edge tiles were stored by the consumers), waits until the
+        // store has read the stage and refills it at once, so loads run up to
+        // STAGES - 1 tiles ahead of the consumers.
         int k = 0;
+        int tq[G::STAGES];  // tile held by each stage (tensor path)
+        bool alive = true;
+        // store of the finished tile t from stage s (lane 0)
+        auto store_tile = [&](int s, int t) {
+            const int4 tl = __ldg(&a.tiles[t]);
+            const LatDev& L =
+                MODE == 1 ? lat0 : *reinterpret_cast<const LatDev*>(smem + G::LATOFF + s * G::LATB);
+            if (tl.y + TX <= L.nx && tl.z + TY <= L.ny) {
+                tensor_s2g(&smap, smem + s * G::STAGEB, tl.y + L.gx, L.row0 + tl.z + GY,
+                           9 * (a.parity ^ 1));
+                bulk_commit();
+                bulk_wait_read<0>();
+            }
+        };
         for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
             if (tile_skipped(a, t)) continue;
-            if (*abort_flag) break;
+            if (*abort_flag) {
+                alive = false;
+                break;
+            }
             const int s = k % G::STAGES;
             if (k >= G::STAGES) {
                 const bool ok = mbar_wait_bounded(&empty[s], (uint32_t)(k / G::STAGES - 1) & 1u);
                 if (!__all_sync(0xffffffffu, ok)) {
                     if (lane == 0) atomicOr(&a.status[__ldg(&a.tiles[t]).x], 2u);
+                    alive = false;
                     break;
+                }
+                if (TMAP) {
+                    if (lane == 0) store_tile(s, tq[s]);
+                    __syncwarp();
                 }
                 // the consumers' generic-proxy reads of the stage come before the refill
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -196,19 +234,39 @@ __global__ void __launch_bounds__(kBlockF, 2)
                 if (lane == 0) {
                     const int4 tl = __ldg(&a.tiles[t]);
                     const int row0 = MODE == 1 ? lat0.row0 : a.lats[tl.x].row0;
-                    mbar_expect_tx(&full[s], (uint32_t)G::TBYTES);
+                    mbar_expect_tx(&full[s], (uint32_t)G::TBYTES +
+                                                 (MODE == 2 ? (uint32_t)sizeof(LatDev) : 0u));
                     tensor_g2s(smem + s * G::STAGEB, &tmap, tl.y, row0 + tl.z, 9 * a.parity,
                                &full[s]);
+                    if (MODE == 2)
+                        bulk_g2s(smem + G::LATOFF + s * G::LATB, a.lats + tl.x,
+                                 (uint32_t)sizeof(LatDev), &full[s]);
                 }
+                tq[s] = t;
                 __syncwarp();
             } else {
                 issue_fused<S, TX, TY>(a, __ldg(&a.tiles[t]), smem + s * G::STAGEB, &full[s]);
             }
             ++k;
         }
-        // drain: the last issue into each stage must have landed before exit
+        // tensor path: store the tiles still held by the stages
+        if (TMAP && alive) {
+            for (int j = (k > G::STAGES ? k - G::STAGES : 0); j < k; ++j) {
+                const int s = j % G::STAGES;
+                const bool ok = mbar_wait_bounded(&empty[s], (uint32_t)(j / G::STAGES) & 1u);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    if (lane == 0) atomicOr(&a.status[__ldg(&a.tiles[tq[s]]).x], 2u);
+                    break;
+                }
+                if (lane == 0) store_tile(s, tq[s]);
+                __syncwarp();
+            }
+        }
+        // drain: the last issue into each stage must have landed, and every
+        // tile store must be complete, before exit
         for (int j = (k > G::STAGES ? k - G::STAGES : 0); j < k; ++j)
             mbar_wait_bounded(&full[j % G::STAGES], (uint32_t)(j / G::STAGES) & 1u);
+        if (TMAP && lane == 0) bulk_wait_all();
         return;
     }
 
@@ -217,19 +275,24 @@ __global__ void __launch_bounds__(kBlockF, 2)
     const int tx = tid % TX, ty0 = tid / TX;
     constexpr int nhalf = TX + TY + 2;  // half of the 2 (TX + TY) + 4 ring cells
     int k = 0;
-    int prev_s = -1;  // tensor path: stage of the tile whose store is in flight
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         if (tile_skipped(a, t)) continue;
         const int s = k % G::STAGES;
         const int4 tl = __ldg(&a.tiles[t]);
-        // one lattice: its constants are kernel parameters (constant-bank operands)
-        const LatDev& L = MODE == 1 ? lat0 : a.lats[tl.x];
-        const int nx = L.nx, ny = L.ny, x0 = tl.y, y0 = tl.z;
-        const int xend = min(x0 + TX, nx), yend = min(y0 + TY, ny);
-        const int x = x0 + tx;
         float* ps = psi_buf + (k & 1) * (G::PSIB / 4);
         const bool ok = __all_sync(0xffffffffu,
                                    mbar_wait_bounded(&full[s], (uint32_t)(k / G::STAGES) & 1u));
+        // one lattice: its constants are kernel parameters (constant-bank
+        // operands); a batch on the tensor path: they arrived with the tile
+        // and stay until the stage goes back; row copies: global (the stage
+        // goes back before the collision)
+        const LatDev& L =
+            MODE == 1   ? lat0
+            : MODE == 2 ? *reinterpret_cast<const LatDev*>(smem + G::LATOFF + s * G::LATB)
+                        : a.lats[tl.x];
+        const int nx = L.nx, ny = L.ny, x0 = tl.y, y0 = tl.z;
+        const int xend = min(x0 + TX, nx), yend = min(y0 + TY, ny);
+        const int x = x0 + tx;
         V g[NV][9];
         V drho[NV];
         if (ok) {
@@ -299,7 +362,6 @@ __global__ void __launch_bounds__(kBlockF, 2)
             if (tid == 0) {
                 *abort_flag = 1;
                 atomicOr(&a.status[tl.x], 2u);
-                if (TMAP) bulk_wait_all();  // tile stores already issued complete on their own
             }
             return;
         }
@@ -311,7 +373,8 @@ __global__ void __launch_bounds__(kBlockF, 2)
         const bool tile_in = x0 >= GW && y0 >= GW && x0 + TX <= nx - GW && y0 + TY <= ny - GW;
         // tensor path, tiles inside the lattice: f* of the tile goes to the
         // stage just consumed, laid out as the store box [plane][TY][TX], and
-        // leaves in one tensor store.  A ragged edge tile uses plain stores:
+        // leaves in one tensor store issued by the producer.  A ragged edge
+        // tile uses plain stores:
         // the store unit clips a box at 16-byte granularity in x (measured), so
         // a partial box would also write the ghost columns just past nx.
         const bool bulk_out = TMAP && x0 + TX <= nx && y0 + TY <= ny;
@@ -340,7 +403,8 @@ __global__ void __launch_bounds__(kBlockF, 2)
                 if (bulk_out) {
 #pragma unroll
                     for (int i = 0; i < 9; ++i) out[(i * TY + ly) * TX + tx] = S::cv(Ln::get(v[i], l));
-                    if (!tile_in)
+                    // sites within GW of an edge: their periodic images too
+                    if (!tile_in && ((x < GW) | (x >= nx - GW) | (y < GW) | (y >= ny - GW)))
 #pragma unroll
                         for (int i = 0; i < 9; ++i)
                             store_images(o + i * L.plane, L.pitch, L.gx, x, y, nx, ny,
@@ -355,32 +419,11 @@ __global__ void __launch_bounds__(kBlockF, 2)
             }
         }
         if (TMAP) {
-            // the tile's f* in shared memory -> one tensor store; a stage goes
-            // back to the producer once the store of its tile has read it
+            // the tile's f* is in the stage (or, for an edge tile, stored):
+            // hand the stage to the producer, which stores and refills it
             if (bulk_out) fence_proxy_async_smem();
-            named_sync(2, kConsumers);
-            if (tid == 0) {
-                if (bulk_out) {
-                    tensor_s2g(&smap, smem + s * G::STAGEB, x0 + L.gx, L.row0 + y0 + GY,
-                               9 * (a.parity ^ 1));
-                    bulk_commit();
-                    if (prev_s >= 0) {
-                        bulk_wait_read<1>();
-                        mbar_arrive(&empty[prev_s]);
-                    }
-                } else {
-                    // no store reads this stage: release it, and the previous one
-                    bulk_wait_read<0>();
-                    if (prev_s >= 0) mbar_arrive(&empty[prev_s]);
-                    mbar_arrive(&empty[s]);
-                }
-            }
-            prev_s = bulk_out ? s : -1;
+            mbar_arrive(&empty[s]);
         }
-    }
-    if (TMAP && tid == 0) {
-        bulk_wait_all();
-        if (prev_s >= 0) mbar_arrive(&empty[prev_s]);
     }
 }
 
