@@ -6,6 +6,8 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 * Maxwell equal-area coexistence, Eq. (MLVDR) with equal bulk pressures.
 * Mechanical-stability coexistence of the pseudopotential method,
   Eq. (PGLDR) with Eqs. (BPLP), (BPVP), epsilon = -2 A1 / (A2 + A3).
+* Planar interface, Eqs. (PTNNPI), (PTTTPI), (STDIM), (STPI): density profile
+  by central differences and Newton-Raphson, surface tension gamma_pi.
 * Lamb's oscillation period, Eq. (DOP).
 * Young-Laplace analysis of a static droplet, Eq. (YLR), with the interface
   at rho_m = (rho_l + rho_g)/2 (Sec. IV.B).
@@ -17,7 +19,8 @@ import math
 import warnings
 
 import numpy as np
-from scipy import integrate, optimize
+from scipy import integrate, optimize, sparse
+from scipy.sparse import linalg as sparse_linalg
 
 CS2 = 1.0 / 3.0
 CS_A = 3.852462257
@@ -133,6 +136,84 @@ def pgldr(T, eps, G=-1.0):
     lo = max(pmin, 0.0) + 1e-9 * pmax
     p0 = optimize.brentq(area, lo, pmax * (1 - 1e-9), xtol=1e-17, rtol=1e-14)
     return roots(p0)
+
+
+def planar_interface(T, eps, sigma=1.0, L=30.0, dx=0.05, G=-1.0, max_newton=30):
+    """Planar liquid-gas interface of the pressure tensor Eq. (GPTRF), Sec. II.
+
+    The procedure the paper describes after Eq. (STPI):
+      1. phase densities rho_g, rho_l from Eq. (PGLDR) (with Eqs. BPLP, BPVP),
+         used as boundary values at x = 0 and x = L;
+      2. mechanical equilibrium p_xx = p0 along x, Eq. (PTNNPI),
+            c_s^2 rho + G psi^2 + G [A1 psi'^2 + (A2 + A3) psi psi''] = p0,
+         with second-order central differences on a uniform mesh of spacing
+         dx, solved by Newton-Raphson;
+      3. psi(x) = psi(rho(x)), Eq. (DED);
+      4. gamma_pi = int (p_xx - p_yy) dx, Eq. (STDIM), with Eqs. (PTNNPI),
+         (PTTTPI): the integrand is G A3 psi psi'' (trapezoid rule, psi'' by
+         central differences).
+    Coefficients of the proposed force, Eq. (PTIFT): A1 = -3 eps c_s^2 / 4,
+    A2 + A3 = 3 c_s^2 / 2, A3 = sigma c_s^2.
+
+    Two readings.  Eq. (STPI) is printed as int A3 psi psi'' dx without G;
+    p_xx - p_yy from Eqs. (PTNNPI), (PTTTPI) is G A3 psi psi'', which gives a
+    positive gamma for G < 0, so G is kept.  With bulk densities at both
+    ends the discrete problem is invariant, up to terms exponentially small
+    in L, under translating the interface, so Newton steps along that mode
+    are ill conditioned; the interface is pinned, rho = (rho_g + rho_l)/2 at
+    the middle node, and p0 joins the unknowns (it converges to the p0 of
+    Eq. PGLDR as L grows).
+
+    Returns (x, rho, p0, gamma).
+    """
+    A1 = -0.75 * eps * CS2
+    A23 = 1.5 * CS2
+    A3 = sigma * CS2
+    rho_g, rho_l = pgldr(T, eps, G)
+    n = int(round(L / dx))
+    if n < 4 or n % 2:
+        raise ValueError("L / dx must be an even integer >= 4")
+    x = np.arange(n + 1) * dx
+    c = n // 2
+    rho_m = 0.5 * (rho_g + rho_l)
+    # initial profile: a tanh of width 2.5 centred at the pinned node
+    rho = rho_m + 0.5 * (rho_l - rho_g) * np.tanh((x - x[c]) / 2.5)
+    rho[0], rho[-1] = rho_g, rho_l
+    p0 = float(eos_pressure(rho_g, T))
+    m = n - 1  # interior unknowns rho_1 .. rho_{n-1}; unknown m is p0
+
+    def psidot(r):
+        # 2 psi psidot = (P' - c_s^2) / G
+        return (dpdrho(r, T) - CS2) / (2 * G * psi(r, T, G))
+
+    for _ in range(max_newton):
+        ps = psi(rho, T, G)
+        pd = psidot(rho)
+        d1 = (ps[2:] - ps[:-2]) / (2 * dx)
+        d2 = (ps[2:] - 2 * ps[1:-1] + ps[:-2]) / dx**2
+        # c_s^2 rho + G psi^2 = P_EOS (Eq. DED)
+        res = eos_pressure(rho[1:-1], T) + G * (A1 * d1**2 + A23 * ps[1:-1] * d2) - p0
+        pin = rho[c] - rho_m
+        # Jacobian: tridiagonal in rho, a column for p0 and the pin row
+        sub = G * (-A1 * d1 / dx + A23 * ps[1:-1] / dx**2) * pd[:-2]
+        sup = G * (A1 * d1 / dx + A23 * ps[1:-1] / dx**2) * pd[2:]
+        dia = dpdrho(rho[1:-1], T) + G * A23 * (d2 - 2 * ps[1:-1] / dx**2) * pd[1:-1]
+        J = sparse.lil_matrix((m + 1, m + 1))
+        J.setdiag(dia)
+        J.setdiag(sub[1:], -1)
+        J.setdiag(sup[:-1], 1)
+        J[:m, m] = -1.0
+        J[m, c - 1] = 1.0
+        step = sparse_linalg.spsolve(J.tocsc(), -np.r_[res, pin])
+        rho[1:-1] += step[:m]
+        p0 += step[m]
+        if np.max(np.abs(step[:m])) < 1e-13 * rho_l:
+            break
+    ps = psi(rho, T, G)
+    d2 = (ps[2:] - 2 * ps[1:-1] + ps[:-2]) / dx**2
+    # the integrand vanishes in the bulk at both ends
+    gamma = G * A3 * integrate.trapezoid(np.r_[0.0, ps[1:-1] * d2, 0.0], dx=dx)
+    return x, rho, p0, float(gamma)
 
 
 def lamb_period(gamma, rho_l, r_max, r_min, n=2):
