@@ -41,14 +41,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="roofline", choices=["roofline", "batched", "served"])
-    ap.add_argument("--requests", type=int, default=300,
+    ap.add_argument("--requests", type=int, default=1000,
                     help="served workload: number of requests of the Poisson stream")
     ap.add_argument("--step-scale", type=int, default=100,
                     help="served workload: divide each request's step count by this")
     ap.add_argument("--target-sites", type=int, default=0,
                     help="served workload: resident-site target of the server (0: default)")
     ap.add_argument("--chunk", type=int, default=100,
-                    help="served workload: steps per server chunk")
+                    help="served workload: most steps per server chunk")
+    ap.add_argument("--chunk-ms", type=float, default=4.0,
+                    help="served workload: GPU time a server chunk aims at (< 0: fixed --chunk)")
     ap.add_argument("--eos", default="df", choices=["f64", "df", "f32"],
                     help="arithmetic of psi/EOS: float-float (default), native FP64 or FP32")
     ap.add_argument("--variant", default="auto", choices=["auto", "tma", "plain"])
@@ -530,7 +532,8 @@ def run_served(args):
     P.lbm_destroy(h)
 
     # results carry rho only, as the sequential runs below read rho only
-    opts = P.lbm_server_opts_default(arena_bytes=64 << 30, chunk_steps=args.chunk, storage=storage,
+    opts = P.lbm_server_opts_default(arena_bytes=64 << 30, chunk_steps=args.chunk,
+                                     chunk_ms=args.chunk_ms, storage=storage,
                                      max_resident=1024, with_velocity=0)
     if args.target_sites:
         opts.target_resident_sites = args.target_sites
@@ -599,7 +602,8 @@ def run_served(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"served: {len(reqs)} requests, Poisson 200/s, sides U{{128..2048}}, "
                                   f"steps U{{1000..50000}}/{args.step_scale}, droplet/band 50/50",
-                      "storage": args.storage, "chunk_steps": args.chunk, "site_steps": work,
+                      "storage": args.storage, "chunk_steps": args.chunk,
+                      "chunk_ms": args.chunk_ms, "site_steps": work,
                       "target_resident_sites": opts.target_resident_sites},
            "served": {"MLUPS": round(served, 1), "p50_s": round(pct(lat, 50), 4),
                       "p99_s": round(pct(lat, 99), 4), "wall_s": round(wall, 3),

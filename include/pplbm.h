@@ -246,20 +246,27 @@ int lbm_autotune(lbm_handle* h, int32_t repeats);
  * fit yet, whenever a slot and arena space (HBM footprint: both population
  * buffers at the arena's common pitch, plus psi) are free and the resident
  * sites stay below a target; a
- * chunk runs each lattice for min(chunk_steps, its remaining steps).  The
+ * chunk runs each lattice for min(k, its remaining steps), where k is the
+ * number of steps that fills about chunk_ms of GPU time at the throughput
+ * measured on earlier chunks (CUDA event timings), capped at chunk_steps.
+ * Short chunks keep admission and completion close to the request's own
+ * work when the GPU is lightly loaded.  The
  * worker keeps two chunks in flight: new requests' fields are uploaded
- * through pinned memory on their own stream while a chunk runs, the next
+ * from pinned memory on their own stream while a chunk runs, the next
  * chunk is queued before the previous one is retired, and a finished
- * lattice's moments are copied out (through pinned memory) while the next
- * chunk runs; its space is then reused.  One native worker thread drives
- * the GPU; the submit and poll calls are thread-safe and never wait for the
- * GPU.  The numerics of a request do not depend on what else is resident. */
+ * lattice's moments are copied out to pinned memory while the next chunk
+ * runs; its space is then reused.  lbm_submit copies the field into a
+ * pinned slot (on the caller's thread) when one is free, and lbm_poll
+ * copies the result from its pinned slot, so the worker thread that drives
+ * the GPU does no large host copies.  The submit and poll calls are
+ * thread-safe and never wait for the GPU.  The numerics of a request do not
+ * depend on what else is resident. */
 typedef struct lbm_server lbm_server;
 
 typedef struct {
     size_t arena_bytes;       /* device bytes for resident lattices (0: 8 GiB)    */
     int32_t max_resident;     /* resident lattices at most (0: 1024)              */
-    int32_t chunk_steps;      /* steps between admission points (0: 100)          */
+    int32_t chunk_steps;      /* most steps between admission points (0: 100)     */
     int64_t max_request_sites;/* largest nx*ny accepted (0: 2048*2048)            */
     int64_t target_resident_sites; /* admit while resident sites stay below this
                                  (0: 16 Mi); enough to keep the GPU busy,
@@ -278,13 +285,15 @@ typedef struct {
                                  width (its ny + 4 rows in each of 18 planes, a
                                  ninth of the arena for psi), so that one tensor
                                  map covers them all for the TMA single pass    */
+    double chunk_ms;          /* GPU time a chunk aims at (0: 4 ms; < 0: every
+                                 chunk runs chunk_steps steps)                   */
 } lbm_server_opts;
 
 typedef struct {
     int64_t submitted, completed, failed;
     int32_t queued, resident;
     int64_t site_steps;       /* lattice-site updates done                       */
-    double busy_s;            /* time the worker spent in GPU chunks             */
+    double busy_s;            /* GPU time of the chunks (CUDA event timings)     */
     int64_t arena_bytes, arena_in_use;
     int64_t launches;         /* kernels launched by the worker                  */
 } lbm_server_stats;

@@ -81,7 +81,7 @@ class ServerOpts(ctypes.Structure):
                 ("kernel_variant", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
                 ("sites_per_thread", ctypes.c_int32), ("with_velocity", ctypes.c_int32),
-                ("max_width", ctypes.c_int32)]
+                ("max_width", ctypes.c_int32), ("chunk_ms", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):

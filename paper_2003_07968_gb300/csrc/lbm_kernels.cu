@@ -329,13 +329,14 @@ __global__ void k_moments(LatDev L, const void* pop, int parity, const float* ps
         jy += kCy[i] * g[i];
     }
     const double rho = d + (double)L.rho0;
+    const int64_t s = (int64_t)y * nx + x;
+    if (rho_out) rho_out[s] = rho;
+    if (!ux_out && !uy_out) return;  // density only: no force, psi not read
     const float* c = psi_arena + L.off_psi + (int64_t)(y + GY) * L.pitch_psi + (x + L.gx_psi);
     const int W = L.pitch_psi;
     const float p[9] = {c[0], c[1], c[W], c[-1], c[-W], c[W + 1], c[W - 1], c[-W - 1], c[-W + 1]};
     float Fx, Fy;
     site_force(site_consts(L), p, Fx, Fy);
-    const int64_t s = (int64_t)y * nx + x;
-    if (rho_out) rho_out[s] = rho;
     if (ux_out) ux_out[s] = (jx + 0.5 * (double)Fx) / rho;
     if (uy_out) uy_out[s] = (jy + 0.5 * (double)Fy) / rho;
 }

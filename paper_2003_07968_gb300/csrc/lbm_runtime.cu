@@ -841,17 +841,21 @@ int lbm_moments(lbm_handle* h, int32_t lattice, double* rho, double* ux, double*
     if (rho || ux || uy) {
         int rc = ensure_staging(h, n);
         if (rc) return rc;
-        // psi of the current state for this lattice's tiles (all tiles: cheap
-        // relative to a D2H copy, and keeps one code path)
-        StepArgs a = step_args(h, h->parity, 0);
-        a.tiles = h->pass[0].tiles + h->pass[0].begin[lattice];
-        a.ntiles = h->pass[0].count[lattice];
-        CK(h, launch_pass(h, 0, a, std::min(h->pass[0].grid, a.ntiles)));
+        // velocities: psi of the current state for this lattice's tiles (the
+        // force-shifted u needs the force); density alone needs neither
+        if (ux || uy) {
+            StepArgs a = step_args(h, h->parity, 0);
+            a.tiles = h->pass[0].tiles + h->pass[0].begin[lattice];
+            a.ntiles = h->pass[0].count[lattice];
+            CK(h, launch_pass(h, 0, a, std::min(h->pass[0].grid, a.ntiles)));
+            h->launches += 1;
+        }
         double* dr = h->staging;
         double* dx = h->staging + h->staging_elems;
         double* dy = h->staging + 2 * h->staging_elems;
-        CK(h, launch_moments(h->f16, L, h->pop, h->parity, h->psi, dr, dx, dy, h->stream));
-        h->launches += 2;
+        CK(h, launch_moments(h->f16, L, h->pop, h->parity, h->psi, dr, (ux || uy) ? dx : nullptr,
+                             (ux || uy) ? dy : nullptr, h->stream));
+        h->launches += 1;
         if (rho) CK(h, cudaMemcpyAsync(rho, dr, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         if (ux) CK(h, cudaMemcpyAsync(ux, dx, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         if (uy) CK(h, cudaMemcpyAsync(uy, dy, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));

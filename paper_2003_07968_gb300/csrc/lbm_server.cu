@@ -6,24 +6,32 @@
 // fit) in each of 18 planes, so that one tensor map covers all resident
 // lattices and the single pass runs on the TMA kernel.
 //
-// One worker thread owns the GPU work and keeps two chunks in flight.  Each
-// turn of its loop:
-//   1. admit queued requests (first come first served, skipping those that
+// One worker thread owns the GPU work and keeps two chunks in flight; it
+// only enqueues work and waits for the GPU, so that short chunks keep the
+// GPU busy.  Large host copies happen elsewhere: lbm_submit copies a field
+// into a pinned input slot on the caller's thread, and lbm_poll copies a
+// result out of its pinned result slot.  Each turn of the loop:
+//   1. finish the requests whose copy-out is done and release the input
+//      slots whose upload is done;
+//   2. admit queued requests (first come first served, skipping those that
 //      do not fit yet) while a slot, arena space and the resident-site
-//      target allow; their initial fields go through a pinned upload buffer
+//      target allow; their fields go from their pinned slots to the device
 //      on the upload stream (overlapping the chunk in flight) and are
 //      initialised at equilibrium on the main stream;
-//   2. launch chunk n: rebuild one of two alternating table sets (lattice
-//      table, tile lists, per-lattice step quotas), one launch per step over
-//      the tile list of every resident lattice, each lattice running
-//      min(chunk_steps, its remaining steps) (the kernels skip the tiles of a
-//      lattice whose quota is used up).  Quotas are known on the host, so the
-//      lattices that finish in chunk n are known when it is launched and are
-//      not part of chunk n + 1;
-//   3. retire chunk n - 1 (which ran while the host did 1 and 2): read its
-//      fault words, copy out the lattices that finished in it (psi pass,
-//      moments, device to pinned host memory, on the side stream, while
-//      chunk n runs) and free their space.
+//   3. launch chunk n: update one of two alternating table sets (step
+//      quotas; lattice table and tile lists only when the resident lattices
+//      changed) through pinned mirrors, then one launch per step over the
+//      tile list of every resident lattice.  Each lattice runs min(k, its
+//      remaining steps), where k fills about chunk_ms of GPU time at the
+//      rate measured on earlier chunks (at most chunk_steps).  The kernels
+//      skip the tiles of a lattice whose quota is used up.  Quotas are known
+//      on the host, so the lattices that finish in chunk n are known when it
+//      is launched and are not part of chunk n + 1;
+//   4. retire chunk n - 1 (which ran while the host did 1-3): read its fault
+//      words and enqueue the copy-outs of the lattices that finished in it
+//      (moments, plus a psi pass when velocities are kept, device to pinned
+//      result slot, on the side stream while chunk n runs).  A request is
+//      done, and its arena space free, once its copy-out has completed.
 // A lattice whose fault bit shows up is dropped one chunk later than it
 // faulted (its extra chunk computes garbage that nobody reads).  Every
 // lattice still resident after a chunk has run all of its steps, so all
@@ -104,12 +112,16 @@ class ArenaAlloc {
 };
 
 enum { ST_QUEUED = 0, ST_RESIDENT = 1, ST_DONE = 2 };
+constexpr size_t kNoSlot = ~size_t(0);
 
 struct Request {
     uint64_t ticket = 0;
     lbm_lattice_desc d{};
-    std::vector<double> rho;  // initial field until admitted, then the result
+    std::vector<double> rho;  // initial field (no pinned slot) or result (no result slot)
     std::vector<double> ux, uy;
+    // pinned slots: the initial field (from submit until its upload is done)
+    // and the result (from its copy-out until it is polled), in doubles
+    size_t in_off = kNoSlot, in_n = 0, out_off = kNoSlot, out_n = 0;
     int64_t nsteps = 0, remaining = 0;
     int state = ST_QUEUED;
     int status = LBM_OK;
@@ -136,6 +148,22 @@ struct TableSet {
     size_t cap[2] = {0, 0};
     int ntiles[2] = {0, 0};
     std::vector<int> begin[2], count[2];
+    // tickets of the lattices (in table order) that the lattice table and
+    // tile lists describe; a chunk over the same lattices only rewrites the
+    // quotas.  Tickets, not addresses: a new request can occupy the memory of
+    // one that was polled
+    std::vector<uint64_t> members;
+    // pinned mirrors of the tables, so that their uploads are asynchronous
+    LatDev* lat_h = nullptr;
+    int* quota_h = nullptr;
+    int4* tiles_h[2] = {nullptr, nullptr};
+    size_t hcap[2] = {0, 0};
+};
+
+// A finished request whose copy-out is in flight on the side stream.
+struct Drain {
+    Request* R;
+    cudaEvent_t done;
 };
 
 }  // namespace
@@ -146,8 +174,11 @@ struct lbm_server {
     int fused = 1;  // one launch per step (LBM_SCHED_FUSED)
     cudaStream_t stream = nullptr, side = nullptr, up = nullptr;
     cudaEvent_t chunk_end[2] = {nullptr, nullptr};  // per table set: its last chunk is done
-    cudaEvent_t up_done = nullptr;    // the last uploads have read up_host
+    cudaEvent_t chunk_begin[2] = {nullptr, nullptr};  // ... and where its steps began (timing)
+    cudaEvent_t up_done = nullptr;    // the last uploads have read their pinned slots
     cudaEvent_t init_done = nullptr;  // the last inits have read staging
+    cudaEvent_t side_done[2] = {nullptr, nullptr};  // copy-outs reading a table set's tiles
+    std::vector<cudaEvent_t> spare_events;          // for copy-outs, reused
     // device arena: the population row space (every resident lattice with the
     // common pitch, its ny + 2 GY rows in each of 18 planes), then psi
     void* arena = nullptr;
@@ -156,15 +187,17 @@ struct lbm_server {
     size_t pop_bytes = 0, psi_region = 0;
     bool tma = false;      // single pass on the TMA kernel (one tensor map for the arena)
     CUtensorMap tmap[2]{};  // loads, stores
-    size_t up_cap = 0;            // doubles of the upload buffers
+    size_t up_cap = 0;            // doubles of the device staging buffer
     double* staging = nullptr;    // rho of the requests admitted in one turn (device)
-    double* up_host = nullptr;    // ... their pinned host copy
+    double* in_host = nullptr;    // pinned slots of initial fields (in_alloc, doubles)
+    double* out_host = nullptr;   // pinned slots of results (out_alloc, doubles)
     double* outbuf = nullptr;     // rho, ux, uy of one finished request (side stream)
-    double* down_host = nullptr;  // ... their pinned host copy
+    double* down_host = nullptr;  // ... pinned copy when no result slot is free
     uint32_t* status_host = nullptr;  // fault words of both table sets (pinned)
     PassState pass[2];
     TableSet set[2];
     ArenaAlloc rows_alloc, psi_alloc;
+    ArenaAlloc in_alloc, out_alloc;  // under mu: submit and poll use them too
     int parity = 0;
     // shared with the API threads
     std::mutex mu;
@@ -183,17 +216,27 @@ void free_server(lbm_server* S) {
     for (auto& T : S->set) {
         for (auto& t : T.tiles)
             if (t) cudaFree(t);
+        for (auto& t : T.tiles_h)
+            if (t) cudaFreeHost(t);
         if (T.lat) cudaFree(T.lat);
         if (T.quota) cudaFree(T.quota);
         if (T.status) cudaFree(T.status);
+        if (T.lat_h) cudaFreeHost(T.lat_h);
+        if (T.quota_h) cudaFreeHost(T.quota_h);
     }
     if (S->status_host) cudaFreeHost(S->status_host);
     if (S->down_host) cudaFreeHost(S->down_host);
-    if (S->up_host) cudaFreeHost(S->up_host);
+    if (S->in_host) cudaFreeHost(S->in_host);
+    if (S->out_host) cudaFreeHost(S->out_host);
+    for (auto& e : S->spare_events) cudaEventDestroy(e);
+    for (auto& e : S->side_done)
+        if (e) cudaEventDestroy(e);
     if (S->outbuf) cudaFree(S->outbuf);
     if (S->staging) cudaFree(S->staging);
     if (S->arena) cudaFree(S->arena);
     for (auto& e : S->chunk_end)
+        if (e) cudaEventDestroy(e);
+    for (auto& e : S->chunk_begin)
         if (e) cudaEventDestroy(e);
     if (S->up_done) cudaEventDestroy(S->up_done);
     if (S->init_done) cudaEventDestroy(S->init_done);
@@ -244,40 +287,41 @@ StepArgs args(lbm_server* S, const TableSet& T, int k, int parity) {
     return a;
 }
 
-// Fill table set T from the resident requests with their chunk quotas.
+// Fill table set T from the resident requests with their chunk quotas,
+// through its pinned mirrors (the caller has waited for the set's previous
+// chunk, so the mirrors' last uploads are done).
 cudaError_t rebuild(lbm_server* S, TableSet& T, std::vector<Request*>& res,
                     const std::vector<int>& quota) {
-    std::vector<LatDev> lats(res.size());
-    for (size_t i = 0; i < res.size(); ++i) {
-        res[i]->L.lattice = (int)i;
-        lats[i] = res[i]->L;
-    }
+    std::vector<uint64_t> members(res.size());
+    for (size_t i = 0; i < res.size(); ++i) members[i] = res[i]->ticket;
     cudaError_t e = cudaSuccess;
-    if (!lats.empty()) {
-        e = cudaMemcpyAsync(T.lat, lats.data(), lats.size() * sizeof(LatDev),
+    if (!res.empty()) {
+        std::memcpy(T.quota_h, quota.data(), quota.size() * sizeof(int));
+        e = cudaMemcpyAsync(T.quota, T.quota_h, quota.size() * sizeof(int),
                             cudaMemcpyHostToDevice, S->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(T.quota, quota.data(), quota.size() * sizeof(int),
-                                cudaMemcpyHostToDevice, S->stream);
         if (e == cudaSuccess)
             e = cudaMemsetAsync(T.status, 0, res.size() * sizeof(uint32_t), S->stream);
     }
+    // same lattices in the same order: lattice table and tile lists stand
+    if (e != cudaSuccess || (!res.empty() && members == T.members)) return e;
+    T.members.clear();
+    for (size_t i = 0; i < res.size(); ++i) {
+        res[i]->L.lattice = (int)i;
+        T.lat_h[i] = res[i]->L;
+    }
+    if (!res.empty())
+        e = cudaMemcpyAsync(T.lat, T.lat_h, res.size() * sizeof(LatDev), cudaMemcpyHostToDevice,
+                            S->stream);
     if (e != cudaSuccess) return e;
     for (int k = 0; k < 2; ++k) {
         const PassState& P = S->pass[k];
-        std::vector<int4> t;
-        T.begin[k].assign(res.size(), 0);
-        T.count[k].assign(res.size(), 0);
-        for (size_t l = 0; l < res.size(); ++l) {
-            T.begin[k][l] = (int)t.size();
-            for (int y0 = 0; y0 < lats[l].ny; y0 += P.ty)
-                for (int x0 = 0; x0 < lats[l].nx; x0 += P.tx) t.push_back(make_int4((int)l, x0, y0, 0));
-            T.count[k][l] = (int)t.size() - T.begin[k][l];
-        }
-        const size_t bytes = t.size() * sizeof(int4);
+        size_t nt = 0;
+        for (Request* R : res)
+            nt += (size_t)((R->L.nx + P.tx - 1) / P.tx) * ((R->L.ny + P.ty - 1) / P.ty);
+        const size_t bytes = nt * sizeof(int4);
         if (bytes > T.cap[k]) {
             if (T.tiles[k]) {
-                cudaDeviceSynchronize();
+                cudaDeviceSynchronize();  // no kernel or copy-out still reads the old list
                 cudaFree(T.tiles[k]);
             }
             T.tiles[k] = nullptr;
@@ -287,48 +331,91 @@ cudaError_t rebuild(lbm_server* S, TableSet& T, std::vector<Request*>& res,
             if (e != cudaSuccess) return e;
             T.cap[k] = cap;
         }
-        // pageable source: the copy has finished reading `t` when the call returns
-        if (bytes) e = cudaMemcpyAsync(T.tiles[k], t.data(), bytes, cudaMemcpyHostToDevice, S->stream);
+        if (bytes > T.hcap[k]) {
+            if (T.tiles_h[k]) cudaFreeHost(T.tiles_h[k]);
+            T.tiles_h[k] = nullptr;
+            T.hcap[k] = 0;
+            e = cudaMallocHost(&T.tiles_h[k], T.cap[k]);
+            if (e != cudaSuccess) return e;
+            T.hcap[k] = T.cap[k];
+        }
+        int4* t = T.tiles_h[k];
+        size_t m = 0;
+        T.begin[k].assign(res.size(), 0);
+        T.count[k].assign(res.size(), 0);
+        for (size_t l = 0; l < res.size(); ++l) {
+            T.begin[k][l] = (int)m;
+            for (int y0 = 0; y0 < res[l]->L.ny; y0 += P.ty)
+                for (int x0 = 0; x0 < res[l]->L.nx; x0 += P.tx) t[m++] = make_int4((int)l, x0, y0, 0);
+            T.count[k][l] = (int)m - T.begin[k][l];
+        }
+        if (bytes)
+            e = cudaMemcpyAsync(T.tiles[k], t, bytes, cudaMemcpyHostToDevice, S->stream);
         if (e != cudaSuccess) return e;
-        T.ntiles[k] = (int)t.size();
+        T.ntiles[k] = (int)nt;
+    }
+    T.members = members;
+    return cudaSuccess;
+}
+
+// Enqueue on the side stream the moments of lattice l of set T (final
+// parity `par`) into the pinned host doubles at `host` (rho, then ux and uy
+// with the server's with_velocity option): psi pass (velocities only: the
+// force-shifted u needs psi), moments into the device buffer, device to
+// host.  The side stream serialises the copy-outs over the one buffer.
+cudaError_t enqueue_copy_out(lbm_server* S, const TableSet& T, const Request& R, int l, int par,
+                             double* host) {
+    const bool vel = S->o.with_velocity != 0;
+    cudaError_t e = cudaSuccess;
+    if (vel) {
+        StepArgs a = args(S, T, 0, par);
+        a.tiles = T.tiles[0] + T.begin[0][l];
+        a.ntiles = T.count[0][l];
+        a.quota = nullptr;
+        e = launch(S, 0, a, pass_grid(S, 0, a.ntiles), S->side);
+        if (e != cudaSuccess) return e;
+    }
+    const size_t n = (size_t)R.L.nx * R.L.ny;
+    double* dr = S->outbuf;
+    double* dx = dr + S->o.max_request_sites;
+    double* dy = dx + S->o.max_request_sites;
+    e = launch_moments(S->f16, R.L, S->arena, par, S->psi_arena, dr, vel ? dx : nullptr,
+                       vel ? dy : nullptr, S->side);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host, dr, n * sizeof(double), cudaMemcpyDeviceToHost, S->side);
+    if (e == cudaSuccess && vel)
+        e = cudaMemcpyAsync(host + n, dx, n * sizeof(double), cudaMemcpyDeviceToHost, S->side);
+    if (e == cudaSuccess && vel)
+        e = cudaMemcpyAsync(host + 2 * n, dy, n * sizeof(double), cudaMemcpyDeviceToHost,
+                            S->side);
+    return e;
+}
+
+// When no result slot is free: the same copy-out through the one pinned
+// buffer, waited for, into R's vectors.
+cudaError_t copy_out_now(lbm_server* S, const TableSet& T, Request& R, int l, int par) {
+    cudaError_t e = enqueue_copy_out(S, T, R, l, par, S->down_host);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->side);
+    if (e != cudaSuccess) return e;
+    const size_t n = (size_t)R.L.nx * R.L.ny;
+    const double* h = S->down_host;
+    R.rho.assign(h, h + n);
+    if (S->o.with_velocity) {
+        R.ux.assign(h + n, h + 2 * n);
+        R.uy.assign(h + 2 * n, h + 3 * n);
     }
     return cudaSuccess;
 }
 
-// Moments of lattice l of set T (final parity `par`) into R, on the side
-// stream after the chunk that finished it: device -> pinned host buffer ->
-// R (velocities only with the server's with_velocity option).
-cudaError_t copy_out(lbm_server* S, const TableSet& T, Request& R, int l, int par) {
-    StepArgs a = args(S, T, 0, par);
-    a.tiles = T.tiles[0] + T.begin[0][l];
-    a.ntiles = T.count[0][l];
-    a.quota = nullptr;
-    cudaError_t e = launch(S, 0, a, pass_grid(S, 0, a.ntiles), S->side);
-    if (e != cudaSuccess) return e;
-    const size_t n = (size_t)R.L.nx * R.L.ny;
-    const bool vel = S->o.with_velocity != 0;
-    double* dr = S->outbuf;
-    double* dx = dr + S->o.max_request_sites;
-    double* dy = dx + S->o.max_request_sites;
-    e = launch_moments(S->f16, R.L, S->arena, par, S->psi_arena, dr,
-                       vel ? dx : nullptr, vel ? dy : nullptr, S->side);
-    if (e != cudaSuccess) return e;
-    double* hr = S->down_host;
-    double* hx = hr + S->o.max_request_sites;
-    double* hy = hx + S->o.max_request_sites;
-    e = cudaMemcpyAsync(hr, dr, n * sizeof(double), cudaMemcpyDeviceToHost, S->side);
-    if (e == cudaSuccess && vel)
-        e = cudaMemcpyAsync(hx, dx, n * sizeof(double), cudaMemcpyDeviceToHost, S->side);
-    if (e == cudaSuccess && vel)
-        e = cudaMemcpyAsync(hy, dy, n * sizeof(double), cudaMemcpyDeviceToHost, S->side);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(S->side);
-    if (e != cudaSuccess) return e;
-    R.rho.assign(hr, hr + n);
-    if (vel) {
-        R.ux.assign(hx, hx + n);
-        R.uy.assign(hy, hy + n);
+cudaEvent_t take_event(lbm_server* S) {
+    if (!S->spare_events.empty()) {
+        cudaEvent_t e = S->spare_events.back();
+        S->spare_events.pop_back();
+        return e;
     }
-    return cudaSuccess;
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    return e;
 }
 
 void fail_all(lbm_server* S, int status) {
@@ -358,7 +445,6 @@ struct Chunk {
     int p0 = 0;                      // buffer parity at its start
     std::vector<Finished> finished;  // ran their last steps in it
     std::vector<Request*> dropped;   // faulted earlier, still part of it: free once it is done
-    Clock::time_point t0;
 };
 
 int64_t arena_in_use(const lbm_server* S) {
@@ -383,22 +469,60 @@ void finish(lbm_server* S, Request* R, int status) {
 void worker_main(lbm_server* S) {
     cudaSetDevice(S->device);
     std::vector<Request*> res;  // resident and still to run (host view)
-    int64_t res_sites = 0;      // sites held in the arena by resident lattices
+    int64_t res_sites = 0;      // sites of the resident lattices still running
     Chunk chunk[2];
     int64_t n = 0;              // chunks launched
+    // site updates per second of the chunks so far (CUDA event timings); the
+    // first chunks assume a modest rate, so they come out short
+    double rate = 2e10;
+    std::deque<Drain> drain;                       // copy-outs in flight, in order
+    std::vector<std::pair<size_t, size_t>> in_pending;  // input slots being uploaded
+    // finish the requests whose copy-out is done, release uploaded input slots
+    auto settle = [&]() -> cudaError_t {
+        while (!drain.empty()) {
+            const cudaError_t q = cudaEventQuery(drain.front().done);
+            if (q == cudaErrorNotReady) break;
+            if (q != cudaSuccess) return q;
+            S->spare_events.push_back(drain.front().done);
+            finish(S, drain.front().R, LBM_OK);
+            drain.pop_front();
+        }
+        if (!in_pending.empty()) {
+            const cudaError_t q = cudaEventQuery(S->up_done);
+            if (q == cudaSuccess) {
+                std::lock_guard<std::mutex> lk(S->mu);
+                for (auto& sl : in_pending) S->in_alloc.release(sl.first, sl.second);
+                in_pending.clear();
+            } else if (q != cudaErrorNotReady) {
+                return q;
+            }
+        }
+        return cudaSuccess;
+    };
     for (;;) {
+        cudaError_t e = settle();
         // ------------------------------------------------------------ admission
-        std::vector<Request*> admitted;
+        std::vector<Request*> admitted, to_stage;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             if (S->stop) break;
             if (res.empty() && S->queue.empty() && !chunk[0].live && !chunk[1].live) {
-                S->cv.wait_for(lk, std::chrono::milliseconds(20));
+                if (drain.empty() && in_pending.empty()) {
+                    S->cv.wait_for(lk, std::chrono::milliseconds(20));
+                    continue;
+                }
+                // only copy-outs or uploads in flight: wait for the oldest
+                lk.unlock();
+                if (!drain.empty())
+                    cudaEventSynchronize(drain.front().done);
+                else
+                    cudaEventSynchronize(S->up_done);
                 continue;
             }
             // first come first served, skipping requests that do not fit yet,
-            // while slots, arena space, the resident-site target and the upload
-            // buffer allow (one request is always admitted into an idle GPU)
+            // while slots, arena space, the resident-site target and the
+            // staging buffer allow (one request is always admitted into an
+            // idle GPU); a field without a pinned slot gets one here
             size_t up_used = 0;
             for (auto it = S->queue.begin(); it != S->queue.end();) {
                 if ((int)(res.size() + admitted.size()) >= S->o.max_resident) break;
@@ -408,9 +532,20 @@ void worker_main(lbm_server* S) {
                 if (res_sites + ns > S->o.target_resident_sites && (res_sites > 0 || !admitted.empty()))
                     break;
                 if (up_used + nup > S->up_cap) break;
+                const bool stage = R.in_off == kNoSlot;
+                size_t io = 0;
+                if (stage && !S->in_alloc.alloc((size_t)ns, &io)) {
+                    ++it;
+                    continue;
+                }
                 size_t po = 0, qo = 0;
                 if (S->rows_alloc.alloc(R.rows, &po)) {
                     if (S->psi_alloc.alloc(R.psi_bytes, &qo)) {
+                        if (stage) {
+                            R.in_off = io;
+                            R.in_n = (size_t)ns;
+                            to_stage.push_back(&R);
+                        }
                         R.row_off = po;
                         R.psi_off = qo;
                         R.stage_off = up_used;
@@ -423,26 +558,28 @@ void worker_main(lbm_server* S) {
                     }
                     S->rows_alloc.release(po, R.rows);
                 }
+                if (stage) S->in_alloc.release(io, (size_t)ns);
                 ++it;
             }
             S->st.queued = (int)S->queue.size();
             S->st.arena_in_use = arena_in_use(S);
         }
-        cudaError_t e = cudaSuccess;
         int64_t launches = 0;
-        if (!admitted.empty()) {
-            // the previous uploads have read up_host, the previous inits staging
-            e = cudaEventSynchronize(S->up_done);
-            size_t total = 0;
-            for (Request* R : admitted) {
-                const size_t ns = (size_t)R->L.nx * R->L.ny;
-                std::memcpy(S->up_host + R->stage_off, R->rho.data(), ns * sizeof(double));
-                total = std::max(total, R->stage_off + ns);
+        if (e == cudaSuccess && !admitted.empty()) {
+            // fields that arrived while the pinned slots were full
+            for (Request* R : to_stage) {
+                std::memcpy(S->in_host + R->in_off, R->rho.data(), R->in_n * sizeof(double));
+                std::vector<double>().swap(R->rho);
             }
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(S->up, S->init_done, 0);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(S->staging, S->up_host, total * sizeof(double),
-                                    cudaMemcpyHostToDevice, S->up);
+            // the previous inits have read the staging buffer
+            e = cudaStreamWaitEvent(S->up, S->init_done, 0);
+            for (Request* R : admitted) {
+                if (e != cudaSuccess) break;
+                e = cudaMemcpyAsync(S->staging + R->stage_off, S->in_host + R->in_off,
+                                    R->in_n * sizeof(double), cudaMemcpyHostToDevice, S->up);
+                in_pending.emplace_back(R->in_off, R->in_n);
+                R->in_off = kNoSlot;  // the slot now belongs to in_pending
+            }
             if (e == cudaSuccess) e = cudaEventRecord(S->up_done, S->up);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(S->stream, S->up_done, 0);
             for (Request* R : admitted) {
@@ -453,13 +590,9 @@ void worker_main(lbm_server* S) {
                 R->L.off_f[0] = (int64_t)R->row_off * S->pitch;
                 R->L.off_f[1] = R->L.off_f[0] + 9 * S->plane;
                 R->L.off_psi = (int64_t)(R->psi_off / 4);
-                const size_t ns = (size_t)R->L.nx * R->L.ny;
-                if (R->d.storage != LBM_STORE_F32 && R->d.rho0 < 0.0)
-                    R->L.rho0 = auto_rho0(R->rho.data(), ns);
                 e = launch_init(S->f16, R->L, S->arena, S->parity, S->staging + R->stage_off,
                                 nullptr, nullptr, S->stream);
                 launches += 1;
-                std::vector<double>().swap(R->rho);
                 res.push_back(R);
             }
             if (e == cudaSuccess) e = cudaEventRecord(S->init_done, S->stream);
@@ -468,18 +601,26 @@ void worker_main(lbm_server* S) {
         const int cur = (int)(n & 1);
         if (e == cudaSuccess && !res.empty()) {
             Chunk& C = chunk[cur];
-            // the table set's previous chunk (n - 2) and its copy-outs are done
+            // the table set's previous chunk (n - 2) is done; its tile lists
+            // are rewritten on the GPU after the copy-outs that read them
             e = cudaEventSynchronize(S->chunk_end[cur]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(S->stream, S->side_done[cur], 0);
             C = Chunk{};
             C.live = true;
             C.res = res;
             C.p0 = S->parity;
-            C.t0 = Clock::now();
             C.quota.resize(res.size());
+            // steps of this chunk: about chunk_ms of GPU time over the
+            // resident sites, at most chunk_steps
+            int64_t steps = S->o.chunk_steps;
+            if (S->o.chunk_ms > 0.0) {
+                const double fit = S->o.chunk_ms * 1e-3 * rate / (double)std::max<int64_t>(res_sites, 1);
+                steps = std::max<int64_t>(1, std::min<int64_t>(steps, (int64_t)fit));
+            }
             int64_t k = 0;
             std::vector<Request*> keep;
             for (size_t l = 0; l < res.size(); ++l) {
-                C.quota[l] = (int)std::min<int64_t>(S->o.chunk_steps, res[l]->remaining);
+                C.quota[l] = (int)std::min<int64_t>(steps, res[l]->remaining);
                 k = std::max<int64_t>(k, C.quota[l]);
                 res[l]->remaining -= C.quota[l];
                 if (res[l]->remaining > 0)
@@ -489,10 +630,11 @@ void worker_main(lbm_server* S) {
             }
             TableSet& T = S->set[cur];
             if (e == cudaSuccess) e = rebuild(S, T, C.res, C.quota);
+            if (e == cudaSuccess) e = cudaEventRecord(S->chunk_begin[cur], S->stream);
             const int g0 = pass_grid(S, 0, T.ntiles[0]), g1 = pass_grid(S, 1, T.ntiles[1]);
-            for (int64_t s = 0; s < k && e == cudaSuccess; ++s) {
+            for (int64_t st = 0; st < k && e == cudaSuccess; ++st) {
                 StepArgs a0 = args(S, T, 0, S->parity), a1 = args(S, T, 1, S->parity);
-                a0.step = a1.step = (int)s;
+                a0.step = a1.step = (int)st;
                 if (!S->fused) e = launch(S, 0, a0, g0, S->stream);
                 if (e == cudaSuccess) e = launch(S, 1, a1, g1, S->stream);
                 launches += S->fused ? 1 : 2;
@@ -503,13 +645,24 @@ void worker_main(lbm_server* S) {
                                     C.res.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost,
                                     S->stream);
             if (e == cudaSuccess) e = cudaEventRecord(S->chunk_end[cur], S->stream);
+            for (const Finished& f : C.finished) res_sites -= (int64_t)f.R->L.nx * f.R->L.ny;
             res.swap(keep);
             ++n;
         }
         // ------------------------------------------------------------ retire n - 1
         Chunk& P = chunk[cur ^ 1];
         if (e == cudaSuccess && P.live) {
-            e = cudaEventSynchronize(S->chunk_end[cur ^ 1]);
+            // copy-outs in flight end before the chunk does: finish their
+            // requests as they complete, then wait for the chunk
+            while (e == cudaSuccess && !drain.empty() &&
+                   cudaEventQuery(S->chunk_end[cur ^ 1]) == cudaErrorNotReady) {
+                e = cudaEventSynchronize(drain.front().done);
+                if (e == cudaSuccess) e = settle();
+            }
+            if (e == cudaSuccess) e = cudaEventSynchronize(S->chunk_end[cur ^ 1]);
+            float gpu_ms = 0.f;
+            if (e == cudaSuccess)
+                e = cudaEventElapsedTime(&gpu_ms, S->chunk_begin[cur ^ 1], S->chunk_end[cur ^ 1]);
             const uint32_t* bits = S->status_host + (cur ^ 1) * S->o.max_resident;
             int64_t done_sites = 0;
             std::vector<Request*> failed_now;
@@ -538,32 +691,61 @@ void worker_main(lbm_server* S) {
                         }
                 if (fin_n) continue;
                 res.erase(std::remove(res.begin(), res.end(), R), res.end());
+                res_sites -= (int64_t)R->L.nx * R->L.ny;
                 if (Cn.live)
                     Cn.dropped.push_back(R);  // freed once chunk n is done
                 else
                     failed_now.push_back(R);
             }
+            // copy-outs into pinned result slots, in flight on the side stream
+            // while chunk n runs; a request is done when its copy-out is
+            const size_t comps = S->o.with_velocity ? 3 : 1;
             for (Finished& f : P.finished) {
                 int status = f.status;
                 if (status == LBM_OK && e == cudaSuccess) {
-                    e = copy_out(S, S->set[cur ^ 1], *f.R, f.l, f.par);
-                    if (e != cudaSuccess) status = LBM_ERR_CUDA;
-                    launches += 2;
+                    const size_t need = comps * (size_t)f.R->L.nx * f.R->L.ny;
+                    size_t off = 0;
+                    bool slot;
+                    {
+                        std::lock_guard<std::mutex> lk(S->mu);
+                        slot = S->out_alloc.alloc(need, &off);
+                    }
+                    cudaEvent_t ev = slot ? take_event(S) : nullptr;
+                    if (slot && ev) {
+                        f.R->out_off = off;
+                        f.R->out_n = need;
+                        e = enqueue_copy_out(S, S->set[cur ^ 1], *f.R, f.l, f.par,
+                                             S->out_host + off);
+                        if (e == cudaSuccess) e = cudaEventRecord(ev, S->side);
+                        launches += S->o.with_velocity ? 2 : 1;
+                        if (e == cudaSuccess) {
+                            drain.push_back(Drain{f.R, ev});
+                            continue;
+                        }
+                        S->spare_events.push_back(ev);
+                        status = LBM_ERR_CUDA;
+                    } else {
+                        if (slot) {
+                            std::lock_guard<std::mutex> lk(S->mu);
+                            S->out_alloc.release(off, need);
+                        }
+                        e = copy_out_now(S, S->set[cur ^ 1], *f.R, f.l, f.par);
+                        launches += S->o.with_velocity ? 2 : 1;
+                        if (e != cudaSuccess) status = LBM_ERR_CUDA;
+                    }
                 }
-                res_sites -= (int64_t)f.R->L.nx * f.R->L.ny;
                 finish(S, f.R, status);
             }
-            for (Request* R : P.dropped) {
-                res_sites -= (int64_t)R->L.nx * R->L.ny;
-                finish(S, R, R->status);
-            }
-            for (Request* R : failed_now) {
-                res_sites -= (int64_t)R->L.nx * R->L.ny;
-                finish(S, R, R->status);
+            if (e == cudaSuccess) e = cudaEventRecord(S->side_done[cur ^ 1], S->side);
+            for (Request* R : P.dropped) finish(S, R, R->status);
+            for (Request* R : failed_now) finish(S, R, R->status);
+            if (gpu_ms > 0.f && done_sites > 0) {
+                const double r = (double)done_sites / (gpu_ms * 1e-3);
+                rate = 0.7 * rate + 0.3 * r;
             }
             std::lock_guard<std::mutex> lk(S->mu);
             S->st.site_steps += done_sites;
-            S->st.busy_s += std::chrono::duration<double>(Clock::now() - P.t0).count();
+            S->st.busy_s += gpu_ms * 1e-3;
             S->st.resident = (int)res.size();
             P.live = false;
         }
@@ -574,14 +756,29 @@ void worker_main(lbm_server* S) {
         if (e != cudaSuccess) {
             cudaStreamSynchronize(S->stream);
             cudaStreamSynchronize(S->side);
+            cudaStreamSynchronize(S->up);
+            // copy-outs in flight keep their result slots (released by poll)
+            for (Drain& d : drain) S->spare_events.push_back(d.done);
+            drain.clear();
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                for (auto& sl : in_pending) S->in_alloc.release(sl.first, sl.second);
+                in_pending.clear();
+            }
             fail_all(S, LBM_ERR_CUDA);
             res.clear();
             res_sites = 0;
             chunk[0] = Chunk{};
             chunk[1] = Chunk{};
+            S->set[0].members.clear();
+            S->set[1].members.clear();
             continue;
         }
     }
+    // stopping: wait for the copies in flight, keep their events for reuse
+    cudaStreamSynchronize(S->side);
+    cudaStreamSynchronize(S->up);
+    for (Drain& d : drain) S->spare_events.push_back(d.done);
 }
 
 }  // namespace
@@ -601,6 +798,7 @@ void lbm_server_opts_default(lbm_server_opts* o) {
     o->kernel_variant = LBM_KERNEL_AUTO;
     o->with_velocity = 1;
     o->max_width = 2048;
+    o->chunk_ms = 4.0;
 }
 
 int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
@@ -617,6 +815,7 @@ int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
         if (!o.max_request_sites) o.max_request_sites = d.max_request_sites;
         if (!o.target_resident_sites) o.target_resident_sites = d.target_resident_sites;
         if (!o.max_width) o.max_width = d.max_width;
+        if (o.chunk_ms == 0.0) o.chunk_ms = d.chunk_ms;
     }
     if (o.max_resident < 1 || o.chunk_steps < 1 || o.max_request_sites < 4 ||
         o.target_resident_sites < 1 || o.storage < LBM_STORE_F32 ||
@@ -671,10 +870,14 @@ int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
         cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&S->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&S->up, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&S->chunk_end[0], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&S->chunk_end[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&S->chunk_end[0]) != cudaSuccess ||
+        cudaEventCreate(&S->chunk_end[1]) != cudaSuccess ||
+        cudaEventCreate(&S->chunk_begin[0]) != cudaSuccess ||
+        cudaEventCreate(&S->chunk_begin[1]) != cudaSuccess ||
         cudaEventCreateWithFlags(&S->up_done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&S->init_done, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&S->init_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S->side_done[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S->side_done[1], cudaEventDisableTiming) != cudaSuccess)
         return fail(LBM_ERR_CUDA);
     const size_t nmax = (size_t)o.max_request_sites;
     // one turn admits at most the resident-site target plus one request
@@ -695,9 +898,16 @@ int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
         if (S->row_cap < 1) return fail(LBM_ERR_ARG);
         S->pop_bytes = (size_t)(18 * S->plane * S->es);
     }
+    // pinned slots for fields waiting to be uploaded and results waiting to
+    // be polled: room for the staging buffer's worth of sites and one more
+    // request, or for everything the arena can hold if that is less
+    const size_t arena_sites = (size_t)S->row_cap * (size_t)o.max_width;
+    const size_t slot_sites = std::min(S->up_cap, arena_sites) + (size_t)round_up((int64_t)nmax, 32);
+    const size_t out_sites = slot_sites * (o.with_velocity ? 3 : 1);
     bool ok = cudaMalloc(&S->arena, o.arena_bytes) == cudaSuccess &&
               cudaMalloc(&S->staging, S->up_cap * sizeof(double)) == cudaSuccess &&
-              cudaMallocHost(&S->up_host, S->up_cap * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost(&S->in_host, slot_sites * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost(&S->out_host, out_sites * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&S->outbuf, 3 * nmax * sizeof(double)) == cudaSuccess &&
               cudaMallocHost(&S->down_host, 3 * nmax * sizeof(double)) == cudaSuccess &&
               cudaMallocHost(&S->status_host, 2 * (size_t)o.max_resident * sizeof(uint32_t)) ==
@@ -705,7 +915,9 @@ int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
     for (auto& T : S->set)
         ok = ok && cudaMalloc(&T.lat, (size_t)o.max_resident * sizeof(LatDev)) == cudaSuccess &&
              cudaMalloc(&T.quota, (size_t)o.max_resident * sizeof(int)) == cudaSuccess &&
-             cudaMalloc(&T.status, (size_t)o.max_resident * sizeof(uint32_t)) == cudaSuccess;
+             cudaMalloc(&T.status, (size_t)o.max_resident * sizeof(uint32_t)) == cudaSuccess &&
+             cudaMallocHost(&T.lat_h, (size_t)o.max_resident * sizeof(LatDev)) == cudaSuccess &&
+             cudaMallocHost(&T.quota_h, (size_t)o.max_resident * sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         return fail(LBM_ERR_OOM);
@@ -714,6 +926,8 @@ int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
     S->psi_arena = reinterpret_cast<float*>(static_cast<char*>(S->arena) + S->pop_bytes);
     S->rows_alloc.reset((size_t)S->row_cap, 1);
     S->psi_alloc.reset(o.arena_bytes - S->pop_bytes);
+    S->in_alloc.reset(slot_sites, 32);
+    S->out_alloc.reset(out_sites, 32);
     // one tensor map for the whole row space (all resident requests)
     if (want_tma)
         S->tma = fused_tma_make_space_map(S->f16, S->pass[1].tx, S->pass[1].ty, S->pitch,
@@ -754,11 +968,29 @@ int lbm_submit(lbm_server* S, const lbm_lattice_desc* d, const double* rho, int6
     if ((int64_t)R.rows > S->row_cap ||
         (size_t)round_up((int64_t)R.psi_bytes, 256) > S->o.arena_bytes - S->pop_bytes)
         return LBM_ERR_CAPACITY;
-    R.rho.assign(rho, rho + n);
+    if (R.d.storage != LBM_STORE_F32 && R.d.rho0 < 0.0) R.L.rho0 = auto_rho0(rho, n);
+    // the field goes to a pinned slot when one is free (the copy runs on the
+    // caller's thread), else to the heap until the worker stages it
+    size_t off = 0;
+    bool slot;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        slot = S->in_alloc.alloc(n, &off);
+    }
+    if (slot) {
+        std::memcpy(S->in_host + off, rho, n * sizeof(double));
+        R.in_off = off;
+        R.in_n = n;
+    } else {
+        R.rho.assign(rho, rho + n);
+    }
     R.nsteps = R.remaining = nsteps;
     R.t_submit = Clock::now();
     std::lock_guard<std::mutex> lk(S->mu);
-    if (S->stop) return LBM_ERR_STATE;
+    if (S->stop) {
+        if (slot) S->in_alloc.release(off, n);
+        return LBM_ERR_STATE;
+    }
     R.ticket = S->next_ticket++;
     *ticket = R.ticket;
     S->queue.push_back(R.ticket);
@@ -779,20 +1011,32 @@ int lbm_poll(lbm_server* S, uint64_t ticket, double* rho, double* ux, double* uy
     if (R.state != ST_DONE) return LBM_PENDING;
     const int status = R.status;
     if (status == LBM_OK) {
-        const size_t n = R.rho.size();
-        if (rho) std::memcpy(rho, R.rho.data(), n * sizeof(double));
+        const size_t n = (size_t)R.L.nx * R.L.ny;
+        const bool vel = S->o.with_velocity != 0;
+        // the result is in its pinned slot, or (no slot was free) in R's vectors
+        const double* src[3] = {R.rho.data(), R.ux.data(), R.uy.data()};
+        if (R.out_off != kNoSlot) {
+            const double* h = S->out_host + R.out_off;
+            src[0] = h;
+            src[1] = vel ? h + n : nullptr;
+            src[2] = vel ? h + 2 * n : nullptr;
+        } else if (!vel) {
+            src[1] = src[2] = nullptr;
+        }
+        if (rho) std::memcpy(rho, src[0], n * sizeof(double));
         // without with_velocity the server keeps no velocities: NaN
-        for (int c = 0; c < 2; ++c) {
-            double* dst = c ? uy : ux;
-            const std::vector<double>& src = c ? R.uy : R.ux;
+        for (int c = 1; c < 3; ++c) {
+            double* dst = c == 1 ? ux : uy;
             if (!dst) continue;
-            if (src.size() == n)
-                std::memcpy(dst, src.data(), n * sizeof(double));
+            if (src[c])
+                std::memcpy(dst, src[c], n * sizeof(double));
             else
                 std::fill(dst, dst + n, std::numeric_limits<double>::quiet_NaN());
         }
     }
     if (latency_s) *latency_s = std::chrono::duration<double>(R.t_done - R.t_submit).count();
+    if (R.out_off != kNoSlot) S->out_alloc.release(R.out_off, R.out_n);
+    if (R.in_off != kNoSlot) S->in_alloc.release(R.in_off, R.in_n);
     S->reqs.erase(it);
     return status;
 }

@@ -53,7 +53,9 @@ def wait(P, srv, tickets, timeout=120.0):
 
 
 def test_served_results_equal_alone_runs(P):
-    opts = P.lbm_server_opts_default(arena_bytes=1 << 30, chunk_steps=37,
+    # fixed chunks of 37 steps (chunk_ms < 0); the other tests run chunks
+    # sized by GPU time, of varying length
+    opts = P.lbm_server_opts_default(arena_bytes=1 << 30, chunk_steps=37, chunk_ms=-1.0,
                                      kernel_variant=P.LBM_KERNEL_PLAIN, tile_x=TILE[0],
                                      tile_y=TILE[1])
     srv = P.lbm_server_create(opts)
@@ -157,3 +159,29 @@ def test_tma_server_results_equal_plain_alone_runs(P):
         a = alone(P, d, rho, n)
         assert np.array_equal(res[t]["rho"], a["rho"]), (d.nx, d.ny)
         assert np.array_equal(res[t]["ux"], a["ux"])
+
+
+def test_requests_in_turn_get_their_own_tables(P):
+    # one request at a time, each polled before the next is submitted: a new
+    # request then often occupies the memory of the one just polled, and the
+    # server must still build its lattice table and tile lists (they are
+    # reused only for the same tickets in the same order).  Shapes alternate
+    # so that stale tables would step the wrong geometry.
+    opts = P.lbm_server_opts_default(arena_bytes=1 << 28, chunk_steps=16,
+                                     kernel_variant=P.LBM_KERNEL_PLAIN, tile_x=TILE[0],
+                                     tile_y=TILE[1])
+    srv = P.lbm_server_create(opts)
+    shapes = [(40, 36, 10.0), (72, 30, 9.0), (33, 66, 10.0), (64, 64, 16.0)]
+    for k in range(12):
+        nx, ny, R = shapes[k % len(shapes)]
+        d = P.lbm_desc_default(nx, ny, T=0.8)
+        rho = synth.droplet(nx, ny, R, 0.8)
+        n = 5 + 7 * k
+        t = P.lbm_submit(srv, d, rho, n)
+        r = wait(P, srv, [t])[t]
+        a = alone(P, d, rho, n)
+        assert np.array_equal(r["rho"], a["rho"]), (k, nx, ny)
+        assert np.array_equal(r["ux"], a["ux"]), (k, nx, ny)
+    st = P.lbm_server_get_stats(srv)
+    assert st["completed"] == 12 and st["failed"] == 0
+    P.lbm_server_destroy(srv)
