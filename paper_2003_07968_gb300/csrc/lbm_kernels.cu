@@ -6,7 +6,8 @@
 //              velocity (Eq. FMD), BGK + Guo (Eqs. BGKCO, SEDF, GFS), store f*
 //   k_init     f* such that the next pull yields f^eq(rho, u)
 //   k_moments  rho, force-shifted u of the current state (FP64 out)
-//   k_mass_*   FP64 sum of the stored populations (two-level reduction)
+//   k_mass_*   FP64 sum of the stored populations (two-level reduction; site
+//              sums as float-float pairs on the FP32 pipe)
 //
 // Both passes walk a global tile list with a persistent grid, so one launch
 // covers one lattice or a batch of uneven lattices alike.
@@ -306,6 +307,32 @@ __global__ void k_init(LatDev L, void* pop, int parity, const double* rho, const
 // ------------------------------------------------------------------ moments
 // rho (FP64 sum of the pulled populations) and u = (j + F/2)/rho, with F from
 // the psi plane of the current state (computed by k_psi just before).
+// Knuth's TwoSum on the FP32 pipe: returns s = fl(a + b) and sets e with
+// s + e = a + b exactly (explicit .rn steps the compiler cannot fold).
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+    const float s = vadd(a, b);
+    const float bb = vsub(s, a);
+    e = vadd(vsub(a, vsub(s, bb)), vsub(b, bb));
+    return s;
+}
+
+// sum_i w_i v_i for weights w_i in {-1, 0, 1} as an unevaluated pair
+// hi + lo: hi by error-free steps, their rounding errors gathered in lo, so
+// that hi + lo is within about 8 u^2 |hi| of the exact sum (u = 2^-24).
+// This keeps the per-site sums off the FP64 pipe, which is slow on GB300.
+__device__ __forceinline__ void signed_sum9(const float v[9], const int w[9], float& hi,
+                                            float& lo) {
+    hi = 0.f;
+    lo = 0.f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        if (w[i] == 0) continue;
+        float e;
+        hi = two_sum(hi, w[i] > 0 ? v[i] : -v[i], e);
+        lo = vadd(lo, e);
+    }
+}
+
 template <class S>
 __global__ void k_moments(LatDev L, const void* pop, int parity, const float* psi_arena,
                           double* rho_out, double* ux_out, double* uy_out) {
@@ -318,48 +345,61 @@ __global__ void k_moments(LatDev L, const void* pop, int parity, const float* ps
     const int64_t plane = L.plane;
     const T* f = reinterpret_cast<const T*>(pop) + L.off_f[parity] + (int64_t)(y + GY) * pitch +
                  (x + L.gx);
-    double g[9];
+    float g[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = (double)S::ld(f + i * plane - kCy[i] * pitch - kCx[i]);
-    double d = 0.0, jx = 0.0, jy = 0.0;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        d += g[i];
-        jx += kCx[i] * g[i];
-        jy += kCy[i] * g[i];
-    }
-    const double rho = d + (double)L.rho0;
+    for (int i = 0; i < 9; ++i) g[i] = S::ld(f + i * plane - kCy[i] * pitch - kCx[i]);
+    constexpr int kOne[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+    float hi, lo;
+    signed_sum9(g, kOne, hi, lo);
+    // rho = sum_i f_i (Eq. FD) plus the deviation reference, in FP64
+    const double rho = ((double)hi + (double)lo) + (double)L.rho0;
     const int64_t s = (int64_t)y * nx + x;
     if (rho_out) rho_out[s] = rho;
     if (!ux_out && !uy_out) return;  // density only: no force, psi not read
+    float jxh, jxl, jyh, jyl;
+    signed_sum9(g, kCx, jxh, jxl);
+    signed_sum9(g, kCy, jyh, jyl);
     const float* c = psi_arena + L.off_psi + (int64_t)(y + GY) * L.pitch_psi + (x + L.gx_psi);
     const int W = L.pitch_psi;
     const float p[9] = {c[0], c[1], c[W], c[-1], c[-W], c[W + 1], c[W - 1], c[-W - 1], c[-W + 1]};
     float Fx, Fy;
     site_force(site_consts(L), p, Fx, Fy);
-    if (ux_out) ux_out[s] = (jx + 0.5 * (double)Fx) / rho;
-    if (uy_out) uy_out[s] = (jy + 0.5 * (double)Fy) / rho;
+    // force-shifted velocity, Eq. FMD
+    const double inv = 1.0 / rho;
+    if (ux_out) ux_out[s] = (((double)jxh + (double)jxl) + 0.5 * (double)Fx) * inv;
+    if (uy_out) uy_out[s] = (((double)jyh + (double)jyl) + 0.5 * (double)Fy) * inv;
 }
 
 // ------------------------------------------------------------------ mass
-// Each block sums whole rows of all nine planes in FP64 and writes one
+// Each block sums whole rows of all nine planes and writes one FP64
 // partial; k_mass_final adds the partials in block order (deterministic).
+// A site's nine values are summed as a float-float pair (signed_sum9); the
+// pairs' leading parts accumulate in FP64, their small trailing parts in
+// FP32, and the sites' rho0 is added once per thread.
 template <class S>
 __global__ void __launch_bounds__(256) k_mass_partial(LatDev L, const void* pop, int parity,
                                                       double* partials) {
     using T = typename S::T;
     const T* f = reinterpret_cast<const T*>(pop) + L.off_f[parity];
     const int nx = L.nx, ny = L.ny;
+    constexpr int kOne[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
     double acc = 0.0;
+    float acc_lo = 0.f;
+    int64_t sites = 0;
     for (int y = blockIdx.x; y < ny; y += gridDim.x) {
         const T* row = f + (int64_t)(y + GY) * L.pitch + L.gx;
         for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-            double s = 0.0;
+            float v[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) s += (double)S::ld(row + i * L.plane + x);
-            acc += s + (double)L.rho0;
+            for (int i = 0; i < 9; ++i) v[i] = S::ld(row + i * L.plane + x);
+            float hi, lo;
+            signed_sum9(v, kOne, hi, lo);
+            acc += (double)hi;
+            acc_lo = vadd(acc_lo, lo);
+            ++sites;
         }
     }
+    acc += (double)acc_lo + (double)sites * (double)L.rho0;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     __shared__ double red[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
