@@ -155,7 +155,8 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n_lattices,
 /* Initialise one lattice at equilibrium, f_i = f_i^eq(rho, u) (the
  * initialisation described after Eq. ISD).  rho, ux, uy: host [ny][nx] FP64,
  * ux/uy may be NULL (zero velocity).  Copies the fields in, then returns
- * with the work queued.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
+ * with the work queued.  Errors: LBM_ERR_ARG (also for a density that is not
+ * finite), LBM_ERR_CUDA. */
 int lbm_init(lbm_handle* h, int32_t lattice, const double* rho, const double* ux,
              const double* uy);
 

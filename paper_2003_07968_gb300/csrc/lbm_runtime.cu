@@ -762,14 +762,13 @@ int lbm_init(lbm_handle* h, int32_t lattice, const double* rho, const double* ux
     const size_t n = (size_t)L.nx * L.ny;
     int rc = ensure_staging(h, n);
     if (rc) return rc;
+    double mn = 0.0;
+    if (!field_scan(rho, n, &mn)) return LBM_ERR_ARG;  // every density finite
     if (h->desc[lattice].storage != LBM_STORE_F32 && h->desc[lattice].rho0 < 0.0) {
         // automatic reference: the smallest density keeps the vapour deviations
         // small (best relative precision where rho is smallest) and the liquid
         // ones no larger than plain storage would hold
-        double m = rho[0];
-        for (size_t i = 1; i < n; ++i) m = std::min(m, rho[i]);
-        if (!std::isfinite(m)) return LBM_ERR_ARG;
-        const float r0 = (float)std::max(m, 0.0);
+        const float r0 = auto_rho0_of_min(mn);
         if (r0 != L.rho0) drop_graph(h);  // captured launches may carry the lattice by value
         L.rho0 = r0;
         CK(h, cudaMemcpyAsync(h->lat_dev + lattice, &L, sizeof(LatDev), cudaMemcpyHostToDevice,

@@ -959,8 +959,8 @@ int lbm_submit(lbm_server* S, const lbm_lattice_desc* d, const double* rho, int6
     if (validate_desc(R.d, why) != LBM_OK || R.d.collision != LBM_COLL_BGK) return LBM_ERR_ARG;
     const size_t n = (size_t)R.d.nx * R.d.ny;
     if ((int64_t)n > S->o.max_request_sites) return LBM_ERR_CAPACITY;
-    for (size_t i = 0; i < n; ++i)
-        if (!std::isfinite(rho[i])) return LBM_ERR_ARG;
+    double mn = 0.0;
+    if (!field_scan(rho, n, &mn)) return LBM_ERR_ARG;  // every density finite
     if (R.d.nx > S->o.max_width) return LBM_ERR_CAPACITY;
     R.L = lat_layout(R.d, 0);
     R.rows = (size_t)(R.d.ny + 2 * GY);  // of the row space, at the common pitch
@@ -968,7 +968,7 @@ int lbm_submit(lbm_server* S, const lbm_lattice_desc* d, const double* rho, int6
     if ((int64_t)R.rows > S->row_cap ||
         (size_t)round_up((int64_t)R.psi_bytes, 256) > S->o.arena_bytes - S->pop_bytes)
         return LBM_ERR_CAPACITY;
-    if (R.d.storage != LBM_STORE_F32 && R.d.rho0 < 0.0) R.L.rho0 = auto_rho0(rho, n);
+    if (R.d.storage != LBM_STORE_F32 && R.d.rho0 < 0.0) R.L.rho0 = auto_rho0_of_min(mn);
     // the field goes to a pinned slot when one is free (the copy runs on the
     // caller's thread), else to the heap until the worker stages it
     size_t off = 0;

@@ -1,5 +1,10 @@
 """The paper's experiments of Sec. IV, run on the CUDA path through the C ABI.
 
+Fig. SDCC (Sec. IV.A) is the coexistence curve of a planar interface over
+temperature, for plain Shan-Chen and the proposed force; its twelve flat
+bands run as one batch handle and are compared with the FP64 oracle and
+with Eq. (PGLDR).
+
 Table DVT (the Young-Laplace test of Sec. IV.B) is a sweep over sigma. Its six
 droplets are independent lattices, so they run as one batch handle: one
 persistent launch per step over all six. Each lattice is read every 100
@@ -13,6 +18,7 @@ from fractions import Fraction
 import numpy as np
 import pytest
 
+import oracle
 from oracle import theory
 import synth
 
@@ -74,3 +80,40 @@ def test_table_dvt_sigma_sweep_in_one_batch(P):
         assert abs(gamma - row["gamma"]) <= tol, (key, gamma)
         assert abs(rg - row["rho_g"]) <= 1.5e-4, (key, rg)
         assert abs(rl - row["rho_l"]) <= 1.5e-4, (key, rl)
+
+
+def test_coexistence_curve_fig_sdcc_in_one_batch(P):
+    # Fig. SDCC: planar interfaces over temperature, plain Shan-Chen (eps = 0)
+    # and the proposed force (eps = 1.73), BGK tau = 0.8.  Twelve flat bands in
+    # one batch handle (32 x 128 each), 60000 steps, against the FP64 oracle
+    # run the same way on 2 x 128 (a flat band is uniform in x, so the
+    # discrete problem is the same).  Plain Shan-Chen started from the
+    # Maxwell densities breaks down below T_r = 0.8 (in the oracle too), so
+    # its curve starts there; where it runs, it sits on the mechanical-
+    # stability densities of Eq. (PGLDR) with eps = 0.
+    cases = [(0.0, T) for T in (0.8, 0.85, 0.9, 0.95)] + \
+            [(1.73, T) for T in (0.6, 0.65, 0.7, 0.75, 0.8, 0.85, 0.9, 0.95)]
+    steps = 60000
+    descs = [P.lbm_desc_default(32, 128, T=T, tau=0.8, eps=eps, sigma=1.0) for eps, T in cases]
+    h = P.lbm_create(descs)
+    for i, (eps, T) in enumerate(cases):
+        P.lbm_init(h, i, synth.band(32, 128, T, 32, 96))
+    P.lbm_step(h, steps)
+    got = [P.lbm_moments(h, i, u=False, mass=False)["rho"] for i in range(len(cases))]
+    P.lbm_destroy(h)
+    for (eps, T), g in zip(cases, got):
+        o = oracle.run(oracle.params(T=T, tau=0.8, eps=eps, sigma=1.0),
+                       synth.band(2, 128, T, 32, 96), steps)["rho"]
+        gl, gg, ol, og = g[64, 0], g[0, 0], o[64, 0], o[0, 0]
+        assert np.ptp(g, axis=1).max() <= 1e-6 * gl, (eps, T)  # still uniform in x
+        assert abs(gl - ol) <= 1e-5 * ol, (eps, T, gl, ol)
+        assert abs(gg - og) <= 1e-4 * og, (eps, T, gg, og)
+        tg, tl = theory.pgldr(T, eps)
+        if eps == 0.0:
+            assert abs(ol - tl) <= 1e-4 * tl and abs(og - tg) <= 1e-3 * tg, (T, ol, og)
+        else:
+            # the liquid branch follows Eq. (PGLDR) closely at every T; the
+            # vapour branch departs as the density ratio grows
+            assert abs(ol - tl) <= 5e-4 * tl, (T, ol, tl)
+            if T >= 0.8:
+                assert abs(og - tg) <= 1e-2 * tg, (T, og, tg)

@@ -147,6 +147,32 @@ def test_uniform_fixed_point(P):
     assert np.abs(g["ux"]).max() <= 1e-7 and np.abs(g["uy"]).max() <= 1e-7
 
 
+def test_non_finite_initial_density_is_refused(P):
+    # every value is checked (one threaded pass for a million or more): a NaN
+    # or an infinity anywhere, not only in the first or smallest value
+    for nx, ny in [(48, 40), (1100, 1000)]:
+        d = P.lbm_desc_default(nx, ny, T=0.8)
+        h = P.lbm_create(d)
+        base = synth.droplet(nx, ny, nx / 4.0, 0.8)
+        for bad, at in [(np.nan, -1), (np.inf, nx * ny // 2 + 3), (-np.inf, 5), (np.nan, 0)]:
+            rho = base.copy()
+            rho.flat[at] = bad
+            with pytest.raises(P.LbmError) as err:
+                P.lbm_init(h, 0, rho)
+            assert err.value.code == P.LBM_ERR_ARG
+        P.lbm_init(h, 0, base)  # the handle stays usable
+        P.lbm_step(h, 2)
+        assert np.isfinite(P.lbm_moments(h, 0, u=False, mass=False)["rho"]).all()
+        P.lbm_destroy(h)
+    srv = P.lbm_server_create(P.lbm_server_opts_default(arena_bytes=1 << 26))
+    rho = synth.droplet(64, 64, 16.0, 0.8)
+    rho[63, 63] = np.nan
+    with pytest.raises(P.LbmError) as err:
+        P.lbm_submit(srv, P.lbm_desc_default(64, 64, T=0.8), rho, 10)
+    assert err.value.code == P.LBM_ERR_ARG
+    P.lbm_server_destroy(srv)
+
+
 def test_mass_drift_fp32(P):
     rho = synth.droplet(128, 128, 30.0, 0.7)
     d = P.lbm_desc_default(128, 128, T=0.7)
