@@ -357,6 +357,18 @@ void lbm_server_destroy(lbm_server* s);
 int lbm_mass_noalloc(const float* values, int64_t count, double offset, double* mass_out,
                      void* stream);
 
+/* The reciprocal and square root of the step kernels (the hardware
+ * approximations, each refined by one Newton-Raphson step on the paired FP32
+ * pipe; used by the float-float EOS, Eqs. DED and CSEOS, and by the velocity of
+ * Eq. FMD), applied on the current device to n host values x (1 <= n <= 2^24):
+ * rcp[i] = the kernels' 1/x[i], sq[i] = their sqrt(x[i]) (meaningful for
+ * normal x[i] > 0, resp. finite x[i] >= 0).  Caller-owned host arrays of n
+ * floats.  For tests of their error bounds against correctly rounded
+ * results.  Also runs each value through the one-value (scalar) lane and
+ * returns LBM_ERR_STATE if any result differs in a bit from the paired lane.
+ * Errors: LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_STATE. */
+int lbm_selfcheck_arith(const float* x, int64_t n, float* rcp, float* sq);
+
 /* Host-only consistency proof of the shared-memory staging used by the
  * LBM_KERNEL_TMA passes (two-pass and single-pass plans): for a set of
  * lattice shapes, every tile shape, both storages and both population

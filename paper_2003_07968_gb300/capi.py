@@ -138,6 +138,9 @@ SIGNATURES = {
     "lbm_info": (ctypes.c_int, [_vp, ctypes.POINTER(Info)]),
     "lbm_autotune": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "lbm_selfcheck": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int32]),
+    "lbm_selfcheck_arith": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.c_int64,
+                                           ctypes.POINTER(ctypes.c_float),
+                                           ctypes.POINTER(ctypes.c_float)]),
     "lbm_mass_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
                                         ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_server_opts_default": (None, [ctypes.POINTER(ServerOpts)]),
@@ -380,6 +383,18 @@ def lbm_selfcheck() -> tuple[int, str]:
     buf = ctypes.create_string_buffer(512)
     rc = load().lbm_selfcheck(buf, 512)
     return rc, buf.value.decode()
+
+
+def lbm_selfcheck_arith(x) -> tuple[np.ndarray, np.ndarray]:
+    """The step kernels' 1/x and sqrt(x) for float32 values x (GPU)."""
+    v = np.ascontiguousarray(x, dtype=np.float32).ravel()
+    r = np.empty_like(v)
+    q = np.empty_like(v)
+    fp = ctypes.POINTER(ctypes.c_float)
+    _check(load().lbm_selfcheck_arith(v.ctypes.data_as(fp), ctypes.c_int64(v.size),
+                                      r.ctypes.data_as(fp), q.ctypes.data_as(fp)),
+           "lbm_selfcheck_arith")
+    return r, q
 
 
 def lbm_autotune(h: Handle, repeats: int = 3) -> dict:

@@ -241,21 +241,72 @@ __device__ __forceinline__ V sum9(const V g[9]) {
                 g[8]);
 }
 
-// 1/x correctly rounded (PTX rcp.rn.f32): a unique result.  (The one-ulp
-// rcp.approx leaves the code generator free to produce different results in
-// different contexts, measured on sm_103a, which would make a site's result
-// depend on the kernel that computes it.)
+// 1/x correctly rounded (PTX rcp.rn.f32): a unique result.  The MRT site
+// collision uses it.
 __device__ __forceinline__ float rcp_rn(float x) {
     float r;
     asm("rcp.rn.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+
+// The hardware approximations (one MUFU instruction each, flush to zero):
+// fixed functions of their input, so every kernel gets the same bits.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// 1/x for normal x > 0 (the EOS and the collision): the hardware
+// approximation r per lane, then one Newton-Raphson step for f(r) = 1/r - x,
+//   r' = r + r (1 - x r),
+// two FMAs on the paired pipe (Muller et al., Handbook of Floating-Point
+// Arithmetic, Newton-Raphson based division).  The step squares the
+// approximation's relative error, so r' is within about 1 ulp of 1/x
+// (tested against correctly rounded reciprocals, lbm_selfcheck_arith).
 template <class V>
 __device__ __forceinline__ V vrcp(V x) {
+    using Ln = Lanes<V>;
     V r;
 #pragma unroll
-    for (int k = 0; k < Lanes<V>::n; ++k) Lanes<V>::put(r, k, rcp_rn(Lanes<V>::get(x, k)));
-    return r;
+    for (int k = 0; k < Ln::n; ++k) Ln::put(r, k, rcp_approx(Ln::get(x, k)));
+    const V e = vfma(vmul(x, Ln::set(-1.f)), r, Ln::set(1.f));  // 1 - x r
+    return vfma(r, e, r);
+}
+
+// sqrt(a) for finite a >= 0 (psi): the hardware reciprocal square root y
+// per lane, s = a y, then one Newton step on the square root (Markstein's
+// method),
+//   s' = s + (y / 2)(a - s^2),
+// on the paired pipe.  a below 2^-100 is scaled by 2^100 first and the root
+// by 2^-50 after (both exact), and a = 0 gives 0, so the flush to zero of the
+// approximation never shows.  Within about 1 ulp of sqrt(a) (tested against
+// correctly rounded roots, lbm_selfcheck_arith).
+template <class V>
+__device__ __forceinline__ V vsqrt(V a) {
+    using Ln = Lanes<V>;
+    V as, y, sc;
+#pragma unroll
+    for (int k = 0; k < Ln::n; ++k) {
+        const float x = Ln::get(a, k);
+        const bool tiny = x < 0x1p-100f;
+        const float xs = tiny ? x * 0x1p100f : x;
+        Ln::put(as, k, xs);
+        Ln::put(sc, k, tiny ? 0x1p-50f : 1.f);
+        Ln::put(y, k, rsqrt_approx(xs));
+    }
+    const V s = vmul(as, y);
+    const V e = vfma(vmul(s, Ln::set(-1.f)), s, as);  // a - s^2
+    const V r = vmul(vfma(vmul(y, Ln::set(0.5f)), e, s), sc);
+    V out;
+#pragma unroll
+    for (int k = 0; k < Ln::n; ++k) Ln::put(out, k, Ln::get(a, k) == 0.f ? 0.f : Ln::get(r, k));
+    return out;
 }
 
 // ---- psi(rho), Eqs. (DED) and (CSEOS) --------------------------------------
@@ -275,13 +326,14 @@ enum { EOS_F64 = 0, EOS_DF = 1, EOS_F32 = 2 };
 template <class V>
 __device__ __forceinline__ V psi_finish(const LatDev& L, V rho, V s, V arg, uint32_t* status,
                                         unsigned live) {
+    const V root = vsqrt(arg);
     V psi;
 #pragma unroll
     for (int k = 0; k < Lanes<V>::n; ++k) {
         const float r = Lanes<V>::get(rho, k), a = Lanes<V>::get(arg, k);
         const bool ok = (r > 0.f) && (Lanes<V>::get(s, k) > 0.f) && (a >= 0.f) && (a < INFINITY);
         if (!ok && ((live >> k) & 1u)) atomicOr(status + L.lattice, 1u);
-        Lanes<V>::put(psi, k, ok ? __fsqrt_rn(a) : __int_as_float(0x7fc00000));
+        Lanes<V>::put(psi, k, ok ? Lanes<V>::get(root, k) : __int_as_float(0x7fc00000));
     }
     return psi;
 }

@@ -420,6 +420,31 @@ __global__ void k_mass_final(const double* partials, int n, double* out) {
     }
 }
 
+// ------------------------------------------------------------------ arithmetic check
+// The step's reciprocal and square root on n values: paired lanes (two
+// values per thread, as the kernels run them) to the outputs, and the scalar
+// lane on each value, compared bitwise (a mismatch sets *mismatch).
+__global__ void k_arith_check(const float* x, int64_t n, float* rcp, float* sq,
+                              uint32_t* mismatch) {
+    const int64_t i = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (i >= n) return;
+    const bool two = i + 1 < n;
+    const float2 v = make_float2(x[i], two ? x[i + 1] : 1.f);
+    const float2 r2 = vrcp(v), s2 = vsqrt(v);
+    bool same = __float_as_uint(vrcp(v.x)) == __float_as_uint(r2.x) &&
+                __float_as_uint(vsqrt(v.x)) == __float_as_uint(s2.x);
+    if (two)
+        same = same && __float_as_uint(vrcp(v.y)) == __float_as_uint(r2.y) &&
+               __float_as_uint(vsqrt(v.y)) == __float_as_uint(s2.y);
+    if (!same) atomicOr(mismatch, 1u);
+    rcp[i] = r2.x;
+    sq[i] = s2.x;
+    if (two) {
+        rcp[i + 1] = r2.y;
+        sq[i + 1] = s2.y;
+    }
+}
+
 // ================================================================ launchers
 namespace {
 template <class S, int SPT>
@@ -578,6 +603,13 @@ cudaError_t launch_mass(int storage_f16, const LatDev& L, const void* pop, int p
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_mass_final<<<1, 32, 0, st>>>(partials, nb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_arith_check(const float* x, int64_t n, float* rcp, float* sq,
+                               uint32_t* mismatch, cudaStream_t st) {
+    const int64_t pairs = (n + 1) / 2;
+    k_arith_check<<<(unsigned)((pairs + 255) / 256), 256, 0, st>>>(x, n, rcp, sq, mismatch);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,8 @@ cudaError_t launch_init(int storage_f16, const LatDev& L, void* pop, int parity,
 cudaError_t launch_moments(int storage_f16, const LatDev& L, const void* pop, int parity,
                            const float* psi, double* rho, double* ux, double* uy,
                            cudaStream_t st);
+cudaError_t launch_arith_check(const float* x, int64_t n, float* rcp, float* sq,
+                               uint32_t* mismatch, cudaStream_t st);
 cudaError_t launch_mass(int storage_f16, const LatDev& L, const void* pop, int parity,
                         double* partials, int n_partials, double* out, cudaStream_t st);
 int occupancy_psi(int storage_f16, int eos, int spt, int threads);

@@ -1031,6 +1031,33 @@ int lbm_autotune(lbm_handle* h, int32_t repeats) {
     return LBM_OK;
 }
 
+int lbm_selfcheck_arith(const float* x, int64_t n, float* rcp, float* sq) {
+    if (!x || !rcp || !sq || n < 1 || n > ((int64_t)1 << 24)) return LBM_ERR_ARG;
+    float* d = nullptr;
+    uint32_t* flag = nullptr;
+    const size_t bytes = (size_t)n * sizeof(float);
+    if (cudaMalloc(&d, 3 * bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_OOM;
+    }
+    if (cudaMalloc(&flag, sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d);
+        return LBM_ERR_OOM;
+    }
+    uint32_t mismatch = 0;
+    cudaError_t e = cudaMemcpy(d, x, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(flag, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = launch_arith_check(d, n, d + n, d + 2 * n, flag, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(rcp, d + n, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(sq, d + 2 * n, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&mismatch, flag, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    cudaFree(flag);
+    cudaFree(d);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    return mismatch ? LBM_ERR_STATE : LBM_OK;
+}
+
 int lbm_selfcheck(char* report, int32_t report_len) {
     std::string msg;
     const int shapes[][2] = {{2, 2},   {3, 5},   {4, 4},    {7, 5},   {31, 33}, {32, 32},

@@ -599,3 +599,35 @@ def test_fused_tma_storage_and_mrt(P, storage, mrt):
         outs.append(P.lbm_moments(h, 0, mass=False))
         P.lbm_destroy(h)
     assert np.array_equal(outs[0]["rho"], outs[1]["rho"])
+
+
+def test_step_reciprocal_and_square_root_error_bounds(P):
+    # the kernels' 1/x and sqrt(x) (hardware approximation + one Newton step,
+    # paired lanes) against correctly rounded float32 results over the ranges
+    # the step uses them on: 1/rho and 1/(1 - b rho) (rho in (0, 8)), psi^2
+    # (0 .. 30), plus tiny, huge, zero and power-of-two arguments
+    rng = np.random.default_rng(2003)
+    x = np.concatenate([
+        rng.uniform(1e-3, 8.0, 200000), rng.uniform(0.05, 1.0, 200000),
+        np.exp(rng.uniform(np.log(1e-37), np.log(1e37), 200000)),
+        2.0 ** np.arange(-120, 121, dtype=np.float64), [1.0, 4.0, 0.25, 3.0, 7.0],
+    ]).astype(np.float32)
+    r, q = P.lbm_selfcheck_arith(x)  # raises LBM_ERR_STATE if paired != scalar lane
+
+    def ulps(a, b):  # distance in units of the last place, same sign, finite
+        ia = a.view(np.int32).astype(np.int64)
+        ib = b.view(np.int32).astype(np.int64)
+        return np.abs(ia - ib)
+
+    normal = (x > 1.2e-38) & (x < 8.5e37)  # 1/x normal too
+    exact_r = (np.float32(1.0) / x[normal]).astype(np.float32)
+    exact_q = np.sqrt(x).astype(np.float32)
+    er, eq = ulps(r[normal], exact_r), ulps(q, exact_q)
+    print(f"1/x: max {er.max()} ulp, {np.mean(er == 0):.4f} exact; "
+          f"sqrt: max {eq.max()} ulp, {np.mean(eq == 0):.4f} exact")
+    assert er.max() <= 1 and eq.max() <= 1
+    assert np.mean(er == 0) > 0.9 and np.mean(eq == 0) > 0.9
+    # zero and the powers of two are exact
+    r0, q0 = P.lbm_selfcheck_arith(np.array([0.0, 2.0 ** -130, 2.0 ** -140], np.float32))
+    assert q0[0] == 0.0
+    assert q0[1] == np.sqrt(np.float32(2.0 ** -130)) and q0[2] == np.float32(2.0 ** -70)
