@@ -147,4 +147,34 @@ __host__ __device__ inline bool ring_cell(int r, int TX, int TY, int x0, int y0,
     return on;
 }
 
+// Tensor-path coordinates of tile (x0, y0) of lattice L, whose ghost row -GY
+// is row `row0` of the row space, reading population buffer `parity`:
+//   load box (TX + 2H) x (TY + 4) x 9 at (x0, row0 + y0, 9 parity): element x0
+//     of a row is lattice column x0 - H (the row starts with gx = H ghost
+//     columns), row row0 + y0 is lattice row y0 - 2;
+//   store box TX x TY x 9 at (x0 + gx, row0 + GY + y0, 9 (parity ^ 1)), used
+//     only for tiles inside the lattice (store set): the store unit clips a
+//     box at 16-byte granularity in x, so a ragged tile would write ghost
+//     columns too.
+// x coordinates must be multiples of 16 bytes (lbm_selfcheck checks them,
+// and that every store box lies inside its lattice).
+struct TmaCoords {
+    int lx, ly, lz;  // load box origin
+    int sx, sy, sz;  // store box origin
+    bool store;      // the tile is stored by one tensor store
+};
+template <int TX, int TY>
+__host__ __device__ inline TmaCoords fused_tma_coords(const LatDev& L, int row0, int parity,
+                                                      int x0, int y0) {
+    TmaCoords c;
+    c.lx = x0;
+    c.ly = row0 + y0;
+    c.lz = 9 * parity;
+    c.sx = x0 + L.gx;
+    c.sy = row0 + GY + y0;
+    c.sz = 9 * (parity ^ 1);
+    c.store = x0 + TX <= L.nx && y0 + TY <= L.ny;
+    return c;
+}
+
 }  // namespace pplbm

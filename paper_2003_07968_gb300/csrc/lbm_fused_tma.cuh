@@ -76,7 +76,8 @@ struct FGeo : FusedGeo<(int)sizeof(typename S::T), TX, TY> {
     // on the tensor path)
     static constexpr int LATB = (int)((sizeof(LatDev) + 15) & ~size_t(15));
     static constexpr int LATOFF = STAGES * STAGEB + 2 * PSIB;
-    static constexpr int BAR = LATOFF + STAGES * LATB;  // mbarriers after stages, psi, constants
+    static constexpr int DESCOFF = LATOFF + STAGES * LATB;  // tile descriptor of each stage
+    static constexpr int BAR = DESCOFF + STAGES * 16;  // mbarriers after stages, psi, constants
     // element offset, inside a stage, of the value that cell (lx, ly) of the
     // tile (lx, ly in -1 .. TX, -1 .. TY) pulls from plane i
     static __host__ __device__ constexpr int pull(int i, int lx, int ly) {
@@ -170,6 +171,9 @@ __global__ void __launch_bounds__(kBlockF, 2)
     uint64_t* empty = full + G::STAGES;
     volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + G::STAGES);
     float* psi_buf = reinterpret_cast<float*>(smem + G::STAGES * G::STAGEB);
+    // the tile each stage holds, written by the producer before its arrival
+    // on the stage's barrier, so a consumer reads it from shared memory
+    int4* desc = reinterpret_cast<int4*>(smem + G::DESCOFF);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < G::STAGES; ++s) {
@@ -199,9 +203,9 @@ __global__ void __launch_bounds__(kBlockF, 2)
             const int4 tl = __ldg(&a.tiles[t]);
             const LatDev& L =
                 MODE == 1 ? lat0 : *reinterpret_cast<const LatDev*>(smem + G::LATOFF + s * G::LATB);
-            if (tl.y + TX <= L.nx && tl.z + TY <= L.ny) {
-                tensor_s2g(&smap, smem + s * G::STAGEB, tl.y + L.gx, L.row0 + tl.z + GY,
-                           9 * (a.parity ^ 1));
+            const TmaCoords c = fused_tma_coords<TX, TY>(L, L.row0, a.parity, tl.y, tl.z);
+            if (c.store) {
+                tensor_s2g(&smap, smem + s * G::STAGEB, c.sx, c.sy, c.sz);
                 bulk_commit();
                 bulk_wait_read<0>();
             }
@@ -233,11 +237,12 @@ __global__ void __launch_bounds__(kBlockF, 2)
                 // space), planes of the current buffer
                 if (lane == 0) {
                     const int4 tl = __ldg(&a.tiles[t]);
-                    const int row0 = MODE == 1 ? lat0.row0 : a.lats[tl.x].row0;
+                    desc[s] = tl;
+                    const LatDev& Lt = MODE == 1 ? lat0 : a.lats[tl.x];
+                    const TmaCoords c = fused_tma_coords<TX, TY>(Lt, Lt.row0, a.parity, tl.y, tl.z);
                     mbar_expect_tx(&full[s], (uint32_t)G::TBYTES +
                                                  (MODE == 2 ? (uint32_t)sizeof(LatDev) : 0u));
-                    tensor_g2s(smem + s * G::STAGEB, &tmap, tl.y, row0 + tl.z, 9 * a.parity,
-                               &full[s]);
+                    tensor_g2s(smem + s * G::STAGEB, &tmap, c.lx, c.ly, c.lz, &full[s]);
                     if (MODE == 2)
                         bulk_g2s(smem + G::LATOFF + s * G::LATB, a.lats + tl.x,
                                  (uint32_t)sizeof(LatDev), &full[s]);
@@ -245,7 +250,10 @@ __global__ void __launch_bounds__(kBlockF, 2)
                 tq[s] = t;
                 __syncwarp();
             } else {
-                issue_fused<S, TX, TY>(a, __ldg(&a.tiles[t]), smem + s * G::STAGEB, &full[s]);
+                const int4 tl = __ldg(&a.tiles[t]);
+                if (lane == 0) desc[s] = tl;
+                __syncwarp();
+                issue_fused<S, TX, TY>(a, tl, smem + s * G::STAGEB, &full[s]);
             }
             ++k;
         }
@@ -278,10 +286,12 @@ __global__ void __launch_bounds__(kBlockF, 2)
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         if (tile_skipped(a, t)) continue;
         const int s = k % G::STAGES;
-        const int4 tl = __ldg(&a.tiles[t]);
         float* ps = psi_buf + (k & 1) * (G::PSIB / 4);
         const bool ok = __all_sync(0xffffffffu,
                                    mbar_wait_bounded(&full[s], (uint32_t)(k / G::STAGES) & 1u));
+        // the tile, from the stage's descriptor (from global memory only if
+        // the wait ran out, to name the lattice in the status word)
+        const int4 tl = ok ? desc[s] : __ldg(&a.tiles[t]);
         // one lattice: its constants are kernel parameters (constant-bank
         // operands); a batch on the tensor path: they arrived with the tile
         // and stay until the stage goes back; row copies: global (the stage
@@ -377,7 +387,7 @@ __global__ void __launch_bounds__(kBlockF, 2)
         // tile uses plain stores:
         // the store unit clips a box at 16-byte granularity in x (measured), so
         // a partial box would also write the ghost columns just past nx.
-        const bool bulk_out = TMAP && x0 + TX <= nx && y0 + TY <= ny;
+        const bool bulk_out = TMAP && fused_tma_coords<TX, TY>(L, 0, 0, x0, y0).store;
         T* out = reinterpret_cast<T*>(smem + s * G::STAGEB);
 #pragma unroll
         for (int j = 0; j < NV; ++j) {

@@ -524,6 +524,73 @@ std::string check_fused_t(const LatDev& L, int par, int x0, int y0, int64_t lo, 
     return "";
 }
 
+// Tensor-path coordinates (fused_tma_coords) of every tile of the lattices
+// in `lats`, as the single pass uses them with one tensor map over a row
+// space of `rows` rows of `pitch` elements whose stores are clipped at
+// (store_x, store_y): 16-byte aligned x, rows and planes in range, and every
+// store box inside its own lattice and inside the clip.  Layouts the runtime
+// gives no tensor map (rows narrower than a load box, too few rows) are
+// skipped, as the runtime falls back to row copies there.
+template <int TX, int TY>
+std::string check_tma_coords(const std::vector<LatDev>& lats, int es, int64_t pitch, int64_t rows,
+                             int64_t store_x, int64_t store_y, int64_t& checked) {
+    const int bw = TX + 2 * (16 / es);
+    if (pitch < bw || rows < TY + 4) return "";
+    for (const LatDev& L : lats)
+        for (int y0 = 0; y0 < L.ny; y0 += TY)
+            for (int x0 = 0; x0 < L.nx; x0 += TX)
+                for (int par = 0; par < 2; ++par) {
+                    const TmaCoords c = fused_tma_coords<TX, TY>(L, L.row0, par, x0, y0);
+                    ++checked;
+                    char buf[200];
+                    std::snprintf(buf, sizeof buf,
+                                  "tensor tile %dx%d of %dx%d at (%d,%d), row0 %d, es %d: ", TX, TY,
+                                  L.nx, L.ny, x0, y0, L.row0, es);
+                    if ((int64_t)c.lx * es % 16 || c.ly < 0 || (c.lz != 0 && c.lz != 9))
+                        return std::string(buf) + "load box origin";
+                    if (!c.store) continue;
+                    if ((int64_t)c.sx * es % 16 || c.sy < 0 || (c.sz != 0 && c.sz != 9))
+                        return std::string(buf) + "store box origin";
+                    if (c.sx < L.gx || c.sx + TX > L.gx + L.nx || c.sy < L.row0 + GY ||
+                        c.sy + TY > L.row0 + GY + L.ny)
+                        return std::string(buf) + "store box outside the lattice";
+                    if (c.sx + TX > store_x || c.sy + TY > store_y)
+                        return std::string(buf) + "store box outside the clip";
+                }
+    return "";
+}
+
+template <int TX, int TY>
+std::string check_tma_layouts(const int (*shapes)[2], int nshapes, int64_t& checked) {
+    for (int f16 = 0; f16 < 2; ++f16) {
+        const int es = f16 ? 2 : 4;
+        std::vector<LatDev> all;
+        for (int i = 0; i < nshapes; ++i) {
+            lbm_lattice_desc d;
+            lbm_desc_default(&d, shapes[i][0], shapes[i][1]);
+            d.storage = f16 ? LBM_STORE_F16_DEV : LBM_STORE_F32_DEV;
+            int64_t pc = 0, qc = 0;
+            LatDev L = make_lat(d, i, pc, qc);
+            all.push_back(L);
+            // one lattice alone: row 0 of its own buffers, stores clipped
+            // after its last interior column and row
+            L.row0 = 0;
+            const std::vector<LatDev> one{L};
+            std::string e = check_tma_coords<TX, TY>(one, es, L.pitch, L.ny + 2 * GY,
+                                                     L.gx + L.nx, GY + L.ny, checked);
+            if (!e.empty()) return e;
+        }
+        // all of them stacked in one row space (a batch, or the server's arena)
+        if (row_space_layout(all, es, 1e30) < 0) return "row space refused";
+        int64_t rows = 0;
+        for (const LatDev& L : all) rows += L.ny + 2 * GY;
+        std::string e =
+            check_tma_coords<TX, TY>(all, es, all[0].pitch, rows, all[0].pitch, rows, checked);
+        if (!e.empty()) return e;
+    }
+    return "";
+}
+
 template <int ES>
 std::string check_fused_shape(int tx, int ty, const LatDev& L, int par, int x0, int y0,
                               int64_t lo, int64_t hi) {
@@ -1129,6 +1196,14 @@ int lbm_selfcheck(char* report, int32_t report_len) {
                             }
                 }
             }
+    }
+    if (msg.empty()) {
+        // the single pass's tensor coordinates, one lattice and row spaces
+        const int n = (int)(sizeof(shapes) / sizeof(shapes[0]));
+        msg = check_tma_layouts<64, 8>(shapes, n, checked);
+        if (msg.empty()) msg = check_tma_layouts<32, 16>(shapes, n, checked);
+        if (msg.empty()) msg = check_tma_layouts<64, 16>(shapes, n, checked);
+        if (msg.empty()) msg = check_tma_layouts<128, 8>(shapes, n, checked);
     }
 done:
     if (msg.empty()) msg = "ok: " + std::to_string(checked) + " tile plans checked";
