@@ -117,3 +117,53 @@ def test_coexistence_curve_fig_sdcc_in_one_batch(P):
             assert abs(ol - tl) <= 5e-4 * tl, (T, ol, tl)
             if T >= 0.8:
                 assert abs(og - tg) <= 1e-2 * tg, (T, og, tg)
+
+
+# Laplace law of configuration 2 against the planar surface tension.  The
+# FP64 oracle, run the same way (tests/golden/make_config2_laplace.py), fits
+# gamma at 0.969, 0.934, 0.933 and 0.891 of gamma_pi for T_r = 0.6, 0.7, 0.8,
+# 0.9, with intercepts of 0.0, 1.3, 2.8 and 5.0 % of the largest Delta P:
+# finite radii, and for T_r = 0.6 a largest droplet still relaxing after the
+# 20000 steps.  The bounds sit just outside those.
+GAMMA_TOL = {0.6: 0.05, 0.7: 0.10, 0.8: 0.10, 0.9: 0.15}
+ICPT_TOL = 0.08
+C2_PATH = os.path.join(os.path.dirname(__file__), "golden", "config2_laplace.json")
+
+
+def test_config2_laplace_law_in_one_batch(P):
+    # configuration 2: droplets R0 = 20 .. 60 on 256^2 at T_r = 0.6 .. 0.9, BGK
+    # tau = 1, 20000 steps, all twenty in one batch handle.
+    #  - each droplet against the oracle: whether it survived (R0 = 20 evaporates
+    #    at T_r 0.8 and 0.9), and its densities, radius and Delta P within 1e-3;
+    #  - per temperature, Delta P against 1/R over the surviving droplets
+    #    (Eq. YLR in 2-D) is a line through about the origin whose slope, the
+    #    surface tension, is compared with gamma_pi of the planar interface
+    #    (Eqs. PTNNPI, STPI; the oracle's theory on a domain wide enough for
+    #    the tails)
+    C2 = json.load(open(C2_PATH))
+    ref = C2["droplets"]
+    n, steps = C2["n"], C2["steps"]
+    h = P.lbm_create([P.lbm_desc_default(n, n, T=d["T"], tau=C2["tau"]) for d in ref])
+    for i, d in enumerate(ref):
+        P.lbm_init(h, i, synth.droplet(n, n, float(d["R0"]), d["T"]))
+    P.lbm_step(h, steps)
+    rho = [P.lbm_moments(h, i, u=False, mass=False)["rho"] for i in range(len(ref))]
+    P.lbm_destroy(h)
+    fits = {}
+    for d, r in zip(ref, rho):
+        rl, rg = r[n // 2, n // 2], r[0, 0]
+        mg, ml = theory.maxwell(d["T"])
+        assert (rl > 0.5 * (mg + ml)) == d["survived"], d
+        assert abs(rl / d["rho_centre"] - 1) <= 1e-3 and abs(rg / d["rho_corner"] - 1) <= 1e-3, d
+        if not d["survived"]:
+            continue
+        R, dP = theory.droplet_radius(r, rl, rg), theory.laplace_pressure(r, d["T"])
+        assert abs(R / d["R"] - 1) <= 1e-3 and abs(dP / d["dP"] - 1) <= 1e-3, (d, R, dP)
+        fits.setdefault(d["T"], []).append((R, dP))
+    for T, pts in sorted(fits.items()):
+        gamma, icpt = theory.surface_tension_fit([p[0] for p in pts], [p[1] for p in pts])
+        gpi = theory.planar_interface(T, 1.73, 1.0, L=60.0, dx=0.05)[3]
+        print(f"T_r {T}: {len(pts)} droplets, gamma {gamma:.5f} (planar {gpi:.5f}, "
+              f"{gamma / gpi:.3f}), intercept {icpt:.2e}")
+        assert abs(gamma / gpi - 1) <= GAMMA_TOL[T], (T, gamma, gpi)
+        assert abs(icpt) <= ICPT_TOL * max(p[1] for p in pts), (T, icpt)
