@@ -18,7 +18,11 @@
  *
  * Conventions for every entry point:
  *   - All functions return an int status: LBM_OK (0), LBM_PENDING (1), or a
- *     negative LBM_ERR_* code.  No C++ exception crosses this boundary.
+ *     negative LBM_ERR_* code.  No C++ exception crosses this boundary: a
+ *     host allocation that fails inside a call returns LBM_ERR_OOM, any other
+ *     internal exception LBM_ERR_STATE.  If the server's worker thread meets
+ *     one, every request fails with LBM_ERR_STATE and lbm_submit refuses
+ *     new ones.
  *   - Host arrays are owned by the caller and only borrowed for the call.
  *     Fields are row-major [ny][nx] FP64 (x fastest).
  *   - Device memory and streams are owned by the handle.  Device memory comes

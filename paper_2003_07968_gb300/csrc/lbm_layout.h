@@ -1,11 +1,8 @@
 // lbm_layout.h -- per-lattice layout and constants (LatDev) from a lattice
 // descriptor; shared by the handle runtime and the server.
 #pragma once
-#include <algorithm>
 #include <cmath>
-#include <functional>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "../../include/pplbm.h"
@@ -119,52 +116,6 @@ struct PassDefault {
 };
 constexpr PassDefault kPassDefaults[2] = {{LBM_KERNEL_PLAIN, 64, 4, 2},
                                           {LBM_KERNEL_PLAIN, 32, 8, 2}};
-
-// One pass over a host field: its smallest value into *mn, and whether every
-// value is finite (x * 0 is 0 for a finite x and NaN otherwise, so the sum
-// of those products stays 0 exactly when all are finite).  Four independent
-// accumulators per thread keep the loop vectorisable; fields of a million
-// values or more are split across up to 16 threads.
-inline bool field_scan(const double* v, size_t n, double* mn) {
-    auto scan = [v](size_t b, size_t e, double& m, double& z) {
-        double m0 = HUGE_VAL, m1 = HUGE_VAL, m2 = HUGE_VAL, m3 = HUGE_VAL;
-        double z0 = 0.0, z1 = 0.0, z2 = 0.0, z3 = 0.0;
-        size_t i = b;
-        for (; i + 4 <= e; i += 4) {
-            m0 = v[i] < m0 ? v[i] : m0;
-            m1 = v[i + 1] < m1 ? v[i + 1] : m1;
-            m2 = v[i + 2] < m2 ? v[i + 2] : m2;
-            m3 = v[i + 3] < m3 ? v[i + 3] : m3;
-            z0 += v[i] * 0.0;
-            z1 += v[i + 1] * 0.0;
-            z2 += v[i + 2] * 0.0;
-            z3 += v[i + 3] * 0.0;
-        }
-        for (; i < e; ++i) {
-            m0 = v[i] < m0 ? v[i] : m0;
-            z0 += v[i] * 0.0;
-        }
-        m = std::min(std::min(m0, m1), std::min(m2, m3));
-        z = (z0 + z1) + (z2 + z3);
-    };
-    const size_t hw = std::max(1u, std::thread::hardware_concurrency());
-    const size_t nt = n < ((size_t)1 << 20) ? 1 : std::min<size_t>({hw, 16, n >> 18});
-    std::vector<double> m(nt), z(nt);
-    std::vector<std::thread> th;
-    const size_t chunk = (n + nt - 1) / nt;
-    for (size_t t = 1; t < nt; ++t)
-        th.emplace_back(scan, std::min(n, t * chunk), std::min(n, (t + 1) * chunk), std::ref(m[t]),
-                        std::ref(z[t]));
-    scan(0, std::min(n, chunk), m[0], z[0]);
-    for (auto& t : th) t.join();
-    double mm = HUGE_VAL, zz = 0.0;
-    for (size_t t = 0; t < nt; ++t) {
-        mm = std::min(mm, m[t]);
-        zz += z[t];
-    }
-    *mn = mm;
-    return zz == 0.0;
-}
 
 // Automatic deviation reference: the smallest density of the field (not
 // below 0), from field_scan's minimum.

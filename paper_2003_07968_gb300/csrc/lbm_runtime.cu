@@ -17,6 +17,7 @@
 #include "../../include/pplbm.h"
 #include "lbm_copy_plan.h"
 #include "lbm_kernels.h"
+#include "lbm_host_scan.h"
 #include "lbm_layout.h"
 
 using namespace pplbm;
@@ -621,6 +622,19 @@ std::string check_tile_plan(int f16, int tx, int ty, bool with_psi, const LatDev
                     : check_shape<4, false>(tx, ty, L, par, x0, y0, lo, hi, plo, phi);
 }
 
+// No exception crosses the C ABI: an allocation failure inside an entry point
+// returns LBM_ERR_OOM, anything else LBM_ERR_STATE.
+template <class F>
+int guarded(F&& f) noexcept {
+    try {
+        return f();
+    } catch (const std::bad_alloc&) {
+        return LBM_ERR_OOM;
+    } catch (...) {
+        return LBM_ERR_STATE;
+    }
+}
+
 }  // namespace
 
 // ================================================================== C ABI
@@ -666,7 +680,7 @@ const char* lbm_strerror(int code) {
 
 const char* lbm_last_error(lbm_handle* h) { return h ? h->err.c_str() : ""; }
 
-int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts* opts,
+static int lbm_create_body(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts* opts,
                lbm_handle** out) {
     if (!out) return LBM_ERR_ARG;
     *out = nullptr;
@@ -822,7 +836,12 @@ int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts*
     return LBM_OK;
 }
 
-int lbm_init(lbm_handle* h, int32_t lattice, const double* rho, const double* ux,
+int lbm_create(const lbm_lattice_desc* descs, int32_t n, const lbm_runtime_opts* opts,
+               lbm_handle** out) {
+    return guarded([&] { return lbm_create_body(descs, n, opts, out); });
+}
+
+static int lbm_init_body(lbm_handle* h, int32_t lattice, const double* rho, const double* ux,
              const double* uy) {
     if (!h || !rho || lattice < 0 || lattice >= (int)h->lat.size()) return LBM_ERR_ARG;
     LatDev& L = h->lat[lattice];
@@ -858,7 +877,12 @@ int lbm_init(lbm_handle* h, int32_t lattice, const double* rho, const double* ux
     return LBM_OK;
 }
 
-int lbm_step(lbm_handle* h, int64_t nsteps) {
+int lbm_init(lbm_handle* h, int32_t lattice, const double* rho, const double* ux,
+             const double* uy) {
+    return guarded([&] { return lbm_init_body(h, lattice, rho, ux, uy); });
+}
+
+static int lbm_step_body(lbm_handle* h, int64_t nsteps) {
     if (!h || nsteps < 0) return LBM_ERR_ARG;
     int rc = check_status_async(h);
     if (rc) return rc;
@@ -888,18 +912,30 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
     return LBM_OK;
 }
 
-int lbm_sync(lbm_handle* h) {
+int lbm_step(lbm_handle* h, int64_t nsteps) {
+    return guarded([&] { return lbm_step_body(h, nsteps); });
+}
+
+static int lbm_sync_body(lbm_handle* h) {
     if (!h) return LBM_ERR_ARG;
     return sync_status(h);
 }
 
-int lbm_status_detail(lbm_handle* h, int32_t* lattice) {
+int lbm_sync(lbm_handle* h) {
+    return guarded([&] { return lbm_sync_body(h); });
+}
+
+static int lbm_status_detail_body(lbm_handle* h, int32_t* lattice) {
     if (!h || !lattice) return LBM_ERR_ARG;
     *lattice = h->numeric_lattice;
     return LBM_OK;
 }
 
-int lbm_moments(lbm_handle* h, int32_t lattice, double* rho, double* ux, double* uy,
+int lbm_status_detail(lbm_handle* h, int32_t* lattice) {
+    return guarded([&] { return lbm_status_detail_body(h, lattice); });
+}
+
+static int lbm_moments_body(lbm_handle* h, int32_t lattice, double* rho, double* ux, double* uy,
                 double* mass) {
     if (!h || lattice < 0 || lattice >= (int)h->lat.size()) return LBM_ERR_ARG;
     const LatDev& L = h->lat[lattice];
@@ -936,9 +972,18 @@ int lbm_moments(lbm_handle* h, int32_t lattice, double* rho, double* ux, double*
     return sync_status(h);
 }
 
-int lbm_mass(lbm_handle* h, int32_t lattice, double* mass) {
+int lbm_moments(lbm_handle* h, int32_t lattice, double* rho, double* ux, double* uy,
+                double* mass) {
+    return guarded([&] { return lbm_moments_body(h, lattice, rho, ux, uy, mass); });
+}
+
+static int lbm_mass_body(lbm_handle* h, int32_t lattice, double* mass) {
     if (!mass) return LBM_ERR_ARG;
     return lbm_moments(h, lattice, nullptr, nullptr, nullptr, mass);
+}
+
+int lbm_mass(lbm_handle* h, int32_t lattice, double* mass) {
+    return guarded([&] { return lbm_mass_body(h, lattice, mass); });
 }
 
 void lbm_destroy(lbm_handle* h) {
@@ -947,13 +992,17 @@ void lbm_destroy(lbm_handle* h) {
     delete h;
 }
 
-int lbm_profile(lbm_handle* h, int32_t on) {
+static int lbm_profile_body(lbm_handle* h, int32_t on) {
     if (!h) return LBM_ERR_ARG;
     h->prof = on != 0;
     return LBM_OK;
 }
 
-int lbm_profile_read(lbm_handle* h, lbm_kernel_stat* out, int32_t max, int32_t* n) {
+int lbm_profile(lbm_handle* h, int32_t on) {
+    return guarded([&] { return lbm_profile_body(h, on); });
+}
+
+static int lbm_profile_read_body(lbm_handle* h, lbm_kernel_stat* out, int32_t max, int32_t* n) {
     if (!h || !n) return LBM_ERR_ARG;
     CK(h, cudaStreamSynchronize(h->stream));
     for (int k = 0; k < 2; ++k) {
@@ -985,9 +1034,13 @@ int lbm_profile_read(lbm_handle* h, lbm_kernel_stat* out, int32_t max, int32_t* 
     return LBM_OK;
 }
 
+int lbm_profile_read(lbm_handle* h, lbm_kernel_stat* out, int32_t max, int32_t* n) {
+    return guarded([&] { return lbm_profile_read_body(h, out, max, n); });
+}
+
 int64_t lbm_launch_count(lbm_handle* h) { return h ? h->launches : 0; }
 
-int lbm_info(lbm_handle* h, lbm_info_t* out) {
+static int lbm_info_body(lbm_handle* h, lbm_info_t* out) {
     if (!h || !out) return LBM_ERR_ARG;
     out->sites = h->sites;
     out->device_bytes = h->device_bytes;
@@ -1009,7 +1062,11 @@ int lbm_info(lbm_handle* h, lbm_info_t* out) {
     return LBM_OK;
 }
 
-int lbm_autotune(lbm_handle* h, int32_t repeats) {
+int lbm_info(lbm_handle* h, lbm_info_t* out) {
+    return guarded([&] { return lbm_info_body(h, out); });
+}
+
+static int lbm_autotune_body(lbm_handle* h, int32_t repeats) {
     if (!h || repeats < 1) return LBM_ERR_ARG;
     CK(h, cudaStreamSynchronize(h->stream));
     static const int shapes_tma[][2] = {{64, 8}, {64, 16}, {128, 4}, {128, 8}, {32, 16}};
@@ -1098,7 +1155,11 @@ int lbm_autotune(lbm_handle* h, int32_t repeats) {
     return LBM_OK;
 }
 
-int lbm_selfcheck_arith(const float* x, int64_t n, float* rcp, float* sq) {
+int lbm_autotune(lbm_handle* h, int32_t repeats) {
+    return guarded([&] { return lbm_autotune_body(h, repeats); });
+}
+
+static int lbm_selfcheck_arith_body(const float* x, int64_t n, float* rcp, float* sq) {
     if (!x || !rcp || !sq || n < 1 || n > ((int64_t)1 << 24)) return LBM_ERR_ARG;
     float* d = nullptr;
     uint32_t* flag = nullptr;
@@ -1125,7 +1186,11 @@ int lbm_selfcheck_arith(const float* x, int64_t n, float* rcp, float* sq) {
     return mismatch ? LBM_ERR_STATE : LBM_OK;
 }
 
-int lbm_selfcheck(char* report, int32_t report_len) {
+int lbm_selfcheck_arith(const float* x, int64_t n, float* rcp, float* sq) {
+    return guarded([&] { return lbm_selfcheck_arith_body(x, n, rcp, sq); });
+}
+
+static int lbm_selfcheck_body(char* report, int32_t report_len) {
     std::string msg;
     const int shapes[][2] = {{2, 2},   {3, 5},   {4, 4},    {7, 5},   {31, 33}, {32, 32},
                              {64, 3},  {65, 9},  {100, 37}, {127, 129}, {128, 8}, {200, 120},
@@ -1209,6 +1274,10 @@ done:
     if (msg.empty()) msg = "ok: " + std::to_string(checked) + " tile plans checked";
     if (report && report_len > 0) std::snprintf(report, (size_t)report_len, "%s", msg.c_str());
     return msg.rfind("ok:", 0) == 0 ? LBM_OK : LBM_ERR_STATE;
+}
+
+int lbm_selfcheck(char* report, int32_t report_len) {
+    return guarded([&] { return lbm_selfcheck_body(report, report_len); });
 }
 
 }  // extern "C"

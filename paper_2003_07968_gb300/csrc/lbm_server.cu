@@ -55,6 +55,7 @@
 
 #include "../../include/pplbm.h"
 #include "lbm_kernels.h"
+#include "lbm_host_scan.h"
 #include "lbm_layout.h"
 
 using namespace pplbm;
@@ -206,6 +207,7 @@ struct lbm_server {
     std::map<uint64_t, Request> reqs;
     uint64_t next_ticket = 1;
     bool stop = false;
+    bool dead = false;  // the worker ended on an exception
     lbm_server_stats st{};
     std::thread worker;
 };
@@ -466,7 +468,7 @@ void finish(lbm_server* S, Request* R, int status) {
     S->st.arena_in_use = arena_in_use(S);
 }
 
-void worker_main(lbm_server* S) {
+void worker_loop(lbm_server* S) {
     cudaSetDevice(S->device);
     std::vector<Request*> res;  // resident and still to run (host view)
     int64_t res_sites = 0;      // sites of the resident lattices still running
@@ -781,6 +783,36 @@ void worker_main(lbm_server* S) {
     for (Drain& d : drain) S->spare_events.push_back(d.done);
 }
 
+// The worker thread: an exception (an allocation that failed) must not end
+// the process; the server fails every request and refuses new ones.
+void worker_main(lbm_server* S) {
+    try {
+        worker_loop(S);
+    } catch (...) {
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->dead = true;
+        }
+        cudaStreamSynchronize(S->stream);
+        cudaStreamSynchronize(S->side);
+        cudaStreamSynchronize(S->up);
+        fail_all(S, LBM_ERR_STATE);
+    }
+}
+
+// No exception crosses the C ABI: an allocation failure inside an entry point
+// returns LBM_ERR_OOM, anything else LBM_ERR_STATE.
+template <class F>
+int guarded(F&& f) noexcept {
+    try {
+        return f();
+    } catch (const std::bad_alloc&) {
+        return LBM_ERR_OOM;
+    } catch (...) {
+        return LBM_ERR_STATE;
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -801,7 +833,7 @@ void lbm_server_opts_default(lbm_server_opts* o) {
     o->chunk_ms = 4.0;
 }
 
-int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
+static int lbm_server_create_body(const lbm_server_opts* opts, lbm_server** out) {
     if (!out) return LBM_ERR_ARG;
     *out = nullptr;
     lbm_server_opts o;
@@ -948,7 +980,11 @@ int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
     return LBM_OK;
 }
 
-int lbm_submit(lbm_server* S, const lbm_lattice_desc* d, const double* rho, int64_t nsteps,
+int lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
+    return guarded([&] { return lbm_server_create_body(opts, out); });
+}
+
+static int lbm_submit_body(lbm_server* S, const lbm_lattice_desc* d, const double* rho, int64_t nsteps,
                uint64_t* ticket) {
     if (!S || !d || !rho || !ticket || nsteps < 1) return LBM_ERR_ARG;
     Request R;
@@ -987,7 +1023,7 @@ int lbm_submit(lbm_server* S, const lbm_lattice_desc* d, const double* rho, int6
     R.nsteps = R.remaining = nsteps;
     R.t_submit = Clock::now();
     std::lock_guard<std::mutex> lk(S->mu);
-    if (S->stop) {
+    if (S->stop || S->dead) {
         if (slot) S->in_alloc.release(off, n);
         return LBM_ERR_STATE;
     }
@@ -1001,7 +1037,12 @@ int lbm_submit(lbm_server* S, const lbm_lattice_desc* d, const double* rho, int6
     return LBM_OK;
 }
 
-int lbm_poll(lbm_server* S, uint64_t ticket, double* rho, double* ux, double* uy,
+int lbm_submit(lbm_server* S, const lbm_lattice_desc* d, const double* rho, int64_t nsteps,
+               uint64_t* ticket) {
+    return guarded([&] { return lbm_submit_body(S, d, rho, nsteps, ticket); });
+}
+
+static int lbm_poll_body(lbm_server* S, uint64_t ticket, double* rho, double* ux, double* uy,
              double* latency_s) {
     if (!S) return LBM_ERR_ARG;
     std::lock_guard<std::mutex> lk(S->mu);
@@ -1041,11 +1082,20 @@ int lbm_poll(lbm_server* S, uint64_t ticket, double* rho, double* ux, double* uy
     return status;
 }
 
-int lbm_server_get_stats(lbm_server* S, lbm_server_stats* out) {
+int lbm_poll(lbm_server* S, uint64_t ticket, double* rho, double* ux, double* uy,
+             double* latency_s) {
+    return guarded([&] { return lbm_poll_body(S, ticket, rho, ux, uy, latency_s); });
+}
+
+static int lbm_server_get_stats_body(lbm_server* S, lbm_server_stats* out) {
     if (!S || !out) return LBM_ERR_ARG;
     std::lock_guard<std::mutex> lk(S->mu);
     *out = S->st;
     return LBM_OK;
+}
+
+int lbm_server_get_stats(lbm_server* S, lbm_server_stats* out) {
+    return guarded([&] { return lbm_server_get_stats_body(S, out); });
 }
 
 void lbm_server_destroy(lbm_server* S) {
