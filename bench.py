@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -29,7 +30,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BASELINE_METRIC = ("MLUPS and % of HBM peak per step; batched/served p50/p99 vs plain FP32 at "
+METRIC = ("MLUPS and % of HBM peak per step; batched/served p50/p99 vs plain FP32 at "
                    "1e-5")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -145,9 +146,8 @@ class ClockSampler:
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{self.index}.csv")
-            self.fh = open(self.path, "w")
+            fd, self.path = tempfile.mkstemp(prefix=f"clocks_rank{self.index}_", suffix=".csv")
+            self.fh = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
@@ -170,7 +170,13 @@ class ClockSampler:
             return None
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        with open(self.path) as fh:
+            lines = fh.readlines()
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -254,7 +260,7 @@ def run_reference(args):
     v = n * n * args.steps / dt / 1e6
     sample = (f"{n}x{n} periodic crop of the 8192^2 droplet across its interface per step, "
               f"FP64 C oracle with OpenMP")
-    out = {"impl": "reference", "metric": BASELINE_METRIC, "value": round(v, 3), "unit": "MLUPS",
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "MLUPS",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(dt / args.steps * 1e3, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -368,7 +374,7 @@ def run_gpu(args):
     es = 2 if args.storage == "f16dev" else 4
     step_bytes = 18 * es  # read 9 and write 9 populations: the method's minimum per site
     out = {
-        "metric": BASELINE_METRIC, "value": round(value, 3), "unit": "MLUPS",
+        "metric": METRIC, "value": round(value, 3), "unit": "MLUPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -476,7 +482,7 @@ def run_batched(args):
     kname, k2 = max(stats.items(), key=lambda kv: kv[1]["total_ms"])  # dominant kernel
     avg = k2["total_ms"] / max(k2["launches"], 1)
     achieved = k2["bytes_per_launch"] / (avg * 1e-3) / 1e9
-    out = {"metric": BASELINE_METRIC, "value": round(batched, 3), "unit": "MLUPS",
+    out = {"metric": METRIC, "value": round(batched, 3), "unit": "MLUPS",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -596,7 +602,7 @@ def run_served(args):
         P.lbm_destroy(hh)
         same = same and results[i]["rho"] is not None and bool(np.array_equal(a, results[i]["rho"]))
     pct = lambda v, q: float(np.percentile(np.array(v), q))
-    out = {"metric": BASELINE_METRIC, "value": round(served, 3), "unit": "MLUPS",
+    out = {"metric": METRIC, "value": round(served, 3), "unit": "MLUPS",
            "n_gpus": world, "steps": len(reqs), "warmup": 0,
            "ms_per_step": round(wall / len(reqs) * 1e3, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

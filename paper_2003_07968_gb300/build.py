@@ -1,7 +1,7 @@
 """Builds the in-tree CUDA library ``_lib/libpplbm.so`` for sm_103a with nvcc.
 
 The translation units compile in parallel; the result links the CUDA
-runtime statically so that only the driver is needed at run time.
+runtime statically so that only the CUDA driver library is needed at run time.
 """
 from __future__ import annotations
 
