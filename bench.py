@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--schedule", default="fused", choices=["two_pass", "fused"],
                     help="fused: one pass per step (default); two_pass: psi pass + collision pass")
     ap.add_argument("--storage", default="f32dev", choices=["f32", "f32dev", "f16dev"])
+    ap.add_argument("--collision", default="bgk", choices=["bgk", "mrt"],
+                    help="collision operator: BGK (default) or MRT with the rates of the "
+                         "paper's oscillation test (s = 1 for the non-hydrodynamic moments, "
+                         "1/tau for the stress)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=int, nargs=3, metavar=("TX", "TY", "SPT"), default=None,
                     help="fixed tile and sites per thread for both passes (no autotune)")
@@ -296,8 +300,11 @@ def run_gpu(args):
                "f16dev": P.LBM_STORE_F16_DEV}[args.storage]
     wl = roofline_workload(args.size)
     rho = wl["field"]()
+    coll = {}
+    if args.collision == "mrt":
+        coll = dict(collision=P.LBM_COLL_MRT, mrt_rates=[1.0] * 7 + [1.0 / wl["tau"]] * 2)
     d = P.lbm_desc_default(wl["nx"], wl["ny"], T=wl["T"], tau=wl["tau"], eos_precision=eos,
-                           storage=storage)
+                           storage=storage, **coll)
     h = P.lbm_create(d, kernel_variant={"auto": P.LBM_KERNEL_AUTO, "tma": P.LBM_KERNEL_TMA,
                                         "plain": P.LBM_KERNEL_PLAIN}[args.variant],
                      schedule={"two_pass": P.LBM_SCHED_TWO_PASS,
@@ -378,7 +385,9 @@ def run_gpu(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl["name"], "storage": args.storage, "eos": args.eos,
+        "config": {"workload": wl["name"] if args.collision == "bgk"
+                   else wl["name"].replace("BGK", "MRT"), "storage": args.storage, "eos": args.eos,
+                   "collision": args.collision,
                    "schedule": args.schedule, "kernel_variant": args.variant,
                    "psi_pass": {"variant": ["auto", "plain", "tma"][info["psi_variant"]],
                                 "tile": [info["psi_tile_x"], info["psi_tile_y"]],
@@ -395,7 +404,14 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": ncu_traffic(dom["name"], wl["key"]), "peak_source": peak_src,
+                     # the committed capture is of one kernel instance: the TMA single
+                     # pass, 32x16 tiles, FP32 deviations, float-float EOS, BGK
+                     "traffic": (ncu_traffic(dom["name"], wl["key"])
+                                 if (args.collision, args.storage, args.eos, args.schedule,
+                                     info["collide_variant"], info["tile_x"], info["tile_y"])
+                                 == ("bgk", "f32dev", "df", "fused", P.LBM_KERNEL_TMA, 32, 16)
+                                 else None),
+                     "peak_source": peak_src,
                      "bytes_per_launch": dom["bytes_per_launch"]},
         "step_roofline": {"algorithmic_bytes_per_site": step_bytes,
                           "effective_GBps": round(value * 1e6 * step_bytes / 1e9 / world, 1),
