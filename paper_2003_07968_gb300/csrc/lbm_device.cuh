@@ -241,14 +241,6 @@ __device__ __forceinline__ V sum9(const V g[9]) {
                 g[8]);
 }
 
-// 1/x correctly rounded (PTX rcp.rn.f32): a unique result.  The MRT site
-// collision uses it.
-__device__ __forceinline__ float rcp_rn(float x) {
-    float r;
-    asm("rcp.rn.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
 // The hardware approximations (one MUFU instruction each, flush to zero):
 // fixed functions of their input, so every kernel gets the same bits.
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -433,9 +425,7 @@ struct Eos<EOS_F32> {
         using Ln = Lanes<V>;
         const V one = Ln::set(1.f);
         const V s = vfma(Ln::set(-L.sb), rho, one);
-        V rr;
-#pragma unroll
-        for (int k = 0; k < Ln::n; ++k) Ln::put(rr, k, __frcp_rn(Ln::get(s, k)));
+        const V rr = vrcp(s);
         const V q = vfma(vadd(rr, rr), vmul(rr, rr), vfma(Ln::set(-2.f), rr, one));
         const V inner = vfma(Ln::set(L.s1), q, vfma(Ln::set(-L.s2), rho, Ln::set(-L.s3)));
         return psi_finish(L, rho, s, vmul(rho, inner), status, live);
@@ -453,6 +443,7 @@ struct Eos<EOS_F32> {
 struct SiteConsts {
     float rho0, om1, wa, wd, ra, rd, sa, sd, ga9, gd9, ga3, gd3, fsc, fk2, fkd;
     int m2v;
+    float zero;  // 0, as a value the compiler cannot see (LatDev::zero)
 };
 
 template <class V>
@@ -482,7 +473,7 @@ __device__ __forceinline__ void site_force(const SiteConsts& C, const V p[9], V&
 
 __device__ __forceinline__ SiteConsts site_consts(const LatDev& L) {
     return SiteConsts{L.rho0, L.om1, L.wa, L.wd, L.ra, L.rd, L.sa, L.sd, L.ga9, L.gd9,
-                      L.ga3, L.gd3, L.fsc, L.fk2, L.fkd, L.m2_variant};
+                      L.ga3, L.gd3, L.fsc, L.fk2, L.fkd, L.m2_variant, L.zero};
 }
 
 // ---- BGK collision with Guo forcing -------------------------------------------
@@ -547,7 +538,7 @@ __device__ __forceinline__ void collide_bgk(const SiteConsts& C, V drho, const V
 }
 
 // MRT collision (Eq. MRTCO) with Guo forcing in moment space (Eq. GFSMRT),
-// for the Gram-Schmidt matrix M of Appendix A, one site.  Written on the
+// for the Gram-Schmidt matrix M of Appendix A.  Written on the
 // non-equilibrium part n = f - f^eq, which is small, so rounding scales with
 // it and not with rho:
 //   f* = f^eq + M^-1 [ (I - Lambda) M n + (I - Lambda/2) M S ],
@@ -557,97 +548,95 @@ __device__ __forceinline__ void collide_bgk(const SiteConsts& C, V drho, const V
 // (M n)_3 = -F_x/2, (M n)_5 = -F_y/2 (Eq. FMD).  Back to populations with
 // M^-1 = M^T D^-1, D = diag(9, 36, 36, 6, 12, 6, 12, 4, 4) (the rows of M are
 // orthogonal); the rest population from mass conservation.
-__device__ __forceinline__ void collide_mrt_site(const SiteConsts& C, const float* s,
-                                                 const float g[9], const float p[9],
-                                                 float o[9]) {
-    const float drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-    const float rho = drho + C.rho0;
-    const float jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
-    const float jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
-    float Fx, Fy;
+// The sites are held in the lanes of V (paired FP32 for two sites), and the
+// code follows the rule of the paired arithmetic: a product
+// that is added enters an FMA, and a product needed as a value of its own
+// (the equilibria) is an FMA with the zero addend the compiler cannot see.
+// Two terms are simplified exactly: (1 - s3)(-Fx/2) + (1 - s3/2) Fx = Fx/2,
+// and likewise Fy/2 for the fifth moment.
+template <class V>
+__device__ __forceinline__ void collide_mrt(const SiteConsts& C, const float* s, V drho,
+                                            const V g[9], const V p[9], V o[9]) {
+    using Ln = Lanes<V>;
+    const V z0 = Ln::set(C.zero), half = Ln::set(0.5f), mone = Ln::set(-1.f);
+    const V rho = vadd(drho, Ln::set(C.rho0));
+    const V jx = vadd(vadd(vsub(g[1], g[3]), vsub(g[5], g[6])), vsub(g[8], g[7]));
+    const V jy = vsub(vadd(vsub(g[2], g[4]), vadd(g[5], g[6])), vadd(g[7], g[8]));
+    V Fx, Fy;
     site_force(C, p, Fx, Fy);
-    const float inv = rcp_rn(rho);
-    const float ux = fmaf(0.5f, Fx, jx) * inv;  // Eq. (FMD)
-    const float uy = fmaf(0.5f, Fy, jy) * inv;
-    const float usq = ux * ux + uy * uy;
-    const float uF = ux * Fx + uy * Fy;
-    const float base = drho - 1.5f * rho * usq;
-    // equilibrium deviations f^eq_i - w_i rho0
-    float e[9];
-    {
-        const float a1 = 4.5f * rho * ux * ux, b1 = 3.f * rho * ux;
-        const float a2 = 4.5f * rho * uy * uy, b2 = 3.f * rho * uy;
-        const float c5 = ux + uy, c6 = uy - ux;
-        const float a5 = 4.5f * rho * c5 * c5, b5 = 3.f * rho * c5;
-        const float a6 = 4.5f * rho * c6 * c6, b6 = 3.f * rho * c6;
-        e[1] = (1.f / 9.f) * (base + a1 + b1);
-        e[3] = (1.f / 9.f) * (base + a1 - b1);
-        e[2] = (1.f / 9.f) * (base + a2 + b2);
-        e[4] = (1.f / 9.f) * (base + a2 - b2);
-        e[5] = (1.f / 36.f) * (base + a5 + b5);
-        e[7] = (1.f / 36.f) * (base + a5 - b5);
-        e[6] = (1.f / 36.f) * (base + a6 + b6);
-        e[8] = (1.f / 36.f) * (base + a6 - b6);
-        e[0] = (4.f / 9.f) * base;
-    }
-    float n[9];
+    const V inv = vrcp(rho);
+    const V ux = vmul(vfma(half, Fx, jx), inv);  // Eq. (FMD)
+    const V uy = vmul(vfma(half, Fy, jy), inv);
+    const V usq = vfma(ux, ux, vmul(uy, uy));
+    const V uF = vfma(ux, Fx, vmul(uy, Fy));
+    const V base = vfma(vmul(Ln::set(-1.5f), rho), usq, drho);
+    // equilibrium deviations f^eq_i - w_i rho0 = w_i (base + 9/2 rho cu^2 +- 3 rho cu)
+    const V r45 = vmul(Ln::set(4.5f), rho), r3 = vmul(Ln::set(3.f), rho);
+    const V nr3 = vmul(Ln::set(-3.f), rho);
+    V e[9];
+    auto pair = [&](V cu, float w, int ip, int im) {
+        const V t = vfma(vmul(r45, cu), cu, base);
+        e[ip] = vfma(Ln::set(w), vfma(r3, cu, t), z0);
+        e[im] = vfma(Ln::set(w), vfma(nr3, cu, t), z0);
+    };
+    pair(ux, 1.f / 9.f, 1, 3);
+    pair(uy, 1.f / 9.f, 2, 4);
+    pair(vadd(ux, uy), 1.f / 36.f, 5, 7);
+    pair(vsub(uy, ux), 1.f / 36.f, 6, 8);
+    e[0] = vfma(Ln::set(4.f / 9.f), base, z0);
+    V n[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) n[i] = g[i] - e[i];
+    for (int i = 0; i < 9; ++i) n[i] = vsub(g[i], e[i]);
     // non-conserved moments of n
-    const float sa = (n[1] + n[2]) + (n[3] + n[4]), sd = (n[5] + n[6]) + (n[7] + n[8]);
-    const float m1 = -4.f * n[0] - sa + 2.f * sd;
-    const float m2 = 4.f * n[0] - 2.f * sa + sd;
-    const float m4 = (-2.f * n[1] + 2.f * n[3]) + ((n[5] - n[6]) + (n[8] - n[7]));
-    const float m6 = (-2.f * n[2] + 2.f * n[4]) + ((n[5] + n[6]) - (n[7] + n[8]));
-    const float m7 = (n[1] - n[2]) + (n[3] - n[4]);
-    const float m8 = (n[5] - n[6]) + (n[7] - n[8]);
+    const V sa = vadd(vadd(n[1], n[2]), vadd(n[3], n[4]));
+    const V sd = vadd(vadd(n[5], n[6]), vadd(n[7], n[8]));
+    const V m1 = vfma(Ln::set(-4.f), n[0], vfma(Ln::set(2.f), sd, vmul(sa, mone)));
+    const V m2 = vfma(Ln::set(4.f), n[0], vfma(Ln::set(-2.f), sa, sd));
+    const V m4 = vfma(Ln::set(-2.f), n[1],
+                      vfma(Ln::set(2.f), n[3], vadd(vsub(n[5], n[6]), vsub(n[8], n[7]))));
+    const V m6 = vfma(Ln::set(-2.f), n[2],
+                      vfma(Ln::set(2.f), n[4], vsub(vadd(n[5], n[6]), vadd(n[7], n[8]))));
+    const V m7 = vadd(vsub(n[1], n[2]), vsub(n[3], n[4]));
+    const V m8 = vadd(vsub(n[5], n[6]), vsub(n[7], n[8]));
     // (I - Lambda) M n + (I - Lambda/2) M S, moment by moment
-    const float p1 = (1.f - s[1]) * m1 + (1.f - 0.5f * s[1]) * (6.f * uF);
-    const float p2 = (1.f - s[2]) * m2 + (1.f - 0.5f * s[2]) * (-6.f * uF);
-    const float p3 = (1.f - s[3]) * (-0.5f * Fx) + (1.f - 0.5f * s[3]) * Fx;
-    const float p4 = (1.f - s[4]) * m4 + (1.f - 0.5f * s[4]) * (-Fx);
-    const float p5 = (1.f - s[5]) * (-0.5f * Fy) + (1.f - 0.5f * s[5]) * Fy;
-    const float p6 = (1.f - s[6]) * m6 + (1.f - 0.5f * s[6]) * (-Fy);
-    const float p7 = (1.f - s[7]) * m7 + (1.f - 0.5f * s[7]) * (2.f * (ux * Fx - uy * Fy));
-    const float p8 = (1.f - s[8]) * m8 + (1.f - 0.5f * s[8]) * (ux * Fy + uy * Fx);
-    // M^T D^-1 (the mass moment of the update is zero)
-    const float q1 = p1 * (1.f / 36.f), q2 = p2 * (1.f / 36.f);
-    const float q3 = p3 * (1.f / 6.f), q4 = p4 * (1.f / 12.f);
-    const float q5 = p5 * (1.f / 6.f), q6 = p6 * (1.f / 12.f);
-    const float q7 = p7 * 0.25f, q8 = p8 * 0.25f;
-    const float ax = -q1 - 2.f * q2;  // common part of the axis directions
-    const float dg = 2.f * q1 + q2;   // common part of the diagonals
-    o[1] = e[1] + (ax + q3 - 2.f * q4 + q7);
-    o[2] = e[2] + (ax + q5 - 2.f * q6 - q7);
-    o[3] = e[3] + (ax - q3 + 2.f * q4 + q7);
-    o[4] = e[4] + (ax - q5 + 2.f * q6 - q7);
-    o[5] = e[5] + (dg + q3 + q4 + q5 + q6 + q8);
-    o[6] = e[6] + (dg - q3 - q4 + q5 + q6 - q8);
-    o[7] = e[7] + (dg - q3 - q4 - q5 - q6 + q8);
-    o[8] = e[8] + (dg + q3 + q4 - q5 - q6 - q8);
-    o[0] = drho - (((o[1] + o[2]) + (o[3] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
+    auto A = [&](int k) { return Ln::set(1.f - s[k]); };
+    auto B = [&](int k, float f) { return Ln::set(f * (1.f - 0.5f * s[k])); };
+    const V p1 = vfma(A(1), m1, vmul(B(1, 6.f), uF));
+    const V p2 = vfma(A(2), m2, vmul(B(2, -6.f), uF));
+    const V p3 = vmul(half, Fx);
+    const V p4 = vfma(A(4), m4, vmul(B(4, -1.f), Fx));
+    const V p5 = vmul(half, Fy);
+    const V p6 = vfma(A(6), m6, vmul(B(6, -1.f), Fy));
+    const V p7 = vfma(A(7), m7, vmul(B(7, 2.f), vfma(ux, Fx, vmul(vmul(uy, mone), Fy))));
+    const V p8 = vfma(A(8), m8, vmul(B(8, 1.f), vfma(ux, Fy, vmul(uy, Fx))));
+    // M^T D^-1 (the mass moment of the update is zero), with the 1/36, 1/6,
+    // 1/12 and 1/4 of D^-1 and the entries of M as FMA multiplicands
+    auto K = [](float c) { return Ln::set(c); };
+    const V ax = vfma(p1, K(-1.f / 36.f), vmul(p2, K(-2.f / 36.f)));  // axis directions
+    const V dg = vfma(p1, K(2.f / 36.f), vmul(p2, K(1.f / 36.f)));    // diagonals
+    o[1] = vfma(p3, K(1.f / 6.f), vfma(p4, K(-2.f / 12.f), vfma(p7, K(0.25f), vadd(e[1], ax))));
+    o[2] = vfma(p5, K(1.f / 6.f), vfma(p6, K(-2.f / 12.f), vfma(p7, K(-0.25f), vadd(e[2], ax))));
+    o[3] = vfma(p3, K(-1.f / 6.f), vfma(p4, K(2.f / 12.f), vfma(p7, K(0.25f), vadd(e[3], ax))));
+    o[4] = vfma(p5, K(-1.f / 6.f), vfma(p6, K(2.f / 12.f), vfma(p7, K(-0.25f), vadd(e[4], ax))));
+    // diagonals: e + dg +- (q3 + q4) +- (q5 + q6) +- q8
+    const V d3 = vfma(p3, K(1.f / 6.f), vmul(p4, K(1.f / 12.f)));  // q3 + q4
+    const V d5 = vfma(p5, K(1.f / 6.f), vmul(p6, K(1.f / 12.f)));  // q5 + q6
+    o[5] = vfma(p8, K(0.25f), vadd(vadd(e[5], dg), vadd(d3, d5)));
+    o[6] = vfma(p8, K(-0.25f), vadd(vadd(e[6], dg), vsub(d5, d3)));
+    o[7] = vfma(p8, K(0.25f), vsub(vadd(e[7], dg), vadd(d3, d5)));
+    o[8] = vfma(p8, K(-0.25f), vadd(vadd(e[8], dg), vsub(d3, d5)));
+    o[0] = vsub(drho, vadd(vadd(vadd(o[1], o[2]), vadd(o[3], o[4])),
+                           vadd(vadd(o[5], o[6]), vadd(o[7], o[8]))));
 }
 
 // One collision (BGK or MRT) of the sites held in the lanes of V.
 template <bool MRT, class V>
 __device__ __forceinline__ void collide(const SiteConsts& C, const float* mrt_s, V drho,
                                         const V g[9], const V p[9], V o[9]) {
-    if (!MRT) {
+    if (!MRT)
         collide_bgk(C, drho, g, p, o);
-    } else {
-#pragma unroll
-        for (int k = 0; k < Lanes<V>::n; ++k) {
-            float gs[9], ps[9], os[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                gs[i] = Lanes<V>::get(g[i], k);
-                ps[i] = Lanes<V>::get(p[i], k);
-            }
-            collide_mrt_site(C, mrt_s, gs, ps, os);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) Lanes<V>::put(o[i], k, os[i]);
-        }
-    }
+    else
+        collide_mrt(C, mrt_s, drho, g, p, o);
 }
 
 // The periodic images of site (x, y) within GW of the interior, without the
