@@ -65,7 +65,8 @@ extern "C" {
 
 /* ---- arithmetic of psi / Eq. (CSEOS) ------------------------------------- */
 #define LBM_EOS_F64 0 /* native FP64                                             */
-#define LBM_EOS_DF 1  /* float-float pairs (about 43 significant bits)           */
+#define LBM_EOS_DF 1  /* float-float pairs (about 43 significant bits on the
+                          radicand), FP32 psi                                  */
 #define LBM_EOS_F32 2 /* FP32                                                    */
 
 /* ---- collision operator -------------------------------------------------- */
@@ -170,9 +171,13 @@ int lbm_init(lbm_handle* h, int32_t lattice, const double* rho, const double* ux
 int lbm_step(lbm_handle* h, int64_t nsteps);
 
 /* Macroscopic fields of one lattice at the current time: rho (Eq. FD), the
- * force-shifted velocity (Eq. FMD) and the total mass sum_x rho, summed in
- * FP64.  Any output may be NULL.  Waits for queued work.
- * Errors: LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_NUMERIC. */
+ * force-shifted velocity (Eq. FMD) and the total mass sum_x rho.  Each
+ * site's nine stored values are summed as a float-float pair and the
+ * result is FP64 (rho to about 2^-47 of the exact sum of the stored
+ * values); the mass is an FP64 sum of those site sums.  Host outputs are
+ * row-major [ny][nx]; any output may be NULL.  Velocities need psi and the
+ * force (one extra pass); rho and the mass alone do not.  Waits for queued
+ * work.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_NUMERIC. */
 int lbm_moments(lbm_handle* h, int32_t lattice, double* rho, double* ux, double* uy,
                 double* mass);
 
