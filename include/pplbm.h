@@ -173,8 +173,8 @@ int lbm_step(lbm_handle* h, int64_t nsteps);
 /* Macroscopic fields of one lattice at the current time: rho (Eq. FD), the
  * force-shifted velocity (Eq. FMD) and the total mass sum_x rho.  Each
  * site's nine stored values are summed as a float-float pair and the
- * result is FP64 (rho to about 2^-47 of the exact sum of the stored
- * values); the mass is an FP64 sum of those site sums.  Host outputs are
+ * result is FP64 (within 2^-42 of the largest partial sum of the exact sum
+ * of the stored values); the mass is an FP64 sum of those site sums.  Host outputs are
  * row-major [ny][nx]; any output may be NULL.  Velocities need psi and the
  * force (one extra pass); rho and the mass alone do not.  Waits for queued
  * work.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_NUMERIC. */

@@ -317,8 +317,10 @@ __device__ __forceinline__ float two_sum(float a, float b, float& e) {
 }
 
 // sum_i w_i v_i for weights w_i in {-1, 0, 1} as an unevaluated pair
-// hi + lo: hi by error-free steps, their rounding errors gathered in lo, so
-// that hi + lo is within about 8 u^2 |hi| of the exact sum (u = 2^-24).
+// hi + lo: hi by error-free steps, their rounding errors (each at most u
+// times a partial sum) gathered in lo with FP32 roundings of their own, so
+// that hi + lo is within 64 u^2 of the largest partial sum of the exact sum
+// (u = 2^-24).
 // This keeps the per-site sums off the FP64 pipe, which is slow on GB300.
 __device__ __forceinline__ void signed_sum9(const float v[9], const int w[9], float& hi,
                                             float& lo) {
