@@ -337,7 +337,9 @@ int lbm_poll(lbm_server* s, uint64_t ticket, double* rho, double* ux, double* uy
 int lbm_server_get_stats(lbm_server* s, lbm_server_stats* out);
 
 /* Stop the worker (finishing the chunk in flight), free everything.  Pending
- * requests are dropped.  NULL is ignored. */
+ * requests are dropped.  No other call on this server may be in progress or
+ * follow (submit and poll are thread-safe among themselves, not against
+ * destroy).  NULL is ignored. */
 void lbm_server_destroy(lbm_server* s);
 
 /* ---- mass without allocation ------------------------------------------- */

@@ -1045,24 +1045,39 @@ int lbm_submit(lbm_server* S, const lbm_lattice_desc* d, const double* rho, int6
 static int lbm_poll_body(lbm_server* S, uint64_t ticket, double* rho, double* ux, double* uy,
              double* latency_s) {
     if (!S) return LBM_ERR_ARG;
-    std::lock_guard<std::mutex> lk(S->mu);
-    auto it = S->reqs.find(ticket);
-    if (it == S->reqs.end()) return LBM_ERR_UNKNOWN_TICKET;
-    Request& R = it->second;
-    if (R.state != ST_DONE) return LBM_PENDING;
-    const int status = R.status;
+    // Under the lock: take the finished request out of the table (its result
+    // slot stays allocated, so nothing else can reuse it).  The copy of the
+    // result runs without the lock, so that the worker is never held up by
+    // a poll; the slot is released afterwards.
+    int status;
+    size_t n = 0, out_off = kNoSlot, out_n = 0;
+    std::vector<double> vr, vx, vy;  // a result that had no pinned slot
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->reqs.find(ticket);
+        if (it == S->reqs.end()) return LBM_ERR_UNKNOWN_TICKET;
+        Request& R = it->second;
+        if (R.state != ST_DONE) return LBM_PENDING;
+        status = R.status;
+        n = (size_t)R.L.nx * R.L.ny;
+        out_off = R.out_off;
+        out_n = R.out_n;
+        vr.swap(R.rho);
+        vx.swap(R.ux);
+        vy.swap(R.uy);
+        if (latency_s) *latency_s = std::chrono::duration<double>(R.t_done - R.t_submit).count();
+        if (R.in_off != kNoSlot) S->in_alloc.release(R.in_off, R.in_n);
+        S->reqs.erase(it);
+    }
     if (status == LBM_OK) {
-        const size_t n = (size_t)R.L.nx * R.L.ny;
         const bool vel = S->o.with_velocity != 0;
-        // the result is in its pinned slot, or (no slot was free) in R's vectors
-        const double* src[3] = {R.rho.data(), R.ux.data(), R.uy.data()};
-        if (R.out_off != kNoSlot) {
-            const double* h = S->out_host + R.out_off;
+        // the result is in its pinned slot, or (no slot was free) in the vectors
+        const double* src[3] = {vr.data(), vel ? vx.data() : nullptr, vel ? vy.data() : nullptr};
+        if (out_off != kNoSlot) {
+            const double* h = S->out_host + out_off;
             src[0] = h;
             src[1] = vel ? h + n : nullptr;
             src[2] = vel ? h + 2 * n : nullptr;
-        } else if (!vel) {
-            src[1] = src[2] = nullptr;
         }
         if (rho) std::memcpy(rho, src[0], n * sizeof(double));
         // without with_velocity the server keeps no velocities: NaN
@@ -1075,10 +1090,10 @@ static int lbm_poll_body(lbm_server* S, uint64_t ticket, double* rho, double* ux
                 std::fill(dst, dst + n, std::numeric_limits<double>::quiet_NaN());
         }
     }
-    if (latency_s) *latency_s = std::chrono::duration<double>(R.t_done - R.t_submit).count();
-    if (R.out_off != kNoSlot) S->out_alloc.release(R.out_off, R.out_n);
-    if (R.in_off != kNoSlot) S->in_alloc.release(R.in_off, R.in_n);
-    S->reqs.erase(it);
+    if (out_off != kNoSlot) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->out_alloc.release(out_off, out_n);
+    }
     return status;
 }
 
