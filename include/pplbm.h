@@ -368,6 +368,19 @@ void lbm_server_destroy(lbm_server* s);
 int lbm_mass_noalloc(const float* values, int64_t count, double offset, double* mass_out,
                      void* stream);
 
+/* Failure-detection test of the single pass (schedule LBM_SCHED_FUSED on the
+ * TMA kernel): the next time step skips the shared-memory staging copy of
+ * tile `tile` (0 <= tile < the pass's tile count, lbm_info n_tiles), so the
+ * consumers' bounded wait for it runs out (about 4e9 SM cycles, 2 s at
+ * 2 GHz), every consumer of that CTA leaves together and the producer drains
+ * its copies (bounded too).  No kernel traps or hangs; the step's results
+ * are garbage and the next lbm_sync reports LBM_ERR_TIMEOUT with the lattice
+ * in lbm_status_detail.  lbm_init of that lattice clears the fault, and the
+ * handle goes on.  Arms one launch; no CUDA graph replays it.
+ * Errors: LBM_ERR_ARG (no handle, another schedule or kernel, tile out of
+ * range). */
+int lbm_inject_copy_timeout(lbm_handle* h, int32_t tile);
+
 /* The reciprocal and square root of the step kernels (the hardware
  * approximations, each refined by one Newton-Raphson step on the paired FP32
  * pipe; used by the float-float EOS, Eqs. DED and CSEOS, and by the velocity of

@@ -137,6 +137,7 @@ SIGNATURES = {
     "lbm_launch_count": (ctypes.c_int64, [_vp]),
     "lbm_info": (ctypes.c_int, [_vp, ctypes.POINTER(Info)]),
     "lbm_autotune": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "lbm_inject_copy_timeout": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "lbm_selfcheck": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int32]),
     "lbm_selfcheck_arith": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.c_int64,
                                            ctypes.POINTER(ctypes.c_float),
@@ -383,6 +384,11 @@ def lbm_selfcheck() -> tuple[int, str]:
     buf = ctypes.create_string_buffer(512)
     rc = load().lbm_selfcheck(buf, 512)
     return rc, buf.value.decode()
+
+
+def lbm_inject_copy_timeout(h: Handle, tile: int) -> None:
+    """Arm the failure-detection test of the single pass for the next step."""
+    _check(load().lbm_inject_copy_timeout(h.ptr, int(tile)), "lbm_inject_copy_timeout", h)
 
 
 def lbm_selfcheck_arith(x) -> tuple[np.ndarray, np.ndarray]:

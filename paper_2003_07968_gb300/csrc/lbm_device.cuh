@@ -97,6 +97,9 @@ struct StepArgs {
     // step >= quota[lattice] are skipped; nullptr for handles
     const int* quota;
     int step;
+    // failure-detection test: tile + 1 whose staging copy the single pass
+    // skips, so that the consumers' bounded wait for it runs out (0: none)
+    int starve = 0;
 };
 
 // ---- storage traits ---------------------------------------------------------

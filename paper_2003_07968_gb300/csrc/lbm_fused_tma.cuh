@@ -217,6 +217,8 @@ __global__ void __launch_bounds__(kBlockF, 2)
                 break;
             }
             const int s = k % G::STAGES;
+            // failure-detection test: no copy and no arrival for this tile
+            const bool starved = a.starve == t + 1;
             if (k >= G::STAGES) {
                 const bool ok = mbar_wait_bounded(&empty[s], (uint32_t)(k / G::STAGES - 1) & 1u);
                 if (!__all_sync(0xffffffffu, ok)) {
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(kBlockF, 2)
                 // one tensor copy: columns from x0 - H (element x0 of the row, a
                 // multiple of 32), rows from y0 - 2 (row row0 + y0 of the row
                 // space), planes of the current buffer
-                if (lane == 0) {
+                if (lane == 0 && !starved) {
                     const int4 tl = __ldg(&a.tiles[t]);
                     desc[s] = tl;
                     const LatDev& Lt = MODE == 1 ? lat0 : a.lats[tl.x];
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(kBlockF, 2)
                 const int4 tl = __ldg(&a.tiles[t]);
                 if (lane == 0) desc[s] = tl;
                 __syncwarp();
-                issue_fused<S, TX, TY>(a, tl, smem + s * G::STAGEB, &full[s]);
+                if (!starved) issue_fused<S, TX, TY>(a, tl, smem + s * G::STAGEB, &full[s]);
             }
             ++k;
         }

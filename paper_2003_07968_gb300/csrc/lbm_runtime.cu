@@ -92,6 +92,7 @@ struct lbm_handle {
     uint32_t* status_host = nullptr;  // pinned
     cudaEvent_t status_ev = nullptr;
     bool status_pending = false;
+    int32_t starve = 0;        // armed failure-detection test (tile + 1), for one launch
     int numeric_lattice = -1;  // first lattice with a device fault bit
     uint32_t fault_bits = 0;   // OR of the device fault bits seen
     int sm_count = 0;
@@ -244,7 +245,7 @@ void drop_graph(lbm_handle* h) {
 }
 
 StepArgs step_args(lbm_handle* h, int parity, int k) {
-    StepArgs a;
+    StepArgs a{};
     a.lats = h->lat_dev;
     a.tiles = h->pass[k].tiles;
     a.ntiles = h->pass[k].ntiles;
@@ -303,7 +304,10 @@ int launch_step(lbm_handle* h, int p) {
     }
     if (!fused) CK(h, launch_pass(h, 0, step_args(h, p, 0), h->pass[0].grid));
     if (h->prof) CK(h, cudaEventRecord(e1, h->stream));
-    CK(h, launch_pass(h, 1, step_args(h, p, 1), h->pass[1].grid));
+    StepArgs a1 = step_args(h, p, 1);
+    a1.starve = h->starve;  // an armed failure-detection test goes into this launch only
+    h->starve = 0;
+    CK(h, launch_pass(h, 1, a1, h->pass[1].grid));
     if (h->prof) {
         CK(h, cudaEventRecord(e2, h->stream));
         // the psi pair owns e0, the step pair owns e1 and e2
@@ -887,7 +891,7 @@ static int lbm_step_body(lbm_handle* h, int64_t nsteps) {
     int rc = check_status_async(h);
     if (rc) return rc;
     int64_t left = nsteps;
-    if (!h->prof && h->graph_steps > 0 && left >= h->graph_steps) {
+    if (!h->prof && !h->starve && h->graph_steps > 0 && left >= h->graph_steps) {
         if (!h->graph[h->parity]) {
             rc = capture_graph(h);
             if (rc) return rc;
@@ -1157,6 +1161,20 @@ static int lbm_autotune_body(lbm_handle* h, int32_t repeats) {
 
 int lbm_autotune(lbm_handle* h, int32_t repeats) {
     return guarded([&] { return lbm_autotune_body(h, repeats); });
+}
+
+static int lbm_inject_copy_timeout_body(lbm_handle* h, int32_t tile) {
+    if (!h) return LBM_ERR_ARG;
+    const Pass& P = h->pass[1];
+    if (h->schedule != LBM_SCHED_FUSED || P.variant != LBM_KERNEL_TMA || tile < 0 ||
+        tile >= P.ntiles)
+        return LBM_ERR_ARG;
+    h->starve = tile + 1;  // the next launch of the single pass; no graph replays it
+    return LBM_OK;
+}
+
+int lbm_inject_copy_timeout(lbm_handle* h, int32_t tile) {
+    return guarded([&] { return lbm_inject_copy_timeout_body(h, tile); });
 }
 
 static int lbm_selfcheck_arith_body(const float* x, int64_t n, float* rcp, float* sq) {

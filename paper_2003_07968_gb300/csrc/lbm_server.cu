@@ -276,7 +276,7 @@ cudaError_t launch(lbm_server* S, int k, const StepArgs& a, int grid, cudaStream
 }
 
 StepArgs args(lbm_server* S, const TableSet& T, int k, int parity) {
-    StepArgs a;
+    StepArgs a{};
     a.lats = T.lat;
     a.tiles = T.tiles[k];
     a.ntiles = T.ntiles[k];

@@ -7,6 +7,7 @@ speed (|u| is tiny and sign-changing, so a pointwise relative norm is
 meaningless there).
 """
 import math
+import time
 
 import numpy as np
 import pytest
@@ -171,6 +172,36 @@ def test_non_finite_initial_density_is_refused(P):
         P.lbm_submit(srv, P.lbm_desc_default(64, 64, T=0.8), rho, 10)
     assert err.value.code == P.LBM_ERR_ARG
     P.lbm_server_destroy(srv)
+
+
+def test_copy_timeout_is_reported_and_the_handle_recovers(P):
+    # failure detection without a GPU fault: one tile's staging copy is
+    # skipped, so the consumers' bounded wait for it runs out (about 2 s), the
+    # CTA's warps leave together and the producer drains its copies; the step
+    # reports LBM_ERR_TIMEOUT, re-initialising the lattice clears it, and the
+    # handle goes on to match the oracle
+    n = 128
+    rho = synth.droplet(n, n, 30.0, 0.8)
+    h = P.lbm_create(P.lbm_desc_default(n, n, T=0.8), kernel_variant=P.LBM_KERNEL_TMA)
+    info = P.lbm_info(h)
+    assert info["collide_variant"] == P.LBM_KERNEL_TMA and info["tensor_map"] == 1
+    P.lbm_init(h, 0, rho)
+    P.lbm_step(h, 3)
+    P.lbm_sync(h)
+    P.lbm_inject_copy_timeout(h, info["n_tiles"] // 2)
+    t0 = time.time()
+    P.lbm_step(h, 2)
+    with pytest.raises(P.LbmError) as err:
+        P.lbm_sync(h)
+    waited = time.time() - t0
+    assert err.value.code == P.LBM_ERR_TIMEOUT and P.lbm_status_detail(h) == 0
+    print(f"copy timeout reported after {waited:.1f} s")
+    assert 0.5 < waited < 60
+    P.lbm_init(h, 0, rho)
+    P.lbm_step(h, 200)
+    got = P.lbm_moments(h, 0, mass=False)["rho"]
+    P.lbm_destroy(h)
+    assert rel(got, oracle_run(rho, 200)["rho"]) <= RTOL_RHO
 
 
 def test_mass_drift_fp32(P):
