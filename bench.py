@@ -70,6 +70,11 @@ def parse():
                          "at least the tile count: one CTA per tile)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip lbm_autotune (tile shapes, sites per thread, grid) before timing")
+    ap.add_argument("--lattices", type=int, default=512,
+                    help="batched workload: the first N lattices of the 512-lattice recipe "
+                         "(512 is the benchmark; fewer are for profiler captures)")
+    ap.add_argument("--no-sequential", dest="sequential", action="store_false",
+                    help="batched workload: skip the one-handle-per-lattice comparison")
     ap.add_argument("--size", type=int, default=8192,
                     help="lattice side of the droplet workload (8192 is the benchmark; "
                          "smaller sides are for profiler captures)")
@@ -315,7 +320,7 @@ def run_gpu(args):
     st = h.stream
     P.lbm_init(h, 0, rho)
     if args.autotune and not args.tile:
-        P.lbm_autotune(h, 3)
+        P.lbm_autotune(h, 10)
     info = P.lbm_info(h)
     sites = info["sites"]
     P.lbm_step(h, args.warmup)
@@ -429,6 +434,30 @@ def run_gpu(args):
 
 
 # ------------------------------------------------------------------ batched workload
+def run_sequential(P, descs, fields, sites, args):
+    """The batch's lattices stepped one handle after another on one stream (MLUPS)."""
+    import torch
+
+    stream = torch.cuda.Stream()
+    hs = []
+    for d, f in zip(descs, fields):
+        hh = P.lbm_create(d, stream=stream)
+        P.lbm_init(hh, 0, f)
+        P.lbm_step(hh, args.warmup)
+        hs.append(hh)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for hh in hs:
+        P.lbm_step(hh, args.steps)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = s0.elapsed_time(s1)
+    for hh in hs:
+        P.lbm_destroy(hh)
+    return sites * args.steps / (seq_ms * 1e-3) / 1e6
+
+
 def run_batched(args):
     """512 independent droplet lattices of uneven sizes (sides U{64..512},
     R = side x U(0.15, 0.35), T_r U(0.6, 0.9), tau = 1) stepped together by
@@ -445,7 +474,7 @@ def run_batched(args):
     P.load()
     storage = {"f32": P.LBM_STORE_F32, "f32dev": P.LBM_STORE_F32_DEV,
                "f16dev": P.LBM_STORE_F16_DEV}[args.storage]
-    rec = synth.batch_recipe()
+    rec = synth.batch_recipe()[:max(1, min(args.lattices, 512))]
     descs = [P.lbm_desc_default(r["nx"], r["ny"], T=r["T"], storage=storage) for r in rec]
     fields = [synth.droplet(r["nx"], r["ny"], r["R"], r["T"]) for r in rec]
     sites = sum(r["nx"] * r["ny"] for r in rec)
@@ -453,7 +482,7 @@ def run_batched(args):
     for i, f in enumerate(fields):
         P.lbm_init(h, i, f)
     if args.autotune:
-        P.lbm_autotune(h, 3)
+        P.lbm_autotune(h, 10)
     P.lbm_step(h, args.warmup)
     P.lbm_sync(h)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -475,24 +504,7 @@ def run_batched(args):
     P.lbm_destroy(h)
     batched = sites * args.steps / (ms * 1e-3) / 1e6
     # sequential: one handle per lattice, stepped one after another on one stream
-    stream = torch.cuda.Stream()
-    hs = []
-    for d, f in zip(descs, fields):
-        hh = P.lbm_create(d, stream=stream)
-        P.lbm_init(hh, 0, f)
-        P.lbm_step(hh, args.warmup)
-        hs.append(hh)
-    torch.cuda.synchronize()
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    for hh in hs:
-        P.lbm_step(hh, args.steps)
-    s1.record(stream)
-    torch.cuda.synchronize()
-    seq_ms = s0.elapsed_time(s1)
-    for hh in hs:
-        P.lbm_destroy(hh)
-    sequential = sites * args.steps / (seq_ms * 1e-3) / 1e6
+    sequential = run_sequential(P, descs, fields, sites, args) if args.sequential else None
     peak, peak_src = measured_hbm_peak()
     es = 2 if args.storage == "f16dev" else 4
     kname, k2 = max(stats.items(), key=lambda kv: kv[1]["total_ms"])  # dominant kernel
@@ -502,15 +514,17 @@ def run_batched(args):
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"batched: 512 droplet lattices, sides U{{64..512}}, {sites} sites",
+           "config": {"workload": f"batched: {len(rec)} droplet lattices, sides U{{64..512}}, "
+                                  f"{sites} sites",
                       "storage": args.storage, "eos": args.eos,
                       "psi_pass": [info["psi_variant"], info["psi_tile_x"], info["psi_tile_y"],
                                    info["psi_spt"], info["psi_grid_ctas"]],
                       "collide_pass": [info["collide_variant"], info["tile_x"], info["tile_y"],
                                        info["spt"], info["grid_ctas"]],
                       "schedule": ["auto", "two_pass", "fused"][info["schedule"]]},
-           "batched": {"MLUPS": round(batched, 1), "sequential_MLUPS": round(sequential, 1),
-                       "speedup": round(batched / sequential, 3),
+           "batched": {"MLUPS": round(batched, 1),
+                       "sequential_MLUPS": round(sequential, 1) if sequential else None,
+                       "speedup": round(batched / sequential, 3) if sequential else None,
                        "sequential": "one handle per lattice, lbm_step one after another"},
            "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                         "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
