@@ -58,7 +58,7 @@ extern "C" {
 #define LBM_ERR_UNKNOWN_TICKET (-7) /* lbm_poll of a ticket never issued        */
 #define LBM_ERR_CAPACITY (-8)       /* request larger than the server can hold  */
 
-/* ---- population storage (spec precision form) ---------------------- */
+/* ---- population storage (precision forms) -------------------------------- */
 #define LBM_STORE_F32 0     /* f_i in FP32                                       */
 #define LBM_STORE_F32_DEV 1 /* f_i - w_i rho0 in FP32                            */
 #define LBM_STORE_F16_DEV 2 /* f_i - w_i rho0 in FP16 (IEEE binary16)            */
