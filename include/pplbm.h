@@ -343,27 +343,32 @@ int lbm_server_get_stats(lbm_server* s, lbm_server_stats* out);
 void lbm_server_destroy(lbm_server* s);
 
 /* ---- mass without allocation ------------------------------------------- */
-/* The paper has no counterpart to this entry point; it serves callers that
- * may not allocate device memory at the moment they want a conserved-mass
- * check: code running while a stream is captured into a CUDA graph,
+/* The paper has no counterpart to this entry point.  It serves callers that
+ * may not allocate device memory at the moment they want a mass check:
  * applications that reserve all device memory up front through their own
- * allocator, or real-time loops that must not take allocator locks.
+ * allocator and forbid later allocations, and real-time loops that must not
+ * take an allocator's locks or wait for it.
  *
  * Writes to *mass_out (device pointer, caller-owned) the FP64 sum of
- * `count` FP32 values at `values` (device pointer, caller-owned, e.g. the
- * nine population planes of a lattice stored densely) plus `offset` (for
- * deviation storage: number of sites x rho0).  Queued on `stream`
- * (cudaStream_t, NULL = the legacy default stream); returns once queued.
+ * `count` FP32 values at `values` (device pointer, caller-owned, dense: every
+ * value in [values, values + count) is added, so a pitched array would add
+ * its padding too) plus `offset`, e.g. a density field the caller holds in
+ * FP32.  A handle's stored population planes are not such values: they hold
+ * rest-referenced deviations whose mass needs weights (lbm_mass gives it).
+ * Queued on `stream` (cudaStream_t, NULL = the legacy default stream);
+ * returns once queued.
  * Allocates nothing: its partial sums live in a fixed array in the
  * library's own device memory, 2 MiB on every GPU that loads the library,
  * held until the process exits.  That array limits `count` to
  * LBM_NOALLOC_MAX_COUNT values (4 GiB of FP32); larger requests fail with
  * LBM_ERR_CAPACITY before any GPU work.  The first call on a device looks up
  * the array's device address (the host only sees a stand-in for the
- * symbol); make that first call before any stream capture.  Every call
- * uses the same array, so calls whose kernels overlap on the GPU race;
- * order them on one stream.  Errors: LBM_ERR_ARG (NULL pointer, count < 1),
- * LBM_ERR_CAPACITY, LBM_ERR_CUDA. */
+ * symbol) and keeps it for the life of the process: make that first call
+ * before any stream capture, and do not use the entry point on a device
+ * after a reset of it (cudaDeviceReset), whose new context would not hold
+ * that address.  Every call uses the same array, so calls whose kernels
+ * overlap on the GPU race; order them on one stream.  Errors: LBM_ERR_ARG
+ * (NULL pointer, count < 1), LBM_ERR_CAPACITY, LBM_ERR_CUDA. */
 #define LBM_NOALLOC_MAX_COUNT 1073741824LL
 int lbm_mass_noalloc(const float* values, int64_t count, double offset, double* mass_out,
                      void* stream);

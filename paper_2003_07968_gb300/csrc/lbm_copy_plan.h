@@ -6,12 +6,14 @@
 // its shared-memory box, and that together the copies cover every value an
 // active site reads.
 //
-// Stage layout (bytes): nine population boxes of BOXB bytes, then (for the
-// collision pass) the psi box.  Population box i holds rows
-// y0 - c_iy + r (r < TY) and lattice columns [x0 - H, x0 + TX + H): the
-// value a site pulls, f*_i(x - c_i, y - c_iy), sits in box row y - y0 at
-// column x - x0 + H - c_ix.  The psi box holds rows y0 - 1 + rr (rr < TY + 2)
-// and columns [x0 - 4, x0 + TX + 4).
+// Stage layout (bytes): nine population boxes, then (for the collision
+// pass) the psi box.  Box 0 (the rest plane) holds rows y0 - 1 + r
+// (r < TY + 2), box i (i >= 1) rows y0 - c_iy + r (r < TY), all with lattice
+// columns [x0 - H, x0 + TX + H): the value a site pulls, f*_i(x - c_i,
+// y - c_iy), sits in box row y - y0 (box 0: y - y0 + 1) at column
+// x - x0 + H - c_ix, and the rest value of its source site, R(x - c_i), in
+// box 0, row y - y0 + 1 - c_iy.  The psi box holds rows y0 - 1 + rr
+// (rr < TY + 2) and columns [x0 - 4, x0 + TX + 4).
 #pragma once
 #include "lbm_device.cuh"
 
@@ -29,14 +31,28 @@ template <int ES, int TX, int TY, bool WITH_PSI>
 struct TileGeo {
     static constexpr int H = 16 / ES;                  // halo columns kept per side (16 bytes)
     static constexpr int BW = TX + 2 * H;              // population box width (elements)
-    static constexpr int BOXB = align128(TY * BW * ES);
-    static constexpr int BOXE = BOXB / ES;             // box stride in elements
+    static constexpr int ROWS0 = TY + 2;               // rows of box 0
+    static constexpr int BOX0B = align128(ROWS0 * BW * ES);
+    static constexpr int BOXB = align128(TY * BW * ES);  // boxes 1..8
+    static constexpr int POPB = BOX0B + 8 * BOXB;       // the psi box starts here
     static constexpr int PW = TX + 8;                  // psi box width (floats)
     static constexpr int PSIB = WITH_PSI ? align128((TY + 2) * PW * 4) : 0;
     static constexpr int HDRB = align128((int)sizeof(LatDev) + 16);  // tile + its lattice
-    static constexpr int HDR = 9 * BOXB + PSIB;                       // header offset
+    static constexpr int HDR = POPB + PSIB;                          // header offset
     static constexpr int STAGEB = HDR + HDRB;
-    static constexpr int NCOPY = 9 * TY + (WITH_PSI ? TY + 2 : 0);
+    static constexpr int NCOPY = ROWS0 + 8 * TY + (WITH_PSI ? TY + 2 : 0);
+    // byte offset of box i in the stage
+    static __host__ __device__ constexpr int boxoff(int i) {
+        return i == 0 ? 0 : BOX0B + (i - 1) * BOXB;
+    }
+    // element offsets, in the stage, of what site (tx, ty) of the tile pulls
+    // from plane i, and of the rest value R(x - c_i) of its source site
+    static __host__ __device__ constexpr int pull(int i, int tx, int ty) {
+        return i == 0 ? (ty + 1) * BW + tx + H : boxoff(i) / ES + ty * BW + tx + H - plane_cx(i);
+    }
+    static __host__ __device__ constexpr int rest(int i, int tx, int ty) {
+        return (ty + 1 - plane_cy(i)) * BW + tx + H - plane_cx(i);
+    }
 };
 
 struct CopyOp {
@@ -53,46 +69,74 @@ template <int ES, int TX, int TY, bool WITH_PSI>
 __host__ __device__ inline bool plan_copy(const LatDev& L, int parity, int x0, int y0, int q,
                                           CopyOp& op) {
     using G = TileGeo<ES, TX, TY, WITH_PSI>;
-    if (q < 9 * TY) {
-        const int i = q / TY, r = q - (q / TY) * TY;
-        const int y = y0 - plane_cy(i) + r;  // lattice row held by box row r
+    if (q < G::ROWS0 + 8 * TY) {
+        int i, r, y;  // box, its row, the lattice row it holds
+        if (q < G::ROWS0) {
+            i = 0;
+            r = q;
+            y = y0 - 1 + r;
+        } else {
+            const int k = q - G::ROWS0;
+            i = 1 + k / TY;
+            r = k - (k / TY) * TY;
+            y = y0 - plane_cy(i) + r;
+        }
         if (y < -1 || y > L.ny) return false;
         const int avail = L.pitch - (x0 - G::H + L.gx);  // columns left in the row
         const int cols = avail < G::BW ? avail : G::BW;
         op.src = (L.off_f[parity] + (int64_t)i * L.plane + (int64_t)(y + GY) * L.pitch +
                   (x0 - G::H + L.gx)) *
                  ES;
-        op.dst = i * G::BOXB + r * G::BW * ES;
+        op.dst = G::boxoff(i) + r * G::BW * ES;
         op.bytes = cols * ES;
         op.psi = false;
         return true;
     }
-    const int rr = q - 9 * TY;
+    const int rr = q - G::ROWS0 - 8 * TY;
     const int y = y0 - 1 + rr;
     if (y > L.ny) return false;
     const int avail = L.pitch_psi - (x0 - 4 + L.gx_psi);
     const int cols = avail < G::PW ? avail : G::PW;
     op.src = (L.off_psi + (int64_t)(y + GY) * L.pitch_psi + (x0 - 4 + L.gx_psi)) * 4;
-    op.dst = 9 * G::BOXB + rr * G::PW * 4;
+    op.dst = G::POPB + rr * G::PW * 4;
     op.bytes = cols * 4;
     op.psi = true;
     return true;
 }
 
 // ---- single-pass (fused) step --------------------------------------------
-// Stage layout (bytes): nine population boxes of BOXB bytes.  Box i holds
+// Stage layout (bytes): nine population boxes.  Box i (i >= 1) holds
 // ROWS = TY + 2 rows: box row rr is lattice row y0 - 1 - c_iy + rr, so the
 // value a cell (x, y) of the tile or of its one-site ring pulls,
 // f*_i(x - c_ix, y - c_iy), sits in box row y - y0 + 1 at column
-// x - c_ix - x0 + H; columns [x0 - H, x0 + TX + H) of the lattice row.
+// x - c_ix - x0 + H.  Box 0 (the rest plane) holds ROWS0 = TY + 4 rows,
+// lattice rows y0 - 2 .. y0 + TY + 1: a cell's own rest value and the rest
+// values R(x - c_i) of all its sources (rows y - c_iy).  Columns
+// [x0 - H, x0 + TX + H) of the lattice rows.
 template <int ES, int TX, int TY>
 struct FusedGeo {
     static constexpr int H = 16 / ES;        // halo columns per side (16 bytes)
     static constexpr int BW = TX + 2 * H;    // box width (elements)
-    static constexpr int ROWS = TY + 2;      // box rows
+    static constexpr int ROWS = TY + 2;      // rows of boxes 1..8
+    static constexpr int ROWS0 = TY + 4;     // rows of box 0
+    static constexpr int BOX0B = align128(ROWS0 * BW * ES);
     static constexpr int BOXB = align128(ROWS * BW * ES);
-    static constexpr int STAGEB = 9 * BOXB;
-    static constexpr int NCOPY = 9 * ROWS;
+    static constexpr int STAGEB = BOX0B + 8 * BOXB;
+    static constexpr int NCOPY = ROWS0 + 8 * ROWS;
+    static __host__ __device__ constexpr int boxoff(int i) {
+        return i == 0 ? 0 : BOX0B + (i - 1) * BOXB;
+    }
+    static __host__ __device__ constexpr int rows(int i) { return i == 0 ? ROWS0 : ROWS; }
+    // element offsets, in the stage, of what cell (lx, ly) of the tile
+    // (-1 .. TX, -1 .. TY) pulls from plane i, and of the rest value of its
+    // source site R(x - c_i)
+    static __host__ __device__ constexpr int pull(int i, int lx, int ly) {
+        return i == 0 ? (ly + 2) * BW + lx + H
+                      : boxoff(i) / ES + (ly + 1) * BW + lx + H - plane_cx(i);
+    }
+    static __host__ __device__ constexpr int rest(int i, int lx, int ly) {
+        return (ly + 2 - plane_cy(i)) * BW + lx + H - plane_cx(i);
+    }
 };
 
 // Copy q of the fused tile with origin (x0, y0) of lattice L, reading
@@ -103,15 +147,24 @@ template <int ES, int TX, int TY>
 __host__ __device__ inline bool plan_copy_fused(const LatDev& L, int parity, int x0, int y0, int q,
                                                 CopyOp& op) {
     using G = FusedGeo<ES, TX, TY>;
-    const int i = q / G::ROWS, rr = q - (q / G::ROWS) * G::ROWS;
-    const int y = y0 - 1 - plane_cy(i) + rr;  // lattice row held by box row rr
+    int i, rr, y;  // box, its row, the lattice row it holds
+    if (q < G::ROWS0) {
+        i = 0;
+        rr = q;
+        y = y0 - 2 + rr;
+    } else {
+        const int k = q - G::ROWS0;
+        i = 1 + k / G::ROWS;
+        rr = k - (k / G::ROWS) * G::ROWS;
+        y = y0 - 1 - plane_cy(i) + rr;
+    }
     if (y < -GY || y > L.ny + GY - 1) return false;
     const int avail = L.pitch - (x0 - G::H + L.gx);  // columns left in the row
     const int cols = avail < G::BW ? avail : G::BW;
     op.src = (L.off_f[parity] + (int64_t)i * L.plane + (int64_t)(y + GY) * L.pitch +
               (x0 - G::H + L.gx)) *
              ES;
-    op.dst = i * G::BOXB + rr * G::BW * ES;
+    op.dst = G::boxoff(i) + rr * G::BW * ES;
     op.bytes = cols * ES;
     op.psi = false;
     return true;

@@ -3,36 +3,39 @@
 // Kernel and launch templates; the instances are compiled in four units
 // (lbm_fused_tma_{f32,f16}_{bgk,mrt}.cu) and dispatched by lbm_fused_tma.cu.
 //
-// One launch per step, persistent CTAs over the global tile list.  Per CTA:
-//   - one producer warp streams, for each of its tiles, the nine population
-//     planes into a ring of shared-memory stages with cp.async.bulk row
-//     copies (lbm_copy_plan.h, FusedGeo): per plane the TY + 2 rows the tile
-//     and its one-site ring pull from, already shifted by -c_iy, with 16
-//     bytes of halo columns on each side;
-//   - eight consumer warps (1, 2 or 4 sites per thread, site pairs on the
-//     paired FP32 instructions) compute, from shared memory, rho (Eq. FD)
-//     and psi (Eqs. DED, CSEOS) of their own sites, keeping the pulled
-//     populations in registers, and psi of the ring cells; they release the
-//     stage to the producer right after these reads, meet at one named
-//     barrier (psi tile complete), then run the force (Eq. IFT) and the
-//     collision (Eqs. BGKCO, GFSBGK, or MRTCO) and store f* with coalesced
-//     plain stores (plus the periodic images of edge sites).
-// Two ways to fill a stage: for a single lattice whose rows are at least a
-// box wide, one 3-D tensor copy per tile (cp.async.bulk.tensor over a tensor
-// map of both population buffers, passed as a __grid_constant__ parameter:
-// box = (TX + 2H) columns x (TY + 4) rows x 9 planes, rows y0 - 2 .. y0 + TY + 1
-// unshifted, parts outside the tensor zero-filled); otherwise (batches,
-// narrow lattices) one bulk row copy per plane and row as above.  One tensor
-// copy replaces 9 (TY + 2) row copies, whose issue cost is what limits the
-// row-copy form (measured about 32 SM cycles per copy on GB300).
-// On the tensor path the consumers write the f* of a tile inside the lattice
-// back into its stage, laid out as the store box, and arrive on the stage's
-// mbarrier; the producer sends it out with one 3-D tensor store, waits until
-// the store has read the stage and refills it (edge tiles: plain stores).
-// The stage ring decouples DRAM latency from the arithmetic: the producer
-// runs up to STAGES - 1 tiles ahead, and the bytes in flight cost no
-// registers.  The psi tile is double-buffered, so one barrier per tile
-// suffices.
+// One launch per step, persistent CTAs over the global tile list.  Per CTA,
+// one producer warp and eight consumer warps (1, 2 or 4 sites per consumer
+// thread, site pairs on the paired FP32 instructions).
+//
+// The default path (one lattice, or a batch whose lattices share one row
+// space, rows at least a box wide): the producer loads each tile with one
+// 3-D tensor copy (cp.async.bulk.tensor over a tensor map of both
+// population buffers, passed as a __grid_constant__ parameter: box =
+// (TX + 2H) columns x (TY + 4) rows x 9 planes, rows y0 - 2 .. y0 + TY + 1,
+// unshifted, parts outside the tensor zero-filled) into a ring of
+// shared-memory stages.  The consumers
+//   - read from the stage the pulled values of their own sites and the rest
+//     values of the sources (make_site, lbm_device.cuh), keep the sites'
+//     states in registers and compute rho (Eq. FD) and psi (Eqs. DED,
+//     CSEOS), and psi on the tile's one-site ring (two ring cells per thread);
+//   - meet at one named barrier (psi tile complete);
+//   - run the force (Eq. IFT) and the collision (Eqs. BGKCO, GFSBGK, or
+//     MRTCO), write the nine stored values of a tile inside the lattice back
+//     into the stage they have just read, laid out as the store box, and
+//     arrive on the stage's mbarrier (edge tiles: plain stores, plus the
+//     periodic images of edge sites).
+// The producer sends a finished tile out with one 3-D tensor store, waits
+// until the store has read the stage and refills it, so loads run up to
+// STAGES - 1 tiles ahead of the consumers.  One tensor copy replaces the
+// 9 (TY + 2) + 2 row copies of the other form, whose issue cost limits it
+// (measured about 32 SM cycles per copy on GB300).
+// The other path (batches in a compact layout, lattices narrower than a
+// box): bulk row copies per plane and row (lbm_copy_plan.h, FusedGeo), rows
+// shifted by -c_iy, the rest plane two rows taller; the stage goes back to
+// the producer after the psi phase and the outputs leave by plain stores.
+// The stage ring decouples DRAM latency from the arithmetic and the bytes in
+// flight cost no registers.  The psi tile is double-buffered, so one barrier
+// per tile suffices.
 //
 // Every mbarrier wait is bounded (lbm_async.cuh).  A consumer warp whose wait
 // runs out does not release its stage; the consumers agree on the failure at
@@ -68,7 +71,7 @@ struct FGeo : FusedGeo<(int)sizeof(typename S::T), TX, TY> {
     static constexpr int TROWS = TY + 4;
     static constexpr int TBYTES = 9 * TROWS * B::BW * ES;
     static constexpr int STAGEB = TMAP ? align128(TBYTES) : B::STAGEB;
-    static constexpr int BOXE = TMAP ? TROWS * B::BW : B::BOXB / ES;  // plane stride (elements)
+    static constexpr int BOXE = TROWS * B::BW;  // plane stride of the tensor box (elements)
     static constexpr int STAGES = kStageBudget / STAGEB >= 4   ? 4
                                   : kStageBudget / STAGEB >= 3 ? 3
                                                                : 2;
@@ -78,11 +81,16 @@ struct FGeo : FusedGeo<(int)sizeof(typename S::T), TX, TY> {
     static constexpr int LATOFF = STAGES * STAGEB + 2 * PSIB;
     static constexpr int DESCOFF = LATOFF + STAGES * LATB;  // tile descriptor of each stage
     static constexpr int BAR = DESCOFF + STAGES * 16;  // mbarriers after stages, psi, constants
-    // element offset, inside a stage, of the value that cell (lx, ly) of the
-    // tile (lx, ly in -1 .. TX, -1 .. TY) pulls from plane i
+    // element offsets, inside a stage, of the value that cell (lx, ly) of the
+    // tile (lx, ly in -1 .. TX, -1 .. TY) pulls from plane i, and of the rest
+    // value R(x - c_i) of its source (both layouts hold the rest plane's rows
+    // y0 - 2 .. y0 + TY + 1 first)
     static __host__ __device__ constexpr int pull(int i, int lx, int ly) {
         return TMAP ? i * BOXE + (ly + 2 - plane_cy(i)) * B::BW + lx + B::H - plane_cx(i)
-                    : i * BOXE + (ly + 1) * B::BW + lx + B::H - plane_cx(i);
+                    : B::pull(i, lx, ly);
+    }
+    static __host__ __device__ constexpr int rest(int i, int lx, int ly) {
+        return (ly + 2 - plane_cy(i)) * B::BW + lx + B::H - plane_cx(i);
     }
     static constexpr int SMEM = BAR + 2 * STAGES * 8 + 16;
     static_assert(SPT == 1 || SPT == 2 || SPT == 4, "a tile holds 256, 512 or 1024 sites");
@@ -315,30 +323,34 @@ __global__ void __launch_bounds__(kBlockF, 2)
         const int nx = L.nx, ny = L.ny, x0 = tl.y, y0 = tl.z;
         const int xend = min(x0 + TX, nx), yend = min(y0 + TY, ny);
         const int x = x0 + tx;
-        V g[NV][9];
-        V drho[NV];
+        Site<V> sv[NV];
         if (ok) {
             const T* st = reinterpret_cast<const T*>(smem + s * G::STAGEB);
-            // own sites: pulled populations into registers, rho, psi
+            // own sites: pulled states into registers, rho, psi
 #pragma unroll
-            for (int kk = 0; kk < G::SPT; ++kk) {
-                const int ly = ty0 + kk * G::RPB;
-                const T* b = st + G::pull(0, tx, ly);  // the other planes at constant offsets
-                V* gk = g[kk / Ln::n];
-                const int l = kk % Ln::n;
+            for (int j = 0; j < NV; ++j) {
+                V R[9], Gs[9];
 #pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    Ln::put(gk[i], l, S::lds(b + (G::pull(i, 0, 0) - G::pull(0, 0, 0))));
+                for (int l = 0; l < Ln::n; ++l) {
+                    const int ly = ty0 + (j * Ln::n + l) * G::RPB;
+                    // the other values at constant offsets from the site's own rest value
+                    const T* b = st + G::pull(0, tx, ly);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        Ln::put(R[i], l, S::lds(b + (G::rest(i, 0, 0) - G::pull(0, 0, 0))));
+                        Ln::put(Gs[i], l,
+                                i ? S::lds(b + (G::pull(i, 0, 0) - G::pull(0, 0, 0))) : 0.f);
+                    }
+                }
+                sv[j] = make_site(R, Gs);
             }
-            const V rho0 = Ln::set(L.rho0);
 #pragma unroll
             for (int j = 0; j < NV; ++j) {
                 unsigned live = 0;
 #pragma unroll
                 for (int l = 0; l < Ln::n; ++l)
                     live |= (unsigned)(x < nx && y0 + ty0 + (j * Ln::n + l) * G::RPB < ny) << l;
-                drho[j] = sum9(g[j]);
-                const V psi = Eos<EOSP>::psi(L, vadd(drho[j], rho0), a.status, live);
+                const V psi = Eos<EOSP>::psi(L, site_rho(sv[j], L.rho0), a.status, live);
 #pragma unroll
                 for (int l = 0; l < Ln::n; ++l)
                     if ((live >> l) & 1u)
@@ -348,21 +360,23 @@ __global__ void __launch_bounds__(kBlockF, 2)
             for (int r = tid; r < nhalf; r += kConsumers) {
                 int gx[2], gy[2];
                 unsigned live = 0;
-                float2 d;
+                float2 R[9], Gs[9];
 #pragma unroll
                 for (int l = 0; l < 2; ++l) {
                     live |= (unsigned)ring_cell(r + l * nhalf, TX, TY, x0, y0, xend, yend, gx[l],
                                                 gy[l])
                             << l;
                     const T* b = st + G::pull(0, gx[l] - x0, gy[l] - y0);
-                    float v[9];
 #pragma unroll
-                    for (int i = 0; i < 9; ++i)
-                        v[i] = S::lds(b + (G::pull(i, 0, 0) - G::pull(0, 0, 0)));
-                    Lanes<float2>::put(d, l, sum9(v));
+                    for (int i = 0; i < 9; ++i) {
+                        Lanes<float2>::put(R[i], l,
+                                           S::lds(b + (G::rest(i, 0, 0) - G::pull(0, 0, 0))));
+                        Lanes<float2>::put(
+                            Gs[i], l, i ? S::lds(b + (G::pull(i, 0, 0) - G::pull(0, 0, 0))) : 0.f);
+                    }
                 }
                 const float2 psi =
-                    Eos<EOSP>::psi(L, vadd(d, Lanes<float2>::set(L.rho0)), a.status, live);
+                    Eos<EOSP>::psi(L, site_rho(make_site(R, Gs), L.rho0), a.status, live);
                 if (live & 1u) ps[(gy[0] - y0 + 1) * PW + (gx[0] - x0 + 1)] = psi.x;
                 if (live & 2u) ps[(gy[1] - y0 + 1) * PW + (gx[1] - x0 + 1)] = psi.y;
             }
@@ -417,7 +431,7 @@ __global__ void __launch_bounds__(kBlockF, 2)
                 Ln::put(p[7], l, c[-PW - 1]);
                 Ln::put(p[8], l, c[-PW + 1]);
             }
-            collide<MRT>(C, L.mrt_s, drho[j], g[j], p, v);
+            collide<S, MRT>(C, L.mrt_s, sv[j], p, v);
 #pragma unroll
             for (int l = 0; l < Ln::n; ++l) {
                 const int ly = ty0 + (j * Ln::n + l) * G::RPB;

@@ -22,21 +22,44 @@ namespace pplbm {
 // sites k and k+1 share the lanes of one float2 and go through the EOS and
 // the collision together on the paired FP32 instructions.
 
-// Pulled density deviation at (x, y): f_i(x) = f*_i(x - c_i) summed in the
-// fixed order of sum9.  `f` points at (x, y) of plane 0 of the buffer.
+// The pulled state of site (x, y) (make_site): `f` points at (x, y) of
+// plane 0 of the buffer; plane i of the source site x - c_i and its rest
+// value R(x - c_i) are read.
 template <class S>
-__device__ __forceinline__ float pulled_drho(const typename S::T* f, int64_t plane, int pitch) {
-    float v[9];
-    v[0] = S::ld(f);
-    v[1] = S::ld(f + 1 * plane - 1);
-    v[2] = S::ld(f + 2 * plane - pitch);
-    v[3] = S::ld(f + 3 * plane + 1);
-    v[4] = S::ld(f + 4 * plane + pitch);
-    v[5] = S::ld(f + 5 * plane - pitch - 1);
-    v[6] = S::ld(f + 6 * plane - pitch + 1);
-    v[7] = S::ld(f + 7 * plane + pitch + 1);
-    v[8] = S::ld(f + 8 * plane + pitch - 1);
-    return sum9(v);
+__device__ __forceinline__ Site<float> pulled_site(const typename S::T* f, int64_t plane,
+                                                   int pitch) {
+    float R[9], Gs[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int64_t src = -(int64_t)plane_cy(i) * pitch - plane_cx(i);
+        R[i] = S::ld(f + src);
+        Gs[i] = i ? S::ld(f + i * plane + src) : 0.f;
+    }
+    return make_site(R, Gs);
+}
+
+// The pulled states of SPT sites of one column (rows y0 + k by, clamped to
+// the last row), in the lanes of V.
+template <class S, int SPT, class V>
+__device__ __forceinline__ void load_sites(const typename S::T* base, int64_t plane, int pitch,
+                                           int y0, int by, int ny, Site<V>* sv) {
+    using Ln = Lanes<V>;
+#pragma unroll
+    for (int j = 0; j < SPT / Ln::n; ++j) {
+        V R[9], Gs[9];
+#pragma unroll
+        for (int l = 0; l < Ln::n; ++l) {
+            const int y = min(y0 + (j * Ln::n + l) * by, ny - 1);
+            const typename S::T* f = base + (int64_t)(y + GY) * pitch;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int64_t src = -(int64_t)plane_cy(i) * pitch - plane_cx(i);
+                Ln::put(R[i], l, S::ld(f + src));
+                Ln::put(Gs[i], l, i ? S::ld(f + i * plane + src) : 0.f);
+            }
+        }
+        sv[j] = make_site(R, Gs);
+    }
 }
 
 // ---------------------------------------------------------------- pass 1: psi
@@ -56,17 +79,11 @@ __global__ void __launch_bounds__(512) k_psi(StepArgs a) {
         const int pitch = L.pitch;
         const int64_t plane = L.plane;
         const T* base = reinterpret_cast<const T*>(a.pop) + L.off_f[a.parity] + (x + L.gx);
-        V d[NV];
-#pragma unroll
-        for (int k = 0; k < SPT; ++k) {
-            const int y = min(tl.z + (int)threadIdx.y + k * (int)blockDim.y, ny - 1);
-            Ln::put(d[k / Ln::n], k % Ln::n,
-                    pulled_drho<S>(base + (int64_t)(y + GY) * pitch, plane, pitch));
-        }
-        const V rho0 = Ln::set(L.rho0);
+        Site<V> sv[NV];
+        load_sites<S, SPT>(base, plane, pitch, tl.z + (int)threadIdx.y, (int)blockDim.y, ny, sv);
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
-            const V psi = Eos<EOSP>::psi(L, vadd(d[j], rho0), a.status);
+            const V psi = Eos<EOSP>::psi(L, site_rho(sv[j], L.rho0), a.status);
 #pragma unroll
             for (int l = 0; l < Ln::n; ++l) {
                 const int y = tl.z + (int)threadIdx.y + (j * Ln::n + l) * (int)blockDim.y;
@@ -75,29 +92,6 @@ __global__ void __launch_bounds__(512) k_psi(StepArgs a) {
                               Ln::get(psi, l));
             }
         }
-    }
-}
-
-// Loads the nine pulled populations of SPT sites of one column into lanes.
-template <class S, int SPT, class V>
-__device__ __forceinline__ void load_sites(const typename S::T* base, int64_t plane, int pitch,
-                                           int y0, int by, int ny, V (*g)[9]) {
-    using Ln = Lanes<V>;
-#pragma unroll
-    for (int k = 0; k < SPT; ++k) {
-        const int y = min(y0 + k * by, ny - 1);
-        const typename S::T* f = base + (int64_t)(y + GY) * pitch;
-        V* gk = g[k / Ln::n];
-        const int l = k % Ln::n;
-        Ln::put(gk[0], l, S::ld(f));
-        Ln::put(gk[1], l, S::ld(f + 1 * plane - 1));
-        Ln::put(gk[2], l, S::ld(f + 2 * plane - pitch));
-        Ln::put(gk[3], l, S::ld(f + 3 * plane + 1));
-        Ln::put(gk[4], l, S::ld(f + 4 * plane + pitch));
-        Ln::put(gk[5], l, S::ld(f + 5 * plane - pitch - 1));
-        Ln::put(gk[6], l, S::ld(f + 6 * plane - pitch + 1));
-        Ln::put(gk[7], l, S::ld(f + 7 * plane + pitch + 1));
-        Ln::put(gk[8], l, S::ld(f + 8 * plane + pitch - 1));
     }
 }
 
@@ -111,8 +105,8 @@ __device__ __forceinline__ bool tile_interior(int x0, int y0, int TX, int TY, in
 // (row stride W, the thread's column at offset tx + 1) and their stores.
 template <class S, int SPT, bool MRT, class V>
 __device__ __forceinline__ void collide_store(const LatDev& L, const float* sps, int W, int tx,
-                                              int ly0, int by, int x, int y0, const V* drho,
-                                              V (*g)[9], typename S::T* o, bool tile_in) {
+                                              int ly0, int by, int x, int y0, const Site<V>* sv,
+                                              typename S::T* o, bool tile_in) {
     using Ln = Lanes<V>;
     constexpr int NV = SPT / Ln::n;
     const SiteConsts C = site_consts(L);
@@ -133,7 +127,7 @@ __device__ __forceinline__ void collide_store(const LatDev& L, const float* sps,
             Ln::put(p[7], l, c[-W - 1]);
             Ln::put(p[8], l, c[-W + 1]);
         }
-        collide<MRT>(C, L.mrt_s, drho[j], g[j], p, v);
+        collide<S, MRT>(C, L.mrt_s, sv[j], p, v);
 #pragma unroll
         for (int l = 0; l < Ln::n; ++l) {
             const int y = y0 + (j * Ln::n + l) * by;
@@ -177,15 +171,12 @@ __global__ void __launch_bounds__(512) k_collide(StepArgs a) {
         }
         const int x = tl.y + threadIdx.x;
         const T* base = reinterpret_cast<const T*>(a.pop) + L.off_f[a.parity] + (x + L.gx);
-        V g[NV][9];
-        if (x < nx) load_sites<S, SPT>(base, L.plane, L.pitch, tl.z + (int)threadIdx.y, BY, ny, g);
+        Site<V> sv[NV];
+        if (x < nx) load_sites<S, SPT>(base, L.plane, L.pitch, tl.z + (int)threadIdx.y, BY, ny, sv);
         __syncthreads();  // psi tile complete
         if (x >= nx) continue;
-        V drho[NV];
-#pragma unroll
-        for (int j = 0; j < NV; ++j) drho[j] = sum9(g[j]);
         collide_store<S, SPT, MRT>(L, sps, W, threadIdx.x, threadIdx.y, BY, x,
-                                   tl.z + (int)threadIdx.y, drho, g,
+                                   tl.z + (int)threadIdx.y, sv,
                                    reinterpret_cast<T*>(a.pop) + L.off_f[a.parity ^ 1],
                                    tile_interior(tl.y, tl.z, TX, TY, nx, ny));
     }
@@ -226,27 +217,24 @@ __global__ void __launch_bounds__(512) k_fused(StepArgs a) {
         const int yend = min(tl.z + TY, ny);
         __syncthreads();  // the previous tile is done with sps
         const int x = tl.y + threadIdx.x;
-        V g[NV][9];
-        if (x < nx) load_sites<S, SPT>(base + x, plane, pitch, tl.z + (int)threadIdx.y, BY, ny, g);
+        Site<V> sv[NV];
+        if (x < nx) load_sites<S, SPT>(base + x, plane, pitch, tl.z + (int)threadIdx.y, BY, ny, sv);
         // the ring, cells r and r + nhalf in the two lanes of a float2
         for (int r = tid; r < nhalf; r += nthr) {
             int cx0, cy0, cx1, cy1;
             const bool on0 = ring_cell(r, TX, TY, tl.y, tl.z, xend, yend, cx0, cy0);
             const bool on1 = ring_cell(r + nhalf, TX, TY, tl.y, tl.z, xend, yend, cx1, cy1);
-            float2 d;
-            d.x = pulled_drho<S>(base + (int64_t)(cy0 + GY) * pitch + cx0, plane, pitch);
-            d.y = pulled_drho<S>(base + (int64_t)(cy1 + GY) * pitch + cx1, plane, pitch);
-            const float2 psi = Eos<EOSP>::psi(L, vadd(d, Lanes<float2>::set(L.rho0)), a.status);
+            const Site<float> s0 = pulled_site<S>(base + (int64_t)(cy0 + GY) * pitch + cx0, plane, pitch);
+            const Site<float> s1 = pulled_site<S>(base + (int64_t)(cy1 + GY) * pitch + cx1, plane, pitch);
+            const float2 rho = make_float2(site_rho(s0, L.rho0), site_rho(s1, L.rho0));
+            const float2 psi = Eos<EOSP>::psi(L, rho, a.status);
             if (on0) sps[(cy0 - tl.z + 1) * W + (cx0 - tl.y + 1)] = psi.x;
             if (on1) sps[(cy1 - tl.z + 1) * W + (cx1 - tl.y + 1)] = psi.y;
         }
-        V drho[NV];
         if (x < nx) {
-            const V rho0 = Ln::set(L.rho0);
 #pragma unroll
             for (int j = 0; j < NV; ++j) {
-                drho[j] = sum9(g[j]);
-                const V psi = Eos<EOSP>::psi(L, vadd(drho[j], rho0), a.status);
+                const V psi = Eos<EOSP>::psi(L, site_rho(sv[j], L.rho0), a.status);
 #pragma unroll
                 for (int l = 0; l < Ln::n; ++l) {
                     const int ly = (int)threadIdx.y + (j * Ln::n + l) * BY;
@@ -257,19 +245,22 @@ __global__ void __launch_bounds__(512) k_fused(StepArgs a) {
         __syncthreads();  // psi tile complete
         if (x >= nx) continue;
         collide_store<S, SPT, MRT>(L, sps, W, threadIdx.x, threadIdx.y, BY, x,
-                                   tl.z + (int)threadIdx.y, drho, g,
+                                   tl.z + (int)threadIdx.y, sv,
                                    reinterpret_cast<T*>(a.pop) + L.off_f[a.parity ^ 1],
                                    tile_interior(tl.y, tl.z, TX, TY, nx, ny));
     }
 }
 
 // ------------------------------------------------------------------ init
-// The value f_i^eq(x) (FP64, then rounded to the storage type as a deviation
-// from w_i rho0) is stored at x - c_i, so that the next pull
-// f_i(x) = f*_i(x - c_i) yields f_i^eq(x).  Each thread computes the
-// equilibrium of its own site once and scatters the nine values.  With
-// u = 0 (no velocity given) the deviation is w_i (rho - rho0): one FP64
-// subtraction and nine multiplies (the FP64 pipe is the slow one on GB300).
+// f*_i(y) = f^eq_i(y + c_i) (FP64), so that the next pull
+// f_i(x) = f*_i(x - c_i) yields f^eq_i(x), written in the stored form
+// (lbm_device.cuh, rest_finish): R(y) = f*_0(y) - w_0 rho0 rounded to the
+// storage type, G_i(y) = (f*_i(y) - w_i rho0) - c'_i (f*_0(y) - w_0 rho0)
+// + E/8 with E = 9/4 (exact R - stored R) = -9/4 e0.  Each thread writes
+// its own site, gathering the densities of its eight neighbours.  With
+// u = 0 (no velocity given) f^eq_i = w_i rho and
+// G_i(y) = w_i (rho(y + c_i) - rho(y)) - 9/32 e0: a subtraction and an FMA
+// per direction on the FP64 pipe (the slow one on GB300).
 template <class S>
 __global__ void k_init(LatDev L, void* pop, int parity, const double* rho, const double* ux,
                        const double* uy) {
@@ -281,26 +272,30 @@ __global__ void k_init(LatDev L, void* pop, int parity, const double* rho, const
     T* o = reinterpret_cast<T*>(pop) + L.off_f[parity];
     const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
                          1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-    const int64_t s = (int64_t)y * nx + x;
-    const double r = rho[s];
-    const bool still = !ux && !uy;  // u = 0: f_i^eq - w_i rho0 = w_i (rho - rho0)
-    const double d = r - (double)L.rho0;
-    const double vx = ux ? ux[s] : 0.0, vy = uy ? uy[s] : 0.0;
+    const bool still = !ux && !uy;
+    const double r0 = (double)L.rho0;
+    // f^eq_i - w_i rho0 at site (sx, sy), Eq. (SEDF)
+    auto geq = [&](int i, int sx, int sy) {
+        const int64_t q = (int64_t)sy * nx + sx;
+        const double r = rho[q];
+        if (still) return w[i] * (r - r0);
+        const double vx = ux ? ux[q] : 0.0, vy = uy ? uy[q] : 0.0;
+        const double cu = kCx[i] * vx + kCy[i] * vy;
+        return w[i] * (r + r * (3.0 * cu + 4.5 * cu * cu - 1.5 * (vx * vx + vy * vy))) - w[i] * r0;
+    };
+    const double g0 = geq(0, x, y);
+    const T R = S::cv((float)g0);
+    const double e0 = (double)S::rt((float)g0) - g0;
+    store_img(o, L.pitch, L.gx, x, y, nx, ny, R);
+    const double rc = rho[(int64_t)y * nx + x];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        double g;
-        if (still) {
-            g = w[i] * d;
-        } else {
-            const double cu = kCx[i] * vx + kCy[i] * vy;
-            const double feq =
-                w[i] * (r + r * (3.0 * cu + 4.5 * cu * cu - 1.5 * (vx * vx + vy * vy)));
-            g = feq - w[i] * (double)L.rho0;
-        }
-        int tx = x - kCx[i], ty = y - kCy[i];
-        tx = tx < 0 ? tx + nx : (tx >= nx ? tx - nx : tx);
-        ty = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
-        store_img(o + i * L.plane, L.pitch, L.gx, tx, ty, nx, ny, S::cv((float)g));
+    for (int i = 1; i < 9; ++i) {
+        int sx = x + kCx[i], sy = y + kCy[i];
+        sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+        sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+        const double G = still ? fma(-0.28125, e0, w[i] * (rho[(int64_t)sy * nx + sx] - rc))
+                               : (geq(i, sx, sy) - (double)cref(i) * g0) - 0.28125 * e0;
+        store_img(o + i * L.plane, L.pitch, L.gx, x, y, nx, ny, S::cv((float)G));
     }
 }
 
@@ -319,15 +314,16 @@ __device__ __forceinline__ float two_sum(float a, float b, float& e) {
 // sum_i w_i v_i for weights w_i in {-1, 0, 1} as an unevaluated pair
 // hi + lo: hi by error-free steps, their rounding errors (each at most u
 // times a partial sum) gathered in lo with FP32 roundings of their own, so
-// that hi + lo is within 64 u^2 of the largest partial sum of the exact sum
+// that hi + lo is within N^2 u^2 of the largest partial sum of the exact sum
 // (u = 2^-24).
 // This keeps the per-site sums off the FP64 pipe, which is slow on GB300.
-__device__ __forceinline__ void signed_sum9(const float v[9], const int w[9], float& hi,
-                                            float& lo) {
+template <int N>
+__device__ __forceinline__ void signed_sum(const float v[N], const int w[N], float& hi,
+                                           float& lo) {
     hi = 0.f;
     lo = 0.f;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
+    for (int i = 0; i < N; ++i) {
         if (w[i] == 0) continue;
         float e;
         hi = two_sum(hi, w[i] > 0 ? v[i] : -v[i], e);
@@ -347,20 +343,36 @@ __global__ void k_moments(LatDev L, const void* pop, int parity, const float* ps
     const int64_t plane = L.plane;
     const T* f = reinterpret_cast<const T*>(pop) + L.off_f[parity] + (int64_t)(y + GY) * pitch +
                  (x + L.gx);
-    float g[9];
+    // the pulled deviations g_i = G_i(x - c_i) + c'_i R(x - c_i) as 17 exact
+    // terms: v[i] = G_i, v[8 + i] = c'_i R(x - c_i) (i = 1..8), v[0] = R(x)
+    float v[17];
+    int ones[17], wx[17], wy[17];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = S::ld(f + i * plane - kCy[i] * pitch - kCx[i]);
-    constexpr int kOne[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+    for (int i = 0; i < 9; ++i) {
+        const int64_t src = -(int64_t)plane_cy(i) * pitch - plane_cx(i);
+        const float R = S::ld(f + src);
+        if (i == 0) {
+            v[0] = R;
+            ones[0] = 1;
+            wx[0] = wy[0] = 0;
+        } else {
+            v[i] = S::ld(f + i * plane + src);
+            v[8 + i] = cref(i) * R;
+            ones[i] = ones[8 + i] = 1;
+            wx[i] = wx[8 + i] = kCx[i];
+            wy[i] = wy[8 + i] = kCy[i];
+        }
+    }
     float hi, lo;
-    signed_sum9(g, kOne, hi, lo);
+    signed_sum<17>(v, ones, hi, lo);
     // rho = sum_i f_i (Eq. FD) plus the deviation reference, in FP64
     const double rho = ((double)hi + (double)lo) + (double)L.rho0;
     const int64_t s = (int64_t)y * nx + x;
     if (rho_out) rho_out[s] = rho;
     if (!ux_out && !uy_out) return;  // density only: no force, psi not read
     float jxh, jxl, jyh, jyl;
-    signed_sum9(g, kCx, jxh, jxl);
-    signed_sum9(g, kCy, jyh, jyl);
+    signed_sum<17>(v, wx, jxh, jxl);
+    signed_sum<17>(v, wy, jyh, jyl);
     const float* c = psi_arena + L.off_psi + (int64_t)(y + GY) * L.pitch_psi + (x + L.gx_psi);
     const int W = L.pitch_psi;
     const float p[9] = {c[0], c[1], c[W], c[-1], c[-W], c[W + 1], c[W - 1], c[-W - 1], c[-W + 1]};
@@ -375,27 +387,30 @@ __global__ void k_moments(LatDev L, const void* pop, int parity, const float* ps
 // ------------------------------------------------------------------ mass
 // Each block sums whole rows of all nine planes and writes one FP64
 // partial; k_mass_final adds the partials in block order (deterministic).
-// A site's nine values are summed as a float-float pair (signed_sum9); the
-// pairs' leading parts accumulate in FP64, their small trailing parts in
-// FP32, and the sites' rho0 is added once per thread.
+// A site's stored mass rho0 + 9/4 R + sum_i G_i (lbm_device.cuh) is summed
+// as a float-float pair over the exact terms R, R, R/4, G_1 .. G_8
+// (signed_sum); the pairs' leading parts accumulate in FP64, their small
+// trailing parts in FP32, and the sites' rho0 is added once per thread.
 template <class S>
 __global__ void __launch_bounds__(256) k_mass_partial(LatDev L, const void* pop, int parity,
                                                       double* partials) {
     using T = typename S::T;
     const T* f = reinterpret_cast<const T*>(pop) + L.off_f[parity];
     const int nx = L.nx, ny = L.ny;
-    constexpr int kOne[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+    constexpr int kOne[11] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
     double acc = 0.0;
     float acc_lo = 0.f;
     int64_t sites = 0;
     for (int y = blockIdx.x; y < ny; y += gridDim.x) {
         const T* row = f + (int64_t)(y + GY) * L.pitch + L.gx;
         for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-            float v[9];
+            float v[11];
 #pragma unroll
             for (int i = 0; i < 9; ++i) v[i] = S::ld(row + i * L.plane + x);
+            v[9] = v[0];
+            v[10] = 0.25f * v[0];
             float hi, lo;
-            signed_sum9(v, kOne, hi, lo);
+            signed_sum<11>(v, kOne, hi, lo);
             acc += (double)hi;
             acc_lo = vadd(acc_lo, lo);
             ++sites;

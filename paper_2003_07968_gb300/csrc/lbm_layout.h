@@ -34,38 +34,43 @@ inline LatDev lat_layout(const lbm_lattice_desc& d, int index) {
     L.plane = round_up((int64_t)L.pitch * rows, 256 / s);
     L.gx_psi = 4;
     L.pitch_psi = (int)round_up(d.nx + 8, 8);
+    // omega rounded once; 1 - omega, guo = 1 - omega/2 and the other BGK
+    // constants but rw0, rg0 are exact FP32 functions of it, so that a
+    // collision adds exactly F to the momentum in real arithmetic
     L.omega = (float)(1.0 / d.tau);
-    L.guo = (float)(1.0 - 1.0 / (2.0 * d.tau));
-    L.k_sc = (float)(-6.0 * d.G);
-    L.k1 = (float)(13.5 * d.eps * d.G);
-    L.k2 = (float)(9.0 * (d.sigma - 1.0) * d.G);
+    L.guo = 1.f - 0.5f * L.omega;
+    L.om1 = 1.f - L.omega;
+    L.ra = 0.5f * L.omega;
+    L.rd = 0.125f * L.omega;
+    L.ga9 = L.guo;
+    L.gd9 = 0.25f * L.guo;
+    L.rw0 = (float)(4.0 * (double)L.omega / 9.0);
+    L.rg0 = (float)(-3.0 * (double)L.guo * 4.0 / 9.0);
+    // The force constant of the Shan-Chen term, -2G/c_s^2/36 = -G/6, rounded
+    // to FP32, fixes the G the force acts with, Ge = -6 fsc; psi (Eq. DED)
+    // and the other force terms are evaluated with that same Ge, so that
+    // G psi^2 = P_EOS - c_s^2 rho holds for the force the kernels apply (a G
+    // in psi that differs from the force's by the rounding of 1/6 would
+    // shift the mechanical balance of an interface every step).
+    L.fsc = (float)(-6.0 * d.G / 36.0);
+    const double Ge = L.fsc != 0.f ? -6.0 * (double)L.fsc : d.G;
+    L.k_sc = (float)(-6.0 * Ge);
+    L.k1 = (float)(13.5 * d.eps * Ge);
+    L.k2 = (float)(9.0 * (d.sigma - 1.0) * Ge);
     {
-        const double ksc = -6.0 * d.G, k1 = 13.5 * d.eps * d.G, k2 = 9.0 * (d.sigma - 1.0) * d.G;
-        L.fsc = (float)(ksc / 36.0);
+        const double k1 = 13.5 * d.eps * Ge, k2 = 9.0 * (d.sigma - 1.0) * Ge;
         L.fk2 = (float)(k2 / 1944.0);
         L.fkd = (float)((k1 - k2) / 1944.0);
-        const double om = 1.0 / d.tau, guo = 1.0 - 1.0 / (2.0 * d.tau);
-        L.om1 = (float)(1.0 - om);
-        L.wa = (float)(om / 9.0);
-        L.wd = (float)(om / 36.0);
-        L.ra = (float)(4.5 * om / 9.0);
-        L.rd = (float)(4.5 * om / 36.0);
-        L.sa = (float)(3.0 * om / 9.0);
-        L.sd = (float)(3.0 * om / 36.0);
-        L.ga9 = (float)(9.0 * guo / 9.0);
-        L.gd9 = (float)(9.0 * guo / 36.0);
-        L.ga3 = (float)(3.0 * guo / 9.0);
-        L.gd3 = (float)(3.0 * guo / 36.0);
     }
     L.rho0 = (d.storage == LBM_STORE_F32 || d.rho0 < 0.0) ? 0.f : (float)d.rho0;
     L.m2_variant = d.m2_trace_variant;
     L.lattice = index;
     L.row0 = -1;
-    // psi^2 = rho (e1 q - e2 rho - e3): e1 = k c T / G, e2 = k a / G, e3 = 1/(3G)
+    // psi^2 = rho (e1 q - e2 rho - e3): e1 = k c T / Ge, e2 = k a / Ge, e3 = 1/(3 Ge)
     L.eb = d.eos_b;
-    L.e1 = d.eos_k * d.eos_c * d.T / d.G;
-    L.e2 = d.eos_k * d.eos_a / d.G;
-    L.e3 = 1.0 / (3.0 * d.G);
+    L.e1 = d.eos_k * d.eos_c * d.T / Ge;
+    L.e2 = d.eos_k * d.eos_a / Ge;
+    L.e3 = 1.0 / (3.0 * Ge);
     split_df(L.eb, L.fb);
     split_df(L.e2, L.f2);
     split_df(L.e1 - L.e3, L.fc0);      // psi^2/rho = c0 + rho (C1 r^2 (1 + r) - e2)

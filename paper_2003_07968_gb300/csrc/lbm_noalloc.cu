@@ -2,15 +2,14 @@
 // library for callers that cannot allocate device memory.
 //
 // Some callers may not call cudaMalloc (or anything that allocates) at the
-// point where they need a conserved-mass check: code that runs while a
-// stream is being captured into a CUDA graph, applications that reserve all
-// device memory up front through their own allocator and forbid later
+// point where they need a mass check: applications that reserve all device
+// memory up front through their own allocator and forbid later
 // allocations, or real-time loops that must not take the allocator's locks.
-// For them this entry point reduces populations they already own into a
-// result buffer they already own, and keeps its per-block partial sums in a
-// fixed array in device global memory that belongs to the library module
-// itself (kNoallocPartials doubles = 2 MiB per GPU that loads the library,
-// held until the process exits).
+// For them this entry point reduces FP32 values they already own (a density
+// field, say) into a result buffer they already own, and keeps its
+// per-block partial sums in a fixed array in device global memory that
+// belongs to the library module itself (kNoallocPartials doubles = 2 MiB per
+// GPU that loads the library, held until the process exits).
 //
 // The reduction is the same two-level scheme as the handle's mass kernels:
 // every block adds a fixed chunk of the input in FP64 and writes one
@@ -75,7 +74,9 @@ __global__ void __launch_bounds__(kThreads) k_noalloc_final(const double* partia
 }
 
 // Device address of g_partials per device, looked up once with that device
-// current (host code only sees a host-side stand-in for the symbol).
+// current (host code only sees a host-side stand-in for the symbol) and kept
+// for the life of the process: a device reset would leave it stale, which
+// the header states as a limit of the entry point.
 std::mutex g_mu;
 double* g_addr[128] = {nullptr};
 

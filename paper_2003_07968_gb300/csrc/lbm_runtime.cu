@@ -444,8 +444,9 @@ std::string check_plan_t(const LatDev& L, int par, int x0, int y0, int64_t lo, i
         }
         // a population copy must stay inside its own box
         if (!op.psi) {
-            const int box = op.dst / G::BOXB;
-            if (op.dst + op.bytes > box * G::BOXB + TY * G::BW * ES) return "copy crosses its box";
+            const int box = op.dst < G::BOX0B ? 0 : 1 + (op.dst - G::BOX0B) / G::BOXB;
+            if (box > 8 || op.dst + op.bytes > G::boxoff(box) + (box ? TY : G::ROWS0) * G::BW * ES)
+                return "copy crosses its box";
         }
         for (int k = 0; k < op.bytes; ++k) cov[op.dst + k] = 1;
         total += op.bytes;
@@ -456,18 +457,22 @@ std::string check_plan_t(const LatDev& L, int par, int x0, int y0, int64_t lo, i
         for (int tx = 0; tx < TX; ++tx) {
             const int x = x0 + tx, y = y0 + ty;
             if (x >= L.nx || y >= L.ny) continue;
-            for (int i = 0; i < 9; ++i) {
-                const int off = i * G::BOXB + (ty * G::BW + tx + G::H - plane_cx(i)) * ES;
+            // the pulled value of every plane and the rest value of its source
+            for (int i = 0; i < 18; ++i) {
+                const int off = (i < 9 ? G::pull(i, tx, ty) : G::rest(i - 9, tx, ty)) * ES;
+                const int b = i < 9 ? i : 0;  // the box the value must lie in
+                const int lo_b = G::boxoff(b), hi_b = lo_b + (b ? TY : G::ROWS0) * G::BW * ES;
                 for (int k = 0; k < ES; ++k)
-                    if (!cov[off + k]) {
-                        std::snprintf(buf, sizeof buf, "uncovered read: plane %d site (%d,%d)", i, x, y);
+                    if (off < lo_b || off + k >= hi_b || !cov[off + k]) {
+                        std::snprintf(buf, sizeof buf, "uncovered read: %s %d site (%d,%d)",
+                                      i < 9 ? "plane" : "rest of", i % 9, x, y);
                         return buf;
                     }
             }
             if (P)
                 for (int dy = -1; dy <= 1; ++dy)
                     for (int dx = -1; dx <= 1; ++dx) {
-                        const int off = 9 * G::BOXB + ((ty + 1 + dy) * G::PW + tx + 4 + dx) * 4;
+                        const int off = G::POPB + ((ty + 1 + dy) * G::PW + tx + 4 + dx) * 4;
                         for (int k = 0; k < 4; ++k)
                             if (!cov[off + k]) return "uncovered psi read";
                     }
@@ -486,10 +491,10 @@ std::string check_fused_t(const LatDev& L, int par, int x0, int y0, int64_t lo, 
     for (int q = 0; q < G::NCOPY; ++q) {
         CopyOp op;
         if (!plan_copy_fused<ES, TX, TY>(L, par, x0, y0, q, op)) continue;
-        const int box = op.dst / G::BOXB;
+        const int box = op.dst < G::BOX0B ? 0 : 1 + (op.dst - G::BOX0B) / G::BOXB;
         if (op.src % 16 || op.dst % 16 || op.bytes % 16 || op.bytes <= 0 || op.src < lo ||
-            op.src + op.bytes > hi || op.dst < 0 ||
-            op.dst + op.bytes > box * G::BOXB + G::ROWS * G::BW * ES) {
+            op.src + op.bytes > hi || op.dst < 0 || box > 8 ||
+            op.dst + op.bytes > G::boxoff(box) + G::rows(box) * G::BW * ES) {
             std::snprintf(buf, sizeof buf,
                           "bad fused copy: es=%d tile=%dx%d lattice %dx%d x0=%d y0=%d q=%d src=%lld "
                           "dst=%d bytes=%d range=[%lld,%lld)",
@@ -500,11 +505,13 @@ std::string check_fused_t(const LatDev& L, int par, int x0, int y0, int64_t lo, 
         for (int k = 0; k < op.bytes; ++k) cov[op.dst + k] = 1;
     }
     const int xend = std::min(x0 + TX, L.nx), yend = std::min(y0 + TY, L.ny);
+    // the pulled value of every plane and the rest value of its source
     auto covered = [&](int gx, int gy) {
-        for (int i = 0; i < 9; ++i) {
-            const int off =
-                i * G::BOXB + ((gy - y0 + 1) * G::BW + (gx - x0 + G::H - plane_cx(i))) * ES;
-            if (off < 0 || off + ES > G::STAGEB) return false;
+        for (int i = 0; i < 18; ++i) {
+            const int off = (i < 9 ? G::pull(i, gx - x0, gy - y0) : G::rest(i - 9, gx - x0, gy - y0)) * ES;
+            const int b = i < 9 ? i : 0;  // the box the value must lie in
+            if (off < G::boxoff(b) || off + ES > G::boxoff(b) + G::rows(b) * G::BW * ES)
+                return false;
             for (int k = 0; k < ES; ++k)
                 if (!cov[off + k]) return false;
         }

@@ -4,8 +4,10 @@
 // first warp issues bulk asynchronous copies (cp.async.bulk, executed by the
 // TMA unit) of whole row segments into shared memory: for each population
 // plane the TY rows the tile pulls from (already shifted by -c_iy, with 16
-// bytes of halo columns on each side), plus the psi rows of the tile and its
-// one-site halo for the collision pass (lbm_copy_plan.h).  The warps are
+// bytes of halo columns on each side; the rest plane also the row above and
+// the row below, which hold the rest values of the sources), plus the psi
+// rows of the tile and its one-site halo for the collision pass
+// (lbm_copy_plan.h).  The warps are
 // specialised: one producer warp only issues copies, eight consumer warps
 // only compute.  Each stage has a "full" mbarrier (completed by the copies'
 // byte count) and an "empty" mbarrier (one arrival per consumer warp once it
@@ -151,6 +153,18 @@ __device__ __forceinline__ void run_pipeline(const StepArgs& a, Body&& body) {
     }
 }
 
+// The pulled state of site (tx, ty) of the staged tile (make_site).
+template <class S, class G>
+__device__ __forceinline__ Site<float> stage_site(const typename S::T* P, int tx, int ty) {
+    float R[9], Gs[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        R[i] = S::lds(P + G::rest(i, tx, ty));
+        Gs[i] = i ? S::lds(P + G::pull(i, tx, ty)) : 0.f;
+    }
+    return make_site(R, Gs);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- pass 1: psi
@@ -164,7 +178,6 @@ __global__ void __launch_bounds__(kBlock, 2) k_psi_tma(StepArgs a) {
         const int4 tl = hd.tile;
         const LatDev& L = hd.lat;
         const int nx = L.nx, ny = L.ny;
-        const float rho0 = L.rho0;
         const T* P = reinterpret_cast<const T*>(stage);
         const int x = tl.y + tx;
         if (x >= nx) return;
@@ -172,18 +185,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_psi_tma(StepArgs a) {
         for (int ty = ty0; ty < TY; ty += G::RP) {
             const int y = tl.z + ty;
             if (y >= ny) break;
-            const T* b = P + ty * G::BW + tx + G::H;
-            float v[9];
-            v[0] = S::lds(b);
-            v[1] = S::lds(b + 1 * G::BOXE - 1);
-            v[2] = S::lds(b + 2 * G::BOXE);
-            v[3] = S::lds(b + 3 * G::BOXE + 1);
-            v[4] = S::lds(b + 4 * G::BOXE);
-            v[5] = S::lds(b + 5 * G::BOXE - 1);
-            v[6] = S::lds(b + 6 * G::BOXE + 1);
-            v[7] = S::lds(b + 7 * G::BOXE + 1);
-            v[8] = S::lds(b + 8 * G::BOXE - 1);
-            const float psi = Eos<EOSP>::psi(L, sum9(v) + rho0, a.status);
+            const Site<float> st = stage_site<S, G>(P, tx, ty);
+            const float psi = Eos<EOSP>::psi(L, site_rho(st, L.rho0), a.status);
             store_img(a.psi + L.off_psi, L.pitch_psi, L.gx_psi, x, y, nx, ny, psi);
         }
     });
@@ -207,22 +210,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_collide_tma(StepArgs a) {
         const int64_t plane = L.plane;
         T* o = reinterpret_cast<T*>(a.pop) + L.off_f[a.parity ^ 1];
         const T* P = reinterpret_cast<const T*>(stage);
-        const float* PS = reinterpret_cast<const float*>(stage + 9 * G::BOXB);
+        const float* PS = reinterpret_cast<const float*>(stage + G::POPB);
 #pragma unroll 1
         for (int ty = ty0; ty < TY; ty += G::RP) {
             const int y = tl.z + ty;
             if (y >= ny) break;
-            const T* b = P + ty * G::BW + tx + G::H;
-            float g[9], p[9], v[9];
-            g[0] = S::lds(b);
-            g[1] = S::lds(b + 1 * G::BOXE - 1);
-            g[2] = S::lds(b + 2 * G::BOXE);
-            g[3] = S::lds(b + 3 * G::BOXE + 1);
-            g[4] = S::lds(b + 4 * G::BOXE);
-            g[5] = S::lds(b + 5 * G::BOXE - 1);
-            g[6] = S::lds(b + 6 * G::BOXE + 1);
-            g[7] = S::lds(b + 7 * G::BOXE + 1);
-            g[8] = S::lds(b + 8 * G::BOXE - 1);
+            const Site<float> st = stage_site<S, G>(P, tx, ty);
+            float p[9], v[9];
             constexpr int W = G::PW;
             const float* c = PS + (ty + 1) * W + tx + 4;
             p[0] = c[0];
@@ -234,7 +228,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_collide_tma(StepArgs a) {
             p[6] = c[W - 1];
             p[7] = c[-W - 1];
             p[8] = c[-W + 1];
-            collide<false>(C, nullptr, sum9(g), g, p, v);
+            collide<S, false>(C, nullptr, st, p, v);
             store_site<S>(o, plane, pitch, gx, x, y, nx, ny, v);
         }
     });

@@ -120,8 +120,9 @@ def test_eos_precision_and_fp32_storage(P, eos, storage):
 @pytest.mark.parametrize("T", [0.8, 0.6])
 def test_fp16_deviation_storage_stated_error(P, T):
     # FP16 keeps 11 significant bits, so this storage has its own stated
-    # bound, not the FP32 one: after 1000 steps, 5e-3 relative in the bulk
-    # phases and 5e-2 at the interface (automatic rho0 = vapour density).
+    # bound, not the FP32 one: after 1000 steps, 2e-3 relative in the bulk
+    # phases and 1e-2 anywhere (automatic rho0 = vapour density; measured
+    # 5.5-6.6e-4 and 1.7-3.2e-3).
     n = 80
     rho = synth.droplet(n, n, 22.0, T)
     g = gpu_run(P, rho, 1000, T=T, storage=2)
@@ -129,7 +130,7 @@ def test_fp16_deviation_storage_stated_error(P, T):
     e = np.abs(g["rho"] - o["rho"]) / o["rho"]
     bulk = max(e[0, 0], e[n // 2, n // 2])
     print(f"fp16 T={T}: max rel rho error {e.max():.3e}, bulk {bulk:.3e}")
-    assert bulk <= 5e-3 and e.max() <= 5e-2
+    assert bulk <= 2e-3 and e.max() <= 1e-2
 
 
 @pytest.mark.parametrize("eps,sigma,m2", [(0.0, 1.0, 0), (1.73, 4.0, 0), (1.73, 0.125, 0),
@@ -407,7 +408,8 @@ def test_config3_oscillation_period_vs_lamb(P):
 
 def test_config4_batch_of_512_against_oracle(P):
     # the 512-lattice uneven batch, 1000 steps in one handle; the smallest and
-    # largest lattice and two seeded others against the oracle
+    # largest lattice and 16 seeded others against the oracle, every one held
+    # to the FP32 bar
     rec = synth.batch_recipe()
     descs = [P.lbm_desc_default(r["nx"], r["ny"], T=r["T"]) for r in rec]
     fields = [synth.droplet(r["nx"], r["ny"], r["R"], r["T"]) for r in rec]
@@ -416,23 +418,47 @@ def test_config4_batch_of_512_against_oracle(P):
         P.lbm_init(h, i, f)
     P.lbm_step(h, 1000)
     sides = np.array([r["nx"] for r in rec])
-    picks = [int(np.argmin(sides)), int(np.argmax(sides))] + synth.randint(77, 2, 0, 511).tolist()
+    picks = [int(np.argmin(sides)), int(np.argmax(sides))] + synth.randint(77, 16, 0, 511).tolist()
+    worst = 0.0
     for i in picks:
         got = P.lbm_moments(h, i, u=False, mass=False)["rho"]
         o = oracle_run(fields[i], 1000, T=rec[i]["T"])["rho"]
-        if rec[i]["nx"] <= 300:
-            assert rel(got, o) <= RTOL_RHO, (i, rec[i])
-        else:
-            # Large droplets: FP32 rounding adds coherently in the uniform bulk
-            # phases while the initial tanh profile relaxes (~1.5e-7 of mass in
-            # the first ~100 steps), which moves a radius-170 interface by
-            # ~1e-5 sites: 1-2.4e-5 pointwise at the interface, 8e-7 in L2.
-            # The FP64 problem itself is well conditioned (a 6e-8 input
-            # perturbation stays below 4e-8).  Stated bound for these sizes
-            # (measured for the 512 x 512 lattice: 2.3e-6 in L2, 5.6e-5 pointwise):
-            assert np.linalg.norm(got - o) / np.linalg.norm(o) <= 5e-6, (i, rec[i])
-            assert rel(got, o) <= 1e-4, (i, rec[i])
+        err = rel(got, o)
+        worst = max(worst, err)
+        print(f"lattice {i} side {rec[i]['nx']} T {rec[i]['T']:.3f}: {err:.2e}")
+        assert err <= RTOL_RHO, (i, rec[i], err)
     P.lbm_destroy(h)
+    print(f"config 4: worst density error after 1000 steps {worst:.2e}")
+
+
+def test_largest_batch_lattice_alone_both_fp32_storages(P):
+    # the batch's 512^2 lattice (R = 170, T_r = 0.70) alone, with FP32
+    # storage of deviations from rho0 = 0 and from the automatic rho0
+    i = int(np.argmax([r["nx"] for r in synth.batch_recipe()]))
+    r = synth.batch_recipe()[i]
+    rho = synth.droplet(r["nx"], r["ny"], r["R"], r["T"])
+    o = oracle_run(rho, 1000, T=r["T"])["rho"]
+    for storage in (0, 1):
+        g = gpu_run(P, rho, 1000, T=r["T"], storage=storage)["rho"]
+        print(f"512^2 alone, storage {storage}: {rel(g, o):.2e}")
+        assert rel(g, o) <= RTOL_RHO, storage
+
+
+def test_config3_ellipse_1000_steps_full_field(P):
+    # configuration 3 (1024^2 ellipse 120/100, T_r = 0.6, BGK tau = 0.8):
+    # the whole density field after 1000 steps against the oracle at the FP32
+    # bar, and both velocity components scaled by the largest speed
+    n, T, tau = 1024, 0.6, 0.8
+    rho = synth.ellipse(n, n, 120.0, 100.0, T)
+    g = gpu_run(P, rho, 1000, T=T, tau=tau)
+    o = oracle_run(rho, 1000, T=T, tau=tau)
+    err = rel(g["rho"], o["rho"])
+    print(f"1024^2 ellipse, 1000 steps: density {err:.2e}")
+    assert err <= RTOL_RHO
+    umax = max(np.abs(o["ux"]).max(), np.abs(o["uy"]).max())
+    for k in ("ux", "uy"):
+        assert np.abs(g[k] - o[k]).max() <= 1e-3 * umax, k
+    assert abs(g["mass"] - o["mass"]) / o["mass"] <= 1e-9
 
 
 @pytest.mark.parametrize("eos", [1, 0])
