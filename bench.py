@@ -7,9 +7,13 @@ pull-stream pass) over that lattice.  The working set (two population
 buffers, 4.8 GB) is far larger than L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--workload roofline|batched]
+                  [--workload roofline|batched|served]
 
-Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+Prints one JSON line (rank 0).  On one GPU the default line also carries
+"batched" (the 512-lattice batch of configuration 4, 100 timed steps, against
+one handle per lattice) and "served" (configuration 5's Poisson stream of
+1000 requests, step counts divided by 100, against one plain handle per
+request), measured after the roofline lattice's timed region.  ``--impl reference`` times the FP64 CPU
 oracle (the only reference this method has) on a bounded crop of the same
 workload, on the host cores.
 """
@@ -63,6 +67,9 @@ def parse():
                          "paper's oscillation test (s = 1 for the non-hydrodynamic moments, "
                          "1/tau for the stress)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--roofline-only", action="store_true",
+                    help="default workload: skip the batched and served measurements that the "
+                         "JSON line otherwise carries beside the roofline lattice")
     ap.add_argument("--tile", type=int, nargs=3, metavar=("TX", "TY", "SPT"), default=None,
                     help="fixed tile and sites per thread for both passes (no autotune)")
     ap.add_argument("--grid", type=int, default=0,
@@ -426,6 +433,16 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    if world == 1 and not args.roofline_only:
+        # the metric's other two parts, measured after the timed region above
+        # and outside it: the 512-lattice batch and the served stream, each
+        # against sequential plain handles on this GPU
+        b = measure_batched(P, storage, steps=100, warmup=5)
+        b.pop("_info")
+        out["batched"] = b
+        sv = measure_served(P, storage, requests=1000, step_scale=100)
+        sv.pop("_target")
+        out["served"] = sv
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)
@@ -434,65 +451,36 @@ def run_gpu(args):
 
 
 # ------------------------------------------------------------------ batched workload
-def run_sequential(P, descs, fields, sites, args):
-    """The batch's lattices stepped one handle after another on one stream (MLUPS)."""
-    import torch
-
-    stream = torch.cuda.Stream()
-    hs = []
-    for d, f in zip(descs, fields):
-        hh = P.lbm_create(d, stream=stream)
-        P.lbm_init(hh, 0, f)
-        P.lbm_step(hh, args.warmup)
-        hs.append(hh)
-    torch.cuda.synchronize()
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    for hh in hs:
-        P.lbm_step(hh, args.steps)
-    s1.record(stream)
-    torch.cuda.synchronize()
-    seq_ms = s0.elapsed_time(s1)
-    for hh in hs:
-        P.lbm_destroy(hh)
-    return sites * args.steps / (seq_ms * 1e-3) / 1e6
-
-
-def run_batched(args):
+def measure_batched(P, storage, steps, warmup, autotune=True, sequential=True, lattices=512):
     """512 independent droplet lattices of uneven sizes (sides U{64..512},
     R = side x U(0.15, 0.35), T_r U(0.6, 0.9), tau = 1) stepped together by
     one batch handle (persistent launches over one tile list, CUDA graphs),
-    against the same lattices stepped one handle after another."""
+    against the same lattices stepped one handle after another on one stream.
+    Three lattices (the first, the middle one, the largest) must come out of
+    the batch bitwise equal to their own handles' runs."""
     import torch
 
     import synth
-    from paper_2003_07968_gb300 import build, capi as P
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    build.build()
-    P.load()
-    storage = {"f32": P.LBM_STORE_F32, "f32dev": P.LBM_STORE_F32_DEV,
-               "f16dev": P.LBM_STORE_F16_DEV}[args.storage]
-    rec = synth.batch_recipe()[:max(1, min(args.lattices, 512))]
+    rec = synth.batch_recipe()[:max(1, min(lattices, 512))]
     descs = [P.lbm_desc_default(r["nx"], r["ny"], T=r["T"], storage=storage) for r in rec]
     fields = [synth.droplet(r["nx"], r["ny"], r["R"], r["T"]) for r in rec]
     sites = sum(r["nx"] * r["ny"] for r in rec)
     h = P.lbm_create(descs)
     for i, f in enumerate(fields):
         P.lbm_init(h, i, f)
-    if args.autotune:
+    if autotune:
         P.lbm_autotune(h, 10)
-    P.lbm_step(h, args.warmup)
+    P.lbm_step(h, warmup)
     P.lbm_sync(h)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     P.lbm_profile(h, True)
     P.lbm_profile_read(h)
     l0 = P.lbm_launch_count(h)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with ClockSampler(torch.cuda.current_device()) as clk:
         e0.record(h.stream)
-        P.lbm_step(h, args.steps)
+        P.lbm_step(h, steps)
         e1.record(h.stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
@@ -501,51 +489,58 @@ def run_batched(args):
     launches = P.lbm_launch_count(h) - l0
     P.lbm_sync(h)
     info = P.lbm_info(h)
+    batched = sites * steps / (ms * 1e-3) / 1e6
+    seq, same = None, None
+    if sequential:
+        stream = torch.cuda.Stream()
+        hs = []
+        for d, f in zip(descs, fields):
+            hh = P.lbm_create(d, stream=stream)
+            P.lbm_init(hh, 0, f)
+            P.lbm_step(hh, warmup)
+            hs.append(hh)
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for hh in hs:
+            P.lbm_step(hh, steps)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        seq = sites * steps / (s0.elapsed_time(s1) * 1e-3) / 1e6
+        big = int(np.argmax([r["nx"] * r["ny"] for r in rec]))
+        same = True
+        for i in sorted({0, len(rec) // 2, big}):
+            a_ = P.lbm_moments(h, i, u=False, mass=False)["rho"]
+            b_ = P.lbm_moments(hs[i], 0, u=False, mass=False)["rho"]
+            same = same and bool(np.array_equal(a_, b_))
+        for hh in hs:
+            P.lbm_destroy(hh)
     P.lbm_destroy(h)
-    batched = sites * args.steps / (ms * 1e-3) / 1e6
-    # sequential: one handle per lattice, stepped one after another on one stream
-    sequential = run_sequential(P, descs, fields, sites, args) if args.sequential else None
     peak, peak_src = measured_hbm_peak()
-    es = 2 if args.storage == "f16dev" else 4
+    es = 2 if storage == P.LBM_STORE_F16_DEV else 4
     kname, k2 = max(stats.items(), key=lambda kv: kv[1]["total_ms"])  # dominant kernel
     avg = k2["total_ms"] / max(k2["launches"], 1)
     achieved = k2["bytes_per_launch"] / (avg * 1e-3) / 1e9
-    out = {"metric": METRIC, "value": round(batched, 3), "unit": "MLUPS",
-           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"batched: {len(rec)} droplet lattices, sides U{{64..512}}, "
-                                  f"{sites} sites",
-                      "storage": args.storage, "eos": args.eos,
-                      "psi_pass": [info["psi_variant"], info["psi_tile_x"], info["psi_tile_y"],
-                                   info["psi_spt"], info["psi_grid_ctas"]],
-                      "collide_pass": [info["collide_variant"], info["tile_x"], info["tile_y"],
-                                       info["spt"], info["grid_ctas"]],
-                      "schedule": ["auto", "two_pass", "fused"][info["schedule"]]},
-           "batched": {"MLUPS": round(batched, 1),
-                       "sequential_MLUPS": round(sequential, 1) if sequential else None,
-                       "speedup": round(batched / sequential, 3) if sequential else None,
-                       "sequential": "one handle per lattice, lbm_step one after another"},
-           "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
-                        "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                        "traffic": None, "peak_source": peak_src},
-           "step_roofline": {"algorithmic_bytes_per_site": 18 * es,
-                             "effective_GBps": round(batched * 1e6 * 18 * es / 1e9, 1)},
-           "gpu_launches": int(launches), "clocks": clk.summary()}
-    print(json.dumps(out), flush=True)
+    return {
+        "MLUPS": round(batched, 1),
+        "sequential_MLUPS": round(seq, 1) if seq else None,
+        "speedup": round(batched / seq, 3) if seq else None,
+        "batch_equals_alone": same,
+        "lattices": len(rec), "sites": sites, "steps": steps, "ms_per_step": round(ms / steps, 5),
+        "sequential": "one handle per lattice, lbm_step one after another on one stream",
+        "kernel": {"name": kname, "tile": [info["tile_x"], info["tile_y"]],
+                   "sites_per_thread": info["spt"], "achieved_GBps": round(achieved, 1),
+                   "frac": round(achieved / peak, 4), "peak_source": peak_src},
+        "algorithmic_bytes_per_site": 18 * es,
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+        "_info": info,
+    }
 
 
-# ------------------------------------------------------------------ served workload
-def run_served(args):
-    """Poisson stream (200/s) of droplet / flat-band solves with sides
-    U{128..2048} and steps U{1000..50000} / step_scale, submitted in real time
-    to one continuous-batching server; against the same requests served one
-    at a time by plain handles (first come first served, same arrivals)."""
-    import threading
-
+def run_batched(args):
+    """The batched workload alone, as its own JSON line."""
     import torch
 
-    import synth
     from paper_2003_07968_gb300 import build, capi as P
 
     rank, world, local = dist_env()
@@ -554,9 +549,46 @@ def run_served(args):
     P.load()
     storage = {"f32": P.LBM_STORE_F32, "f32dev": P.LBM_STORE_F32_DEV,
                "f16dev": P.LBM_STORE_F16_DEV}[args.storage]
-    reqs = synth.serving_stream(n=args.requests)
+    b = measure_batched(P, storage, args.steps, args.warmup, args.autotune, args.sequential,
+                        args.lattices)
+    info = b.pop("_info")
+    peak, peak_src = measured_hbm_peak()
+    out = {"metric": METRIC, "value": b["MLUPS"], "unit": "MLUPS",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": b["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"batched: {b['lattices']} droplet lattices, sides U{{64..512}}, "
+                                  f"{b['sites']} sites",
+                      "storage": args.storage, "eos": args.eos,
+                      "psi_pass": [info["psi_variant"], info["psi_tile_x"], info["psi_tile_y"],
+                                   info["psi_spt"], info["psi_grid_ctas"]],
+                      "collide_pass": [info["collide_variant"], info["tile_x"], info["tile_y"],
+                                       info["spt"], info["grid_ctas"]],
+                      "schedule": ["auto", "two_pass", "fused"][info["schedule"]]},
+           "batched": b,
+           "roofline": {"bound": "hbm", "kernel": b["kernel"]["name"],
+                        "achieved": b["kernel"]["achieved_GBps"], "peak": peak, "unit": "GB/s",
+                        "frac": b["kernel"]["frac"], "traffic": None, "peak_source": peak_src},
+           "gpu_launches": b["gpu_launches"], "clocks": b["clocks"]}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ served workload
+def measure_served(P, storage, requests, step_scale, chunk=100, chunk_ms=4.0, target_sites=0):
+    """Poisson stream (200/s) of droplet / flat-band solves with sides
+    U{128..2048} and steps U{1000..50000} / step_scale, submitted in real time
+    to one continuous-batching server; against the same requests served one
+    at a time by plain handles (first come first served, same arrivals).
+    Three served results must equal the same lattice stepped alone, bitwise."""
+    import threading
+
+    import torch
+
+    import synth
+
+    reqs = synth.serving_stream(n=requests)
     for r in reqs:
-        r["steps"] = max(1, r["steps"] // args.step_scale)
+        r["steps"] = max(1, r["steps"] // step_scale)
     fields = [synth.request_field(r) for r in reqs]
     descs = [P.lbm_desc_default(r["nx"], r["ny"], T=r["T"], storage=storage) for r in reqs]
     work = sum(r["nx"] * r["ny"] * r["steps"] for r in reqs)
@@ -568,11 +600,11 @@ def run_served(args):
     P.lbm_destroy(h)
 
     # results carry rho only, as the sequential runs below read rho only
-    opts = P.lbm_server_opts_default(arena_bytes=64 << 30, chunk_steps=args.chunk,
-                                     chunk_ms=args.chunk_ms, storage=storage,
+    opts = P.lbm_server_opts_default(arena_bytes=64 << 30, chunk_steps=chunk,
+                                     chunk_ms=chunk_ms, storage=storage,
                                      max_resident=1024, with_velocity=0)
-    if args.target_sites:
-        opts.target_resident_sites = args.target_sites
+    if target_sites:
+        opts.target_resident_sites = target_sites
     srv = P.lbm_server_create(opts)
     tickets = [None] * len(reqs)
     t_start = time.perf_counter()
@@ -585,7 +617,7 @@ def run_served(args):
             tickets[i] = P.lbm_submit(srv, descs[i], fields[i], r["steps"])
 
     th = threading.Thread(target=submitter)
-    with ClockSampler(local) as clk:
+    with ClockSampler(torch.cuda.current_device()) as clk:
         th.start()
         results, lat, failed = {}, [], 0
         while len(results) < len(reqs):
@@ -632,24 +664,46 @@ def run_served(args):
         P.lbm_destroy(hh)
         same = same and results[i]["rho"] is not None and bool(np.array_equal(a, results[i]["rho"]))
     pct = lambda v, q: float(np.percentile(np.array(v), q))
-    out = {"metric": METRIC, "value": round(served, 3), "unit": "MLUPS",
-           "n_gpus": world, "steps": len(reqs), "warmup": 0,
-           "ms_per_step": round(wall / len(reqs) * 1e3, 4), "higher_is_better": True,
+    return {"MLUPS": round(served, 1), "p50_s": round(pct(lat, 50), 4),
+            "p99_s": round(pct(lat, 99), 4), "wall_s": round(wall, 3),
+            "gpu_busy_s": round(stats["busy_s"], 3),
+            "sequential_MLUPS": round(work / seq_wall / 1e6, 1),
+            "sequential_p50_s": round(pct(seq_lat, 50), 4),
+            "sequential_p99_s": round(pct(seq_lat, 99), 4),
+            "speedup": round(served / (work / seq_wall / 1e6), 3),
+            "mix_equals_alone": same, "failed_requests": failed,
+            "requests": len(reqs), "step_scale": step_scale, "site_steps": work,
+            "stream": f"Poisson 200/s, sides U{{128..2048}}, steps U{{1000..50000}}/{step_scale}, "
+                      "droplet/band 50/50",
+            "sequential": "one plain handle per request, first come first served, same arrivals",
+            "gpu_launches": int(stats["launches"]), "clocks": clk.summary(),
+            "_target": opts.target_resident_sites}
+
+
+def run_served(args):
+    """The served workload alone, as its own JSON line."""
+    import torch
+
+    from paper_2003_07968_gb300 import build, capi as P
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    P.load()
+    storage = {"f32": P.LBM_STORE_F32, "f32dev": P.LBM_STORE_F32_DEV,
+               "f16dev": P.LBM_STORE_F16_DEV}[args.storage]
+    sv = measure_served(P, storage, args.requests, args.step_scale, args.chunk, args.chunk_ms,
+                        args.target_sites)
+    target = sv.pop("_target")
+    out = {"metric": METRIC, "value": sv["MLUPS"], "unit": "MLUPS",
+           "n_gpus": world, "steps": sv["requests"], "warmup": 0,
+           "ms_per_step": round(sv["wall_s"] / sv["requests"] * 1e3, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"served: {len(reqs)} requests, Poisson 200/s, sides U{{128..2048}}, "
-                                  f"steps U{{1000..50000}}/{args.step_scale}, droplet/band 50/50",
+           "config": {"workload": f"served: {sv['requests']} requests, " + sv["stream"],
                       "storage": args.storage, "chunk_steps": args.chunk,
-                      "chunk_ms": args.chunk_ms, "site_steps": work,
-                      "target_resident_sites": opts.target_resident_sites},
-           "served": {"MLUPS": round(served, 1), "p50_s": round(pct(lat, 50), 4),
-                      "p99_s": round(pct(lat, 99), 4), "wall_s": round(wall, 3),
-                      "gpu_busy_s": round(stats["busy_s"], 3),
-                      "sequential_MLUPS": round(work / seq_wall / 1e6, 1),
-                      "sequential_p50_s": round(pct(seq_lat, 50), 4),
-                      "sequential_p99_s": round(pct(seq_lat, 99), 4),
-                      "speedup": round(served / (work / seq_wall / 1e6), 3),
-                      "mix_equals_alone": same, "failed_requests": failed},
-           "gpu_launches": int(stats["launches"]), "clocks": clk.summary()}
+                      "chunk_ms": args.chunk_ms, "site_steps": sv["site_steps"],
+                      "target_resident_sites": target},
+           "served": sv, "gpu_launches": sv["gpu_launches"], "clocks": sv["clocks"]}
     print(json.dumps(out), flush=True)
 
 

@@ -288,14 +288,57 @@ __global__ void k_init(LatDev L, void* pop, int parity, const double* rho, const
     const double e0 = (double)S::rt((float)g0) - g0;
     store_img(o, L.pitch, L.gx, x, y, nx, ny, R);
     const double rc = rho[(int64_t)y * nx + x];
+    const float e0f = (float)e0;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         int sx = x + kCx[i], sy = y + kCy[i];
         sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
         sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-        const double G = still ? fma(-0.28125, e0, w[i] * (rho[(int64_t)sy * nx + sx] - rc))
-                               : (geq(i, sx, sy) - (double)cref(i) * g0) - 0.28125 * e0;
-        store_img(o + i * L.plane, L.pitch, L.gx, x, y, nx, ny, S::cv((float)G));
+        // u = 0: the difference of the two densities in FP64, the rest (small
+        // numbers) in FP32
+        const float G = still ? fmaf(-0.28125f, e0f,
+                                     (float)w[i] * (float)(rho[(int64_t)sy * nx + sx] - rc))
+                              : (float)((geq(i, sx, sy) - (double)cref(i) * g0) - 0.28125 * e0);
+        store_img(o + i * L.plane, L.pitch, L.gx, x, y, nx, ny, S::cv(G));
+    }
+}
+
+// ------------------------------------------------------------------ field scan
+// The smallest value of a device field and whether every value is finite
+// (lbm_init's check of the densities it was handed, on the staged copy):
+// each block writes its minimum, or NaN if it met a value that is not
+// finite; k_scan_final reduces the partials the same way into *out.
+__global__ void __launch_bounds__(256) k_scan_partial(const double* v, int64_t n, double* partials) {
+    double m = HUGE_VAL;
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = v[i];
+        bad |= !isfinite(x);
+        m = fmin(m, x);
+    }
+    bad = __syncthreads_or(bad);
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_down_sync(0xffffffffu, m, o));
+    __shared__ double red[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = red[0];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) b = fmin(b, red[k]);
+        partials[blockIdx.x] = bad ? __longlong_as_double(0x7ff8000000000000LL) : b;
+    }
+}
+
+__global__ void k_scan_final(const double* partials, int n, double* out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double m = HUGE_VAL;
+        bool bad = false;
+        for (int i = 0; i < n; ++i) {
+            bad |= isnan(partials[i]);
+            m = fmin(m, partials[i]);
+        }
+        *out = bad ? __longlong_as_double(0x7ff8000000000000LL) : m;
     }
 }
 
@@ -620,6 +663,17 @@ cudaError_t launch_mass(int storage_f16, const LatDev& L, const void* pop, int p
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_mass_final<<<1, 32, 0, st>>>(partials, nb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const double* v, int64_t n, double* partials, int n_partials, double* out,
+                        cudaStream_t st) {
+    const int64_t want = (n + 255) / 256;
+    const int nb = (int)(want < n_partials ? want : n_partials);
+    k_scan_partial<<<nb, 256, 0, st>>>(v, n, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_scan_final<<<1, 32, 0, st>>>(partials, nb, out);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,10 @@ cudaError_t launch_init(int storage_f16, const LatDev& L, void* pop, int parity,
 cudaError_t launch_moments(int storage_f16, const LatDev& L, const void* pop, int parity,
                            const float* psi, double* rho, double* ux, double* uy,
                            cudaStream_t st);
+// The smallest of n device values into *out, or NaN if any is not finite
+// (partials: at least n_partials doubles of scratch).
+cudaError_t launch_scan(const double* v, int64_t n, double* partials, int n_partials, double* out,
+                        cudaStream_t st);
 cudaError_t launch_arith_check(const float* x, int64_t n, float* rcp, float* sq,
                                uint32_t* mismatch, cudaStream_t st);
 cudaError_t launch_mass(int storage_f16, const LatDev& L, const void* pop, int parity,

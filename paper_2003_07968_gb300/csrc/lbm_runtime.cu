@@ -90,6 +90,7 @@ struct lbm_handle {
     int64_t device_bytes = 0;
     // host side
     uint32_t* status_host = nullptr;  // pinned
+    double* scan_host = nullptr;      // pinned: lbm_init's field scan result
     cudaEvent_t status_ev = nullptr;
     bool status_pending = false;
     int32_t starve = 0;        // armed failure-detection test (tile + 1), for one launch
@@ -410,6 +411,7 @@ void release(lbm_handle* h) {
     h->ev_pool.clear();
     if (h->status_ev) cudaEventDestroy(h->status_ev);
     if (h->status_host) cudaFreeHost(h->status_host);
+    if (h->scan_host) cudaFreeHost(h->scan_host);
     dev_free(h, h->staging, h->staging_elems * 3 * sizeof(double));
     dev_free(h, h->partials, (kMassPartials + 1) * sizeof(double));
     for (auto& P : h->pass) dev_free(h, P.tiles, P.cap);
@@ -792,7 +794,8 @@ static int lbm_create_body(const lbm_lattice_desc* descs, int32_t n, const lbm_r
     h->partials = (double*)dev_alloc(h, (kMassPartials + 1) * sizeof(double));
     if (!h->pop || !h->psi || !h->lat_dev || !h->status || !h->partials)
         return fail(LBM_ERR_OOM);
-    if (cudaMallocHost(&h->status_host, n * sizeof(uint32_t)) != cudaSuccess)
+    if (cudaMallocHost(&h->status_host, n * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost(&h->scan_host, sizeof(double)) != cudaSuccess)
         return fail(LBM_ERR_OOM);
     if (cudaEventCreateWithFlags(&h->status_ev, cudaEventDisableTiming) != cudaSuccess)
         return fail(LBM_ERR_CUDA);
@@ -859,8 +862,23 @@ static int lbm_init_body(lbm_handle* h, int32_t lattice, const double* rho, cons
     const size_t n = (size_t)L.nx * L.ny;
     int rc = ensure_staging(h, n);
     if (rc) return rc;
-    double mn = 0.0;
-    if (!field_scan(rho, n, &mn)) return LBM_ERR_ARG;  // every density finite
+    double* dr = h->staging;
+    double* dx = h->staging + h->staging_elems;
+    double* dy = h->staging + 2 * h->staging_elems;
+    // the staged densities are scanned on the GPU (every one finite, and the
+    // smallest); the staging buffers hold nothing else, and nothing reads
+    // them unless the scan passes
+    CK(h, cudaMemcpyAsync(dr, rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (ux) CK(h, cudaMemcpyAsync(dx, ux, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (uy) CK(h, cudaMemcpyAsync(dy, uy, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, launch_scan(dr, (int64_t)n, h->partials, kMassPartials, h->partials + kMassPartials,
+                      h->stream));
+    h->launches += 2;
+    CK(h, cudaMemcpyAsync(h->scan_host, h->partials + kMassPartials, sizeof(double),
+                          cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    const double mn = *h->scan_host;
+    if (std::isnan(mn)) return LBM_ERR_ARG;  // a density that is not finite
     if (h->desc[lattice].storage != LBM_STORE_F32 && h->desc[lattice].rho0 < 0.0) {
         // automatic reference: the smallest density keeps the vapour deviations
         // small (best relative precision where rho is smallest) and the liquid
@@ -871,12 +889,6 @@ static int lbm_init_body(lbm_handle* h, int32_t lattice, const double* rho, cons
         CK(h, cudaMemcpyAsync(h->lat_dev + lattice, &L, sizeof(LatDev), cudaMemcpyHostToDevice,
                               h->stream));
     }
-    double* dr = h->staging;
-    double* dx = h->staging + h->staging_elems;
-    double* dy = h->staging + 2 * h->staging_elems;
-    CK(h, cudaMemcpyAsync(dr, rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    if (ux) CK(h, cudaMemcpyAsync(dx, ux, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    if (uy) CK(h, cudaMemcpyAsync(dy, uy, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(h, launch_init(h->f16, L, h->pop, h->parity, dr, ux ? dx : nullptr, uy ? dy : nullptr,
                       h->stream));
     h->launches += 1;
@@ -969,16 +981,23 @@ static int lbm_moments_body(lbm_handle* h, int32_t lattice, double* rho, double*
         CK(h, launch_moments(h->f16, L, h->pop, h->parity, h->psi, dr, (ux || uy) ? dx : nullptr,
                              (ux || uy) ? dy : nullptr, h->stream));
         h->launches += 1;
-        if (rho) CK(h, cudaMemcpyAsync(rho, dr, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-        if (ux) CK(h, cudaMemcpyAsync(ux, dx, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-        if (uy) CK(h, cudaMemcpyAsync(uy, dy, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     }
+    // the mass reduction is queued before the large copies, so it does not
+    // wait for them
     if (mass) {
         CK(h, launch_mass(h->f16, L, h->pop, h->parity, h->partials, kMassPartials,
                           h->partials + kMassPartials, h->stream));
         h->launches += 2;
         CK(h, cudaMemcpyAsync(mass, h->partials + kMassPartials, sizeof(double),
                               cudaMemcpyDeviceToHost, h->stream));
+    }
+    if (rho || ux || uy) {
+        const double* dr = h->staging;
+        const double* dx = h->staging + h->staging_elems;
+        const double* dy = h->staging + 2 * h->staging_elems;
+        if (rho) CK(h, cudaMemcpyAsync(rho, dr, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (ux) CK(h, cudaMemcpyAsync(ux, dx, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (uy) CK(h, cudaMemcpyAsync(uy, dy, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     }
     return sync_status(h);
 }

@@ -355,6 +355,35 @@ def test_full_size_sampled_parity(P, case):
     assert abs(g["mass"] - exact) / exact <= 1e-6
 
 
+def test_roofline_droplet_1000_steps_against_oracle_golden(P):
+    # the 8192^2 droplet the throughput is measured on (R = 2048, T_r = 0.8,
+    # tau = 1), 1000 steps in the launch configuration bench.py times
+    # (autotuned single pass), against the FP64 oracle's values at 614
+    # sampled sites (interface crossings along both axes and a diagonal,
+    # corners, edges, centre, 200 seeded sites) and its total mass, written
+    # by tests/golden/make_roofline_1000.py
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "roofline_1000.json")) as fh:
+        gold = json.load(fh)
+    n, T, tau = gold["n"], gold["T"], gold["tau"]
+    rho = synth.droplet(n, n, gold["R"], T)
+    d = P.lbm_desc_default(n, n, T=T, tau=tau)
+    h = P.lbm_create(d)
+    P.lbm_init(h, 0, rho)
+    P.lbm_autotune(h)  # trial launches leave the state unchanged
+    P.lbm_step(h, gold["steps"])
+    out = P.lbm_moments(h, 0, u=False)
+    P.lbm_destroy(h)
+    ys, xs, want = (np.array(c) for c in zip(*gold["sites"]))
+    got = out["rho"][ys.astype(int), xs.astype(int)]
+    err = rel(got, want)
+    print(f"8192^2 droplet, 1000 steps, {len(want)} sampled sites: {err:.2e}")
+    assert err <= RTOL_RHO
+    assert abs(out["mass"] - gold["mass"]) / gold["mass"] <= 1e-9
+
+
 # ------------------------------------------------------------- derived quantities
 def test_config2_laplace_quantities(P):
     # 256 x 256 droplet R = 30 at T_r = 0.7, tau = 1, 20000 steps: coexistence
