@@ -59,15 +59,29 @@ extern "C" {
 #define LBM_ERR_CAPACITY (-8)       /* request larger than the server can hold  */
 
 /* ---- population storage (precision forms) -------------------------------- */
-#define LBM_STORE_F32 0     /* f_i in FP32                                       */
-#define LBM_STORE_F32_DEV 1 /* f_i - w_i rho0 in FP32                            */
-#define LBM_STORE_F16_DEV 2 /* f_i - w_i rho0 in FP16 (IEEE binary16)            */
+/* Every form stores rest-referenced deviations: per site, plane 0 holds
+ * R = f_0 - w_0 rho0 and plane i (1..8) holds (f_i - w_i rho0) - (w_i/w_0) R
+ * plus a share of R's rounding, so that eight of the nine stored numbers are
+ * small and a site's stored mass, rho0 + 9/4 R + sum_i (plane i), is exact
+ * to roundings of small numbers.  The forms differ in element type and rho0. */
+#define LBM_STORE_F32 0     /* FP32, rho0 = 0                                    */
+#define LBM_STORE_F32_DEV 1 /* FP32, rho0 from the descriptor or automatic       */
+#define LBM_STORE_F16_DEV 2 /* FP16 (IEEE binary16), rho0 as LBM_STORE_F32_DEV   */
 
 /* ---- arithmetic of psi / Eq. (CSEOS) ------------------------------------- */
 #define LBM_EOS_F64 0 /* native FP64                                             */
 #define LBM_EOS_DF 1  /* float-float pairs (about 43 significant bits on the
                           radicand), FP32 psi                                  */
 #define LBM_EOS_F32 2 /* FP32                                                    */
+
+/* ---- equation of state behind psi, Eq. (DED) ----------------------------- */
+#define LBM_EOS_KIND_CS 0  /* Carnahan-Starling, Eq. (CSEOS):
+                              P = k [c rho T (1 + b rho + (b rho)^2 - (b rho)^3)
+                                     / (1 - b rho)^3 - a rho^2]              */
+#define LBM_EOS_KIND_VDW 1 /* van der Waals in the same constants:
+                              P = k [c rho T / (1 - b rho) - a rho^2]; with
+                              a = 3, b = 1/3, c = 8/3 the reduced equation,
+                              critical point rho = T = 1, P = k              */
 
 /* ---- collision operator -------------------------------------------------- */
 #define LBM_COLL_BGK 0 /* Eq. (BGKCO) with Guo forcing Eq. (GFSBGK)            */
@@ -103,7 +117,9 @@ extern "C" {
 /* One lattice.  Defaults (lbm_desc_default): tau = 1, G = -1, eps = 1.73,
  * sigma = 1, T = 0.8, a/b/c/k = 3.852462257 / 0.1304438842 / 2.785855166 /
  * 0.01 (Sec. IV.A), rho0 = -1 (automatic), LBM_STORE_F32_DEV, LBM_EOS_DF,
- * direct trace, BGK, MRT rates diag(1,1,1,1,1,1,1,1/tau,1/tau) (Eq. RM). */
+ * direct trace, BGK, MRT rates diag(1,1,1,1,1,1,1,1/tau,1/tau) (Eq. RM),
+ * LBM_EOS_KIND_CS.  For LBM_EOS_KIND_VDW set a, b, c as well (3, 1/3, 8/3
+ * for the reduced van der Waals equation). */
 typedef struct {
     int32_t nx, ny;           /* lattice size, each >= 2                        */
     double tau;               /* relaxation time, > 0.5                         */
@@ -120,6 +136,7 @@ typedef struct {
                                  1: 2 c_s^2 (M0 - psi) (text after Eq. DFTCST)  */
     int32_t collision;        /* LBM_COLL_*                                      */
     double mrt_rates[9];      /* diagonal of Lambda (Eq. RelaxationMatrix)      */
+    int32_t eos_kind;         /* LBM_EOS_KIND_*; may differ between lattices    */
 } lbm_lattice_desc;
 
 /* Optional runtime settings; pass NULL for defaults. */
@@ -297,6 +314,17 @@ typedef struct {
                                  map covers them all for the TMA single pass    */
     double chunk_ms;          /* GPU time a chunk aims at (0: 4 ms; < 0: every
                                  chunk runs chunk_steps steps)                   */
+    /* Device allocator for the arena, staging and tables, as in
+       lbm_runtime_opts: alloc returns a device pointer aligned to >= 256
+       bytes, or NULL on failure (lbm_server_create then fails with
+       LBM_ERR_OOM after freeing what it took; a table that grows later fails
+       the requests of that chunk); free releases it.  Both NULL:
+       cudaMalloc/cudaFree.  Called from the creating thread and from the
+       server's worker thread; it must outlive the server.  Pinned host
+       buffers always come from cudaMallocHost. */
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free)(void* ptr, size_t bytes, void* ctx);
+    void* alloc_ctx;
 } lbm_server_opts;
 
 typedef struct {
@@ -397,6 +425,22 @@ int lbm_inject_copy_timeout(lbm_handle* h, int32_t tile);
  * returns LBM_ERR_STATE if any result differs in a bit from the paired lane.
  * Errors: LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_STATE. */
 int lbm_selfcheck_arith(const float* x, int64_t n, float* rcp, float* sq);
+
+/* psi of Eq. (DED) (with Eq. CSEOS or the van der Waals equation, as
+ * d->eos_kind says) exactly as the step kernels evaluate it, in the
+ * arithmetic d->eos_precision names and with the lattice constants that
+ * lbm_create derives from *d, for n host densities rho (1 <= n <= 2^24,
+ * FP32, the type the kernels hold rho in): psi[i] (NaN where psi is not
+ * defined: rho <= 0, b rho >= 1 or a negative radicand) and, for
+ * LBM_EOS_DF, radicand[i] = psi^2 before its one rounding to FP32, in FP64
+ * (NaN for the other arithmetics).  Caller-owned host arrays of n values.
+ * For tests of the EOS arithmetic against an FP64 evaluation.  Also runs
+ * each value through the one-value (scalar) lane and returns LBM_ERR_STATE
+ * if any psi differs in a bit from the paired lane.
+ * Errors: LBM_ERR_ARG (bad descriptor or sizes), LBM_ERR_OOM, LBM_ERR_CUDA,
+ * LBM_ERR_STATE. */
+int lbm_selfcheck_psi(const lbm_lattice_desc* d, const float* rho, int64_t n, float* psi,
+                      double* radicand);
 
 /* Host-only consistency proof of the shared-memory staging used by the
  * LBM_KERNEL_TMA passes (two-pass and single-pass plans): for a set of

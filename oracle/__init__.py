@@ -34,6 +34,13 @@ CS_A = 3.852462257
 CS_B = 0.1304438842
 CS_C = 2.785855166
 CS_K = 0.01
+# van der Waals in the same constants, P = k [c rho T / (1 - b rho) - a rho^2]:
+# the reduced equation 8 rho T / (3 - rho) - 3 rho^2, critical point (1, 1, k)
+VDW_A = 3.0
+VDW_B = 1.0 / 3.0
+VDW_C = 8.0 / 3.0
+VDW_K = 0.01
+EOS_KINDS = {"cs": 0, "vdw": 1}
 
 
 class OrcParams(ctypes.Structure):
@@ -52,16 +59,22 @@ class OrcParams(ctypes.Structure):
         ("m2_trace_variant", ctypes.c_int32),
         ("collision", ctypes.c_int32),
         ("mrt_rates", ctypes.c_double * 9),
+        ("eos_kind", ctypes.c_int32),
     ]
 
 
 def params(tau=1.0, G=-1.0, eps=1.73, sigma=1.0, T=0.8, m2_trace_variant=0,
-           collision="bgk", mrt_rates=None, eos=(CS_A, CS_B, CS_C, CS_K)) -> OrcParams:
+           collision="bgk", mrt_rates=None, eos=None, eos_kind="cs") -> OrcParams:
     """Build an :class:`OrcParams`.  ``collision`` is "bgk" or "mrt"; for MRT
-    the default relaxation matrix is Eq. (RM): diag(1,...,1, 1/tau, 1/tau)."""
+    the default relaxation matrix is Eq. (RM): diag(1,...,1, 1/tau, 1/tau).
+    ``eos_kind`` is "cs" (Eq. CSEOS, the paper's) or "vdw" (van der Waals);
+    ``eos`` = (a, b, c, k) overrides that kind's constants."""
     p = OrcParams()
     p.tau, p.G, p.eps, p.sigma, p.T = tau, G, eps, sigma, T
+    if eos is None:
+        eos = (CS_A, CS_B, CS_C, CS_K) if eos_kind == "cs" else (VDW_A, VDW_B, VDW_C, VDW_K)
     p.eos_a, p.eos_b, p.eos_c, p.eos_k = eos
+    p.eos_kind = EOS_KINDS[eos_kind]
     p.m2_trace_variant = int(m2_trace_variant)
     p.collision = {"bgk": 0, "mrt": 1}[collision]
     rates = mrt_rates if mrt_rates is not None else [1.0] * 7 + [1.0 / tau] * 2

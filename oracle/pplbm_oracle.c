@@ -48,6 +48,7 @@ typedef struct {
     int32_t m2_trace_variant; /* 0: direct trace, 1: 2 c_s^2 (M0 - psi)     */
     int32_t collision;        /* 0: BGK (Eq. BGKCO), 1: MRT (Eq. MRTCO)     */
     double mrt_rates[9];      /* diagonal of Lambda, Eq. (RelaxationMatrix) */
+    int32_t eos_kind;         /* 0: Carnahan-Starling, Eq. (CSEOS); 1: van der Waals */
 } orc_params;
 
 /* D2Q9 velocity set, Eq. (VelocitySet), and weights (text after Eq. SEDF). */
@@ -63,9 +64,16 @@ static int wrap(int i, int n) {
     return r < 0 ? r + n : r;
 }
 
-/* Carnahan-Starling equation of state, Eq. (CSEOS). */
+/* The equation of state P_EOS(rho) that Eq. (DED) turns into psi:
+ *   eos_kind 0, Carnahan-Starling, Eq. (CSEOS):
+ *     P = k [c rho T (1 + b rho + (b rho)^2 - (b rho)^3) / (1 - b rho)^3 - a rho^2];
+ *   eos_kind 1, van der Waals (the textbook form, in the same constants):
+ *     P = k [c rho T / (1 - b rho) - a rho^2];
+ *     with a = 3, b = 1/3, c = 8/3 it is the reduced equation
+ *     P / k = 8 rho T / (3 - rho) - 3 rho^2, critical point (1, 1, k). */
 double orc_eos_pressure(const orc_params* p, double rho) {
     double br = p->eos_b * rho;
+    if (p->eos_kind == 1) return p->eos_k * (p->eos_c * rho * p->T / (1.0 - br) - p->eos_a * rho * rho);
     double num = 1.0 + br + br * br - br * br * br;
     double den = (1.0 - br) * (1.0 - br) * (1.0 - br);
     return p->eos_k * (p->eos_c * rho * p->T * num / den - p->eos_a * rho * rho);

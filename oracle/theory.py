@@ -2,7 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-* Carnahan-Starling EOS, Eq. (CSEOS), and psi, Eq. (DED).
+* Carnahan-Starling EOS, Eq. (CSEOS), and psi, Eq. (DED); the van der Waals
+  EOS in the same constants (kind="vdw") behind the same psi.
 * Maxwell equal-area coexistence, Eq. (MLVDR) with equal bulk pressures.
 * Mechanical-stability coexistence of the pseudopotential method,
   Eq. (PGLDR) with Eqs. (BPLP), (BPVP), epsilon = -2 A1 / (A2 + A3).
@@ -27,30 +28,39 @@ CS_A = 3.852462257
 CS_B = 0.1304438842
 CS_C = 2.785855166
 CS_K = 0.01
+VDW = (3.0, 1.0 / 3.0, 8.0 / 3.0, 0.01)  # reduced van der Waals, critical point (1, 1, k)
+_CONST = {"cs": (CS_A, CS_B, CS_C, CS_K), "vdw": VDW}
 
 
-def eos_pressure(rho, T, a=CS_A, b=CS_B, c=CS_C, k=CS_K):
-    """Eq. (CSEOS): P = k [c rho T (1 + b rho + (b rho)^2 - (b rho)^3)/(1 - b rho)^3 - a rho^2]."""
+def eos_pressure(rho, T, a=None, b=None, c=None, k=None, kind="cs"):
+    """The equation of state of Eq. (DED).
+    kind "cs", Eq. (CSEOS): P = k [c rho T (1 + b rho + (b rho)^2 - (b rho)^3)/(1 - b rho)^3 - a rho^2];
+    kind "vdw": P = k [c rho T / (1 - b rho) - a rho^2] (van der Waals)."""
+    A, B, C, K = _CONST[kind]
+    a, b, c, k = (A if a is None else a, B if b is None else b, C if c is None else c,
+                  K if k is None else k)
     br = b * rho
+    if kind == "vdw":
+        return k * (c * rho * T / (1 - br) - a * rho**2)
     return k * (c * rho * T * (1 + br + br**2 - br**3) / (1 - br) ** 3 - a * rho**2)
 
 
-def dpdrho(rho, T):
+def dpdrho(rho, T, kind="cs"):
     """dP/drho by the complex-step derivative (exact to rounding for analytic P)."""
     h = 1e-30
-    return np.imag(eos_pressure(np.asarray(rho, dtype=complex) + 1j * h, T)) / h
+    return np.imag(eos_pressure(np.asarray(rho, dtype=complex) + 1j * h, T, kind=kind)) / h
 
 
-def psi(rho, T, G=-1.0):
+def psi(rho, T, G=-1.0, kind="cs"):
     """Eq. (DED): psi = sqrt((P_EOS - c_s^2 rho)/G)."""
-    return np.sqrt((eos_pressure(rho, T) - CS2 * rho) / G)
+    return np.sqrt((eos_pressure(rho, T, kind=kind) - CS2 * rho) / G)
 
 
-def critical_point(a=CS_A, b=CS_B, c=CS_C, k=CS_K):
+def critical_point(a=None, b=None, c=None, k=None, kind="cs"):
     """(rho_c, T_c, P_c): where dP/drho = d2P/drho2 = 0 (plain root solve)."""
 
     def p(r, t):
-        return eos_pressure(r, t, a, b, c, k)
+        return eos_pressure(r, t, a, b, c, k, kind=kind)
 
     def d1(r, t):
         hc = 1e-30
@@ -67,35 +77,39 @@ def critical_point(a=CS_A, b=CS_B, c=CS_C, k=CS_K):
     return r, t, p(r, t)
 
 
-def _spinodals(T):
+def _spinodals(T, kind="cs"):
     """Densities where dP/drho = 0 (the van-der-Waals loop ends), T < 1."""
-    rs = np.linspace(1e-3, 1 / CS_B - 1e-3, 20001)
-    d = dpdrho(rs, T)
+    b = _CONST[kind][1]
+    rs = np.linspace(1e-3, 1 / b - 1e-3, 20001)
+    d = dpdrho(rs, T, kind)
     idx = np.where(np.sign(d[:-1]) != np.sign(d[1:]))[0]
-    roots = [optimize.brentq(lambda r: dpdrho(r, T), rs[i], rs[i + 1], xtol=1e-15) for i in idx]
+    roots = [optimize.brentq(lambda r: dpdrho(r, T, kind), rs[i], rs[i + 1], xtol=1e-15)
+             for i in idx]
     if len(roots) < 2:
         raise ValueError(f"no two-phase region at T={T}")
     return roots[0], roots[1]
 
 
-def maxwell(T):
+def maxwell(T, kind="cs"):
     """Maxwell coexistence (rho_g, rho_l) at reduced temperature T.
 
     Unknown p0 with P(rho_g) = P(rho_l) = p0 and the equal-area condition of
     Eq. (MLVDR), int_{rho_g}^{rho_l} (p0 - P) drho / rho^2 = 0.
     """
-    s1, s2 = _spinodals(T)
-    pmin = eos_pressure(s2, T)
-    pmax = eos_pressure(s1, T)
+    s1, s2 = _spinodals(T, kind)
+    pmin = eos_pressure(s2, T, kind=kind)
+    pmax = eos_pressure(s1, T, kind=kind)
+    b = _CONST[kind][1]
 
     def roots(p0):
-        rg = optimize.brentq(lambda r: eos_pressure(r, T) - p0, 1e-12, s1, xtol=1e-15)
-        rl = optimize.brentq(lambda r: eos_pressure(r, T) - p0, s2, 1 / CS_B - 1e-9, xtol=1e-15)
+        rg = optimize.brentq(lambda r: eos_pressure(r, T, kind=kind) - p0, 1e-12, s1, xtol=1e-15)
+        rl = optimize.brentq(lambda r: eos_pressure(r, T, kind=kind) - p0, s2, 1 / b - 1e-9,
+                             xtol=1e-15)
         return rg, rl
 
     def area(p0):
         rg, rl = roots(p0)
-        val, _ = integrate.quad(lambda r: (p0 - eos_pressure(r, T)) / r**2, rg, rl,
+        val, _ = integrate.quad(lambda r: (p0 - eos_pressure(r, T, kind=kind)) / r**2, rg, rl,
                                 epsabs=1e-15, epsrel=1e-13, limit=400)
         return val
 
@@ -104,25 +118,27 @@ def maxwell(T):
     return roots(p0)
 
 
-def pgldr(T, eps, G=-1.0):
+def pgldr(T, eps, G=-1.0, kind="cs"):
     """Coexistence (rho_g, rho_l) of the pseudopotential method, Eq. (PGLDR):
     int_{rho_g}^{rho_l} (p0 - c_s^2 rho - G psi^2) psidot / psi^(1+eps) drho = 0,
     with p0 = c_s^2 rho + G psi(rho)^2 at both ends (Eqs. BPLP, BPVP).  Since
     c_s^2 rho + G psi^2 = P_EOS by Eq. (DED), the bulk condition is
     P(rho_g) = P(rho_l) = p0.  psidot comes from 2 psi psidot = (P' - c_s^2)/G."""
-    s1, s2 = _spinodals(T)
-    pmin = eos_pressure(s2, T)
-    pmax = eos_pressure(s1, T)
+    s1, s2 = _spinodals(T, kind)
+    pmin = eos_pressure(s2, T, kind=kind)
+    pmax = eos_pressure(s1, T, kind=kind)
+    b = _CONST[kind][1]
 
     def roots(p0):
-        rg = optimize.brentq(lambda r: eos_pressure(r, T) - p0, 1e-12, s1, xtol=1e-15)
-        rl = optimize.brentq(lambda r: eos_pressure(r, T) - p0, s2, 1 / CS_B - 1e-9, xtol=1e-15)
+        rg = optimize.brentq(lambda r: eos_pressure(r, T, kind=kind) - p0, 1e-12, s1, xtol=1e-15)
+        rl = optimize.brentq(lambda r: eos_pressure(r, T, kind=kind) - p0, s2, 1 / b - 1e-9,
+                             xtol=1e-15)
         return rg, rl
 
     def integrand(r, p0):
-        ps = psi(r, T, G)
+        ps = psi(r, T, G, kind)
         # psidot from 2 psi psidot = (P' - c_s^2)/G
-        psidot = (dpdrho(r, T) - CS2) / (2 * G * ps)
+        psidot = (dpdrho(r, T, kind) - CS2) / (2 * G * ps)
         return (p0 - CS2 * r - G * ps**2) * psidot / ps ** (1 + eps)
 
     def area(p0):

@@ -36,6 +36,8 @@ LBM_EOS_DF = 1
 LBM_EOS_F32 = 2
 LBM_COLL_BGK = 0
 LBM_COLL_MRT = 1
+LBM_EOS_KIND_CS = 0
+LBM_EOS_KIND_VDW = 1
 LBM_KERNEL_AUTO = 0
 LBM_KERNEL_PLAIN = 1
 LBM_KERNEL_TMA = 2
@@ -55,7 +57,7 @@ class LatticeDesc(ctypes.Structure):
                 ("rho0", ctypes.c_double),
                 ("storage", ctypes.c_int32), ("eos_precision", ctypes.c_int32),
                 ("m2_trace_variant", ctypes.c_int32), ("collision", ctypes.c_int32),
-                ("mrt_rates", ctypes.c_double * 9)]
+                ("mrt_rates", ctypes.c_double * 9), ("eos_kind", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -81,7 +83,8 @@ class ServerOpts(ctypes.Structure):
                 ("kernel_variant", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
                 ("sites_per_thread", ctypes.c_int32), ("with_velocity", ctypes.c_int32),
-                ("max_width", ctypes.c_int32), ("chunk_ms", ctypes.c_double)]
+                ("max_width", ctypes.c_int32), ("chunk_ms", ctypes.c_double),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
 
 
 class ServerStats(ctypes.Structure):
@@ -142,6 +145,9 @@ SIGNATURES = {
     "lbm_selfcheck_arith": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.c_int64,
                                            ctypes.POINTER(ctypes.c_float),
                                            ctypes.POINTER(ctypes.c_float)]),
+    "lbm_selfcheck_psi": (ctypes.c_int, [ctypes.POINTER(LatticeDesc), ctypes.POINTER(ctypes.c_float),
+                                         ctypes.c_int64, ctypes.POINTER(ctypes.c_float),
+                                         ctypes.POINTER(ctypes.c_double)]),
     "lbm_mass_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
                                         ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_server_opts_default": (None, [ctypes.POINTER(ServerOpts)]),
@@ -238,8 +244,13 @@ class Handle:
 
 
 def lbm_desc_default(nx: int, ny: int, **kw) -> LatticeDesc:
+    """lbm_desc_default, then the given fields; eos_kind=LBM_EOS_KIND_VDW
+    also sets the reduced van der Waals constants a, b, c (3, 1/3, 8/3)
+    unless they are given too."""
     d = LatticeDesc()
     load().lbm_desc_default(ctypes.byref(d), int(nx), int(ny))
+    if kw.get("eos_kind") == LBM_EOS_KIND_VDW:
+        d.eos_a, d.eos_b, d.eos_c = 3.0, 1.0 / 3.0, 8.0 / 3.0
     for k, v in kw.items():
         if k == "mrt_rates":
             for i in range(9):
@@ -253,9 +264,11 @@ def lbm_desc_default(nx: int, ny: int, **kw) -> LatticeDesc:
 
 def lbm_create(descs, tile=None, grid_ctas=0, schedule=LBM_SCHED_AUTO, graph_steps=0,
                stream=None, device=None, kernel_variant=LBM_KERNEL_AUTO,
-               sites_per_thread=0) -> Handle:
+               sites_per_thread=0, allocator=None) -> Handle:
     """Create a handle over one descriptor or a list of them.  ``tile`` =
-    (tile_x, tile_y) fixes both passes' tiles, with ``sites_per_thread``."""
+    (tile_x, tile_y) fixes both passes' tiles, with ``sites_per_thread``.
+    ``allocator``: an object with ctypes callbacks ``alloc`` and ``free``
+    (default: torch's caching allocator)."""
     import torch
 
     if isinstance(descs, LatticeDesc):
@@ -265,7 +278,7 @@ def lbm_create(descs, tile=None, grid_ctas=0, schedule=LBM_SCHED_AUTO, graph_ste
     dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
     if stream is None:
         stream = torch.cuda.Stream(device=dev)
-    alloc = _TorchAllocator(dev)
+    alloc = allocator if allocator is not None else _TorchAllocator(dev)
     o = RuntimeOpts()
     o.alloc, o.free, o.alloc_ctx = alloc.alloc, alloc.free, None
     o.stream = stream.cuda_stream
@@ -391,6 +404,20 @@ def lbm_inject_copy_timeout(h: Handle, tile: int) -> None:
     _check(load().lbm_inject_copy_timeout(h.ptr, int(tile)), "lbm_inject_copy_timeout", h)
 
 
+def lbm_selfcheck_psi(desc: LatticeDesc, rho) -> tuple[np.ndarray, np.ndarray]:
+    """(psi, radicand) of the step kernels for the FP32 densities ``rho`` with
+    the constants of ``desc`` (radicand: float-float arithmetic only)."""
+    v = np.ascontiguousarray(rho, dtype=np.float32).ravel()
+    psi = np.empty_like(v)
+    rad = np.empty(v.size, dtype=np.float64)
+    fp = ctypes.POINTER(ctypes.c_float)
+    _check(load().lbm_selfcheck_psi(ctypes.byref(desc), v.ctypes.data_as(fp),
+                                    ctypes.c_int64(v.size), psi.ctypes.data_as(fp),
+                                    rad.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           "lbm_selfcheck_psi")
+    return psi, rad
+
+
 def lbm_selfcheck_arith(x) -> tuple[np.ndarray, np.ndarray]:
     """The step kernels' 1/x and sqrt(x) for float32 values x (GPU)."""
     v = np.ascontiguousarray(x, dtype=np.float32).ravel()
@@ -435,11 +462,22 @@ def lbm_server_opts_default(**kw) -> ServerOpts:
     return o
 
 
-def lbm_server_create(opts: ServerOpts | None = None) -> Server:
+def lbm_server_create(opts: ServerOpts | None = None, device=None) -> Server:
+    """A server whose device memory comes from torch's caching allocator,
+    unless ``opts`` already name an allocator."""
+    import torch
+
+    o = opts if opts is not None else lbm_server_opts_default()
+    alloc = None
+    if not o.alloc:
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        alloc = _TorchAllocator(dev)
+        o.alloc, o.free, o.alloc_ctx = alloc.alloc, alloc.free, None
     out = ctypes.c_void_p()
-    _check(load().lbm_server_create(ctypes.byref(opts) if opts is not None else None,
-                                    ctypes.byref(out)), "lbm_server_create")
-    return Server(out)
+    _check(load().lbm_server_create(ctypes.byref(o), ctypes.byref(out)), "lbm_server_create")
+    srv = Server(out)
+    srv.alloc = alloc  # keeps the callbacks alive as long as the server
+    return srv
 
 
 def lbm_submit(s: Server, desc: LatticeDesc, rho, nsteps: int) -> int:

@@ -91,13 +91,16 @@ struct LatDev {
     float ga9, gd9;     // 9 guo w = guo, guo/4
     float rho0;         // deviation reference (0 for plain FP32 storage)
     int32_t m2_variant; // 0: direct trace; 1: 2 c_s^2 (M0 - psi)
+    int32_t eos_kind;   // 0: Carnahan-Starling, Eq. (CSEOS); 1: van der Waals
     int32_t lattice;    // index for the status word
     int32_t row0;       // row of the arena's row space where this lattice's ghost
                         // row -GY starts (off_f[0] = row0 * pitch), or -1
     // psi(rho)^2 = (P_EOS - c_s^2 rho)/G = rho (e1 q(rho) - e2 rho - e3),
-    // q = (1 + eta + eta^2 - eta^3)/(1 - eta)^3, eta = b rho      Eqs. (DED), (CSEOS)
+    // eta = b rho, q = (1 + eta + eta^2 - eta^3)/(1 - eta)^3 (Carnahan-Starling,
+    // Eq. CSEOS) or q = 1/(1 - eta) (van der Waals)               Eq. (DED)
     double eb, e1, e2, e3;
-    df2 fb, f2, fc0, fC1;  // b, e2, c0 = e1 - e3, C1 = 2 b e1 as float-float pairs
+    df2 fb, f2, fc0, fC1;  // b, e2, c0 = e1 - e3, C1 (2 b e1; van der Waals b e1)
+                           // as float-float pairs
     float sb, s1, s2, s3;  // b, e1, e2, e3 as floats
     float zero;            // 0, as a value the compiler cannot see (Eos<EOS_DF>)
     // MRT relaxation rates (Eq. RelaxationMatrix), used by the MRT kernels
@@ -362,6 +365,9 @@ __device__ __forceinline__ V vsqrt(V a) {
 // one has eta r = r - 1 and (2 - eta) r = 1 + r, so q = 1 - 2r + 2r^3 =
 // 1 + 2 eta r^2 (1 + r) exactly, and
 //   psi^2 / rho = c0 + rho (C1 r^2 (1 + r) - e2),   c0 = e1 - e3,  C1 = 2 b e1.
+// The van der Waals equation behind the same psi (eos_kind 1) has q = r =
+// 1 + eta r, so psi^2 / rho = c0 + rho (C1 r - e2) with C1 = b e1: the same
+// sums with r in place of r^2 (1 + r).
 // For the Carnahan-Starling constants at 0.55 <= T_r <= 1 and rho <= 3.6 no sum
 // here cancels by more than a factor of about 8, and the float-float version
 // (below) keeps about 43 significant bits of the radicand.
@@ -400,7 +406,7 @@ struct Eos<EOS_F64> {
             const double r = (double)Lanes<V>::get(rho, k);
             const double sd = fma(-L.eb, r, 1.0);
             const double rr = 1.0 / sd;
-            const double q = fma(2.0 * rr, rr * rr, fma(-2.0, rr, 1.0));
+            const double q = L.eos_kind ? rr : fma(2.0 * rr, rr * rr, fma(-2.0, rr, 1.0));
             const double a = r * fma(L.e1, q, -fma(L.e2, r, L.e3));
             Lanes<V>::put(s, k, sd > 0.0 ? 1.f : -1.f);
             Lanes<V>::put(arg, k, (float)a);
@@ -419,9 +425,10 @@ struct Eos<EOS_F64> {
 // but it cannot fuse an FMA.
 template <>
 struct Eos<EOS_DF> {
+    // psi^2 = rho (hh + hl) before its one rounding to FP32, and
+    // sh = 1 - b rho (rounded), for psi() and for the self-check of the radicand
     template <class V>
-    static __device__ __forceinline__ V psi(const LatDev& L, V rho, uint32_t* status,
-                                            unsigned live = ~0u) {
+    static __device__ __forceinline__ void radicand(const LatDev& L, V rho, V& sh, V& hh, V& hl) {
         using Ln = Lanes<V>;
         const V one = Ln::set(1.f), mone = Ln::set(-1.f), z0 = Ln::set(L.zero);
         // b rho = p - en
@@ -429,7 +436,7 @@ struct Eos<EOS_DF> {
         V en = vfma(Ln::set(-L.fb.hi), rho, p);
         en = vfma(Ln::set(-L.fb.lo), rho, en);
         // s = 1 - b rho = sh + sl  (FastTwoSum, 1 > b rho)
-        const V sh = vsub(one, p);
+        sh = vsub(one, p);
         const V sl = vadd(vsub(vsub(one, sh), p), en);
         // r = 1/s = q - rl  (q the rounded 1/sh, one Newton step)
         const V q = vrcp(sh);
@@ -439,15 +446,22 @@ struct Eos<EOS_DF> {
         // 1 + r = oh + ol  (FastTwoSum, q >= 1)
         const V oh = vadd(q, one);
         const V ol = vsub(vadd(vsub(q, oh), one), rl);
-        // r^2 = r2h + r2l
-        const V nq = vmul(q, mone);
-        const V r2h = vmul(q, q), nr2h = vmul(nq, q);
-        const V r2l = vfma(vmul(q, Ln::set(-2.f)), rl, vfma(q, q, nr2h));
-        // A = r^2 (1 + r) = Ah + Ae
-        const V Ah = vmul(r2h, oh);
-        V Ae = vfma(r2h, oh, vmul(nr2h, oh));
-        Ae = vfma(r2h, ol, Ae);
-        Ae = vfma(r2l, oh, Ae);
+        V Ah, Ae;
+        if (L.eos_kind) {
+            // van der Waals: A = r = q - rl
+            Ah = q;
+            Ae = vmul(rl, mone);
+        } else {
+            // r^2 = r2h + r2l
+            const V nq = vmul(q, mone);
+            const V r2h = vmul(q, q), nr2h = vmul(nq, q);
+            const V r2l = vfma(vmul(q, Ln::set(-2.f)), rl, vfma(q, q, nr2h));
+            // A = r^2 (1 + r) = Ah + Ae
+            Ah = vmul(r2h, oh);
+            Ae = vfma(r2h, oh, vmul(nr2h, oh));
+            Ae = vfma(r2h, ol, Ae);
+            Ae = vfma(r2l, oh, Ae);
+        }
         // C1 A = Bh - nBl
         const V Bh = vfma(Ln::set(L.fC1.hi), Ah, z0);
         V nBl = vfma(Ln::set(-L.fC1.hi), Ah, Bh);
@@ -463,10 +477,25 @@ struct Eos<EOS_DF> {
         const V wh = vfma(vh, rho, z0);
         V we = vfma(vh, rho, vmul(vh, vmul(rho, mone)));
         we = vfma(vl, rho, we);
-        // c0 + w = hh + hl  (FastTwoSum, |c0| >= |w| wherever psi is defined)
+        // c0 + w = hh + hl: FastTwoSum for Carnahan-Starling, whose c0 has at
+        // least the exponent of w wherever psi is defined; TwoSum for van der
+        // Waals, whose w outgrows c0 as b rho -> 1
         const V c0h = Ln::set(L.fc0.hi);
-        const V hh = vadd(c0h, wh);
-        const V hl = vadd(vadd(vsub(c0h, hh), wh), vadd(Ln::set(L.fc0.lo), we));
+        hh = vadd(c0h, wh);
+        V e;
+        if (L.eos_kind) {
+            const V bw = vsub(hh, c0h);
+            e = vadd(vsub(c0h, vsub(hh, bw)), vsub(wh, bw));
+        } else {
+            e = vadd(vsub(c0h, hh), wh);
+        }
+        hl = vadd(e, vadd(Ln::set(L.fc0.lo), we));
+    }
+    template <class V>
+    static __device__ __forceinline__ V psi(const LatDev& L, V rho, uint32_t* status,
+                                            unsigned live = ~0u) {
+        V sh, hh, hl;
+        radicand(L, rho, sh, hh, hl);
         return psi_finish(L, rho, sh, vfma(rho, hh, vmul(rho, hl)), status, live);
     }
 };
@@ -481,7 +510,7 @@ struct Eos<EOS_F32> {
         const V one = Ln::set(1.f);
         const V s = vfma(Ln::set(-L.sb), rho, one);
         const V rr = vrcp(s);
-        const V q = vfma(vadd(rr, rr), vmul(rr, rr), vfma(Ln::set(-2.f), rr, one));
+        const V q = L.eos_kind ? rr : vfma(vadd(rr, rr), vmul(rr, rr), vfma(Ln::set(-2.f), rr, one));
         const V inner = vfma(Ln::set(L.s1), q, vfma(Ln::set(-L.s2), rho, Ln::set(-L.s3)));
         return psi_finish(L, rho, s, vmul(rho, inner), status, live);
     }

@@ -505,6 +505,51 @@ __global__ void k_arith_check(const float* x, int64_t n, float* rcp, float* sq,
     }
 }
 
+// ------------------------------------------------------------------ EOS check
+// The step's psi (Eqs. DED and CSEOS, or van der Waals) of n given densities
+// with the constants of lattice L: paired lanes (two values per thread, as
+// the kernels run them) to psi, the scalar lane on each value compared
+// bitwise (a mismatch sets bit 0 of *flags); for the float-float arithmetic
+// also the radicand rho (hh + hl) before its rounding to FP32, in FP64
+// (NaN for the other arithmetics).
+template <int EOSP>
+__global__ void k_eos_check(LatDev L, const float* rho, int64_t n, float* psi, double* rad,
+                            uint32_t* flags) {
+    const int64_t i = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (i >= n) return;
+    const bool two = i + 1 < n;
+    const float2 r2 = make_float2(rho[i], two ? rho[i + 1] : rho[i]);
+    uint32_t* st = flags + 1;  // numeric fault bits land here, not in a handle
+    const float2 p2 = Eos<EOSP>::psi(L, r2, st);
+    const float p0 = Eos<EOSP>::psi(L, r2.x, st), p1 = Eos<EOSP>::psi(L, r2.y, st);
+    if (__float_as_uint(p0) != __float_as_uint(p2.x) || (two && __float_as_uint(p1) != __float_as_uint(p2.y)))
+        atomicOr(flags, 1u);
+    psi[i] = p2.x;
+    if (two) psi[i + 1] = p2.y;
+    double r0 = __longlong_as_double(0x7ff8000000000000LL), r1 = r0;
+    if (EOSP == EOS_DF) {
+        float2 sh, hh, hl;
+        Eos<EOS_DF>::radicand(L, r2, sh, hh, hl);
+        r0 = (double)r2.x * (double)hh.x + (double)r2.x * (double)hl.x;
+        r1 = (double)r2.y * (double)hh.y + (double)r2.y * (double)hl.y;
+    }
+    rad[i] = r0;
+    if (two) rad[i + 1] = r1;
+}
+
+cudaError_t launch_eos_check(int eos, const LatDev& L, const float* rho, int64_t n, float* psi,
+                             double* rad, uint32_t* flags, cudaStream_t st) {
+    const int64_t pairs = (n + 1) / 2;
+    const unsigned g = (unsigned)((pairs + 255) / 256);
+    switch (eos) {
+        case EOS_F64: k_eos_check<EOS_F64><<<g, 256, 0, st>>>(L, rho, n, psi, rad, flags); break;
+        case EOS_DF: k_eos_check<EOS_DF><<<g, 256, 0, st>>>(L, rho, n, psi, rad, flags); break;
+        case EOS_F32: k_eos_check<EOS_F32><<<g, 256, 0, st>>>(L, rho, n, psi, rad, flags); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 // ================================================================ launchers
 namespace {
 template <class S, int SPT>

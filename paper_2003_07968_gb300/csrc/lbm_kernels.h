@@ -22,6 +22,11 @@ cudaError_t launch_moments(int storage_f16, const LatDev& L, const void* pop, in
 // (partials: at least n_partials doubles of scratch).
 cudaError_t launch_scan(const double* v, int64_t n, double* partials, int n_partials, double* out,
                         cudaStream_t st);
+// The step's psi of n device densities with lattice L's constants, the
+// float-float radicand (FP64; NaN for other arithmetics), lane check in flags[0]
+// (flags: 2 words, zeroed by the caller).
+cudaError_t launch_eos_check(int eos, const LatDev& L, const float* rho, int64_t n, float* psi,
+                             double* rad, uint32_t* flags, cudaStream_t st);
 cudaError_t launch_arith_check(const float* x, int64_t n, float* rcp, float* sq,
                                uint32_t* mismatch, cudaStream_t st);
 cudaError_t launch_mass(int storage_f16, const LatDev& L, const void* pop, int parity,

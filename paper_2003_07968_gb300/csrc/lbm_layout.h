@@ -64,6 +64,7 @@ inline LatDev lat_layout(const lbm_lattice_desc& d, int index) {
     }
     L.rho0 = (d.storage == LBM_STORE_F32 || d.rho0 < 0.0) ? 0.f : (float)d.rho0;
     L.m2_variant = d.m2_trace_variant;
+    L.eos_kind = d.eos_kind;
     L.lattice = index;
     L.row0 = -1;
     // psi^2 = rho (e1 q - e2 rho - e3): e1 = k c T / Ge, e2 = k a / Ge, e3 = 1/(3 Ge)
@@ -74,7 +75,7 @@ inline LatDev lat_layout(const lbm_lattice_desc& d, int index) {
     split_df(L.eb, L.fb);
     split_df(L.e2, L.f2);
     split_df(L.e1 - L.e3, L.fc0);      // psi^2/rho = c0 + rho (C1 r^2 (1 + r) - e2)
-    split_df(2.0 * L.eb * L.e1, L.fC1);
+    split_df((d.eos_kind == LBM_EOS_KIND_VDW ? 1.0 : 2.0) * L.eb * L.e1, L.fC1);
     L.sb = (float)L.eb;
     L.s1 = (float)L.e1;
     L.s2 = (float)L.e2;
@@ -105,6 +106,8 @@ inline int validate_desc(const lbm_lattice_desc& d, std::string& why) {
         return why = "m2_trace_variant must be 0 or 1", LBM_ERR_ARG;
     if (d.collision != LBM_COLL_BGK && d.collision != LBM_COLL_MRT)
         return why = "unknown collision", LBM_ERR_ARG;
+    if (d.eos_kind != LBM_EOS_KIND_CS && d.eos_kind != LBM_EOS_KIND_VDW)
+        return why = "unknown eos_kind", LBM_ERR_ARG;
     if (d.collision == LBM_COLL_MRT)
         for (int i = 0; i < 9; ++i)
             if (!(d.mrt_rates[i] > 0.0 && d.mrt_rates[i] < 2.0))

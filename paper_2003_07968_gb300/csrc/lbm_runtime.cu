@@ -1234,6 +1234,39 @@ int lbm_selfcheck_arith(const float* x, int64_t n, float* rcp, float* sq) {
     return guarded([&] { return lbm_selfcheck_arith_body(x, n, rcp, sq); });
 }
 
+static int lbm_selfcheck_psi_body(const lbm_lattice_desc* d, const float* rho, int64_t n,
+                                  float* psi, double* radicand) {
+    if (!d || !rho || !psi || !radicand || n < 1 || n > ((int64_t)1 << 24)) return LBM_ERR_ARG;
+    std::string why;
+    if (validate_desc(*d, why) != LBM_OK) return LBM_ERR_ARG;
+    const LatDev L = lat_layout(*d, 0);
+    const size_t fb = (size_t)n * sizeof(float), db = (size_t)n * sizeof(double);
+    char* buf = nullptr;
+    if (cudaMalloc(&buf, 2 * fb + db + 2 * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_OOM;
+    }
+    float* dr = reinterpret_cast<float*>(buf);
+    float* dp = dr + n;
+    double* dq = reinterpret_cast<double*>(buf + 2 * fb);  // 2 fb is a multiple of 8
+    uint32_t* flags = reinterpret_cast<uint32_t*>(buf + 2 * fb + db);
+    uint32_t fl[2] = {0, 0};
+    cudaError_t e = cudaMemcpy(dr, rho, fb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(flags, 0, 2 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = launch_eos_check(d->eos_precision, L, dr, n, dp, dq, flags, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(psi, dp, fb, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(radicand, dq, db, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(fl, flags, sizeof fl, cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    return fl[0] ? LBM_ERR_STATE : LBM_OK;
+}
+
+int lbm_selfcheck_psi(const lbm_lattice_desc* d, const float* rho, int64_t n, float* psi,
+                      double* radicand) {
+    return guarded([&] { return lbm_selfcheck_psi_body(d, rho, n, psi, radicand); });
+}
+
 static int lbm_selfcheck_body(char* report, int32_t report_len) {
     std::string msg;
     const int shapes[][2] = {{2, 2},   {3, 5},   {4, 4},    {7, 5},   {31, 33}, {32, 32},

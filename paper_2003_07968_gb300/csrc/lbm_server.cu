@@ -214,15 +214,42 @@ struct lbm_server {
 
 namespace {
 
+// Device memory of the server: from the caller's allocator when opts give
+// one (it must return 256-byte aligned memory), else cudaMalloc.
+void* srv_alloc(lbm_server* S, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (S->o.alloc) {
+        p = S->o.alloc(bytes, S->o.alloc_ctx);
+        if (p && (reinterpret_cast<uintptr_t>(p) & 255u)) {
+            S->o.free(p, bytes, S->o.alloc_ctx);
+            p = nullptr;
+        }
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void srv_free(lbm_server* S, void* p, size_t bytes) {
+    if (!p) return;
+    if (bytes == 0) bytes = 256;
+    if (S->o.alloc)
+        S->o.free(p, bytes, S->o.alloc_ctx);
+    else
+        cudaFree(p);
+}
+
 void free_server(lbm_server* S) {
+    const size_t nmax = (size_t)S->o.max_request_sites, nres = (size_t)S->o.max_resident;
     for (auto& T : S->set) {
-        for (auto& t : T.tiles)
-            if (t) cudaFree(t);
+        for (int k = 0; k < 2; ++k) srv_free(S, T.tiles[k], T.cap[k]);
         for (auto& t : T.tiles_h)
             if (t) cudaFreeHost(t);
-        if (T.lat) cudaFree(T.lat);
-        if (T.quota) cudaFree(T.quota);
-        if (T.status) cudaFree(T.status);
+        srv_free(S, T.lat, nres * sizeof(LatDev));
+        srv_free(S, T.quota, nres * sizeof(int));
+        srv_free(S, T.status, nres * sizeof(uint32_t));
         if (T.lat_h) cudaFreeHost(T.lat_h);
         if (T.quota_h) cudaFreeHost(T.quota_h);
     }
@@ -233,9 +260,9 @@ void free_server(lbm_server* S) {
     for (auto& e : S->spare_events) cudaEventDestroy(e);
     for (auto& e : S->side_done)
         if (e) cudaEventDestroy(e);
-    if (S->outbuf) cudaFree(S->outbuf);
-    if (S->staging) cudaFree(S->staging);
-    if (S->arena) cudaFree(S->arena);
+    srv_free(S, S->outbuf, 3 * nmax * sizeof(double));
+    srv_free(S, S->staging, S->up_cap * sizeof(double));
+    srv_free(S, S->arena, S->o.arena_bytes);
     for (auto& e : S->chunk_end)
         if (e) cudaEventDestroy(e);
     for (auto& e : S->chunk_begin)
@@ -324,13 +351,13 @@ cudaError_t rebuild(lbm_server* S, TableSet& T, std::vector<Request*>& res,
         if (bytes > T.cap[k]) {
             if (T.tiles[k]) {
                 cudaDeviceSynchronize();  // no kernel or copy-out still reads the old list
-                cudaFree(T.tiles[k]);
+                srv_free(S, T.tiles[k], T.cap[k]);
             }
             T.tiles[k] = nullptr;
             T.cap[k] = 0;
             const size_t cap = std::max<size_t>(bytes * 2, 4096);
-            e = cudaMalloc(&T.tiles[k], cap);
-            if (e != cudaSuccess) return e;
+            T.tiles[k] = static_cast<int4*>(srv_alloc(S, cap));
+            if (!T.tiles[k]) return cudaErrorMemoryAllocation;
             T.cap[k] = cap;
         }
         if (bytes > T.hcap[k]) {
@@ -857,7 +884,8 @@ static int lbm_server_create_body(const lbm_server_opts* opts, lbm_server** out)
          o.kernel_variant != LBM_KERNEL_TMA) ||
         (o.schedule != LBM_SCHED_AUTO && o.schedule != LBM_SCHED_TWO_PASS &&
          o.schedule != LBM_SCHED_FUSED) ||
-        (o.kernel_variant == LBM_KERNEL_TMA && o.schedule == LBM_SCHED_TWO_PASS))
+        (o.kernel_variant == LBM_KERNEL_TMA && o.schedule == LBM_SCHED_TWO_PASS) ||
+        (o.alloc == nullptr) != (o.free == nullptr))
         return LBM_ERR_ARG;
     lbm_server* S = new (std::nothrow) lbm_server();
     if (!S) return LBM_ERR_OOM;
@@ -936,18 +964,20 @@ static int lbm_server_create_body(const lbm_server_opts* opts, lbm_server** out)
     const size_t arena_sites = (size_t)S->row_cap * (size_t)o.max_width;
     const size_t slot_sites = std::min(S->up_cap, arena_sites) + (size_t)round_up((int64_t)nmax, 32);
     const size_t out_sites = slot_sites * (o.with_velocity ? 3 : 1);
-    bool ok = cudaMalloc(&S->arena, o.arena_bytes) == cudaSuccess &&
-              cudaMalloc(&S->staging, S->up_cap * sizeof(double)) == cudaSuccess &&
+    bool ok = (S->arena = srv_alloc(S, o.arena_bytes)) != nullptr &&
+              (S->staging = static_cast<double*>(srv_alloc(S, S->up_cap * sizeof(double)))) &&
               cudaMallocHost(&S->in_host, slot_sites * sizeof(double)) == cudaSuccess &&
               cudaMallocHost(&S->out_host, out_sites * sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&S->outbuf, 3 * nmax * sizeof(double)) == cudaSuccess &&
+              (S->outbuf = static_cast<double*>(srv_alloc(S, 3 * nmax * sizeof(double)))) &&
               cudaMallocHost(&S->down_host, 3 * nmax * sizeof(double)) == cudaSuccess &&
               cudaMallocHost(&S->status_host, 2 * (size_t)o.max_resident * sizeof(uint32_t)) ==
                   cudaSuccess;
     for (auto& T : S->set)
-        ok = ok && cudaMalloc(&T.lat, (size_t)o.max_resident * sizeof(LatDev)) == cudaSuccess &&
-             cudaMalloc(&T.quota, (size_t)o.max_resident * sizeof(int)) == cudaSuccess &&
-             cudaMalloc(&T.status, (size_t)o.max_resident * sizeof(uint32_t)) == cudaSuccess &&
+        ok = ok &&
+             (T.lat = static_cast<LatDev*>(srv_alloc(S, (size_t)o.max_resident * sizeof(LatDev)))) &&
+             (T.quota = static_cast<int*>(srv_alloc(S, (size_t)o.max_resident * sizeof(int)))) &&
+             (T.status =
+                  static_cast<uint32_t*>(srv_alloc(S, (size_t)o.max_resident * sizeof(uint32_t)))) &&
              cudaMallocHost(&T.lat_h, (size_t)o.max_resident * sizeof(LatDev)) == cudaSuccess &&
              cudaMallocHost(&T.quota_h, (size_t)o.max_resident * sizeof(int)) == cudaSuccess;
     if (!ok) {
