@@ -68,10 +68,10 @@ def test_vdw_flat_interface_matches_pgldr():
 
     T = 0.8
     mg, ml = theory.maxwell(T, kind="vdw")
-    rho = np.full((64, 2), mg)
-    rho[16:48, :] = ml
+    rho = np.full((96, 2), mg)
+    rho[24:72, :] = ml
     p = oracle.params(T=T, tau=1.0, eps=1.73, sigma=1.0, eos_kind="vdw")
     r, _, _ = _run_to_steady(p, rho, tol=1e-9)
     tg, tl = theory.pgldr(T, 1.73, kind="vdw")
-    assert abs(r[32, 0] - tl) / tl < 5e-4
+    assert abs(r[48, 0] - tl) / tl < 5e-4
     assert abs(r[0, 0] - tg) / tg < 1.5e-2
