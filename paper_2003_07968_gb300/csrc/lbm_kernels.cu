@@ -262,8 +262,8 @@ __global__ void __launch_bounds__(512) k_fused(StepArgs a) {
 // G_i(y) = w_i (rho(y + c_i) - rho(y)) - 9/32 e0: a subtraction and an FMA
 // per direction on the FP64 pipe (the slow one on GB300).
 template <class S>
-__global__ void k_init(LatDev L, void* pop, int parity, const double* rho, const double* ux,
-                       const double* uy) {
+__global__ void k_init(LatDev L, void* pop, int parity, const double* rho, const float* rho32,
+                       const double* ux, const double* uy) {
     using T = typename S::T;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -287,18 +287,20 @@ __global__ void k_init(LatDev L, void* pop, int parity, const double* rho, const
     const T R = S::cv((float)g0);
     const double e0 = (double)S::rt((float)g0) - g0;
     store_img(o, L.pitch, L.gx, x, y, nx, ny, R);
-    const double rc = rho[(int64_t)y * nx + x];
+    const float rc = rho32 ? rho32[(int64_t)y * nx + x] : 0.f;
     const float e0f = (float)e0;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         int sx = x + kCx[i], sy = y + kCy[i];
         sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
         sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-        // u = 0: the difference of the two densities in FP64, the rest (small
-        // numbers) in FP32
-        const float G = still ? fmaf(-0.28125f, e0f,
-                                     (float)w[i] * (float)(rho[(int64_t)sy * nx + sx] - rc))
-                              : (float)((geq(i, sx, sy) - (double)cref(i) * g0) - 0.28125 * e0);
+        // u = 0: w_i (rho(y + c_i) - rho(y)) from the FP32 copy of the field
+        // (the differences of the rounded values sum to zero over the lattice,
+        // so the stored mass stays that of the FP64 field), e0 in FP32
+        const float G =
+            still && rho32
+                ? fmaf(-0.28125f, e0f, (float)w[i] * (rho32[(int64_t)sy * nx + sx] - rc))
+                : (float)((geq(i, sx, sy) - (double)cref(i) * g0) - 0.28125 * e0);
         store_img(o + i * L.plane, L.pitch, L.gx, x, y, nx, ny, S::cv(G));
     }
 }
@@ -307,8 +309,10 @@ __global__ void k_init(LatDev L, void* pop, int parity, const double* rho, const
 // The smallest value of a device field and whether every value is finite
 // (lbm_init's check of the densities it was handed, on the staged copy):
 // each block writes its minimum, or NaN if it met a value that is not
-// finite; k_scan_final reduces the partials the same way into *out.
-__global__ void __launch_bounds__(256) k_scan_partial(const double* v, int64_t n, double* partials) {
+// finite; k_scan_final reduces the partials the same way into *out.  The
+// values are also written rounded to FP32 into v32 (k_init's copy).
+__global__ void __launch_bounds__(256) k_scan_partial(const double* v, int64_t n, double* partials,
+                                                      float* v32) {
     double m = HUGE_VAL;
     bool bad = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -316,6 +320,7 @@ __global__ void __launch_bounds__(256) k_scan_partial(const double* v, int64_t n
         const double x = v[i];
         bad |= !isfinite(x);
         m = fmin(m, x);
+        v32[i] = (float)x;
     }
     bad = __syncthreads_or(bad);
     for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_down_sync(0xffffffffu, m, o));
@@ -328,6 +333,14 @@ __global__ void __launch_bounds__(256) k_scan_partial(const double* v, int64_t n
         for (int k = 1; k < (int)(blockDim.x >> 5); ++k) b = fmin(b, red[k]);
         partials[blockIdx.x] = bad ? __longlong_as_double(0x7ff8000000000000LL) : b;
     }
+}
+
+// v rounded to FP32 (the copy k_init reads the neighbours' densities from,
+// for fields that are not scanned on the device).
+__global__ void k_to_f32(const double* v, int64_t n, float* v32) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        v32[i] = (float)v[i];
 }
 
 __global__ void k_scan_final(const double* partials, int n, double* out) {
@@ -374,14 +387,15 @@ __device__ __forceinline__ void signed_sum(const float v[N], const int w[N], flo
     }
 }
 
+// Rows y0 .. y1 - 1; the output pointers point at row y0 of their fields.
 template <class S>
 __global__ void k_moments(LatDev L, const void* pop, int parity, const float* psi_arena,
-                          double* rho_out, double* ux_out, double* uy_out) {
+                          double* rho_out, double* ux_out, double* uy_out, int y0, int y1) {
     using T = typename S::T;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int nx = L.nx, ny = L.ny;
-    if (x >= nx || y >= ny) return;
+    const int y = y0 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+    const int nx = L.nx;
+    if (x >= nx || y >= y1) return;
     const int pitch = L.pitch;
     const int64_t plane = L.plane;
     const T* f = reinterpret_cast<const T*>(pop) + L.off_f[parity] + (int64_t)(y + GY) * pitch +
@@ -410,7 +424,7 @@ __global__ void k_moments(LatDev L, const void* pop, int parity, const float* ps
     signed_sum<17>(v, ones, hi, lo);
     // rho = sum_i f_i (Eq. FD) plus the deviation reference, in FP64
     const double rho = ((double)hi + (double)lo) + (double)L.rho0;
-    const int64_t s = (int64_t)y * nx + x;
+    const int64_t s = (int64_t)(y - y0) * nx + x;
     if (rho_out) rho_out[s] = rho;
     if (!ux_out && !uy_out) return;  // density only: no force, psi not read
     float jxh, jxl, jyh, jyl;
@@ -677,24 +691,30 @@ cudaError_t launch_collide(int storage_f16, int mrt, int spt, const StepArgs& a,
 }
 
 cudaError_t launch_init(int storage_f16, const LatDev& L, void* pop, int parity,
-                        const double* rho, const double* ux, const double* uy,
+                        const double* rho, const float* rho32, const double* ux, const double* uy,
                         cudaStream_t st) {
     dim3 b(32, 8), g((L.nx + 31) / 32, (L.ny + 7) / 8);
     if (storage_f16)
-        k_init<StoreF16><<<g, b, 0, st>>>(L, pop, parity, rho, ux, uy);
+        k_init<StoreF16><<<g, b, 0, st>>>(L, pop, parity, rho, rho32, ux, uy);
     else
-        k_init<StoreF32><<<g, b, 0, st>>>(L, pop, parity, rho, ux, uy);
+        k_init<StoreF32><<<g, b, 0, st>>>(L, pop, parity, rho, rho32, ux, uy);
     return cudaGetLastError();
 }
 
 cudaError_t launch_moments(int storage_f16, const LatDev& L, const void* pop, int parity,
-                           const float* psi, double* rho, double* ux, double* uy,
+                           const float* psi, double* rho, double* ux, double* uy, int y0, int y1,
                            cudaStream_t st) {
-    dim3 b(32, 8), g((L.nx + 31) / 32, (L.ny + 7) / 8);
+    if (y1 <= y0) return cudaSuccess;
+    // rows y0 .. y1 - 1: the outputs' rows start at row y0 of the [ny][nx] fields
+    dim3 b(32, 8), g((L.nx + 31) / 32, (y1 - y0 + 7) / 8);
+    const int64_t off = (int64_t)y0 * L.nx;
+    double* r = rho ? rho + off : nullptr;
+    double* u = ux ? ux + off : nullptr;
+    double* v = uy ? uy + off : nullptr;
     if (storage_f16)
-        k_moments<StoreF16><<<g, b, 0, st>>>(L, pop, parity, psi, rho, ux, uy);
+        k_moments<StoreF16><<<g, b, 0, st>>>(L, pop, parity, psi, r, u, v, y0, y1);
     else
-        k_moments<StoreF32><<<g, b, 0, st>>>(L, pop, parity, psi, rho, ux, uy);
+        k_moments<StoreF32><<<g, b, 0, st>>>(L, pop, parity, psi, r, u, v, y0, y1);
     return cudaGetLastError();
 }
 
@@ -712,13 +732,19 @@ cudaError_t launch_mass(int storage_f16, const LatDev& L, const void* pop, int p
 }
 
 cudaError_t launch_scan(const double* v, int64_t n, double* partials, int n_partials, double* out,
-                        cudaStream_t st) {
+                        float* v32, cudaStream_t st) {
     const int64_t want = (n + 255) / 256;
     const int nb = (int)(want < n_partials ? want : n_partials);
-    k_scan_partial<<<nb, 256, 0, st>>>(v, n, partials);
+    k_scan_partial<<<nb, 256, 0, st>>>(v, n, partials, v32);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_scan_final<<<1, 32, 0, st>>>(partials, nb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const double* v, int64_t n, float* v32, cudaStream_t st) {
+    const int64_t want = (n + 255) / 256;
+    k_to_f32<<<(unsigned)(want < 4096 ? want : 4096), 256, 0, st>>>(v, n, v32);
     return cudaGetLastError();
 }
 

@@ -12,16 +12,22 @@ cudaError_t launch_psi(int storage_f16, int eos, int spt, const StepArgs& a, dim
                        cudaStream_t st);
 cudaError_t launch_collide(int storage_f16, int mrt, int spt, const StepArgs& a, dim3 g,
                            dim3 b, size_t smem, cudaStream_t st);
+// rho32: the field rounded to FP32 (launch_scan writes it), used for the
+// neighbours' densities when ux and uy are NULL.
 cudaError_t launch_init(int storage_f16, const LatDev& L, void* pop, int parity,
-                        const double* rho, const double* ux, const double* uy,
+                        const double* rho, const float* rho32, const double* ux, const double* uy,
                         cudaStream_t st);
+// rho, u of rows y0 .. y1 - 1 into [ny][nx] fields (any may be NULL).
 cudaError_t launch_moments(int storage_f16, const LatDev& L, const void* pop, int parity,
-                           const float* psi, double* rho, double* ux, double* uy,
+                           const float* psi, double* rho, double* ux, double* uy, int y0, int y1,
                            cudaStream_t st);
 // The smallest of n device values into *out, or NaN if any is not finite
-// (partials: at least n_partials doubles of scratch).
+// (partials: at least n_partials doubles of scratch); the values rounded to
+// FP32 into v32.
 cudaError_t launch_scan(const double* v, int64_t n, double* partials, int n_partials, double* out,
-                        cudaStream_t st);
+                        float* v32, cudaStream_t st);
+// v rounded to FP32 into v32 (n values).
+cudaError_t launch_to_f32(const double* v, int64_t n, float* v32, cudaStream_t st);
 // The step's psi of n device densities with lattice L's constants, the
 // float-float radicand (FP64; NaN for other arithmetics), lane check in flags[0]
 // (flags: 2 words, zeroed by the caller).

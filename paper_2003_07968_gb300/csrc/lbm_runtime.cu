@@ -85,8 +85,10 @@ struct lbm_handle {
     uint32_t* status = nullptr;
     Pass pass[2];
     double* partials = nullptr;  // mass partials + one result slot
-    double* staging = nullptr;   // FP64 field staging (rho, ux, uy)
+    double* staging = nullptr;   // FP64 field staging (rho, ux, uy), then rho in FP32
     size_t staging_elems = 0;
+    cudaStream_t side = nullptr;  // copies of lbm_moments results, beside the kernels
+    cudaEvent_t chunk_ev[5] = {};
     int64_t device_bytes = 0;
     // host side
     uint32_t* status_host = nullptr;  // pinned
@@ -384,10 +386,15 @@ int sync_status(lbm_handle* h) {
     return fault_code(h);
 }
 
+// Bytes of the staging buffer for fields of `elems` sites: three FP64 fields
+// and one FP32 copy of the density.
+size_t staging_bytes(size_t elems) { return elems * (3 * sizeof(double) + sizeof(float)); }
+float* staging32(lbm_handle* h) { return reinterpret_cast<float*>(h->staging + 3 * h->staging_elems); }
+
 int ensure_staging(lbm_handle* h, size_t elems) {
     if (elems <= h->staging_elems) return LBM_OK;
-    dev_free(h, h->staging, h->staging_elems * 3 * sizeof(double));
-    h->staging = (double*)dev_alloc(h, elems * 3 * sizeof(double));
+    dev_free(h, h->staging, staging_bytes(h->staging_elems));
+    h->staging = (double*)dev_alloc(h, staging_bytes(elems));
     if (!h->staging) {
         h->staging_elems = 0;
         return LBM_ERR_OOM;
@@ -412,8 +419,11 @@ void release(lbm_handle* h) {
     if (h->status_ev) cudaEventDestroy(h->status_ev);
     if (h->status_host) cudaFreeHost(h->status_host);
     if (h->scan_host) cudaFreeHost(h->scan_host);
-    dev_free(h, h->staging, h->staging_elems * 3 * sizeof(double));
+    dev_free(h, h->staging, staging_bytes(h->staging_elems));
     dev_free(h, h->partials, (kMassPartials + 1) * sizeof(double));
+    for (cudaEvent_t& e : h->chunk_ev)
+        if (e) cudaEventDestroy(e);
+    if (h->side) cudaStreamDestroy(h->side);
     for (auto& P : h->pass) dev_free(h, P.tiles, P.cap);
     dev_free(h, h->status, h->lat.size() * sizeof(uint32_t));
     dev_free(h, h->lat_dev, h->lat.size() * sizeof(LatDev));
@@ -797,8 +807,12 @@ static int lbm_create_body(const lbm_lattice_desc* descs, int32_t n, const lbm_r
     if (cudaMallocHost(&h->status_host, n * sizeof(uint32_t)) != cudaSuccess ||
         cudaMallocHost(&h->scan_host, sizeof(double)) != cudaSuccess)
         return fail(LBM_ERR_OOM);
-    if (cudaEventCreateWithFlags(&h->status_ev, cudaEventDisableTiming) != cudaSuccess)
+    if (cudaEventCreateWithFlags(&h->status_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess)
         return fail(LBM_ERR_CUDA);
+    for (cudaEvent_t& e : h->chunk_ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return fail(LBM_ERR_CUDA);
     if (cudaMemsetAsync(h->pop, 0, h->pop_bytes, h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->psi, 0, h->psi_bytes, h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->status, 0, n * sizeof(uint32_t), h->stream) != cudaSuccess ||
@@ -872,7 +886,7 @@ static int lbm_init_body(lbm_handle* h, int32_t lattice, const double* rho, cons
     if (ux) CK(h, cudaMemcpyAsync(dx, ux, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     if (uy) CK(h, cudaMemcpyAsync(dy, uy, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(h, launch_scan(dr, (int64_t)n, h->partials, kMassPartials, h->partials + kMassPartials,
-                      h->stream));
+                      staging32(h), h->stream));
     h->launches += 2;
     CK(h, cudaMemcpyAsync(h->scan_host, h->partials + kMassPartials, sizeof(double),
                           cudaMemcpyDeviceToHost, h->stream));
@@ -889,7 +903,8 @@ static int lbm_init_body(lbm_handle* h, int32_t lattice, const double* rho, cons
         CK(h, cudaMemcpyAsync(h->lat_dev + lattice, &L, sizeof(LatDev), cudaMemcpyHostToDevice,
                               h->stream));
     }
-    CK(h, launch_init(h->f16, L, h->pop, h->parity, dr, ux ? dx : nullptr, uy ? dy : nullptr,
+    CK(h, launch_init(h->f16, L, h->pop, h->parity, dr, staging32(h), ux ? dx : nullptr,
+                      uy ? dy : nullptr,
                       h->stream));
     h->launches += 1;
     CK(h, cudaMemsetAsync(h->status + lattice, 0, sizeof(uint32_t), h->stream));
@@ -975,15 +990,28 @@ static int lbm_moments_body(lbm_handle* h, int32_t lattice, double* rho, double*
             CK(h, launch_pass(h, 0, a, std::min(h->pass[0].grid, a.ntiles)));
             h->launches += 1;
         }
+    }
+    // The fields are computed in row chunks on the handle's stream; the side
+    // stream copies each finished chunk to the caller while the next chunk
+    // and the mass reduction run.  The handle's stream then waits for the
+    // copies, so nothing later reuses the staging buffer before they are done.
+    const int nchunk = (rho || ux || uy) ? (n >= ((size_t)1 << 22) ? 4 : 1) : 0;
+    for (int c = 0; c < nchunk; ++c) {
+        const int y0 = (int)((int64_t)L.ny * c / nchunk), y1 = (int)((int64_t)L.ny * (c + 1) / nchunk);
+        const size_t off = (size_t)y0 * L.nx, cnt = (size_t)(y1 - y0) * L.nx;
         double* dr = h->staging;
         double* dx = h->staging + h->staging_elems;
         double* dy = h->staging + 2 * h->staging_elems;
         CK(h, launch_moments(h->f16, L, h->pop, h->parity, h->psi, dr, (ux || uy) ? dx : nullptr,
-                             (ux || uy) ? dy : nullptr, h->stream));
+                             (ux || uy) ? dy : nullptr, y0, y1, h->stream));
         h->launches += 1;
+        CK(h, cudaEventRecord(h->chunk_ev[c], h->stream));
+        CK(h, cudaStreamWaitEvent(h->side, h->chunk_ev[c], 0));
+        const size_t b = cnt * sizeof(double);
+        if (rho) CK(h, cudaMemcpyAsync(rho + off, dr + off, b, cudaMemcpyDeviceToHost, h->side));
+        if (ux) CK(h, cudaMemcpyAsync(ux + off, dx + off, b, cudaMemcpyDeviceToHost, h->side));
+        if (uy) CK(h, cudaMemcpyAsync(uy + off, dy + off, b, cudaMemcpyDeviceToHost, h->side));
     }
-    // the mass reduction is queued before the large copies, so it does not
-    // wait for them
     if (mass) {
         CK(h, launch_mass(h->f16, L, h->pop, h->parity, h->partials, kMassPartials,
                           h->partials + kMassPartials, h->stream));
@@ -991,13 +1019,9 @@ static int lbm_moments_body(lbm_handle* h, int32_t lattice, double* rho, double*
         CK(h, cudaMemcpyAsync(mass, h->partials + kMassPartials, sizeof(double),
                               cudaMemcpyDeviceToHost, h->stream));
     }
-    if (rho || ux || uy) {
-        const double* dr = h->staging;
-        const double* dx = h->staging + h->staging_elems;
-        const double* dy = h->staging + 2 * h->staging_elems;
-        if (rho) CK(h, cudaMemcpyAsync(rho, dr, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-        if (ux) CK(h, cudaMemcpyAsync(ux, dx, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-        if (uy) CK(h, cudaMemcpyAsync(uy, dy, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (nchunk) {
+        CK(h, cudaEventRecord(h->chunk_ev[4], h->side));
+        CK(h, cudaStreamWaitEvent(h->stream, h->chunk_ev[4], 0));
     }
     return sync_status(h);
 }

@@ -190,6 +190,7 @@ struct lbm_server {
     CUtensorMap tmap[2]{};  // loads, stores
     size_t up_cap = 0;            // doubles of the device staging buffer
     double* staging = nullptr;    // rho of the requests admitted in one turn (device)
+    float* staging32 = nullptr;   // the same rounded to FP32, as lbm_init's init reads it
     double* in_host = nullptr;    // pinned slots of initial fields (in_alloc, doubles)
     double* out_host = nullptr;   // pinned slots of results (out_alloc, doubles)
     double* outbuf = nullptr;     // rho, ux, uy of one finished request (side stream)
@@ -262,6 +263,7 @@ void free_server(lbm_server* S) {
         if (e) cudaEventDestroy(e);
     srv_free(S, S->outbuf, 3 * nmax * sizeof(double));
     srv_free(S, S->staging, S->up_cap * sizeof(double));
+    srv_free(S, S->staging32, S->up_cap * sizeof(float));
     srv_free(S, S->arena, S->o.arena_bytes);
     for (auto& e : S->chunk_end)
         if (e) cudaEventDestroy(e);
@@ -409,7 +411,7 @@ cudaError_t enqueue_copy_out(lbm_server* S, const TableSet& T, const Request& R,
     double* dx = dr + S->o.max_request_sites;
     double* dy = dx + S->o.max_request_sites;
     e = launch_moments(S->f16, R.L, S->arena, par, S->psi_arena, dr, vel ? dx : nullptr,
-                       vel ? dy : nullptr, S->side);
+                       vel ? dy : nullptr, 0, R.L.ny, S->side);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(host, dr, n * sizeof(double), cudaMemcpyDeviceToHost, S->side);
     if (e == cudaSuccess && vel)
@@ -619,9 +621,14 @@ void worker_loop(lbm_server* S) {
                 R->L.off_f[0] = (int64_t)R->row_off * S->pitch;
                 R->L.off_f[1] = R->L.off_f[0] + 9 * S->plane;
                 R->L.off_psi = (int64_t)(R->psi_off / 4);
-                e = launch_init(S->f16, R->L, S->arena, S->parity, S->staging + R->stage_off,
-                                nullptr, nullptr, S->stream);
-                launches += 1;
+                // the same init arithmetic as lbm_init: neighbours' densities
+                // from an FP32 copy of the field
+                e = launch_to_f32(S->staging + R->stage_off, (int64_t)R->L.nx * R->L.ny,
+                                  S->staging32 + R->stage_off, S->stream);
+                if (e == cudaSuccess)
+                    e = launch_init(S->f16, R->L, S->arena, S->parity, S->staging + R->stage_off,
+                                    S->staging32 + R->stage_off, nullptr, nullptr, S->stream);
+                launches += 2;
                 res.push_back(R);
             }
             if (e == cudaSuccess) e = cudaEventRecord(S->init_done, S->stream);
@@ -966,6 +973,7 @@ static int lbm_server_create_body(const lbm_server_opts* opts, lbm_server** out)
     const size_t out_sites = slot_sites * (o.with_velocity ? 3 : 1);
     bool ok = (S->arena = srv_alloc(S, o.arena_bytes)) != nullptr &&
               (S->staging = static_cast<double*>(srv_alloc(S, S->up_cap * sizeof(double)))) &&
+              (S->staging32 = static_cast<float*>(srv_alloc(S, S->up_cap * sizeof(float)))) &&
               cudaMallocHost(&S->in_host, slot_sites * sizeof(double)) == cudaSuccess &&
               cudaMallocHost(&S->out_host, out_sites * sizeof(double)) == cudaSuccess &&
               (S->outbuf = static_cast<double*>(srv_alloc(S, 3 * nmax * sizeof(double)))) &&
