@@ -167,3 +167,12 @@ def test_config2_laplace_law_in_one_batch(P):
               f"{gamma / gpi:.3f}), intercept {icpt:.2e}")
         assert abs(gamma / gpi - 1) <= GAMMA_TOL[T], (T, gamma, gpi)
         assert abs(icpt) <= ICPT_TOL * max(p[1] for p in pts), (T, icpt)
+    # pin P8 as the survey states it: at T_r = 0.8 and R >= 40, the slope of
+    # Delta P = gamma / R (Eq. YLR, a line through the origin) within 5 % of
+    # the printed gamma_pi = 0.0148 (Sec. IV.B)
+    big = [p for p in fits[0.8] if p[0] >= 38.0]
+    x = np.array([1.0 / p[0] for p in big])
+    y = np.array([p[1] for p in big])
+    g8 = float(np.sum(x * y) / np.sum(x * x))
+    print(f"T_r 0.8, R >= 40: gamma {g8:.5f} ({g8 / 0.0148:.3f} of 0.0148)")
+    assert len(big) == 3 and abs(g8 / 0.0148 - 1) <= 0.05

@@ -401,37 +401,55 @@ def test_config2_laplace_quantities(P):
     assert abs(ra - rb) / rb <= 1e-3
 
 
-def test_config3_oscillation_period_vs_lamb(P):
-    # 1024 x 1024 ellipse 120/100 at T_r = 0.6, BGK tau = 0.8, 50000 steps: the
-    # period of the x-extremity follows Eq. (DOP) with the paper's Table
-    # PRCases gamma and rho_l, within 10 % (BGK damping and the finite
-    # interface width are not part of Lamb's result).
-    n, T = 1024, 0.6
-    rho = synth.ellipse(n, n, 120.0, 100.0, T)
-    rg, rl = synth.coexistence(T)
-    d = P.lbm_desc_default(n, n, T=T, tau=0.8)
-    h = P.lbm_create(d)
-    P.lbm_init(h, 0, rho)
-    ts, ext = [], []
-    for k in range(101):
-        if k:
-            P.lbm_step(h, 500)
-        r = P.lbm_moments(h, 0, u=False, mass=False)["rho"]
-        ray = r[n // 2, n // 2:]
-        rm = 0.5 * (rl + rg)
-        j = int(np.argmax(ray < rm))
-        ext.append((j - 1) + (ray[j - 1] - rm) / (ray[j - 1] - ray[j]))
-        ts.append(500 * k)
-    P.lbm_destroy(h)
-    ext = np.array(ext)
-    t = np.array(ts, dtype=float)
-    # first minimum, then the next maximum: one full period after t = 0
+def _first_period(ext, every):
+    """Period from the +x extremity sampled every `every` steps: the first
+    minimum, then the next maximum (one full period after t = 0), located
+    by a parabola through the seven samples around it."""
+    ext = np.asarray(ext, dtype=float)
+    t = every * np.arange(len(ext), dtype=float)
     k1 = int(np.argmin(ext[: len(ext) // 2 + 10]))
     k2 = k1 + int(np.argmax(ext[k1:]))
     a, b, _ = np.polyfit(t[k2 - 3:k2 + 4], ext[k2 - 3:k2 + 4], 2)
-    period = -b / (2 * a)
+    return -b / (2 * a)
+
+
+def test_config3_oscillation_period(P):
+    # 1024 x 1024 ellipse 120/100 at T_r = 0.6, BGK tau = 0.8, 50000 steps,
+    # the +x extremity sampled every 500 steps (Sec. IV.C): the period within
+    # 1e-3 of the FP64 oracle's (tests/golden/config3_period.json, written by
+    # make_config3_period.py), the sampled extremities within 0.02 sites of
+    # the oracle's, and the period within 10 % of Lamb's Eq. (DOP) with the
+    # paper's Table PRCases gamma and rho_l (BGK damping and the finite
+    # interface width are not part of Lamb's result)
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "config3_period.json")) as fh:
+        gold = json.load(fh)
+    n, T, every = gold["n"], gold["T"], gold["every"]
+    rho = synth.ellipse(n, n, 120.0, 100.0, T)
+    rg, rl = synth.coexistence(T)
+    d = P.lbm_desc_default(n, n, T=T, tau=gold["tau"])
+    h = P.lbm_create(d)
+    P.lbm_init(h, 0, rho)
+    ext = []
+    rm = 0.5 * (rl + rg)
+    for k in range(len(gold["extremity"])):
+        if k:
+            P.lbm_step(h, every)
+        r = P.lbm_moments(h, 0, u=False, mass=False)["rho"]
+        ray = r[n // 2, n // 2:]
+        j = int(np.argmax(ray < rm))
+        ext.append((j - 1) + (ray[j - 1] - rm) / (ray[j - 1] - ray[j]))
+    P.lbm_destroy(h)
+    period = _first_period(ext, every)
+    want = _first_period(gold["extremity"], every)
     ta = theory.lamb_period(0.0461, 3.1192, 120.0, 100.0)
-    print(f"oscillation period {period:.0f} steps, Lamb {ta:.0f}")
+    dev = float(np.max(np.abs(np.array(ext) - np.array(gold["extremity"]))))
+    print(f"oscillation period {period:.1f} steps (oracle {want:.1f}, Lamb {ta:.0f}); "
+          f"extremities within {dev:.2e} sites of the oracle's")
+    assert abs(period - want) / want <= 1e-3
+    assert dev <= 0.02
     assert abs(period - ta) / ta <= 0.10
 
 
