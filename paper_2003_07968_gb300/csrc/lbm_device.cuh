@@ -372,22 +372,43 @@ __device__ __forceinline__ V vsqrt(V a) {
 // here cancels by more than a factor of about 8, and the float-float version
 // (below) keeps about 43 significant bits of the radicand.
 // A lane is valid when rho > 0, b rho < 1 and the radicand is finite and
-// >= 0; an invalid lane gets psi = NaN and, if its bit in `live` is set,
-// raises status bit 1 of its lattice (lanes without a site are not live).
+// positive and normal (at least 2^-126); an invalid lane gets psi = NaN and, if its
+// bit in `live` is set, raises status bit 1 of its lattice (lanes without a
+// site are not live).
 enum { EOS_F64 = 0, EOS_DF = 1, EOS_F32 = 2 };
+
+// sqrt of the EOS radicand: vsqrt without its scaling of tiny arguments
+// (the same operations, so the same bits, for a >= 2^-100; down to 2^-126
+// the residual a - s^2 is exact in the fused multiply-add, so the root stays
+// within about 1 ulp).  A subnormal radicand (the approximation flushes it
+// to zero), zero or a negative one gives a root that is not finite, which
+// psi_finish reports as psi undefined.
+template <class V>
+__device__ __forceinline__ V vsqrt_eos(V a) {
+    using Ln = Lanes<V>;
+    V y;
+#pragma unroll
+    for (int k = 0; k < Ln::n; ++k) Ln::put(y, k, rsqrt_approx(Ln::get(a, k)));
+    const V s = vmul(a, y);
+    const V e = vfma(vmul(s, Ln::set(-1.f)), s, a);  // a - s^2
+    return vfma(vmul(y, Ln::set(0.5f)), e, s);
+}
 
 template <class V>
 __device__ __forceinline__ V psi_finish(const LatDev& L, V rho, V s, V arg, uint32_t* status,
                                         unsigned live) {
-    const V root = vsqrt(arg);
+    const V root = vsqrt_eos(arg);
     V psi;
+    unsigned bad = 0;
 #pragma unroll
     for (int k = 0; k < Lanes<V>::n; ++k) {
-        const float r = Lanes<V>::get(rho, k), a = Lanes<V>::get(arg, k);
-        const bool ok = (r > 0.f) && (Lanes<V>::get(s, k) > 0.f) && (a >= 0.f) && (a < INFINITY);
-        if (!ok && ((live >> k) & 1u)) atomicOr(status + L.lattice, 1u);
-        Lanes<V>::put(psi, k, ok ? Lanes<V>::get(root, k) : __int_as_float(0x7fc00000));
+        const float q = Lanes<V>::get(root, k);
+        const bool ok =
+            (Lanes<V>::get(rho, k) > 0.f) && (Lanes<V>::get(s, k) > 0.f) && (fabsf(q) < INFINITY);
+        bad |= (unsigned)!ok << k;
+        Lanes<V>::put(psi, k, ok ? q : __int_as_float(0x7fc00000));
     }
+    if (bad & live) atomicOr(status + L.lattice, 1u);
     return psi;
 }
 

@@ -204,8 +204,8 @@ __global__ void __launch_bounds__(kBlockF, 2)
         // store has read the stage and refills it at once, so loads run up to
         // STAGES - 1 tiles ahead of the consumers.
         int k = 0;
-        int tq[G::STAGES];  // tile held by each stage (tensor path)
-        int2 sq[G::STAGES];  // its store box origin (x, row), row -1: stored by the consumers
+        int tq[G::STAGES] = {};  // tile held by each stage (tensor path)
+        int2 sq[G::STAGES] = {};  // its store box origin (x, row), row -1: stored by the consumers
         bool alive = true;
         const int sz = 9 * (a.parity ^ 1);
         // store of the finished tile in stage s (lane 0), at the coordinates
@@ -300,7 +300,10 @@ __global__ void __launch_bounds__(kBlockF, 2)
 
     // ---------------------------------------------------------------- consumers
     const int tid = threadIdx.x;  // 0 .. kConsumers-1
-    const int tx = tid % TX, ty0 = tid / TX;
+    // a thread's SPT sites are consecutive rows of one column, ly0 .. ly0 +
+    // SPT - 1, so that their 3 x 3 windows of rest values and of psi overlap:
+    // (SPT + 2) x 3 loads each instead of 9 SPT
+    const int tx = tid % TX, ly0 = (tid / TX) * G::SPT;
     constexpr int nhalf = TX + TY + 2;  // half of the 2 (TX + TY) + 4 ring cells
     int k = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
@@ -327,17 +330,27 @@ __global__ void __launch_bounds__(kBlockF, 2)
         if (ok) {
             const T* st = reinterpret_cast<const T*>(smem + s * G::STAGEB);
             // own sites: pulled states into registers, rho, psi
+            // rest values of the (SPT + 2) x 3 window: rows ly0 - 1 .. ly0 + SPT,
+            // columns tx - 1 .. tx + 1 (the rest plane's value at (lx, ly) is
+            // G::rest(0, lx, ly))
+            float Rw[G::SPT + 2][3];
+#pragma unroll
+            for (int r = 0; r < G::SPT + 2; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    Rw[r][c] = S::lds(st + G::rest(0, tx + c - 1, ly0 + r - 1));
 #pragma unroll
             for (int j = 0; j < NV; ++j) {
                 V R[9], Gs[9];
 #pragma unroll
                 for (int l = 0; l < Ln::n; ++l) {
-                    const int ly = ty0 + (j * Ln::n + l) * G::RPB;
-                    // the other values at constant offsets from the site's own rest value
-                    const T* b = st + G::pull(0, tx, ly);
+                    const int kk = j * Ln::n + l;  // row ly0 + kk
+                    // the other planes at constant offsets from the site's own value
+                    const T* b = st + G::pull(0, tx, ly0 + kk);
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
-                        Ln::put(R[i], l, S::lds(b + (G::rest(i, 0, 0) - G::pull(0, 0, 0))));
+                        // R(x - c_i): row kk - c_iy, column -c_ix of the window
+                        Ln::put(R[i], l, Rw[kk + 1 - plane_cy(i)][1 - plane_cx(i)]);
                         Ln::put(Gs[i], l,
                                 i ? S::lds(b + (G::pull(i, 0, 0) - G::pull(0, 0, 0))) : 0.f);
                     }
@@ -349,12 +362,12 @@ __global__ void __launch_bounds__(kBlockF, 2)
                 unsigned live = 0;
 #pragma unroll
                 for (int l = 0; l < Ln::n; ++l)
-                    live |= (unsigned)(x < nx && y0 + ty0 + (j * Ln::n + l) * G::RPB < ny) << l;
+                    live |= (unsigned)(x < nx && y0 + ly0 + j * Ln::n + l < ny) << l;
                 const V psi = Eos<EOSP>::psi(L, site_rho(sv[j], L.rho0), a.status, live);
 #pragma unroll
                 for (int l = 0; l < Ln::n; ++l)
                     if ((live >> l) & 1u)
-                        ps[(ty0 + (j * Ln::n + l) * G::RPB + 1) * PW + tx + 1] = Ln::get(psi, l);
+                        ps[(ly0 + j * Ln::n + l + 1) * PW + tx + 1] = Ln::get(psi, l);
             }
             // the ring, cells r and r + nhalf in the two lanes of a float2
             for (int r = tid; r < nhalf; r += kConsumers) {
@@ -415,26 +428,27 @@ __global__ void __launch_bounds__(kBlockF, 2)
         // a partial box would also write the ghost columns just past nx.
         const bool bulk_out = TMAP && fused_tma_coords<TX, TY>(L, 0, 0, x0, y0).store;
         T* out = reinterpret_cast<T*>(smem + s * G::STAGEB);
+        // psi of the (SPT + 2) x 3 window around the thread's column: rows
+        // ly0 - 1 .. ly0 + SPT, columns tx - 1 .. tx + 1
+        float Pw[G::SPT + 2][3];
+#pragma unroll
+        for (int r = 0; r < G::SPT + 2; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Pw[r][c] = ps[(ly0 + r) * PW + tx + c];
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
             V p[9], v[9];
 #pragma unroll
             for (int l = 0; l < Ln::n; ++l) {
-                const float* c = ps + (ty0 + (j * Ln::n + l) * G::RPB + 1) * PW + (tx + 1);
-                Ln::put(p[0], l, c[0]);
-                Ln::put(p[1], l, c[1]);
-                Ln::put(p[2], l, c[PW]);
-                Ln::put(p[3], l, c[-1]);
-                Ln::put(p[4], l, c[-PW]);
-                Ln::put(p[5], l, c[PW + 1]);
-                Ln::put(p[6], l, c[PW - 1]);
-                Ln::put(p[7], l, c[-PW - 1]);
-                Ln::put(p[8], l, c[-PW + 1]);
+                const int kk = j * Ln::n + l;
+#pragma unroll
+                for (int i = 0; i < 9; ++i)  // psi(x + c_i)
+                    Ln::put(p[i], l, Pw[kk + 1 + plane_cy(i)][1 + plane_cx(i)]);
             }
             collide<S, MRT>(C, L.mrt_s, sv[j], p, v);
 #pragma unroll
             for (int l = 0; l < Ln::n; ++l) {
-                const int ly = ty0 + (j * Ln::n + l) * G::RPB;
+                const int ly = ly0 + j * Ln::n + l;
                 const int y = y0 + ly;
                 if (bulk_out) {
 #pragma unroll
