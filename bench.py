@@ -13,7 +13,9 @@ Prints one JSON line (rank 0).  On one GPU the default line also carries
 "batched" (the 512-lattice batch of configuration 4, 100 timed steps, against
 one handle per lattice) and "served" (configuration 5's Poisson stream of
 1000 requests, step counts divided by 100, against one plain handle per
-request), measured after the roofline lattice's timed region.  ``--impl reference`` times the FP64 CPU
+request), measured after the roofline lattice's timed region, and in
+"config" the same lattice's step rate with psi in native FP64 (20 steps).
+``--impl reference`` times the FP64 CPU
 oracle (the only reference this method has) on a bounded crop of the same
 workload, on the host cores.
 """
@@ -399,6 +401,7 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl["name"] if args.collision == "bgk"
                    else wl["name"].replace("BGK", "MRT"), "storage": args.storage, "eos": args.eos,
+                   "eos_arithmetic": EOS_ARITH[args.eos],
                    "collision": args.collision,
                    "schedule": args.schedule, "kernel_variant": args.variant,
                    "psi_pass": {"variant": ["auto", "plain", "tma"][info["psi_variant"]],
@@ -433,6 +436,8 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    if world == 1 and not args.roofline_only and args.eos == "df":
+        out["config"]["native_f64_eos"] = measure_native_f64_eos(P, wl, rho, storage, coll)
     if world == 1 and not args.roofline_only:
         # the metric's other two parts, measured after the timed region above
         # and outside it: the 512-lattice batch and the served stream, each
@@ -451,6 +456,41 @@ def run_gpu(args):
 
 
 # ------------------------------------------------------------------ batched workload
+EOS_ARITH = {
+    "df": "float-float radicand (about 43 bits, FP64-equivalent at physical densities), "
+          "FP32 square root",
+    "f64": "native FP64 radicand and square root",
+    "f32": "FP32 radicand and square root",
+}
+
+
+def measure_native_f64_eos(P, wl, rho, storage, coll, steps=20):
+    """The same lattice with psi evaluated in native FP64 (LBM_EOS_F64), the
+    tile autotuned for it: context beside the float-float default, whose
+    radicand keeps about 43 bits.  FP64 runs at a small fraction of the FP32
+    rate on this GPU."""
+    import torch
+
+    d = P.lbm_desc_default(wl["nx"], wl["ny"], T=wl["T"], tau=wl["tau"],
+                           eos_precision=P.LBM_EOS_F64, storage=storage, **coll)
+    h = P.lbm_create(d, schedule=P.LBM_SCHED_FUSED)
+    P.lbm_init(h, 0, rho)
+    P.lbm_autotune(h, 5)
+    P.lbm_step(h, 3)
+    P.lbm_sync(h)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(h.stream)
+    P.lbm_step(h, steps)
+    e1.record(h.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sites = P.lbm_info(h)["sites"]
+    P.lbm_destroy(h)
+    return {"MLUPS": round(sites * steps / (ms * 1e-3) / 1e6, 1), "steps": steps,
+            "ms_per_step": round(ms / steps, 5)}
+
+
 def measure_batched(P, storage, steps, warmup, autotune=True, sequential=True, lattices=512):
     """512 independent droplet lattices of uneven sizes (sides U{64..512},
     R = side x U(0.15, 0.35), T_r U(0.6, 0.9), tau = 1) stepped together by

@@ -404,8 +404,9 @@ int lbm_mass_noalloc(const float* values, int64_t count, double offset, double* 
 /* Failure-detection test of the single pass (schedule LBM_SCHED_FUSED on the
  * TMA kernel): the next time step skips the shared-memory staging copy of
  * tile `tile` (0 <= tile < the pass's tile count, lbm_info n_tiles), so the
- * consumers' bounded wait for it runs out (about 4e9 SM cycles, 2 s at
- * 2 GHz), every consumer of that CTA leaves together and the producer drains
+ * consumers' bounded wait for it runs out (that launch's waits are limited
+ * to 2e8 SM cycles, about 0.1 s at 2 GHz; other launches wait up to 4e9
+ * cycles, about 2 s), every consumer of that CTA leaves together and the producer drains
  * its copies (bounded too).  No kernel traps or hangs; the step's results
  * are garbage and the next lbm_sync reports LBM_ERR_TIMEOUT with the lattice
  * in lbm_status_detail.  lbm_init of that lattice clears the fault, and the

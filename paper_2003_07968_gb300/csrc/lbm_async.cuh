@@ -10,6 +10,9 @@
 namespace pplbm {
 
 constexpr long long kWaitBudgetCycles = 4000000000LL;  // about 2 s at 2 GHz
+// the launch that carries an armed failure-detection test (a staging copy
+// left out on purpose) waits at most this long: about 0.1 s at 2 GHz
+constexpr long long kTestWaitBudgetCycles = 200000000LL;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -40,13 +43,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Wait for phase `parity` of *bar; false if the clock budget ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Wait for phase `parity` of *bar; false if the clock budget (SM cycles)
+// ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long budget = kWaitBudgetCycles) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (long long it = 0; it < (1LL << 40); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > kWaitBudgetCycles) return false;
+        if (clock64() - t0 > budget) return false;
     }
     return false;
 }

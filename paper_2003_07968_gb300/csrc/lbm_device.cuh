@@ -42,6 +42,13 @@ constexpr int GY = 2;  // ghost rows above and below
 // D2Q9 velocity set, Eq. (VelocitySet); weights from the text after Eq. (SEDF).
 __device__ __constant__ static const int kCx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 __device__ __constant__ static const int kCy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+// the same directions as compile-time functions of the plane index
+__host__ __device__ constexpr int plane_cy(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int plane_cx(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
 
 template <int I> struct Vel;
 template <> struct Vel<0> { static constexpr int x = 0, y = 0; static constexpr float w = 4.f / 9.f; };
@@ -123,6 +130,10 @@ struct StepArgs {
     // failure-detection test: tile + 1 whose staging copy the single pass
     // skips, so that the consumers' bounded wait for it runs out (0: none)
     int starve = 0;
+    // clock budget of the single pass's waits (SM cycles): kWaitBudgetCycles,
+    // or kTestWaitBudgetCycles in the launch that carries an armed test.  A
+    // kernel parameter, read only once a wait has not finished at once
+    long long wait_cycles = 4000000000LL;
 };
 
 // ---- storage traits ---------------------------------------------------------
@@ -800,13 +811,25 @@ __device__ __forceinline__ void collide(const SiteConsts& C, const float* mrt_s,
         collide_mrt<S>(C, mrt_s, st, p, o);
 }
 
-// The periodic images of site (x, y) within GW of the interior, without the
-// site itself (which a bulk tile store writes).
+// The periodic images of population i of site (x, y) that a step reads,
+// without the site itself (which a bulk tile store writes).  Readers pull
+// f*_i(x - c_i) for cells x from -1 to n: the single pass rebuilds psi on a
+// one-site ring around each tile, the other passes pull for x in 0 .. n - 1
+// only.  And every cell reads the rest plane at x - c for each c.  So along
+// one axis, the image at x + n of a site x < GW (the high side) is read for
+// c_i <= -x, the image at x - n of a site x >= n - GW (the low side) for
+// c_i >= n - 1 - x, and the rest plane at every image.  With i a constant
+// (an unrolled loop over the planes) the tests fold: a left-edge site skips
+// the images of the planes that move to the left, and so on.  i = 0 (the
+// rest plane) writes every image.
 template <class T>
-__device__ __forceinline__ void store_images(T* plane, int pitch, int gx, int x, int y, int nx,
-                                             int ny, T v) {
+__device__ __forceinline__ void store_images(T* plane, int i, int pitch, int gx, int x, int y,
+                                             int nx, int ny, T v) {
     T* const row = plane + (int64_t)(y + GY) * pitch + gx;
-    const bool xl = x < GW, xh = x >= nx - GW, yl = y < GW, yh = y >= ny - GW;
+    const int cx = plane_cx(i), cy = plane_cy(i);
+    const bool all = i == 0;
+    const bool xl = x < GW && (all || cx <= -x), xh = x >= nx - GW && (all || cx >= nx - 1 - x);
+    const bool yl = y < GW && (all || cy <= -y), yh = y >= ny - GW && (all || cy >= ny - 1 - y);
     if (xl) row[x + nx] = v;
     if (xh) row[x - nx] = v;
     if (yl) {
@@ -824,7 +847,7 @@ __device__ __forceinline__ void store_images(T* plane, int pitch, int gx, int x,
 }
 
 // Store the nine outputs of site (x, y): interior sites with plain stores,
-// sites within GW of an edge also into their periodic images.  `tile_in`
+// sites within GW of an edge also into all their periodic images.  `tile_in`
 // says the whole tile is interior (uniform per block), which skips the
 // per-site test.
 template <class S>
@@ -838,6 +861,25 @@ __device__ __forceinline__ void store_site(typename S::T* o, int64_t plane, int 
     } else {
 #pragma unroll
         for (int i = 0; i < 9; ++i) store_img(o + i * plane, pitch, gx, x, y, nx, ny, S::cv(v[i]));
+    }
+}
+
+// store_site writing only the periodic images a step reads (store_images):
+// the batch form of the single pass, whose small lattices make edge sites
+// common.  (Kept apart from store_site: the single-lattice kernel, which
+// compiles store_site for its ragged tiles, ran 2 % slower with this form
+// in it, measured.)
+template <class S>
+__device__ __forceinline__ void store_site_read(typename S::T* o, int64_t plane, int pitch, int gx,
+                                                int x, int y, int nx, int ny, const float v[9],
+                                                bool tile_in = false) {
+    typename S::T* q = o + (int64_t)(y + GY) * pitch + (x + gx);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) q[i * plane] = S::cv(v[i]);
+    if (!tile_in && !((x >= GW) & (x < nx - GW) & (y >= GW) & (y < ny - GW))) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            store_images(o + i * plane, i, pitch, gx, x, y, nx, ny, S::cv(v[i]));
     }
 }
 

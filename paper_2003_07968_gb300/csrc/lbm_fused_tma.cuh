@@ -234,12 +234,14 @@ __global__ void __launch_bounds__(kBlockF, 2)
             TmaCoords c{};
             auto locate = [&] {
                 tl = __ldg(&a.tiles[t]);
-                const LatDev& Lt = MODE == 1 ? lat0 : a.lats[tl.x];
-                c = fused_tma_coords<TX, TY>(Lt, Lt.row0, a.parity, tl.y, tl.z);
+                // a batch: the entry carries its row-space row and store flag
+                c = MODE == 1 ? fused_tma_coords<TX, TY>(lat0, lat0.row0, a.parity, tl.y, tl.z)
+                              : tile_coords(tl, S::kGx, a.parity);
             };
             if (MODE == 1 && lane == 0) locate();
             if (k >= G::STAGES) {
-                const bool ok = mbar_wait_bounded(&empty[s], (uint32_t)(k / G::STAGES - 1) & 1u);
+                const bool ok =
+                    mbar_wait_bounded(&empty[s], (uint32_t)(k / G::STAGES - 1) & 1u, a.wait_cycles);
                 if (!__all_sync(0xffffffffu, ok)) {
                     if (lane == 0) atomicOr(&a.status[__ldg(&a.tiles[t]).x], 2u);
                     alive = false;
@@ -281,7 +283,8 @@ __global__ void __launch_bounds__(kBlockF, 2)
         if (TMAP && alive) {
             for (int j = (k > G::STAGES ? k - G::STAGES : 0); j < k; ++j) {
                 const int s = j % G::STAGES;
-                const bool ok = mbar_wait_bounded(&empty[s], (uint32_t)(j / G::STAGES) & 1u);
+                const bool ok =
+                    mbar_wait_bounded(&empty[s], (uint32_t)(j / G::STAGES) & 1u, a.wait_cycles);
                 if (!__all_sync(0xffffffffu, ok)) {
                     if (lane == 0) atomicOr(&a.status[__ldg(&a.tiles[tq[s]]).x], 2u);
                     break;
@@ -293,7 +296,8 @@ __global__ void __launch_bounds__(kBlockF, 2)
         // drain: the last issue into each stage must have landed, and every
         // tile store must be complete, before exit
         for (int j = (k > G::STAGES ? k - G::STAGES : 0); j < k; ++j)
-            mbar_wait_bounded(&full[j % G::STAGES], (uint32_t)(j / G::STAGES) & 1u);
+            mbar_wait_bounded(&full[j % G::STAGES], (uint32_t)(j / G::STAGES) & 1u,
+                              a.wait_cycles);
         if (TMAP && lane == 0) bulk_wait_all();
         return;
     }
@@ -310,8 +314,8 @@ __global__ void __launch_bounds__(kBlockF, 2)
         if (tile_skipped(a, t)) continue;
         const int s = k % G::STAGES;
         float* ps = psi_buf + (k & 1) * (G::PSIB / 4);
-        const bool ok = __all_sync(0xffffffffu,
-                                   mbar_wait_bounded(&full[s], (uint32_t)(k / G::STAGES) & 1u));
+        const bool ok = __all_sync(
+            0xffffffffu, mbar_wait_bounded(&full[s], (uint32_t)(k / G::STAGES) & 1u, a.wait_cycles));
         // the tile, from the stage's descriptor (from global memory only if
         // the wait ran out, to name the lattice in the status word)
         const int4 tl = ok ? desc[s] : __ldg(&a.tiles[t]);
@@ -426,7 +430,9 @@ __global__ void __launch_bounds__(kBlockF, 2)
         // tile uses plain stores:
         // the store unit clips a box at 16-byte granularity in x (measured), so
         // a partial box would also write the ghost columns just past nx.
-        const bool bulk_out = TMAP && fused_tma_coords<TX, TY>(L, 0, 0, x0, y0).store;
+        const bool bulk_out = MODE == 2   ? tl.w >= 0
+                              : MODE == 1 ? fused_tma_coords<TX, TY>(L, 0, 0, x0, y0).store
+                                          : false;
         T* out = reinterpret_cast<T*>(smem + s * G::STAGEB);
         // psi of the (SPT + 2) x 3 window around the thread's column: rows
         // ly0 - 1 .. ly0 + SPT, columns tx - 1 .. tx + 1
@@ -457,14 +463,17 @@ __global__ void __launch_bounds__(kBlockF, 2)
                     if (!tile_in && ((x < GW) | (x >= nx - GW) | (y < GW) | (y >= ny - GW)))
 #pragma unroll
                         for (int i = 0; i < 9; ++i)
-                            store_images(o + i * L.plane, L.pitch, L.gx, x, y, nx, ny,
-                                         S::cv(Ln::get(v[i], l)));
+                            store_images(o + i * L.plane, MODE == 2 ? i : 0, L.pitch, L.gx, x,
+                                         y, nx, ny, S::cv(Ln::get(v[i], l)));
                 } else {
                     if (x >= nx || y >= ny) continue;
                     float vs[9];
 #pragma unroll
                     for (int i = 0; i < 9; ++i) vs[i] = Ln::get(v[i], l);
-                    store_site<S>(o, L.plane, L.pitch, L.gx, x, y, nx, ny, vs, tile_in);
+                    if (MODE == 2)
+                        store_site_read<S>(o, L.plane, L.pitch, L.gx, x, y, nx, ny, vs, tile_in);
+                    else
+                        store_site<S>(o, L.plane, L.pitch, L.gx, x, y, nx, ny, vs, tile_in);
                 }
             }
         }

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/pplbm.h"
+#include "lbm_async.cuh"
 #include "lbm_copy_plan.h"
 #include "lbm_kernels.h"
 #include "lbm_host_scan.h"
@@ -189,7 +190,8 @@ int build_tiles(lbm_handle* h, int k, int tx, int ty) {
         const LatDev& L = h->lat[l];
         P.begin[l] = (int)t.size();
         for (int y0 = 0; y0 < L.ny; y0 += ty)
-            for (int x0 = 0; x0 < L.nx; x0 += tx) t.push_back(make_int4((int)l, x0, y0, 0));
+            for (int x0 = 0; x0 < L.nx; x0 += tx)
+                t.push_back(make_int4((int)l, x0, y0, tile_word(L, tx, ty, x0, y0)));
         P.count[l] = (int)t.size() - P.begin[l];
     }
     const size_t bytes = t.size() * sizeof(int4);
@@ -309,6 +311,7 @@ int launch_step(lbm_handle* h, int p) {
     if (h->prof) CK(h, cudaEventRecord(e1, h->stream));
     StepArgs a1 = step_args(h, p, 1);
     a1.starve = h->starve;  // an armed failure-detection test goes into this launch only
+    if (h->starve) a1.wait_cycles = kTestWaitBudgetCycles;
     h->starve = 0;
     CK(h, launch_pass(h, 1, a1, h->pass[1].grid));
     if (h->prof) {
@@ -570,6 +573,13 @@ std::string check_tma_coords(const std::vector<LatDev>& lats, int es, int64_t pi
                     std::snprintf(buf, sizeof buf,
                                   "tensor tile %dx%d of %dx%d at (%d,%d), row0 %d, es %d: ", TX, TY,
                                   L.nx, L.ny, x0, y0, L.row0, es);
+                    // the batch form reads the same coordinates from the tile entry
+                    const TmaCoords e = tile_coords(
+                        make_int4(0, x0, y0, tile_word(L, TX, TY, x0, y0)), 16 / es, par);
+                    if (L.gx != 16 / es || e.lx != c.lx || e.ly != c.ly || e.lz != c.lz ||
+                        e.store != c.store ||
+                        (c.store && (e.sx != c.sx || e.sy != c.sy || e.sz != c.sz)))
+                        return std::string(buf) + "tile entry coordinates";
                     if ((int64_t)c.lx * es % 16 || c.ly < 0 || (c.lz != 0 && c.lz != 9))
                         return std::string(buf) + "load box origin";
                     if (!c.store) continue;

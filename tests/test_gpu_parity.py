@@ -177,10 +177,11 @@ def test_non_finite_initial_density_is_refused(P):
 
 def test_copy_timeout_is_reported_and_the_handle_recovers(P):
     # failure detection without a GPU fault: one tile's staging copy is
-    # skipped, so the consumers' bounded wait for it runs out (about 2 s), the
-    # CTA's warps leave together and the producer drains its copies; the step
-    # reports LBM_ERR_TIMEOUT, re-initialising the lattice clears it, and the
-    # handle goes on to match the oracle
+    # skipped, so the consumers' bounded wait for it runs out (each wait of
+    # that launch gives up after about 0.1 s), the CTA's warps leave together
+    # and the producer drains its copies; the step reports LBM_ERR_TIMEOUT,
+    # re-initialising the lattice clears it, and the handle goes on to match
+    # the oracle
     n = 128
     rho = synth.droplet(n, n, 30.0, 0.8)
     h = P.lbm_create(P.lbm_desc_default(n, n, T=0.8), kernel_variant=P.LBM_KERNEL_TMA)
@@ -197,7 +198,7 @@ def test_copy_timeout_is_reported_and_the_handle_recovers(P):
     waited = time.time() - t0
     assert err.value.code == P.LBM_ERR_TIMEOUT and P.lbm_status_detail(h) == 0
     print(f"copy timeout reported after {waited:.1f} s")
-    assert 0.5 < waited < 60
+    assert 0.05 < waited < 30
     P.lbm_init(h, 0, rho)
     P.lbm_step(h, 200)
     got = P.lbm_moments(h, 0, mass=False)["rho"]
