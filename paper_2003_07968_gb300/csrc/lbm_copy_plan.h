@@ -224,29 +224,4 @@ __host__ __device__ inline TmaCoords fused_tma_coords(const LatDev& L, int row0,
     return c;
 }
 
-// The fourth word of a tile-list entry (lattice, x0, y0, w) in a row space:
-// the row-space row of the tile's load box (row0 + y0), bitwise negated when
-// the tile is not stored by one tensor store (an edge tile).  The host writes
-// it with the tile list, so the batch form of the single pass finds a tile's
-// tensor coordinates in the entry alone, without reading its lattice.
-inline int tile_word(const LatDev& L, int tx, int ty, int x0, int y0) {
-    if (L.row0 < 0) return 0;  // no row space: the word is not used
-    const int row = L.row0 + y0;
-    return (x0 + tx <= L.nx && y0 + ty <= L.ny) ? row : ~row;
-}
-// fused_tma_coords of entry t, whose lattice has gx ghost columns, from the
-// entry alone (lbm_selfcheck checks that the two agree on every tile)
-__host__ __device__ inline TmaCoords tile_coords(int4 t, int gx, int parity) {
-    TmaCoords c;
-    const int row = t.w >= 0 ? t.w : ~t.w;
-    c.lx = t.y;
-    c.ly = row;
-    c.lz = 9 * parity;
-    c.sx = t.y + gx;
-    c.sy = row + GY;
-    c.sz = 9 * (parity ^ 1);
-    c.store = t.w >= 0;
-    return c;
-}
-
 }  // namespace pplbm

@@ -234,9 +234,8 @@ __global__ void __launch_bounds__(kBlockF, 2)
             TmaCoords c{};
             auto locate = [&] {
                 tl = __ldg(&a.tiles[t]);
-                // a batch: the entry carries its row-space row and store flag
-                c = MODE == 1 ? fused_tma_coords<TX, TY>(lat0, lat0.row0, a.parity, tl.y, tl.z)
-                              : tile_coords(tl, S::kGx, a.parity);
+                const LatDev& Lt = MODE == 1 ? lat0 : a.lats[tl.x];
+                c = fused_tma_coords<TX, TY>(Lt, Lt.row0, a.parity, tl.y, tl.z);
             };
             if (MODE == 1 && lane == 0) locate();
             if (k >= G::STAGES) {
@@ -430,9 +429,7 @@ __global__ void __launch_bounds__(kBlockF, 2)
         // tile uses plain stores:
         // the store unit clips a box at 16-byte granularity in x (measured), so
         // a partial box would also write the ghost columns just past nx.
-        const bool bulk_out = MODE == 2   ? tl.w >= 0
-                              : MODE == 1 ? fused_tma_coords<TX, TY>(L, 0, 0, x0, y0).store
-                                          : false;
+        const bool bulk_out = TMAP && fused_tma_coords<TX, TY>(L, 0, 0, x0, y0).store;
         T* out = reinterpret_cast<T*>(smem + s * G::STAGEB);
         // psi of the (SPT + 2) x 3 window around the thread's column: rows
         // ly0 - 1 .. ly0 + SPT, columns tx - 1 .. tx + 1

@@ -54,7 +54,6 @@
 #include <vector>
 
 #include "../../include/pplbm.h"
-#include "lbm_copy_plan.h"
 #include "lbm_kernels.h"
 #include "lbm_host_scan.h"
 #include "lbm_layout.h"
@@ -378,8 +377,7 @@ cudaError_t rebuild(lbm_server* S, TableSet& T, std::vector<Request*>& res,
         for (size_t l = 0; l < res.size(); ++l) {
             T.begin[k][l] = (int)m;
             for (int y0 = 0; y0 < res[l]->L.ny; y0 += P.ty)
-                for (int x0 = 0; x0 < res[l]->L.nx; x0 += P.tx)
-                    t[m++] = make_int4((int)l, x0, y0, tile_word(res[l]->L, P.tx, P.ty, x0, y0));
+                for (int x0 = 0; x0 < res[l]->L.nx; x0 += P.tx) t[m++] = make_int4((int)l, x0, y0, 0);
             T.count[k][l] = (int)m - T.begin[k][l];
         }
         if (bytes)
