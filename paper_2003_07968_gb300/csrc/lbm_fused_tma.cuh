@@ -5,7 +5,8 @@
 //
 // One launch per step, persistent CTAs over the global tile list.  Per CTA,
 // one producer warp and eight consumer warps (1, 2 or 4 sites per consumer
-// thread, site pairs on the paired FP32 instructions).
+// thread, site pairs on the paired FP32 instructions), and for tiles of one
+// or two sites per thread a ring warp.
 //
 // The default path (one lattice, or a batch whose lattices share one row
 // space, rows at least a box wide): the producer loads each tile with one
@@ -17,8 +18,11 @@
 //   - read from the stage the pulled values of their own sites and the rest
 //     values of the sources (make_site, lbm_device.cuh), keep the sites'
 //     states in registers and compute rho (Eq. FD) and psi (Eqs. DED,
-//     CSEOS), and psi on the tile's one-site ring (two ring cells per thread);
-//   - meet at one named barrier (psi tile complete);
+//     CSEOS);
+//   - psi on the tile's one-site ring comes from the ring warp, which
+//     computes tile k's ring while the consumers still collide tile k - 1
+//     (at four sites per thread the consumers compute it themselves);
+//   - consumers and ring warp meet at one named barrier (psi tile complete);
 //   - run the force (Eq. IFT) and the collision (Eqs. BGKCO, GFSBGK, or
 //     MRTCO), write the nine stored values of a tile inside the lattice back
 //     into the stage they have just read, laid out as the store box, and
@@ -56,7 +60,6 @@ namespace pplbm {
 namespace {
 
 constexpr int kConsumers = 256;             // eight consumer warps
-constexpr int kBlockF = kConsumers + 32;    // plus one producer warp
 constexpr int kStageBudget = 100 * 1024;    // bytes of stages per CTA (two CTAs per SM)
 
 template <class S, int TX, int TY, bool TMAP>
@@ -64,6 +67,13 @@ struct FGeo : FusedGeo<(int)sizeof(typename S::T), TX, TY> {
     using B = FusedGeo<(int)sizeof(typename S::T), TX, TY>;
     static constexpr int ES = (int)sizeof(typename S::T);
     static constexpr int SPT = TX * TY / kConsumers;  // sites per consumer thread
+    // tiles of one or two sites per consumer thread get a ring warp, which
+    // computes psi on the tile's one-site ring while the consumers collide
+    // the tile before; at four sites per thread the consumers keep the ring
+    // (the extra warp's registers would make those instances spill)
+    static constexpr bool RINGW = SPT <= 2;
+    static constexpr int THREADS = kConsumers + (RINGW ? 64 : 32);  // + producer (+ ring warp)
+    static constexpr int PSIBAR = kConsumers + (RINGW ? 32 : 0);    // threads at the psi barrier
     static constexpr int RPB = kConsumers / TX;       // tile rows per pass of the block
     static constexpr int PW = TX + 2;                 // psi tile width (with the ring)
     static constexpr int PSIB = align128(PW * (TY + 2) * 4);
@@ -160,11 +170,44 @@ __device__ __forceinline__ void issue_fused(const StepArgs& a, int4 tl, unsigned
         if (on[k]) bulk_g2s(stage + op[k].dst, pop + op[k].src, (uint32_t)op[k].bytes, bar);
 }
 
+// psi on the one-site ring of tile (x0, y0) of lattice L, from the tile's
+// stage st into the psi tile ps: ring cells r and r + nhalf in the two lanes
+// of a float2, for r = first, first + stride, ... below nhalf.
+template <class S, int EOSP, int TX, int TY, bool TMAP>
+__device__ __forceinline__ void ring_psi(const StepArgs& a, const LatDev& L,
+                                         const typename S::T* st, float* ps, int x0, int y0,
+                                         int first, int stride) {
+    using G = FGeo<S, TX, TY, TMAP>;
+    using T = typename S::T;
+    constexpr int nhalf = TX + TY + 2;  // half of the 2 (TX + TY) + 4 ring cells
+    const int xend = min(x0 + TX, L.nx), yend = min(y0 + TY, L.ny);
+    for (int r = first; r < nhalf; r += stride) {
+        int gx[2], gy[2];
+        unsigned live = 0;
+        float2 R[9], Gs[9];
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            live |= (unsigned)ring_cell(r + l * nhalf, TX, TY, x0, y0, xend, yend, gx[l], gy[l])
+                    << l;
+            const T* b = st + G::pull(0, gx[l] - x0, gy[l] - y0);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                Lanes<float2>::put(R[i], l, S::lds(b + (G::rest(i, 0, 0) - G::pull(0, 0, 0))));
+                Lanes<float2>::put(Gs[i], l,
+                                   i ? S::lds(b + (G::pull(i, 0, 0) - G::pull(0, 0, 0))) : 0.f);
+            }
+        }
+        const float2 psi = Eos<EOSP>::psi(L, site_rho(make_site(R, Gs), L.rho0), a.status, live);
+        if (live & 1u) ps[(gy[0] - y0 + 1) * G::PW + (gx[0] - x0 + 1)] = psi.x;
+        if (live & 2u) ps[(gy[1] - y0 + 1) * G::PW + (gx[1] - x0 + 1)] = psi.y;
+    }
+}
+
 // MODE 0: row copies, lattice constants from a.lats; 1: tensor copies, one
 // lattice whose constants are the parameter lat0; 2: tensor copies, a batch
 // in one row space, constants from a.lats.
 template <class S, int EOSP, int TX, int TY, bool MRT, int MODE>
-__global__ void __launch_bounds__(kBlockF, 2)
+__global__ void __launch_bounds__((FGeo<S, TX, TY, MODE != 0>::THREADS), 2)
     k_fused_tma(StepArgs a, const __grid_constant__ CUtensorMap tmap,
                 const __grid_constant__ CUtensorMap smap, const __grid_constant__ LatDev lat0) {
     constexpr bool TMAP = MODE != 0;
@@ -189,7 +232,7 @@ __global__ void __launch_bounds__(kBlockF, 2)
             // row copies: each consumer warp releases a stage after reading it;
             // tensor path: every consumer arrives once the tile's f* is in the
             // stage (the producer stores it, then refills the stage)
-            mbar_init(&empty[s], TMAP ? kConsumers : kConsumers / 32);
+            mbar_init(&empty[s], TMAP ? kConsumers : kConsumers / 32 + (G::RINGW ? 1 : 0));
         }
         *abort_flag = 0;
         mbar_fence_init();
@@ -301,13 +344,53 @@ __global__ void __launch_bounds__(kBlockF, 2)
         return;
     }
 
+    if (G::RINGW && warp == kConsumers / 32 + 1) {
+        // ------------------------------------------------------------ ring warp
+        // psi on the tile's one-site ring.  Tile k's ring is computed while
+        // the consumers still run the collision of tile k - 1 (the psi tile
+        // is double buffered): only the consumers' own psi stands before the
+        // barrier.
+        int k = 0;
+        for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+            if (tile_skipped(a, t)) continue;
+            const int s = k % G::STAGES;
+            float* ps = psi_buf + (k & 1) * (G::PSIB / 4);
+            const bool ok = __all_sync(
+                0xffffffffu,
+                mbar_wait_bounded(&full[s], (uint32_t)(k / G::STAGES) & 1u, a.wait_cycles));
+            if (ok) {
+                const int4 tl = desc[s];
+                const LatDev& L =
+                    MODE == 1   ? lat0
+                    : MODE == 2 ? *reinterpret_cast<const LatDev*>(smem + G::LATOFF + s * G::LATB)
+                                : a.lats[tl.x];
+                ring_psi<S, EOSP, TX, TY, TMAP>(
+                    a, L, reinterpret_cast<const T*>(smem + s * G::STAGEB), ps, tl.y, tl.z, lane, 32);
+                // row copies: this warp's reads of the stage are done
+                if (!TMAP) {
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[s]);
+                }
+            }
+            uint32_t failed;
+            asm volatile(
+                "{\n\t.reg .pred p, q;\n\tsetp.eq.u32 p, %1, 0;\n\t"
+                "bar.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+                : "=r"(failed)
+                : "r"((uint32_t)ok), "n"(G::PSIBAR)
+                : "memory");
+            if (failed) return;
+            ++k;
+        }
+        return;
+    }
+
     // ---------------------------------------------------------------- consumers
     const int tid = threadIdx.x;  // 0 .. kConsumers-1
     // a thread's SPT sites are consecutive rows of one column, ly0 .. ly0 +
     // SPT - 1, so that their 3 x 3 windows of rest values and of psi overlap:
     // (SPT + 2) x 3 loads each instead of 9 SPT
     const int tx = tid % TX, ly0 = (tid / TX) * G::SPT;
-    constexpr int nhalf = TX + TY + 2;  // half of the 2 (TX + TY) + 4 ring cells
     int k = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         if (tile_skipped(a, t)) continue;
@@ -372,43 +455,22 @@ __global__ void __launch_bounds__(kBlockF, 2)
                     if ((live >> l) & 1u)
                         ps[(ly0 + j * Ln::n + l + 1) * PW + tx + 1] = Ln::get(psi, l);
             }
-            // the ring, cells r and r + nhalf in the two lanes of a float2
-            for (int r = tid; r < nhalf; r += kConsumers) {
-                int gx[2], gy[2];
-                unsigned live = 0;
-                float2 R[9], Gs[9];
-#pragma unroll
-                for (int l = 0; l < 2; ++l) {
-                    live |= (unsigned)ring_cell(r + l * nhalf, TX, TY, x0, y0, xend, yend, gx[l],
-                                                gy[l])
-                            << l;
-                    const T* b = st + G::pull(0, gx[l] - x0, gy[l] - y0);
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        Lanes<float2>::put(R[i], l,
-                                           S::lds(b + (G::rest(i, 0, 0) - G::pull(0, 0, 0))));
-                        Lanes<float2>::put(
-                            Gs[i], l, i ? S::lds(b + (G::pull(i, 0, 0) - G::pull(0, 0, 0))) : 0.f);
-                    }
-                }
-                const float2 psi =
-                    Eos<EOSP>::psi(L, site_rho(make_site(R, Gs), L.rho0), a.status, live);
-                if (live & 1u) ps[(gy[0] - y0 + 1) * PW + (gx[0] - x0 + 1)] = psi.x;
-                if (live & 2u) ps[(gy[1] - y0 + 1) * PW + (gx[1] - x0 + 1)] = psi.y;
-            }
+            if (!G::RINGW)
+                ring_psi<S, EOSP, TX, TY, TMAP>(a, L, st, ps, x0, y0, tid, kConsumers);
             // row copies: every read of the stage is done, hand it back
             if (!TMAP) {
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
             }
         }
-        // psi tile complete; a warp whose wait ran out makes every consumer leave
+        // psi tile complete (own sites here, the ring from the ring warp); a
+        // warp whose wait ran out makes every consumer and the ring warp leave
         uint32_t failed;
         asm volatile(
             "{\n\t.reg .pred p, q;\n\tsetp.eq.u32 p, %1, 0;\n\t"
             "bar.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
             : "=r"(failed)
-            : "r"((uint32_t)ok), "n"(kConsumers)
+            : "r"((uint32_t)ok), "n"(G::PSIBAR)
             : "memory");
         if (failed) {
             if (tid == 0) {
@@ -492,11 +554,11 @@ cudaError_t fused_inst(const StepArgs& a, const CUtensorMap* map, const LatDev* 
     const void* fn = (const void*)k_fused_tma<S, EOSP, TX, TY, MRT, MODE>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
     if (e != cudaSuccess) return e;
-    if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fn, kBlockF, G::SMEM);
+    if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fn, G::THREADS, G::SMEM);
     CUtensorMap none;
     std::memset(&none, 0, sizeof none);
     const LatDev nolat{};
-    k_fused_tma<S, EOSP, TX, TY, MRT, MODE><<<grid, dim3(kBlockF), G::SMEM, st>>>(
+    k_fused_tma<S, EOSP, TX, TY, MRT, MODE><<<grid, dim3(G::THREADS), G::SMEM, st>>>(
         a, map ? map[0] : none, map ? map[1] : none, lat0 ? *lat0 : nolat);
     return cudaGetLastError();
 }

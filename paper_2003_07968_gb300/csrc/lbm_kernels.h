@@ -52,8 +52,9 @@ int occupancy_collide(int storage_f16, int mrt, int spt, int threads, size_t sme
 cudaError_t launch_fused(int storage_f16, int mrt, int eos, int spt, const StepArgs& a, dim3 g,
                          dim3 b, size_t smem, cudaStream_t st);
 int occupancy_fused(int storage_f16, int mrt, int eos, int spt, int threads, size_t smem);
-// Single-pass step with TMA-staged tiles (lbm_fused_tma.cu): 288 threads
-// (eight consumer warps and a producer warp), persistent over the tile list.
+// Single-pass step with TMA-staged tiles (lbm_fused_tma.cu): eight consumer
+// warps, a producer warp and, at one or two sites per consumer thread, a
+// ring warp (288 or 320 threads), persistent over the tile list.
 // With tensor maps (fused_tma_make_map: one lattice, or a batch in one row
 // space (row_space_layout), rows at least a box wide; map[0] loads, map[1]
 // stores) each tile is one 3-D tensor copy in and, inside its lattice, one
