@@ -11,6 +11,8 @@
 //
 // Both passes walk a global tile list with a persistent grid, so one launch
 // covers one lattice or a batch of uneven lattices alike.
+#include <climits>
+
 #include "lbm_copy_plan.h"
 #include "lbm_kernels.h"
 
@@ -311,27 +313,55 @@ __global__ void k_init(LatDev L, void* pop, int parity, const double* rho, const
 // each block writes its minimum, or NaN if it met a value that is not
 // finite; k_scan_final reduces the partials the same way into *out.  The
 // values are also written rounded to FP32 into v32 (k_init's copy).
+// The minimum and the finiteness test work on the 64-bit patterns, on the
+// integer pipe (GB300's FP64 pipe is slow): a finite double has an exponent
+// field below 0x7ff, and flipping the other 63 bits of a negative double
+// gives a signed integer key whose order is the order of the values.
+__device__ __forceinline__ long long order_key(long long b) {
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool finite_bits(long long b) {
+    return (b & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+
 __global__ void __launch_bounds__(256) k_scan_partial(const double* v, int64_t n, double* partials,
                                                       float* v32) {
-    double m = HUGE_VAL;
+    long long m = LLONG_MAX;  // order key of the smallest value so far
     bool bad = false;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // four independent loads in flight per thread
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        double x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = v[i + k * stride];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long b = __double_as_longlong(x[k]);
+            bad |= !finite_bits(b);
+            m = min(m, order_key(b));
+            v32[i + k * stride] = (float)x[k];
+        }
+    }
+    for (; i < n; i += stride) {
         const double x = v[i];
-        bad |= !isfinite(x);
-        m = fmin(m, x);
+        const long long b = __double_as_longlong(x);
+        bad |= !finite_bits(b);
+        m = min(m, order_key(b));
         v32[i] = (float)x;
     }
     bad = __syncthreads_or(bad);
-    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_down_sync(0xffffffffu, m, o));
-    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_down_sync(0xffffffffu, m, o));
+    __shared__ long long red[8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) red[wid] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double b = red[0];
-        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) b = fmin(b, red[k]);
-        partials[blockIdx.x] = bad ? __longlong_as_double(0x7ff8000000000000LL) : b;
+        long long k = red[0];
+        for (int j = 1; j < (int)(blockDim.x >> 5); ++j) k = min(k, red[j]);
+        // the key of a value is its own inverse
+        partials[blockIdx.x] =
+            bad ? __longlong_as_double(0x7ff8000000000000LL) : __longlong_as_double(order_key(k));
     }
 }
 
@@ -343,16 +373,20 @@ __global__ void k_to_f32(const double* v, int64_t n, float* v32) {
         v32[i] = (float)v[i];
 }
 
+// One warp: lane l takes partials l, l + 32, ...; then a shuffle tree.
 __global__ void k_scan_final(const double* partials, int n, double* out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double m = HUGE_VAL;
-        bool bad = false;
-        for (int i = 0; i < n; ++i) {
-            bad |= isnan(partials[i]);
-            m = fmin(m, partials[i]);
-        }
-        *out = bad ? __longlong_as_double(0x7ff8000000000000LL) : m;
+    const int lane = threadIdx.x & 31;
+    long long m = LLONG_MAX;
+    bool bad = false;
+    for (int i = lane; i < n; i += 32) {
+        const long long b = __double_as_longlong(partials[i]);
+        bad |= !finite_bits(b);
+        m = min(m, order_key(b));
     }
+    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_down_sync(0xffffffffu, m, o));
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0)
+        *out = bad ? __longlong_as_double(0x7ff8000000000000LL) : __longlong_as_double(order_key(m));
 }
 
 // ------------------------------------------------------------------ moments
@@ -443,7 +477,7 @@ __global__ void k_moments(LatDev L, const void* pop, int parity, const float* ps
 
 // ------------------------------------------------------------------ mass
 // Each block sums whole rows of all nine planes and writes one FP64
-// partial; k_mass_final adds the partials in block order (deterministic).
+// partial; k_mass_final adds the partials in a fixed order (deterministic).
 // A site's stored mass rho0 + 9/4 R + sum_i G_i (lbm_device.cuh) is summed
 // as a float-float pair over the exact terms R, R, R/4, G_1 .. G_8
 // (signed_sum); the pairs' leading parts accumulate in FP64, their small
@@ -487,11 +521,13 @@ __global__ void __launch_bounds__(256) k_mass_partial(LatDev L, const void* pop,
 }
 
 __global__ void k_mass_final(const double* partials, int n, double* out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double m = 0.0;
-        for (int i = 0; i < n; ++i) m += partials[i];
-        *out = m;
-    }
+    // one warp: lane l adds partials l, l + 32, ... in order, then a fixed
+    // shuffle tree (deterministic)
+    const int lane = threadIdx.x & 31;
+    double m = 0.0;
+    for (int i = lane; i < n; i += 32) m += partials[i];
+    for (int o = 16; o > 0; o >>= 1) m += __shfl_down_sync(0xffffffffu, m, o);
+    if (lane == 0) *out = m;
 }
 
 // ------------------------------------------------------------------ arithmetic check
