@@ -391,10 +391,9 @@ void lbm_server_destroy(lbm_server* s);
  * LBM_NOALLOC_MAX_COUNT values (4 GiB of FP32); larger requests fail with
  * LBM_ERR_CAPACITY before any GPU work.  The first call on a device looks up
  * the array's device address (the host only sees a stand-in for the
- * symbol) and keeps it for the life of the process: make that first call
- * before any stream capture, and do not use the entry point on a device
- * after a reset of it (cudaDeviceReset), whose new context would not hold
- * that address.  Every call uses the same array, so calls whose kernels
+ * symbol) and keeps it for the life of the process: do not use the entry
+ * point on a device after a reset of it (cudaDeviceReset), whose new
+ * context would not hold that address.  Every call uses the same array, so calls whose kernels
  * overlap on the GPU race; order them on one stream.  Errors: LBM_ERR_ARG
  * (NULL pointer, count < 1), LBM_ERR_CAPACITY, LBM_ERR_CUDA. */
 #define LBM_NOALLOC_MAX_COUNT 1073741824LL
