@@ -2,9 +2,10 @@
 
 Default workload: one 8192 x 8192 FP32 droplet lattice (R = 2048, T_r = 0.8,
 BGK tau = 1, eps = 1.73, sigma = 1), the roofline configuration.  A "step"
-is one time step of the whole hot path (psi pass + fused force / collision /
-pull-stream pass) over that lattice.  The working set (two population
-buffers, 4.8 GB) is far larger than L2, so no flush is needed between steps.
+is one time step of the whole hot path over that lattice: pull, density,
+psi, force, collision and store, by default in one kernel launch (the
+single pass).  The working set (two population buffers, 4.8 GB) is far
+larger than L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
                   [--workload roofline|batched|served]
