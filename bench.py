@@ -126,13 +126,24 @@ KERNEL_SOURCES = ("lbm_device.cuh", "lbm_async.cuh", "lbm_copy_plan.h", "lbm_lay
                   "lbm_kernels.h", "lbm_fused_tma.cuh")
 
 
+def _code_only(text):
+    """C++ source without its comments and blank space, so that an edit of a
+    comment leaves the hash of the code unchanged."""
+    import re
+
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash():
-    """Hash of the files that define the single-pass step kernel (not the host runtime)."""
+    """Hash of the code (comments left out) of the files that define the
+    single-pass step kernel (not the host runtime)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2003_07968_gb300", "csrc")
     for f in KERNEL_SOURCES:
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+        with open(os.path.join(d, f), encoding="utf-8") as fh:
+            h.update(f.encode() + _code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -7,8 +7,9 @@
 //   [-gx, pitch-gx).  Ghost sites within GW of the interior hold periodic
 //   images, written by the same kernel that writes the interior site, so
 //   readers never wrap indices (the batch form writes only the planes a
-//   step reads at each image: store_images).  Two population buffers (A/B) alternate
-//   between steps; a float psi plane with the same ghost frame sits beside.
+//   step reads at each image: store_images).  Two population buffers (A/B)
+//   alternate between steps; a float psi plane with the same ghost frame
+//   sits beside.
 //   The buffers hold POST-collision, PRE-streaming populations f*; a step
 //   pulls f_i(x) = f*_i(x - c_i) (streaming of Eq. TLBE in pull form).
 //
