@@ -269,10 +269,10 @@ __global__ void __launch_bounds__((FGeo<S, TX, TY, MODE != 0>::THREADS), 2)
             const int s = k % G::STAGES;
             // failure-detection test: no copy and no arrival for this tile
             const bool starved = a.starve == t + 1;
-            // the tile and its box coordinates (lane 0).  One lattice: read
-            // before the wait for the stage, so that the load overlaps it
-            // (2 % faster on an 8192^2 lattice); a batch: read after the wait
-            // (on 512 uneven lattices 8 % faster than before it, measured)
+            // the tile and its box coordinates (lane 0), read before the wait
+            // for the stage so that the loads overlap it (2 % faster on an
+            // 8192^2 lattice; 5 % on 512 uneven lattices, where reading them
+            // after the wait had measured faster on earlier forms of the kernel)
             int4 tl = make_int4(0, 0, 0, 0);
             TmaCoords c{};
             auto locate = [&] {
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__((FGeo<S, TX, TY, MODE != 0>::THREADS), 2)
                 const LatDev& Lt = MODE == 1 ? lat0 : a.lats[tl.x];
                 c = fused_tma_coords<TX, TY>(Lt, Lt.row0, a.parity, tl.y, tl.z);
             };
-            if (MODE == 1 && lane == 0) locate();
+            if (TMAP && lane == 0) locate();
             if (k >= G::STAGES) {
                 const bool ok =
                     mbar_wait_bounded(&empty[s], (uint32_t)(k / G::STAGES - 1) & 1u, a.wait_cycles);
@@ -300,7 +300,6 @@ __global__ void __launch_bounds__((FGeo<S, TX, TY, MODE != 0>::THREADS), 2)
                 // one tensor copy: columns from x0 - H (element x0 of the row, a
                 // multiple of 32), rows from y0 - 2 (row row0 + y0 of the row
                 // space), planes of the current buffer
-                if (MODE == 2 && lane == 0) locate();
                 if (lane == 0 && !starved) {
                     desc[s] = tl;
                     mbar_expect_tx(&full[s], (uint32_t)G::TBYTES +
